@@ -1,0 +1,315 @@
+"""Benchmark: SLPF parse throughput (text GB/s) on a DNA-like motif workload.
+
+One step = one full parse of a device-resident text: forward / backward
+speculative reach, join, checkpoint fix-up and build & merge with compose
+(every kernel of the path), the clean SLPF written to HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Workload: RE ([ACGT]|ATG([ACGT][ACGT][ACGT])*(TAA|TAG|TGA))* over a 256 MiB
+text of i.i.d. uniform bases with ORF motifs planted at 1 per 10 kB (seed 1
+on rank 0).  The text is larger than L2, so every step streams it from HBM.
+N > 1 (torchrun): every rank parses its own text of the same size (weak
+scaling, no collective on the data path); time is the max over ranks.
+
+Printed: one JSON line (rank 0) with the contract keys plus ``roofline``
+(the dominant kernel timed live with the library's per-phase CUDA events),
+``cpu_baseline`` (the CPU oracle on a bounded sample), ``e2e`` (host buffers
+in, SLPF back to host, through the same C-ABI call) and ``clocks``.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SLPF parse GB/s of text on 1 GB300, % of HBM roofline; p50/p99 latency served"
+WORKLOAD = "dna-motif: RE ([ACGT]|ATG([ACGT][ACGT][ACGT])*(TAA|TAG|TGA))*, 256 MiB uniform ACGT, ORFs 30-900 codons at 1 per 10 kB, seed 1"
+N_BYTES = 256 << 20
+CPU_SAMPLE = 6 << 20
+FALLBACK_HBM = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--bytes", type=int, default=N_BYTES, help="text size (default 256 MiB)")
+    ap.add_argument("--chunk-len", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 10:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        loaded = [r for r in rows if (num(r[4]) or 0) >= 50] or rows
+        sm = [num(r[1]) for r in loaded if num(r[1]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in loaded:
+            for j, nm in enumerate(names):
+                if r[6 + j].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": num(loaded[0][2]), "reasons": sorted(reasons),
+                "samples": len(loaded), "power_w_max": max((num(r[3]) or 0) for r in loaded)}
+
+
+def cpu_baseline(text_host, pattern):
+    """The CPU oracle as it stands (serial two-way NFA parser, one core) on a
+    bounded prefix of the same text."""
+    from oracle import serial
+    from oracle.re_front import compile_re
+    c = compile_re(pattern)
+    sample = text_host[:CPU_SAMPLE].tobytes()
+    t0 = time.perf_counter()
+    serial.parse(c, sample)
+    dt = time.perf_counter() - t0
+    return {"value": len(sample) / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {len(sample) >> 20} MiB of the workload text, serial oracle (Eq. matrixmul), "
+                      f"{dt:.1f} s, host {os.uname().machine} nproc={os.cpu_count()}"}
+
+
+def traffic_for(kernel: str, n: int):
+    """ncu DRAM bytes of the dominant kernel, scaled per text byte, if the
+    committed capture matches the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        src = open(os.path.join(ROOT, "paper_2503_06763_gb300", "csrc", "parse_kernels.cu"), "rb").read()
+        if d.get("csrc_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        per = d.get("dram_bytes_per_text_byte", {}).get(kernel)
+        return None if per is None else per * n
+    except Exception:
+        return None
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import numpy as np
+    import workloads as W
+
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_2503_06763_gb300 import Regex
+    from paper_2503_06763_gb300.native import PHASES
+
+    n = args.bytes
+    host = W.dna_text(n, seed=1 + 1000 * rank)
+    rx = Regex(W.DNA_RE)
+    dev = torch.device("cuda", local)
+    text = torch.from_numpy(host).to(dev)
+    kind, cb, out_bytes = rx.layout(n, "auto")
+    dt = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}[cb]
+    out = torch.empty(n + 1, dtype=dt, device=dev)
+    status = torch.empty(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(rx.workspace_size(n, args.chunk_len), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+
+    def step(i=None):
+        rx.parse(text, kind=kind, chunk_len=args.chunk_len, out=out, status=status, workspace=ws,
+                 events=ev[i] if i is not None else None)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    st = int(status.item())
+    if st != 0:
+        raise SystemExit(f"parse status {st}")
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            step(i)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    clocks = clk.summary()
+    ms_total = t_start.elapsed_time(t_end)
+    if dist:
+        tt = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms = ms_total / args.steps
+    value = (n * world) / (ms / 1e3) / 1e9
+
+    # per-phase device times (averaged over the timed steps)
+    phase_ms = {p: statistics.mean(ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(args.steps))
+                for j, p in enumerate(PHASES)}
+    dominant = max(phase_ms, key=phase_ms.get)
+    # algorithmic bytes per launch: text read once, plus the SLPF written by build & merge
+    alg = {"reach_fwd": n, "reach_bwd": n, "join": 0, "fixup": 0, "build_merge": n + (n + 1) * cb}
+    hbm, src = peaks()
+    achieved = alg[dominant] / (phase_ms[dominant] / 1e3) / 1e9 if alg[dominant] else 0.0
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1), "peak": hbm,
+                "peak_source": src, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "traffic": traffic_for(dominant, n),
+                "phase_ms": {k: round(v, 4) for k, v in phase_ms.items()},
+                "whole_step_frac": round((n + (n + 1) * cb) / (ms / 1e3) / 1e9 / hbm, 4)}
+
+    # end to end through the same call: pinned host text in, SLPF and status back
+    pin_in = torch.from_numpy(host).pin_memory()
+    pin_out = torch.empty(n + 1, dtype=dt).pin_memory()
+    pin_st = torch.empty(1, dtype=torch.int32).pin_memory()
+    e_steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        text.copy_(pin_in, non_blocking=True); step(); pin_out.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e_steps):
+        text.copy_(pin_in, non_blocking=True)
+        step()
+        pin_out.copy_(out, non_blocking=True)
+        pin_st.copy_(status, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e_ms = e0.elapsed_time(e1) / e_steps
+    e2e = {"value": round(n * world / (e_ms / 1e3) / 1e9, 3), "unit": "GB/s",
+           "h2d_bytes_per_step": n, "d2h_bytes_per_step": (n + 1) * cb + 4}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(host, W.DNA_RE)
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "text_bytes_per_gpu": n, "encoding": f"{kind}-{8 * cb}bit",
+                   "chunk_len": args.chunk_len or "auto", "segments": rx.ell,
+                   "l2": "text 256 MiB > 129 MB L2 (no flush needed)",
+                   "parallelism": f"independent texts per GPU x{world}"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": 9 * args.steps, "clocks": clocks,
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def reference_arm(args, rank, world):
+    """The oracle timed on the host cores on a bounded sample per step."""
+    if rank != 0:
+        return
+    import numpy as np
+    import workloads as W
+    from oracle import serial
+    from oracle.re_front import compile_re
+    host = W.dna_text(min(args.bytes, 64 << 20), seed=1)
+    c = compile_re(W.DNA_RE)
+    sample = host[:1 << 20].tobytes()
+    for _ in range(args.warmup):
+        serial.parse(c, sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        serial.parse(c, sample)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = len(sample) / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "text_bytes_per_step": len(sample)},
+            "cpu_baseline": {"value": round(v, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": "first 1 MiB of the workload text per step, serial oracle"},
+            "e2e": {"value": round(v, 6), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * slpf_parser.h -- C ABI of the GB300 parallel regular-expression parser.
+ *
+ * The library computes the clean shared linearized parse forest (SLPF) of a
+ * text under a regular expression, following arXiv 2503.06763
+ * ("A parallel parser for regular expressions"):
+ *   - the SLPF is the series of columns C_0 .. C_n, each a set of segments
+ *     (Sect. 2.3.5; definition after Fig. SLPFe3), computed here by the
+ *     chunked speculative algorithm of Sect. 3.2 (Eqs. reacher, joiner,
+ *     builder, merger) on the device;
+ *   - segments, the parser NFA and its DFA / multi-entry DFA are built on the
+ *     host by re_compile (Sects. 2.2, 2.3, 3.1, App. A).
+ *
+ * Conventions for every call:
+ *   - Pointers named d_* are device pointers on the device that was current
+ *     when the handle was compiled; all other pointers are host pointers.
+ *   - Device buffers passed in are owned by the caller and must stay alive
+ *     until the stream work that uses them has finished.
+ *   - Calls return a re_status synchronously for argument, compile and launch
+ *     errors.  Data-dependent results (text accepted / rejected, internal
+ *     consistency failure) are written to the device word slpf->status and
+ *     are valid once the stream has been synchronised.
+ *   - Nothing aborts the process and nothing falls back to the CPU.  When the
+ *     CUDA runtime reports an error the call returns RE_E_CUDA and
+ *     re_last_error() describes it.
+ *   - A handle may be used by several host threads for re_parse concurrently;
+ *     re_compile / re_free of the same handle must not race with its use.
+ */
+#ifndef SLPF_PARSER_H
+#define SLPF_PARSER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct re_handle re_handle;     /* opaque: owns host and device tables */
+typedef struct CUstream_st *re_stream;  /* a cudaStream_t; NULL = legacy default */
+
+typedef enum {
+    RE_OK = 0,
+    RE_REJECTED = 1,               /* status word only: text not in L(e); all columns empty */
+    RE_E_INVALID_ARG = -1,
+    RE_E_SYNTAX = -2,              /* malformed RE */
+    RE_E_INFINITE_AMBIGUITY = -3,  /* an iterated sub-RE derives the empty text (Sect. 2.1, App. A) */
+    RE_E_TOO_MANY_STATES = -4,     /* automaton exceeds re_compile_opts.max_states */
+    RE_E_NOMEM = -5,               /* host or device allocation failed (re_compile only) */
+    RE_E_CUDA = -6,                /* CUDA runtime error; see re_last_error() */
+    RE_E_CAPACITY = -8,            /* an output / workspace buffer is smaller than required */
+    RE_E_INTERNAL = -9             /* status word only: a device consistency check failed */
+} re_status;
+
+/* SLPF column encodings.
+ *   DENSE : column r is the bitset of its segments (bit j = segment id j),
+ *           stored little-endian in col_bytes = 1, 2, 4 or 8 bytes.  Needs
+ *           ell <= 64.  Segment ids are the canonical order reported by
+ *           re_segment_name.
+ *   DICT  : column r is an index into the handle's column dictionary
+ *           (re_dict_copy); index 0 is the empty column.  col_bytes = 2 when
+ *           the dictionary has fewer than 65536 entries, else 4.
+ *   AUTO  : DENSE when ell <= 16, else DICT when the handle has a
+ *           dictionary, else DENSE when ell <= 64.                            */
+typedef enum { RE_SLPF_AUTO = 0, RE_SLPF_DENSE = 1, RE_SLPF_DICT = 2 } re_slpf_kind;
+
+typedef struct {
+    uint32_t max_states;      /* cap on forward + reverse automaton states; 0 = 1<<20 */
+    uint32_t max_dict;        /* cap on dictionary pairs considered; 0 = 1<<24 */
+    uint32_t flags;           /* 0 or RE_COMPILE_HOST_ONLY */
+} re_compile_opts;
+
+/* Build the host tables only (no device upload, no CUDA call): the handle
+ * answers re_get_info / re_segment_name / re_dict_copy / re_slpf_layout but
+ * re_parse rejects it with RE_E_INVALID_ARG.  For inspection on machines
+ * without a GPU.                                                            */
+#define RE_COMPILE_HOST_ONLY 1u
+
+typedef struct {
+    re_slpf_kind kind;        /* requested encoding */
+    uint32_t chunk_len;       /* text chunk length k in bytes (multiple of 64); 0 = automatic */
+    uint32_t flags;           /* RE_PARSE_RECOGNIZE_ONLY or 0 */
+    uint32_t n_events;        /* 0, or RE_PHASE_EVENTS */
+    void **events;            /* n_events cudaEvent_t created by the caller; recorded on the
+                                 parse stream before the first phase and after each phase */
+} re_parse_opts;
+
+/* Phase boundaries recorded into re_parse_opts.events: [0] start,
+ * [1] after forward reach, [2] after backward reach (Eq. reacher),
+ * [3] after join (Eq. joiner) and status, [4] after checkpoint fix-up,
+ * [5] after build & merge (Eqs. builder, merger) and compose.               */
+#define RE_PHASE_EVENTS 6u
+
+/* Recognizer mode (Sect. 4.2, "Mere recognizer"): run forward reach and join
+ * only, write the accept / reject status and no columns.                    */
+#define RE_PARSE_RECOGNIZE_ONLY 1u
+
+/* Output descriptor.  Filled by the caller: kind, col_bytes, d_cols,
+ * cols_cap_bytes and d_status; re_slpf_layout gives the sizes.  n_cols is
+ * written by re_parse (len + 1).                                            */
+typedef struct {
+    re_slpf_kind kind;        /* DENSE or DICT (never AUTO once laid out) */
+    uint32_t col_bytes;       /* bytes per column */
+    uint64_t n_cols;          /* number of columns, len + 1 */
+    void *d_cols;             /* device: n_cols * col_bytes bytes, written by re_parse */
+    uint64_t cols_cap_bytes;  /* capacity of d_cols */
+    int32_t *d_status;        /* device: one re_status word (RE_OK / RE_REJECTED / RE_E_INTERNAL) */
+} re_slpf;
+
+typedef struct {
+    uint32_t n_segments;      /* ell = |Q| (Sect. 2.4) */
+    uint32_t n_positions;     /* numbered terminals (character-set positions) */
+    uint32_t n_classes;       /* byte classes */
+    uint32_t words_per_col;   /* ceil(ell / 64) */
+    uint32_t fwd_states;      /* forward DFA + ME-DFA states, without the empty set */
+    uint32_t fwd_dfa_states;  /* of which reachable from I (the classic DFA, Sect. 3.1) */
+    uint32_t bwd_states;      /* reverse DFA + ME-DFA states, without the empty set */
+    uint32_t bwd_dfa_states;  /* of which reachable from F */
+    uint32_t fwd_slots_max;   /* most forward speculative runs for one chunk */
+    uint32_t bwd_slots_max;   /* most backward speculative runs for one chunk */
+    uint64_t dict_size;       /* distinct non-empty columns C = B ∩ B̂ (0 = no dictionary) */
+} re_info;
+
+/* Compile a pattern (Sect. 2.1 syntax plus App. A character features:
+ * '|' union, juxtaposition, postfix '*', '+', '?', 'e{k}', '(' ')' groups,
+ * '[...]' / '[^...]' byte sets, '.', '\' escapes incl. \n \t \r \xHH; an empty
+ * alternative is ε).  Builds segments (Fig. segmentalgo), FolSeg
+ * (Eq. folsegdef), forward / reverse DFA and ME-DFA (Sect. 3.1) and uploads
+ * them to the current device.  On success *out owns host and device memory
+ * until re_free.                                                            */
+re_status re_compile(const char *pattern, size_t len, const re_compile_opts *opts,
+                     re_handle **out);
+void re_free(re_handle *h);
+
+re_status re_get_info(const re_handle *h, re_info *info);
+
+/* Name of segment id (canonical order): tokens 'k(' ')k' 'tk' 'ek' '$'
+ * separated by one space, e.g. "1( 2( t3".  Writes a NUL-terminated string
+ * of at most cap bytes.                                                     */
+re_status re_segment_name(const re_handle *h, uint32_t id, char *buf, size_t cap);
+
+/* Column dictionary for DICT output: entry d (1-based) occupies words
+ * [(d-1)*W, d*W) of host_words; the empty column (index 0) is not stored.   */
+re_status re_dict_copy(const re_handle *h, uint64_t *host_words, uint64_t cap_words);
+
+/* Resolve AUTO and report the output size for a text of len bytes.        */
+re_status re_slpf_layout(const re_handle *h, uint64_t len, re_slpf_kind kind,
+                         re_slpf_kind *kind_out, uint32_t *col_bytes, uint64_t *bytes);
+
+/* Device workspace needed by re_parse for len bytes with these options.    */
+re_status re_workspace_size(const re_handle *h, uint64_t len, const re_parse_opts *opts,
+                            uint64_t *bytes);
+
+/* Enqueue the parse of d_text[0..len) on stream: reach, join, build&merge and
+ * compose (Sect. 3.2).  Asynchronous: returns once the kernels are launched.
+ * d_workspace must hold re_workspace_size bytes (256-byte aligned).        */
+re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream stream,
+                   re_slpf *slpf, void *d_workspace, uint64_t workspace_bytes,
+                   const re_parse_opts *opts);
+
+/* Thread-local description of the last error returned on this thread.     */
+const char *re_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SLPF_PARSER_H */

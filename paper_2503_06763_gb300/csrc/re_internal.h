@@ -1,0 +1,91 @@
+// Internal definitions shared by the host compiler (re_compile.cpp) and the
+// device parse path (parse_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/slpf_parser.h"
+
+#ifndef __CUDACC__
+#define __host__
+#define __device__
+#endif
+
+namespace slpf {
+
+constexpr uint32_t kSub = 64;            // sub-chunk length L (bytes) of the checkpoints
+constexpr uint32_t kUnknown = 0xFFFFFFFFu;  // checkpoint not produced by a converged reach run
+
+// Hash of a segment bitset; used by the host to build and by the device to
+// probe the state tables (bitset -> state id).
+__host__ __device__ inline uint64_t bits_hash(const uint64_t *w, uint32_t W) {
+    uint64_t h = 0x9E3779B97F4A7C15ull;
+    for (uint32_t i = 0; i < W; ++i) {
+        h ^= w[i] + 0x632BE59BD9B4E019ull + (h << 6) + (h >> 2);
+        h *= 0xFF51AFD7ED558CCDull;
+        h ^= h >> 33;
+    }
+    return h;
+}
+
+// Device tables of one compiled RE (all pointers are device pointers into
+// one allocation owned by the handle).
+struct DevTables {
+    const uint8_t *cls;          // [256] byte -> class
+    const uint32_t *fT;          // [nf][ncls] forward next state (0 = empty set)
+    const uint32_t *bT;          // [nb][ncls] reverse next state
+    const uint64_t *fBits;       // [nf][W] segment set of each forward state
+    const uint64_t *bBits;       // [nb][W]
+    const uint32_t *fHash;       // [fHashMask+1] forward state ids by bits_hash (0 = free)
+    const uint32_t *bHash;       // [bHashMask+1]
+    const uint32_t *fSlotStart;  // [ncls][ncls][msf] start state after the chunk's first byte
+    const uint64_t *fSlotMask;   // [ncls][ncls][msf][W] segments whose end-letter is a key of the slot
+    const uint32_t *fSlotCount;  // [ncls][ncls]
+    const uint32_t *bSlotStart;  // [ncls][ncls][msb] start state after the chunk's last byte
+    const uint64_t *bSlotMask;   // [ncls][ncls][msb][W] segments whose first symbol is a key
+    const uint32_t *bSlotCount;  // [ncls][ncls]
+    const uint32_t *pt;          // [(nfd+1)][(nbd+1)] dictionary index of B ∩ B̂ (DICT)
+    uint32_t fHashMask, bHashMask;
+    uint32_t ncls, W, ell;
+    uint32_t nf, nb, nfd, nbd;   // states incl. empty row 0; nfd/nbd = classic DFA states
+    uint32_t msf, msb;           // slot capacity per class pair
+    uint32_t fI, bF;             // state ids of I (forward) and F (reverse)
+    uint32_t dict_size;
+};
+
+// Host-side compiled RE.
+struct Compiled {
+    uint32_t ell = 0, W = 0, npos = 0, ncls = 0;
+    std::vector<std::string> names;           // canonical segment order
+    uint8_t cls[256];
+    uint32_t nf = 0, nb = 0, nfd = 0, nbd = 0, msf = 0, msb = 0;
+    std::vector<uint32_t> fT, bT;             // [n][ncls]
+    std::vector<uint64_t> fBits, bBits;       // [n][W]
+    std::vector<uint32_t> fHash, bHash;
+    uint32_t fHashMask = 0, bHashMask = 0;
+    std::vector<uint32_t> fSlotStart, fSlotCount, bSlotStart, bSlotCount;
+    std::vector<uint64_t> fSlotMask, bSlotMask;
+    std::vector<uint32_t> pt;                 // [(nfd+1)][(nbd+1)]
+    std::vector<uint64_t> dict;               // [dict_size][W]
+    uint32_t dict_size = 0;
+    bool has_dict = false;
+};
+
+// Compile; returns RE_OK or an error with a message in err.
+re_status compile_pattern(const char *pattern, size_t len, const re_compile_opts *opts,
+                          Compiled &out, std::string &err);
+
+void set_error(const std::string &msg);
+
+}  // namespace slpf
+
+struct re_handle {
+    slpf::Compiled host;
+    slpf::DevTables dev;
+    void *d_alloc = nullptr;
+    size_t d_bytes = 0;
+    int device = 0;
+    bool host_only = false;
+};

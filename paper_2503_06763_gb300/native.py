@@ -1,0 +1,204 @@
+"""ctypes binding of libslpf.so (include/slpf_parser.h), argument marshalling only.
+
+Every step of the parse runs in the library's CUDA kernels; this module only
+allocates device buffers with PyTorch and passes their pointers and the
+current CUDA stream.  There is no CPU fallback: importing it without the built
+library raises ImportError.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libslpf.so")
+
+RE_OK, RE_REJECTED = 0, 1
+STATUS_NAMES = {0: "RE_OK", 1: "RE_REJECTED", -1: "RE_E_INVALID_ARG", -2: "RE_E_SYNTAX",
+                -3: "RE_E_INFINITE_AMBIGUITY", -4: "RE_E_TOO_MANY_STATES", -5: "RE_E_NOMEM",
+                -6: "RE_E_CUDA", -8: "RE_E_CAPACITY", -9: "RE_E_INTERNAL"}
+KINDS = {"auto": 0, "dense": 1, "dict": 2}
+KIND_NAMES = {0: "auto", 1: "dense", 2: "dict"}
+RE_COMPILE_HOST_ONLY = 1
+RE_PARSE_RECOGNIZE_ONLY = 1
+
+EXPORTS = ["re_compile", "re_free", "re_get_info", "re_segment_name", "re_dict_copy",
+           "re_slpf_layout", "re_workspace_size", "re_parse", "re_last_error"]
+
+
+class ReError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class CompileOpts(ctypes.Structure):
+    _fields_ = [("max_states", ctypes.c_uint32), ("max_dict", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class ParseOpts(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("chunk_len", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("n_events", ctypes.c_uint32), ("events", ctypes.POINTER(ctypes.c_void_p))]
+
+
+RE_PHASE_EVENTS = 6
+PHASES = ["reach_fwd", "reach_bwd", "join", "fixup", "build_merge"]
+
+
+class Slpf(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("col_bytes", ctypes.c_uint32), ("n_cols", ctypes.c_uint64),
+                ("d_cols", ctypes.c_void_p), ("cols_cap_bytes", ctypes.c_uint64),
+                ("d_status", ctypes.c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in (
+        "n_segments", "n_positions", "n_classes", "words_per_col", "fwd_states", "fwd_dfa_states",
+        "bwd_states", "bwd_dfa_states", "fwd_slots_max", "bwd_slots_max")] + [("dict_size", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def load():
+    """Load libslpf.so; raise ImportError when it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    lib.re_compile.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(CompileOpts), ctypes.POINTER(vp)]
+    lib.re_compile.restype = i32
+    lib.re_free.argtypes = [vp]
+    lib.re_free.restype = None
+    lib.re_get_info.argtypes = [vp, ctypes.POINTER(Info)]
+    lib.re_get_info.restype = i32
+    lib.re_segment_name.argtypes = [vp, u32, ctypes.c_char_p, ctypes.c_size_t]
+    lib.re_segment_name.restype = i32
+    lib.re_dict_copy.argtypes = [vp, vp, u64]
+    lib.re_dict_copy.restype = i32
+    lib.re_slpf_layout.argtypes = [vp, u64, i32, ctypes.POINTER(i32), ctypes.POINTER(u32), ctypes.POINTER(u64)]
+    lib.re_slpf_layout.restype = i32
+    lib.re_workspace_size.argtypes = [vp, u64, ctypes.POINTER(ParseOpts), ctypes.POINTER(u64)]
+    lib.re_workspace_size.restype = i32
+    lib.re_parse.argtypes = [vp, vp, u64, vp, ctypes.POINTER(Slpf), vp, u64, ctypes.POINTER(ParseOpts)]
+    lib.re_parse.restype = i32
+    lib.re_last_error.argtypes = []
+    lib.re_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def check(status: int):
+    if status != RE_OK:
+        raise ReError(status, load().re_last_error().decode(errors="replace"))
+
+
+class Regex:
+    """A compiled RE (owns the library handle and its device tables)."""
+
+    def __init__(self, pattern, max_states: int = 0, max_dict: int = 0, host_only: bool = False):
+        lib = load()
+        pat = pattern.encode("latin-1") if isinstance(pattern, str) else bytes(pattern)
+        self.pattern = pat
+        opts = CompileOpts(max_states, max_dict, RE_COMPILE_HOST_ONLY if host_only else 0)
+        h = ctypes.c_void_p()
+        check(lib.re_compile(pat, len(pat), ctypes.byref(opts), ctypes.byref(h)))
+        self._h = h
+        info = Info()
+        check(lib.re_get_info(h, ctypes.byref(info)))
+        self.info = {n: getattr(info, n) for n, _ in Info._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().re_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def ell(self) -> int:
+        return self.info["n_segments"]
+
+    @property
+    def words(self) -> int:
+        return self.info["words_per_col"]
+
+    def segment_names(self):
+        lib = load()
+        buf = ctypes.create_string_buffer(1 << 16)
+        out = []
+        for i in range(self.ell):
+            check(lib.re_segment_name(self._h, i, buf, len(buf)))
+            out.append(buf.value.decode())
+        return out
+
+    def dictionary(self):
+        import numpy as np
+        d = self.info["dict_size"]
+        arr = np.zeros((d, self.words), dtype=np.uint64)
+        if d:
+            check(load().re_dict_copy(self._h, arr.ctypes.data, arr.size))
+        return arr
+
+    def layout(self, n: int, kind: str = "auto"):
+        k, cb, nb = ctypes.c_int(), ctypes.c_uint32(), ctypes.c_uint64()
+        check(load().re_slpf_layout(self._h, n, KINDS[kind], ctypes.byref(k), ctypes.byref(cb), ctypes.byref(nb)))
+        return KIND_NAMES[k.value], cb.value, nb.value
+
+    def workspace_size(self, n: int, chunk_len: int = 0, flags: int = 0) -> int:
+        b = ctypes.c_uint64()
+        opts = ParseOpts(0, chunk_len, flags, 0, None)
+        check(load().re_workspace_size(self._h, n, ctypes.byref(opts), ctypes.byref(b)))
+        return b.value
+
+    def parse(self, text, kind: str = "auto", chunk_len: int = 0, stream=None, out=None, status=None,
+              workspace=None, recognize_only: bool = False, events=None):
+        """Enqueue the parse of a CUDA uint8 tensor; returns (cols, status, kind).
+
+        ``cols`` is a CUDA tensor of n+1 columns (uint8/int16/int32/int64 view of
+        the DENSE bitsets or DICT indices), ``status`` a one-element int32 CUDA
+        tensor holding the re_status word.  Nothing is synchronised here."""
+        import torch
+        if not (isinstance(text, torch.Tensor) and text.is_cuda and text.dtype == torch.uint8):
+            raise TypeError("text must be a CUDA uint8 tensor")
+        text = text.contiguous()
+        n = text.numel()
+        kname, cb, nbytes = self.layout(n, kind)
+        dt = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}[cb]
+        if out is None:
+            out = torch.empty(n + 1, dtype=dt, device=text.device)
+        if status is None:
+            status = torch.empty(1, dtype=torch.int32, device=text.device)
+        flags = RE_PARSE_RECOGNIZE_ONLY if recognize_only else 0
+        wsz = self.workspace_size(n, chunk_len, flags)
+        if workspace is None or workspace.numel() < wsz:
+            workspace = torch.empty(max(wsz, 256), dtype=torch.uint8, device=text.device)
+        s = stream if stream is not None else torch.cuda.current_stream(text.device)
+        slpf = Slpf(KINDS[kname], cb, 0, out.data_ptr(), out.numel() * out.element_size(), status.data_ptr())
+        opts = ParseOpts(KINDS[kname], chunk_len, flags, 0, None)
+        if events is not None:          # RE_PHASE_EVENTS torch.cuda.Event objects
+            arr = (ctypes.c_void_p * RE_PHASE_EVENTS)(*[ctypes.c_void_p(e.cuda_event) for e in events])
+            opts.n_events, opts.events = RE_PHASE_EVENTS, ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p))
+        check(load().re_parse(self._h, text.data_ptr() if n else None, n, ctypes.c_void_p(s.cuda_stream),
+                              ctypes.byref(slpf), workspace.data_ptr(), workspace.numel(), ctypes.byref(opts)))
+        return out, status, kname
+
+    # ------------------------------------------------------------------ decoding
+    def decode(self, cols, kind: str):
+        """Columns (host numpy array from ``parse``) -> [(n+1), W] uint64 bitsets."""
+        import numpy as np
+        cols = np.asarray(cols)
+        if kind == "dense":
+            v = cols.view({1: np.uint8, 2: np.uint16, 4: np.uint32, 8: np.uint64}[cols.dtype.itemsize])
+            return v.astype(np.uint64).reshape(-1, 1)
+        idx = cols.view(np.uint16 if cols.dtype.itemsize == 2 else np.uint32).astype(np.int64)
+        d = self.dictionary()
+        table = np.concatenate([np.zeros((1, self.words), dtype=np.uint64), d], axis=0)
+        return table[idx]

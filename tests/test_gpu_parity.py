@@ -1,0 +1,127 @@
+"""GPU parity: the CUDA path through the C ABI vs the CPU oracle, bit-exact.
+
+The SLPF is integer data: every column (a set of segments) must be identical.
+Segment ids agree because both sides use the canonical segment order, which
+``test_native_abi`` checks by name.  Sizes span many chunks and sub-chunks and
+end in ragged tails; chunk lengths are swept so speculation, join chains and
+checkpoint fixups all run.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import serial
+from oracle.re_front import compile_re
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2503_06763_gb300 import Regex
+    return Regex
+
+
+_oracle_cache = {}
+
+
+def oracle_cols(pattern, text: bytes):
+    c = _oracle_cache.get(pattern)
+    if c is None:
+        c = _oracle_cache[pattern] = compile_re(pattern)
+    return serial.parse(c, text)
+
+
+def gpu_cols(rx, host: np.ndarray, kind="auto", chunk_len=0):
+    t = torch.from_numpy(np.array(host, dtype=np.uint8, copy=True)).cuda()
+    cols, status, k = rx.parse(t, kind=kind, chunk_len=chunk_len)
+    torch.cuda.synchronize()
+    return rx.decode(cols.cpu().numpy(), k), int(status.item())
+
+
+def check(rx, pattern, host, kind="auto", chunk_len=0):
+    got, st = gpu_cols(rx, host, kind, chunk_len)
+    want = oracle_cols(pattern, host.tobytes())
+    accepted = serial.accepted(want)
+    assert st == (0 if accepted else 1), f"status {st}, oracle accepted={accepted}"
+    assert got.shape == want.shape
+    bad = np.nonzero(np.any(got != want, axis=1))[0]
+    assert bad.size == 0, f"{bad.size} columns differ, first at r={bad[:5].tolist()}"
+
+
+SIZES = [0, 1, 2, 63, 64, 65, 127, 1000, 4097, 20000]
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("chunk_len", [64, 192, 0])
+def test_ab_star(lib, n, chunk_len):
+    rx = lib(W.AB_RE)
+    check(rx, W.AB_RE, W.ab_text(n, seed=n), chunk_len=chunk_len)
+    check(rx, W.AB_RE, W.ab_text(n, seed=n), kind="dict", chunk_len=chunk_len)
+
+
+@pytest.mark.parametrize("n", [5, 64, 1000, 30000, 100_003])
+@pytest.mark.parametrize("chunk_len", [64, 128, 1024, 0])
+def test_dna(lib, n, chunk_len):
+    rx = lib(W.DNA_RE)
+    x = W.dna_text(n, seed=1, mean_gap=500)
+    check(rx, W.DNA_RE, x, chunk_len=chunk_len)
+    if n <= 30000:
+        check(rx, W.DNA_RE, x, kind="dense", chunk_len=chunk_len)
+
+
+@pytest.mark.parametrize("pattern", ["(ab|a)*", "(a|ab|aba)+", "(a|b)*a(a|b){3}", "((ab)*c|a(bc)*)*",
+                                     "[ab]([^b]|bb)*", "(aa)*", "(a|b)*(aaa|bbb)(a|b)*"])
+def test_fixed_res_random_texts(lib, pattern):
+    rx = lib(pattern)
+    rng = np.random.Generator(np.random.PCG64(len(pattern)))
+    for n in (0, 1, 100, 777, 5000):
+        for chunk_len in (64, 128, 0):
+            x = rng.choice(np.frombuffer(b"aabbc", dtype=np.uint8), size=n)
+            check(rx, pattern, x, chunk_len=chunk_len)
+
+
+def test_unconverged_parity_chunks(lib):
+    """(aa)* on a^n: speculative runs never meet, every chunk is chained."""
+    rx = lib("(aa)*")
+    for n in (64 * 5, 64 * 5 + 1, 64 * 40, 64 * 40 + 2):
+        x = np.full(n, ord("a"), dtype=np.uint8)
+        check(rx, "(aa)*", x, chunk_len=64)
+        check(rx, "(aa)*", x, chunk_len=128)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_res_valid_texts(lib, seed):
+    pattern, tree, _ = W.random_re(100 + seed, max_pos=80)
+    rx = lib(pattern)
+    for n, cl in ((300, 64), (5000, 128), (20000, 0)):
+        x = W.sample_text(tree, n, seed)
+        check(rx, pattern, x, chunk_len=cl)
+
+
+def test_rejected_texts(lib):
+    rx = lib("(ab|a)*")
+    x = np.frombuffer(b"ab" * 500 + b"b" + b"a" * 300, dtype=np.uint8)
+    got, st = gpu_cols(rx, x, chunk_len=64)
+    assert st == 1 and not got.any()
+    x2 = np.frombuffer(b"ab" * 2000 + b"bb", dtype=np.uint8)      # dies in the last chunk
+    got, st = gpu_cols(rx, x2, chunk_len=64)
+    assert st == 1 and not got.any()
+
+
+def test_log_records(lib):
+    x = W.log_text(60_000, seed=2)
+    rx = lib(W.LOG_RE)
+    check(rx, W.LOG_RE, x, chunk_len=256)
+    check(rx, W.LOG_RE, x, chunk_len=0)
+
+
+def test_epsilon_and_single_terminal(lib):
+    for pattern, text in (("(a|)b", b"b"), ("(a|)b", b"ab"), ("a", b"a"), ("a", b""), ("()", b""),
+                          ("()", b"x"), ("(a|b)?", b"")):
+        rx = lib(pattern)
+        check(rx, pattern, np.frombuffer(text, dtype=np.uint8).copy())

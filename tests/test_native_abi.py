@@ -1,0 +1,87 @@
+"""CPU checks of the native library: exports, host-only compile vs the oracle.
+
+No CUDA call is made here (handles are compiled with RE_COMPILE_HOST_ONLY).
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import parallel_equations as pe
+from oracle.re_front import compile_re
+from oracle import serial
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+PATTERNS = ["(a|b|ab)*", "(ab|a)*", "(a|ab|aba)+", "(a|)b", "(a|b)*a(a|b){3}", "a", "()",
+            "([ACGT]|ATG([ACGT][ACGT][ACGT])*(TAA|TAG|TGA))*", "((ab)*c|a(bc)*)*", "[ab]([^b]|bb)*",
+            "(x(y|z)?w|[^a-c]+)*q", "a(b(c(d)))", "(a|(b|c)|d)*", "(\\.|[0-9]+\\.?)+", "((a|b)(a|b))*"]
+
+
+@pytest.fixture(scope="module")
+def native():
+    try:
+        from paper_2503_06763_gb300 import native
+        native.load()
+    except ImportError:
+        import __graft_entry__
+        __graft_entry__.build()
+        from paper_2503_06763_gb300 import native
+        native.load()
+    return native
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "slpf_parser.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(re_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(native):
+    lib = native.load()
+    names = header_functions()
+    assert "re_parse" in names and "re_compile" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(native.EXPORTS) <= set(names)
+
+
+@pytest.mark.parametrize("pattern", PATTERNS)
+def test_host_compile_matches_oracle_segments_and_dfa(native, pattern):
+    r = native.Regex(pattern, host_only=True)
+    c = compile_re(pattern)
+    assert r.segment_names() == c.names()
+    assert r.info["fwd_dfa_states"] == len(pe.dfa_states(c))
+    assert r.info["bwd_dfa_states"] == len(pe.dfa_states(c, reverse=True))
+    # dictionary: distinct, non-empty, canonical order, every column a B ∩ B̂
+    if r.info["dict_size"]:
+        d = r.dictionary()
+        sets = [tuple(sorted(serial.from_bits(row))) for row in d]
+        assert all(sets) and len(set(sets)) == len(sets)
+        assert sets == sorted(sets)
+        fw, bw = pe.dfa_states(c), pe.dfa_states(c, reverse=True)
+        inter = {tuple(sorted(a & b)) for a in fw for b in bw if a & b}
+        assert set(sets) == inter
+
+
+def test_layout_and_errors(native):
+    r = native.Regex("(a|b|ab)*", host_only=True)
+    assert r.layout(100, "auto") == ("dense", 2, 202)
+    assert r.layout(100, "dict")[0] == "dict"
+    big = native.Regex("([ACGT]|ATG([ACGT][ACGT][ACGT])*(TAA|TAG|TGA))*", host_only=True)
+    assert big.layout(10, "auto") == ("dict", 2, 22)
+    assert big.layout(10, "dense") == ("dense", 8, 88)
+    for bad, code in (("(a", -2), ("a)", -2), ("(a|)*", -3), ("(a*)*", -3), ("a{0}", -2)):
+        with pytest.raises(native.ReError) as e:
+            native.Regex(bad, host_only=True)
+        assert e.value.status == code
+    with pytest.raises(native.ReError) as e:
+        native.Regex("(a|b)*a(a|b){12}", max_states=200, host_only=True)
+    assert e.value.status == -4
+
+
+def test_ek_family_state_counts(native):
+    for k in range(1, 8):
+        r = native.Regex("(a|b)*a(a|b){%d}" % k, host_only=True)
+        assert r.info["fwd_dfa_states"] == 2 ** (k + 1) + 1
