@@ -184,6 +184,9 @@ class Regex:
         slpf = Slpf(KINDS[kname], cb, 0, out.data_ptr(), out.numel() * out.element_size(), status.data_ptr())
         opts = ParseOpts(KINDS[kname], chunk_len, flags, 0, None)
         if events is not None:          # RE_PHASE_EVENTS torch.cuda.Event objects
+            for e in events:
+                if not e.cuda_event:        # torch creates the CUDA event on first record
+                    e.record(s)
             arr = (ctypes.c_void_p * RE_PHASE_EVENTS)(*[ctypes.c_void_p(e.cuda_event) for e in events])
             opts.n_events, opts.events = RE_PHASE_EVENTS, ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p))
         check(load().re_parse(self._h, text.data_ptr() if n else None, n, ctypes.c_void_p(s.cuda_stream),
