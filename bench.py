@@ -150,7 +150,8 @@ def traffic_for(kernel: str, n: int):
     try:
         with open(path) as f:
             d = json.load(f)
-        src = open(os.path.join(ROOT, "paper_2503_06763_gb300", "csrc", "parse_kernels.cu"), "rb").read()
+        src = b"".join(open(os.path.join(ROOT, "paper_2503_06763_gb300", "csrc", f), "rb").read()
+                       for f in ("kernels.cuh", "reach.cu", "merge.cu"))
         if d.get("csrc_sha256") != hashlib.sha256(src).hexdigest():
             return None
         per = d.get("dram_bytes_per_text_byte", {}).get(kernel)
@@ -191,7 +192,7 @@ def main():
     status = torch.empty(1, dtype=torch.int32, device=dev)
     ws = torch.empty(rx.workspace_size(n, args.chunk_len), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(PHASES) + 1)] for _ in range(args.steps)]
 
     def step(i=None):
         rx.parse(text, kind=kind, chunk_len=args.chunk_len, out=out, status=status, workspace=ws,
@@ -230,7 +231,7 @@ def main():
                 for j, p in enumerate(PHASES)}
     dominant = max(phase_ms, key=phase_ms.get)
     # algorithmic bytes per launch: text read once, plus the SLPF written by build & merge
-    alg = {"reach_fwd": n, "reach_bwd": n, "join": 0, "fixup": 0, "build_merge": n + (n + 1) * cb}
+    alg = {"reach": n, "join": 0, "fixup": 0, "build_merge": n + (n + 1) * cb}
     hbm, src = peaks()
     achieved = alg[dominant] / (phase_ms[dominant] / 1e3) / 1e9 if alg[dominant] else 0.0
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1), "peak": hbm,
@@ -276,7 +277,7 @@ def main():
                    "l2": "text 256 MiB > 129 MB L2 (no flush needed)",
                    "parallelism": f"independent texts per GPU x{world}"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": 9 * args.steps, "clocks": clocks,
+        "gpu_launches": 8 * args.steps, "clocks": clocks,
     }
     print(json.dumps(line))
     if dist:

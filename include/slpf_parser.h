@@ -86,10 +86,11 @@ typedef struct {
 } re_parse_opts;
 
 /* Phase boundaries recorded into re_parse_opts.events: [0] start,
- * [1] after forward reach, [2] after backward reach (Eq. reacher),
- * [3] after join (Eq. joiner) and status, [4] after checkpoint fix-up,
- * [5] after build & merge (Eqs. builder, merger) and compose.               */
-#define RE_PHASE_EVENTS 6u
+ * [1] after reach (forward and backward, Eq. reacher), [2] after join
+ * (Eq. joiner) and the status word, [3] after checkpoint fix-up, [4] after
+ * build & merge (Eqs. builder, merger) and compose.  In recognizer mode
+ * [3] and [4] follow [2] immediately.                                      */
+#define RE_PHASE_EVENTS 5u
 
 /* Recognizer mode (Sect. 4.2, "Mere recognizer"): run forward reach and join
  * only, write the accept / reject status and no columns.                    */

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libslpf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 HOST_SOURCES = ["re_compile.cpp"]
-CUDA_SOURCES = ["parse_kernels.cu"]
+CUDA_SOURCES = ["api.cu", "reach.cu", "join.cu", "merge.cu"]
 
 
 def _cuda_home() -> str:
@@ -35,7 +35,7 @@ def _sources_newer(target: str) -> bool:
     if not os.path.exists(target):
         return True
     t = os.path.getmtime(target)
-    roots = [CSRC, os.path.join(os.path.dirname(HERE), "include")]
+    roots = [CSRC, os.path.join(os.path.dirname(HERE), "include"), HERE]
     for root in roots:
         for name in os.listdir(root):
             if os.path.getmtime(os.path.join(root, name)) > t:

@@ -1,0 +1,214 @@
+// Join phase (arXiv 2503.06763, Eq. joiner): FJ[i] = J_i, the forward state at
+// the boundary before chunk i (J_0 = I), and BJ[i] = Ĵ at that boundary
+// (BJ[c] = F).
+//
+// Every chunk maps an input state S to the union, over its slots whose keys
+// S contains, of the slot's end state.  When all live slots of a chunk end in
+// one state (the common case: speculative runs meet within a few hundred
+// bytes, Sect. 4.3) the chunk's output is that state for every input that
+// enters a live slot, so it is known without its neighbour.  The remaining
+// chunks form chains that are evaluated in order from the nearest known
+// neighbour.  A verify pass checks each guessed output against its actual
+// input; the first chunk where the text cannot continue makes the whole text
+// rejected (no accepting run: every clean column is empty).
+#include "kernels.cuh"
+
+namespace slpf {
+namespace {
+
+__device__ uint32_t probe(const uint32_t *hash, uint32_t mask, const uint64_t *bits, uint32_t W,
+                          const uint64_t *key) {
+    uint64_t h = bits_hash(key, W) & mask;
+    for (uint32_t step = 0; step <= mask; ++step) {
+        const uint32_t id = __ldg(hash + h);
+        if (id == 0) return 0;
+        bool eq = true;
+        for (uint32_t w = 0; w < W; ++w)
+            if (__ldg(bits + (size_t)id * W + w) != key[w]) { eq = false; break; }
+        if (eq) return id;
+        h = (h + 1) & mask;
+    }
+    return 0;
+}
+
+__device__ __forceinline__ uint32_t pair_fwd(const Params &p, uint32_t i) {
+    const uint64_t base = (uint64_t)i * p.k;
+    return __ldg(p.t.cls + __ldg(p.x + base - 1)) * p.t.ncls + __ldg(p.t.cls + __ldg(p.x + base));
+}
+__device__ __forceinline__ uint32_t pair_bwd(const Params &p, uint32_t i) {
+    const uint64_t end = (uint64_t)i * p.k + chunk_len(p, i);
+    return __ldg(p.t.cls + __ldg(p.x + end - 1)) * p.t.ncls + __ldg(p.t.cls + __ldg(p.x + end));
+}
+
+// State after chunk i for input state S: union over the slots S enters.
+__device__ uint32_t eval_chunk(const Params &p, bool fwd, uint32_t i, uint32_t S, bool &bad) {
+    const DevTables &t = p.t;
+    if (S == 0) return 0;
+    const uint32_t W = t.W;
+    uint32_t pr, m, ms;
+    const uint32_t *R;
+    const uint64_t *mask, *bits;
+    if (fwd) {
+        pr = pair_fwd(p, i); m = __ldg(t.fSlotCount + pr); ms = t.msf; R = p.w.Rf + (size_t)i * ms;
+        mask = t.fSlotMask + (size_t)pr * ms * W; bits = t.fBits;
+    } else {
+        pr = pair_bwd(p, i); m = __ldg(t.bSlotCount + pr); ms = t.msb; R = p.w.Rb + (size_t)i * ms;
+        mask = t.bSlotMask + (size_t)pr * ms * W; bits = t.bBits;
+    }
+    const uint64_t *sb = bits + (size_t)S * W;
+    uint32_t single = 0;
+    bool multi = false;
+    uint64_t acc[kMaxW];
+    for (uint32_t w = 0; w < W; ++w) acc[w] = 0;
+    for (uint32_t s = 0; s < m; ++s) {
+        const uint32_t e = R[s];
+        if (!e || !any_and(sb, mask + (size_t)s * W, W)) continue;
+        if (!single) single = e;
+        else if (e != single) multi = true;
+        for (uint32_t w = 0; w < W; ++w) acc[w] |= __ldg(bits + (size_t)e * W + w);
+    }
+    if (!multi) return single;
+    const uint32_t id = fwd ? probe(t.fHash, t.fHashMask, t.fBits, W, acc)
+                            : probe(t.bHash, t.bHashMask, t.bBits, W, acc);
+    if (!id) bad = true;
+    return id;
+}
+
+// One live end state (or none) for every chunk?  Record it as the guess.
+__device__ void classify(const Params &p, bool fwd, uint32_t i) {
+    const DevTables &t = p.t;
+    const uint32_t pr = fwd ? pair_fwd(p, i) : pair_bwd(p, i);
+    const uint32_t m = __ldg((fwd ? t.fSlotCount : t.bSlotCount) + pr);
+    const uint32_t ms = fwd ? t.msf : t.msb;
+    const uint32_t *R = (fwd ? p.w.Rf : p.w.Rb) + (size_t)i * ms;
+    uint32_t rep = 0;
+    bool gen = false;
+    for (uint32_t s = 0; s < m; ++s) {
+        const uint32_t e = R[s];
+        if (e) { if (!rep) rep = e; else if (e != rep) gen = true; }
+    }
+    if (fwd) {
+        p.w.fkind[i] = gen ? 1u : 0u;
+        if (!gen) p.w.FJ[i + 1] = rep;
+    } else {
+        p.w.bkind[i] = gen ? 1u : 0u;
+        if (!gen) p.w.BJ[i] = rep;
+    }
+}
+
+__global__ void join_classify_kernel(Params p) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.c) return;
+    if (i == 0) {
+        p.w.FJ[0] = p.t.fI;
+        p.w.FJ[1] = p.w.Rf[0];
+        p.w.fkind[0] = 0;
+    } else {
+        classify(p, true, i);
+    }
+    if (p.recognize) return;
+    if (i == p.c - 1) {
+        p.w.BJ[p.c] = p.t.bF;
+        p.w.BJ[i] = p.w.Rb[(size_t)i * p.t.msb];
+        p.w.bkind[i] = 0;
+    } else {
+        classify(p, false, i);
+    }
+}
+
+__global__ void join_chain_kernel(Params p) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.c) return;
+    bool bad = false;
+    if (p.w.fkind[i] == 1 && p.w.fkind[i - 1] == 0) {     // i >= 1: fkind[0] == 0
+        uint32_t cur = p.w.FJ[i];
+        for (uint32_t j = i; j < p.c && p.w.fkind[j] == 1; ++j) {
+            cur = eval_chunk(p, true, j, cur, bad);
+            p.w.FJ[j + 1] = cur;
+        }
+    }
+    if (!p.recognize && p.w.bkind[i] == 1 && p.w.bkind[i + 1] == 0) {   // i <= c-2: bkind[c-1] == 0
+        uint32_t cur = p.w.BJ[i + 1];
+        for (int64_t j = i; j >= 0 && p.w.bkind[j] == 1; --j) {
+            cur = eval_chunk(p, false, (uint32_t)j, cur, bad);
+            p.w.BJ[j] = cur;
+        }
+    }
+    if (bad) atomicExch(&p.w.flags[FLAG_INTERNAL], 1);
+}
+
+// Does input state S enter a live slot of chunk i?
+__device__ bool hits_live(const Params &p, bool fwd, uint32_t i, uint32_t S) {
+    const DevTables &t = p.t;
+    const uint32_t W = t.W;
+    const uint32_t pr = fwd ? pair_fwd(p, i) : pair_bwd(p, i);
+    const uint32_t m = __ldg((fwd ? t.fSlotCount : t.bSlotCount) + pr);
+    const uint32_t ms = fwd ? t.msf : t.msb;
+    const uint32_t *R = (fwd ? p.w.Rf : p.w.Rb) + (size_t)i * ms;
+    const uint64_t *mask = (fwd ? t.fSlotMask : t.bSlotMask) + (size_t)pr * ms * W;
+    const uint64_t *sb = (fwd ? t.fBits : t.bBits) + (size_t)S * W;
+    for (uint32_t s = 0; s < m; ++s)
+        if (R[s] && any_and(sb, mask + (size_t)s * W, W)) return true;
+    return false;
+}
+
+__global__ void join_verify_kernel(Params p) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.c) return;
+    {   // forward: input FJ[i] -> output FJ[i+1]
+        const uint32_t in = p.w.FJ[i], out = p.w.FJ[i + 1];
+        bool fail = in == 0 || out == 0;
+        if (!fail && i > 0 && p.w.fkind[i] == 0) fail = !hits_live(p, true, i, in);
+        if (fail) atomicMin(&p.w.flags[FLAG_FFAIL], (int32_t)i);
+        p.w.FC[(uint64_t)i * p.S] = in;                              // position i*k
+        if (i == p.c - 1 && (p.n & 63) == 0) p.w.FC[p.n >> 6] = p.w.FJ[p.c];   // position n
+    }
+    if (p.recognize) return;
+    {   // backward: input BJ[i+1] -> output BJ[i]
+        const uint32_t in = p.w.BJ[i + 1], out = p.w.BJ[i];
+        bool fail = in == 0 || out == 0;
+        if (!fail && i < p.c - 1 && p.w.bkind[i] == 0) fail = !hits_live(p, false, i, in);
+        if (fail) atomicMin(&p.w.flags[FLAG_BFAIL], (int32_t)i);
+        if (i + 1 < p.c) {
+            p.w.BC[(uint64_t)(i + 1) * p.S - 1] = in;                // position (i+1)*k
+        } else {                                                     // groups whose end is clipped to n
+            for (uint64_t g = (p.n + 63) / 64 - 1; g < p.Gc; ++g) p.w.BC[g] = in;
+        }
+    }
+}
+
+// Accept iff both joins ran through and C_0 = I ∩ Ĵ_1 is not empty
+// (recognizer: iff the forward join ran through and J_c ∩ F is not empty).
+__global__ void status_kernel(Params p) {
+    const DevTables &t = p.t;
+    int32_t st = RE_OK;
+    if (p.w.flags[FLAG_FFAIL] < (int32_t)p.c || (!p.recognize && p.w.flags[FLAG_BFAIL] < (int32_t)p.c)) {
+        st = RE_REJECTED;
+    } else if (p.recognize) {
+        const uint32_t jc = p.w.FJ[p.c];
+        if (!any_and(t.fBits + (size_t)jc * t.W, t.bBits + (size_t)t.bF * t.W, t.W)) st = RE_REJECTED;
+    } else {
+        const uint32_t b0 = p.w.BJ[0];
+        if (!(b0 && any_and(t.fBits + (size_t)t.fI * t.W, t.bBits + (size_t)b0 * t.W, t.W))) st = RE_REJECTED;
+    }
+    if (p.w.flags[FLAG_INTERNAL]) st = RE_E_INTERNAL;
+    *p.status = st;
+}
+
+__global__ void flags_init_kernel(Params p) {
+    if (threadIdx.x < FLAG_COUNT) p.w.flags[threadIdx.x] = threadIdx.x < 2 ? (int32_t)p.c : 0;
+}
+
+}  // namespace
+
+void launch_join(const Params &p, cudaStream_t s) {
+    const uint32_t blocks = (p.c + kBlockThreads - 1) / kBlockThreads;
+    join_classify_kernel<<<blocks, kBlockThreads, 0, s>>>(p);
+    join_chain_kernel<<<blocks, kBlockThreads, 0, s>>>(p);
+    join_verify_kernel<<<blocks, kBlockThreads, 0, s>>>(p);
+    status_kernel<<<1, 1, 0, s>>>(p);
+}
+
+void launch_flags_init(const Params &p, cudaStream_t s) { flags_init_kernel<<<1, 32, 0, s>>>(p); }
+
+}  // namespace slpf

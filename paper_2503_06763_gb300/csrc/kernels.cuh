@@ -1,0 +1,147 @@
+// Device-side definitions shared by the parse kernels (reach.cu, join.cu,
+// merge.cu) and the host launcher (api.cu).
+//
+// Geometry of one parse (arXiv 2503.06763, Sect. 3.2, split phase):
+//   text x[0..n), n >= 1; chunks y_i = x[i*k, min((i+1)*k, n)), k a multiple of
+//   L = 64, c = ceil(n/k) chunks of S = k/L sub-chunks; SLPF columns r = 0..n
+//   (column r lies between bytes r-1 and r).
+//   Column groups g = 0 .. Gc-1, Gc = floor(n/L) + 1: group g holds columns
+//   64g .. min(64g+63, n), so each group's output starts on a 64-column
+//   boundary of the output array.
+//   Checkpoints: FC[g] = forward state B at position 64g,
+//                BC[g] = backward state B̂ at position min(64g+64, n).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "re_internal.h"
+
+namespace slpf {
+
+constexpr int kMaxW = 64;           // segments per column <= 4096
+constexpr uint32_t kBlockThreads = 256;
+
+enum Flag { FLAG_FFAIL = 0, FLAG_BFAIL = 1, FLAG_INTERNAL = 2, FLAG_COUNT = 4 };
+
+struct Work {                       // device workspace, carved from the caller's buffer
+    uint32_t *Rf, *Rb;              // [c][msf], [c][msb] end state of each speculation slot
+    uint32_t *FJ, *BJ;              // [c+1]: state at the boundary before chunk i
+    uint32_t *FC, *BC;              // [Gc] checkpoints
+    uint32_t *fconv, *bconv;        // [c] first / last sub-chunk boundary the reach runs agree on
+    uint32_t *fkind, *bkind;        // [c] 0: every live slot ends in one state, 1: several
+    int32_t *flags;                 // [FLAG_COUNT]
+};
+
+struct Params {
+    DevTables t;
+    const uint8_t *x;
+    uint64_t n;
+    uint32_t k, c, S;               // chunk length, chunks, sub-chunks per chunk
+    uint64_t Gc;                    // column groups
+    Work w;
+    void *out;
+    uint32_t col_bytes, kind;       // output encoding (re_slpf_kind)
+    int32_t *status;
+    uint32_t recognize;             // forward reach + join only
+    uint32_t smem_tables;           // transition tables staged in shared memory (u16)
+    uint32_t pt_in_smem;            // dictionary pair table staged in shared memory
+};
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ uint32_t chunk_len(const Params &p, uint32_t i) {
+    uint64_t rest = p.n - (uint64_t)i * p.k;
+    return rest < p.k ? (uint32_t)rest : p.k;
+}
+
+__device__ __forceinline__ bool any_and(const uint64_t *a, const uint64_t *b, uint32_t W) {
+    for (uint32_t w = 0; w < W; ++w)
+        if (__ldg(a + w) & __ldg(b + w)) return true;
+    return false;
+}
+
+// 16 text bytes from x[at..at+16); bytes at or past n read as 0.
+__device__ __forceinline__ uint4 load16(const uint8_t *x, uint64_t n, uint64_t at) {
+    if (at + 16 <= n) return __ldg(reinterpret_cast<const uint4 *>(x + at));
+    uint32_t w[4] = {0, 0, 0, 0};
+    for (int j = 0; j < 16; ++j)
+        if (at + j < n) w[j >> 2] |= (uint32_t)__ldg(x + at + j) << (8 * (j & 3));
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+__device__ __forceinline__ uint32_t byte_of(const uint4 &v, int u) {   // u in 0..15, unrolled
+    uint32_t w = (u < 4) ? v.x : (u < 8) ? v.y : (u < 12) ? v.z : v.w;
+    return (w >> (8 * (u & 3))) & 0xFFu;
+}
+
+// ---------------------------------------------------------------- tables
+// Transition tables, either staged in shared memory as u16 (SMEM) or read
+// from global memory as u32.  Row s, column = byte class.
+struct Tabs {
+    const uint8_t *cls;
+    const uint16_t *f16, *b16;
+    const uint32_t *f32, *b32;
+    uint32_t ncls;
+};
+
+template <bool SMEM>
+__device__ __forceinline__ uint32_t fnext(const Tabs &T, uint32_t s, uint32_t c) {
+    if (SMEM) return T.f16[s * T.ncls + c];
+    return __ldg(T.f32 + (size_t)s * T.ncls + c);
+}
+template <bool SMEM>
+__device__ __forceinline__ uint32_t bnext(const Tabs &T, uint32_t s, uint32_t c) {
+    if (SMEM) return T.b16[s * T.ncls + c];
+    return __ldg(T.b32 + (size_t)s * T.ncls + c);
+}
+template <bool SMEM>
+__device__ __forceinline__ uint32_t clsof(const Tabs &T, uint32_t b) {
+    if (SMEM) return T.cls[b];
+    return __ldg(T.cls + b);
+}
+
+// Bytes of shared memory used by stage_tables (tables only).
+__host__ __device__ inline size_t tables_smem_bytes(const DevTables &t) {
+    size_t a = 256;
+    a += ((size_t)t.nf * t.ncls * 2 + 15) & ~(size_t)15;
+    a += ((size_t)t.nb * t.ncls * 2 + 15) & ~(size_t)15;
+    return a;
+}
+
+// Stage the byte-class map and both transition tables in shared memory
+// (block-wide; ends with __syncthreads).  Returns the end of the used area.
+template <bool SMEM>
+__device__ uint8_t *stage_tables(const Params &p, uint8_t *sm, Tabs &T) {
+    const DevTables &t = p.t;
+    T.ncls = t.ncls;
+    T.f32 = t.fT;
+    T.b32 = t.bT;
+    if (!SMEM) {
+        T.cls = t.cls;
+        T.f16 = T.b16 = nullptr;
+        return sm;
+    }
+    uint8_t *cls = sm;
+    uint16_t *f16 = reinterpret_cast<uint16_t *>(sm + 256);
+    size_t fsz = (size_t)t.nf * t.ncls;
+    uint16_t *b16 = reinterpret_cast<uint16_t *>(sm + 256 + ((fsz * 2 + 15) & ~(size_t)15));
+    size_t bsz = (size_t)t.nb * t.ncls;
+    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) cls[i] = __ldg(t.cls + i);
+    for (size_t i = threadIdx.x; i < fsz; i += blockDim.x) f16[i] = (uint16_t)__ldg(t.fT + i);
+    for (size_t i = threadIdx.x; i < bsz; i += blockDim.x) b16[i] = (uint16_t)__ldg(t.bT + i);
+    T.cls = cls;
+    T.f16 = f16;
+    T.b16 = b16;
+    __syncthreads();
+    return reinterpret_cast<uint8_t *>(b16) + ((bsz * 2 + 15) & ~(size_t)15);
+}
+
+// ---------------------------------------------------------------- launchers
+size_t merge_extra_smem(const Params &p);
+bool launch_reach(const Params &p, cudaStream_t s, uint32_t ms, int sm_count);
+void launch_join(const Params &p, cudaStream_t s);
+void launch_fixup(const Params &p, cudaStream_t s, int sm_count);
+void launch_merge(const Params &p, cudaStream_t s, int sm_count);
+void launch_empty(const Params &p, cudaStream_t s);
+cudaError_t set_kernel_attributes();   // max dynamic shared memory, once per process
+
+}  // namespace slpf

@@ -41,8 +41,8 @@ class ParseOpts(ctypes.Structure):
                 ("n_events", ctypes.c_uint32), ("events", ctypes.POINTER(ctypes.c_void_p))]
 
 
-RE_PHASE_EVENTS = 6
-PHASES = ["reach_fwd", "reach_bwd", "join", "fixup", "build_merge"]
+RE_PHASE_EVENTS = 5
+PHASES = ["reach", "join", "fixup", "build_merge"]
 
 
 class Slpf(ctypes.Structure):
