@@ -52,10 +52,12 @@ uint32_t choose_chunk(uint64_t n, int sms, const re_parse_opts *opts) {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+constexpr int kArrays = 17;
+
 struct Layout {
     uint32_t k, c, S;
     uint64_t Gc;
-    size_t off[11];
+    size_t off[kArrays];
     size_t total;
 };
 
@@ -65,13 +67,18 @@ Layout layout_for(const re_handle *h, uint64_t n, uint32_t k) {
     L.c = (uint32_t)((n + k - 1) / k);
     L.S = k / kSub;
     L.Gc = n / kSub + 1;
-    const size_t sizes[11] = {
-        (size_t)L.c * h->host.msf * 4, (size_t)L.c * h->host.msb * 4, (size_t)(L.c + 1) * 4,
-        (size_t)(L.c + 1) * 4,         (size_t)L.Gc * 4,             (size_t)L.Gc * 4,
-        (size_t)L.c * 4,               (size_t)L.c * 4,              (size_t)L.c * 4,
-        (size_t)L.c * 4,               FLAG_COUNT * 4};
+    const size_t c = L.c;
+    const size_t sizes[kArrays] = {
+        c * h->host.msf * 4, c * h->host.msb * 4,        // Rf, Rb
+        (c + 1) * 4, (c + 1) * 4,                         // FJ, BJ
+        (size_t)L.Gc * 4, (size_t)L.Gc * 4,               // FC, BC
+        c * 4, c * 4, c * 4, c * 4,                       // fconv, bconv, fkind, bkind
+        c * 4, c * 4,                                     // fnrec, bnrec
+        c * kRecBounds * 4, c * kRecBounds * 4,           // recFc, recBc
+        c * kRecEntries * 8, c * kRecEntries * 8,         // recFe, recBe
+        FLAG_COUNT * 4};
     size_t o = 0;
-    for (int j = 0; j < 11; ++j) {
+    for (int j = 0; j < kArrays; ++j) {
         L.off[j] = o;
         o += align256(sizes[j] ? sizes[j] : 4);
     }
@@ -298,7 +305,10 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     p.w.FC = (uint32_t *)(w + L.off[4]); p.w.BC = (uint32_t *)(w + L.off[5]);
     p.w.fconv = (uint32_t *)(w + L.off[6]); p.w.bconv = (uint32_t *)(w + L.off[7]);
     p.w.fkind = (uint32_t *)(w + L.off[8]); p.w.bkind = (uint32_t *)(w + L.off[9]);
-    p.w.flags = (int32_t *)(w + L.off[10]);
+    p.w.fnrec = (uint32_t *)(w + L.off[10]); p.w.bnrec = (uint32_t *)(w + L.off[11]);
+    p.w.recFc = (uint32_t *)(w + L.off[12]); p.w.recBc = (uint32_t *)(w + L.off[13]);
+    p.w.recFe = (uint2 *)(w + L.off[14]); p.w.recBe = (uint2 *)(w + L.off[15]);
+    p.w.flags = (int32_t *)(w + L.off[16]);
     CUDA_TRY(mark(0), "event");
     launch_flags_init(p, s);
     if (!launch_reach(p, s, std::max(t.msf, recognize ? 1u : t.msb), sms)) {

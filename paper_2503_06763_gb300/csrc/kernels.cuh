@@ -20,6 +20,8 @@ namespace slpf {
 
 constexpr int kMaxW = 64;           // segments per column <= 4096
 constexpr uint32_t kBlockThreads = 256;
+constexpr uint32_t kRecBounds = 16;   // boundaries recorded per chunk and direction before runs meet
+constexpr uint32_t kRecEntries = 48;  // (state, slot set) entries recorded per chunk and direction
 
 enum Flag { FLAG_FFAIL = 0, FLAG_BFAIL = 1, FLAG_INTERNAL = 2, FLAG_COUNT = 4 };
 
@@ -29,6 +31,9 @@ struct Work {                       // device workspace, carved from the caller'
     uint32_t *FC, *BC;              // [Gc] checkpoints
     uint32_t *fconv, *bconv;        // [c] first / last sub-chunk boundary the reach runs agree on
     uint32_t *fkind, *bkind;        // [c] 0: every live slot ends in one state, 1: several
+    uint32_t *fnrec, *bnrec;        // [c] boundaries recorded (from the chunk's start / end)
+    uint32_t *recFc, *recBc;        // [c][kRecBounds] runs recorded at each boundary
+    uint2 *recFe, *recBe;           // [c][kRecEntries] (state, slot set) of those runs
     int32_t *flags;                 // [FLAG_COUNT]
 };
 

@@ -1,52 +1,146 @@
 // Checkpoint fix-up and build & merge (arXiv 2503.06763, Eqs. builder and
 // merger, Fig. builders&merger, compose of Sect. 3.2).
 //
-// fix-up: for the sub-chunk boundaries a chunk's reach runs reached before
-//   they agreed, walk the DFA from J_{i-1} (forward) and the reverse DFA from
-//   Ĵ_{i+1} (backward) and write the exact checkpoints.
-// build & merge: one thread per column group g (64 columns).  Forward
-//   B_{64g+u} from FC[g] over bytes 64g.., backward B̂ from BC[g] over the same
-//   bytes right to left, and the clean column C_r = B_r ∩ B̂_r written in the
+// fix-up: the exact checkpoints a chunk's reach runs could not give before
+//   they met.  At every recorded boundary the exact state is the union, over
+//   the runs whose slot set the chunk's input J_{i-1} (or Ĵ_{i+1}) enters, of
+//   the run states: Eq. joiner applied at sub-chunk granularity.  Boundaries
+//   beyond the record are walked with the DFA from the last exact state.
+// build & merge: one thread per column group g (64 columns).  The forward
+//   builder (B from FC[g]) and the backward builder (B̂ from BC[g]) run at the
+//   same time from the two ends of the group, keep their first 32 states in
+//   shared memory, meet in the middle and then merge while they proceed to the
+//   opposite ends: each new state is intersected with the stored state of the
+//   other direction, C_r = B_r ∩ B̂_r (Eq. merger), and written in the
 //   requested encoding (DENSE bitset, or DICT index through the pair table
-//   built at compile time).  The forward states of a group stay in registers
-//   (the fused builder & merger of Fig. builders&merger keeps B in M and
-//   intersects during the backward scan; here M is the register file).
+//   built at compile time).  This is the fused builder & merger schedule of
+//   Sect. 3.3 (Fig. builders&merger, merging from the midpoint outwards).
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace slpf {
 namespace {
 
 // ------------------------------------------------------------------ fix-up
+__device__ uint32_t probe_state(const uint32_t *hash, uint32_t mask, const uint64_t *bits, uint32_t W,
+                                const uint64_t *key) {
+    uint64_t h = bits_hash(key, W) & mask;
+    for (uint32_t step = 0; step <= mask; ++step) {
+        const uint32_t id = __ldg(hash + h);
+        if (id == 0) return 0;
+        bool eq = true;
+        for (uint32_t w = 0; w < W; ++w)
+            if (__ldg(bits + (size_t)id * W + w) != key[w]) { eq = false; break; }
+        if (eq) return id;
+        h = (h + 1) & mask;
+    }
+    return 0;
+}
+
+// Exact state at a recorded boundary: union of the runs whose slots H enters.
+__device__ uint32_t record_union(const Params &p, bool fwd, const uint2 *ent, uint32_t cnt, uint32_t H, bool &bad) {
+    const DevTables &t = p.t;
+    const uint32_t W = t.W;
+    const uint64_t *bits = fwd ? t.fBits : t.bBits;
+    uint32_t single = 0;
+    bool multi = false;
+    uint64_t acc[kMaxW];
+    for (uint32_t w = 0; w < W; ++w) acc[w] = 0;
+    for (uint32_t e = 0; e < cnt; ++e) {
+        const uint2 r = ent[e];
+        if (!(r.y & H)) continue;
+        if (!single) single = r.x;
+        else if (r.x != single) multi = true;
+        for (uint32_t w = 0; w < W; ++w) acc[w] |= __ldg(bits + (size_t)r.x * W + w);
+    }
+    if (!multi) return single;
+    const uint32_t id = fwd ? probe_state(t.fHash, t.fHashMask, t.fBits, W, acc)
+                            : probe_state(t.bHash, t.bHashMask, t.bBits, W, acc);
+    if (!id) bad = true;
+    return id;
+}
+
+// Slots of the chunk's boundary class pair that input state S enters.
+__device__ uint32_t hit_mask(const Params &p, bool fwd, uint32_t pr, uint32_t S) {
+    const DevTables &t = p.t;
+    const uint32_t W = t.W;
+    const uint32_t m = __ldg((fwd ? t.fSlotCount : t.bSlotCount) + pr);
+    const uint32_t ms = fwd ? t.msf : t.msb;
+    const uint64_t *mask = (fwd ? t.fSlotMask : t.bSlotMask) + (size_t)pr * ms * W;
+    const uint64_t *sb = (fwd ? t.fBits : t.bBits) + (size_t)S * W;
+    uint32_t H = 0;
+    for (uint32_t j = 0; j < m; ++j)
+        if (any_and(sb, mask + (size_t)j * W, W)) H |= 1u << j;
+    return H;
+}
+
 template <bool SMEM>
 __global__ void __launch_bounds__(kBlockThreads) fixup_kernel(Params p) {
     extern __shared__ __align__(16) uint8_t sm[];
     Tabs T;
     stage_tables<SMEM>(p, sm, T);
     if (*p.status != RE_OK) return;
+    const DevTables &t = p.t;
+    bool bad = false;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < p.c; i += stride) {
         const uint64_t base = (uint64_t)i * p.k;
         const uint32_t len = chunk_len(p, i);
         const uint32_t nsub = (len + 63) / 64;
-        const uint32_t fcs = p.w.fconv[i], bcs = p.w.bconv[i];
-        const uint32_t fsteps = fcs > 1 ? (fcs - 1) * 64 : 0;            // bytes [0, fsteps)
-        const uint32_t bstop = (bcs + 1) * 64;                            // bytes [bstop, len) backwards
-        const uint32_t bsteps = (nsub >= 2 && bcs + 1 <= nsub - 1) ? len - bstop : 0;
-        uint32_t sF = p.w.FJ[i], sB = p.w.BJ[i + 1];
-        const uint32_t steps = max(fsteps, bsteps);
-        for (uint32_t s = 0; s < steps; ++s) {
-            if (s < fsteps) {
-                const uint32_t t = s;
-                sF = fnext<SMEM>(T, sF, clsof<SMEM>(T, __ldg(p.x + base + t)));
-                if (((t + 1) & 63) == 0) p.w.FC[(uint64_t)i * p.S + (t + 1) / 64] = sF;
+        const uint64_t g0 = (uint64_t)i * p.S;
+        // forward: boundaries 1 .. fconv-1
+        const uint32_t fcs = p.w.fconv[i];
+        if (fcs > 1) {
+            const uint32_t J = p.w.FJ[i];
+            const uint32_t pr = clsof<SMEM>(T, __ldg(p.x + base - 1)) * t.ncls + clsof<SMEM>(T, __ldg(p.x + base));
+            const uint32_t H = hit_mask(p, true, pr, J);
+            const uint32_t nrec = p.w.fnrec[i];
+            const uint32_t *cnt = p.w.recFc + (size_t)i * kRecBounds;
+            const uint2 *ent = p.w.recFe + (size_t)i * kRecEntries;
+            uint32_t exact = J, s = 1, off = 0;
+            for (; s < fcs && s - 1 < nrec; ++s) {
+                const uint32_t m = cnt[s - 1];
+                exact = record_union(p, true, ent + off, m, H, bad);
+                off += m;
+                p.w.FC[g0 + s] = exact;
             }
-            if (s < bsteps) {
-                const uint32_t t = len - 1 - s;
-                sB = bnext<SMEM>(T, sB, clsof<SMEM>(T, __ldg(p.x + base + t)));
-                if ((t & 63) == 0) p.w.BC[(uint64_t)i * p.S + t / 64 - 1] = sB;
+            for (uint32_t tt = 64 * (s - 1); s < fcs; ++tt) {       // walk the rest
+                exact = fnext<SMEM>(T, exact, clsof<SMEM>(T, __ldg(p.x + base + tt)));
+                if (((tt + 1) & 63) == 0) { p.w.FC[g0 + (tt + 1) / 64] = exact; ++s; }
+            }
+        }
+        if (p.recognize) continue;
+        // backward: boundaries nsub-1 down to bconv+1
+        const uint32_t bcs = p.w.bconv[i];
+        if (nsub >= 2 && bcs + 1 <= nsub - 1) {
+            const uint32_t J = p.w.BJ[i + 1];
+            uint32_t H = 0;
+            if (i + 1 < p.c) {
+                const uint32_t pr = clsof<SMEM>(T, __ldg(p.x + base + len - 1)) * t.ncls +
+                                    clsof<SMEM>(T, __ldg(p.x + base + len));
+                H = hit_mask(p, false, pr, J);
+            }
+            const uint32_t nrec = p.w.bnrec[i];
+            const uint32_t *cnt = p.w.recBc + (size_t)i * kRecBounds;
+            const uint2 *ent = p.w.recBe + (size_t)i * kRecEntries;
+            uint32_t exact = J, bb = nsub - 1, r = 0, off = 0;
+            for (; bb > bcs && r < nrec; --bb, ++r) {
+                const uint32_t m = cnt[r];
+                exact = record_union(p, false, ent + off, m, H, bad);
+                off += m;
+                p.w.BC[g0 + bb - 1] = exact;
+            }
+            if (bb > bcs) {                                           // walk the rest
+                int64_t tt = (r == 0) ? (int64_t)len - 1 : 64 * (int64_t)(bb + 1) - 1;
+                for (; bb > bcs; --tt) {
+                    exact = bnext<SMEM>(T, exact, clsof<SMEM>(T, __ldg(p.x + base + tt)));
+                    if ((tt & 63) == 0) { p.w.BC[g0 + tt / 64 - 1] = exact; --bb; }
+                }
             }
         }
     }
+    if (bad) atomicExch(p.status, RE_E_INTERNAL);
 }
 
 // ------------------------------------------------------------------ encodings
@@ -82,63 +176,78 @@ __device__ __forceinline__ void store_col(void *out, uint64_t r, uint64_t v) {
 
 constexpr int bytes_of(int E) { return (E == ENC_X2) ? 2 : (E == ENC_X4) ? 4 : E; }
 
-// Full group: 64 columns, forward 63 steps, backward 64 steps, all unrolled.
-template <bool SMEM, int E>
-__device__ __forceinline__ void group_full(const Params &p, const Tabs &T, const Enc &e, uint64_t g, bool &bad) {
-    const uint64_t pos = g * 64;
-    uint4 xv[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) xv[q] = __ldg(reinterpret_cast<const uint4 *>(p.x + pos) + q);
-    uint32_t f = p.w.FC[g];
-    uint32_t b = p.w.BC[g];
-    if (f == kUnknown || b == kUnknown) { bad = true; f = 0; b = 0; }   // never index with the sentinel
-    // forward states B_{pos+u}, two 16-bit states per register when the tables allow
-    constexpr bool PACK = SMEM;                      // shared-memory tables: state ids < 65536
-    uint32_t F[PACK ? 32 : 64];
-    {
-        uint32_t cur = f;
-#pragma unroll
-        for (int u = 0; u < 64; ++u) {
-            if (u > 0) cur = fnext<SMEM>(T, cur, clsof<SMEM>(T, byte_of(xv[(u - 1) >> 4], (u - 1) & 15)));
-            if (PACK) {
-                if (u & 1) F[u >> 1] |= cur << 16;
-                else F[u >> 1] = cur;
-            } else {
-                F[u] = cur;
-            }
-        }
-    }
-    auto fwd_at = [&](int u) -> uint32_t { return PACK ? ((F[u >> 1] >> (16 * (u & 1))) & 0xFFFFu) : F[u]; };
-    constexpr int CB = bytes_of(E);
-    // backward walk from the right end; columns are packed and stored in 16-byte
-    // vectors as soon as a vector is complete (stores run from the group's end)
-    uint8_t *gout = reinterpret_cast<uint8_t *>(p.out) + pos * CB;
-    if constexpr (CB == 8) {
-        uint64_t hi = 0;
-#pragma unroll
-        for (int u = 63; u >= 0; --u) {
-            b = bnext<SMEM>(T, b, clsof<SMEM>(T, byte_of(xv[u >> 4], u & 15)));
-            const uint64_t v = enc_d8(e, fwd_at(u), b);
-            if (u & 1) hi = v;
-            else reinterpret_cast<uint4 *>(gout)[u >> 1] =
-                make_uint4((uint32_t)v, (uint32_t)(v >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
-        }
+// Put one column value into a 16-byte vector being assembled (slot k).
+template <int CB>
+__device__ __forceinline__ void put_col(uint32_t (&w4)[4], int k, uint64_t v) {
+    if (CB == 8) {
+        w4[2 * k] = (uint32_t)v;
+        w4[2 * k + 1] = (uint32_t)(v >> 32);
+    } else if (CB == 4) {
+        w4[k] = (uint32_t)v;
     } else {
-        constexpr int PER = 4 / CB;                  // columns per 32-bit word
-        uint32_t word = 0, w4[4];
+        const uint32_t m = (1u << (8 * CB)) - 1;
+        w4[(k * CB) >> 2] |= ((uint32_t)v & m) << (8 * ((k * CB) & 3));
+    }
+}
+
+template <bool SMEM, int E>
+__device__ __forceinline__ uint64_t enc_col(const Enc &e, uint32_t f, uint32_t b, bool &bad) {
+    if (bytes_of(E) == 8) return enc_d8(e, f, b);
+    return enc_lo<E>(e, f, b, bad);
+}
+
+// Full group: 64 columns.  Forward states B_0..B_31 and backward states
+// B̂_32..B̂_63 go to this thread's column of sF / sB (stride blockDim), then
+// the two builders continue past the midpoint and merge.
+template <bool SMEM, int E, typename St>
+__device__ __forceinline__ void group_full(const Params &p, const Tabs &T, const Enc &e, uint64_t g, bool &bad,
+                                           St *sF, St *sB) {
+    constexpr uint32_t BD = kBlockThreads;                     // compile-time stride: immediate offsets
+    const uint64_t pos = g * 64;
+    // byte classes of the group's 64 bytes, four 8-bit codes per register
+    uint32_t cw[16];
 #pragma unroll
-        for (int u = 63; u >= 0; --u) {
-            b = bnext<SMEM>(T, b, clsof<SMEM>(T, byte_of(xv[u >> 4], u & 15)));
-            uint32_t v = enc_lo<E>(e, fwd_at(u), b, bad);
-            if (CB < 4) v &= (1u << (8 * CB)) - 1;
-            word |= v << (8 * CB * (u % PER));
-            if (u % PER == 0) {
-                const int w = u / PER;               // word index within the group
-                w4[w & 3] = word;
-                word = 0;
-                if ((w & 3) == 0) reinterpret_cast<uint4 *>(gout)[w >> 2] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-            }
+    for (int q = 0; q < 4; ++q) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p.x + pos) + q);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            cw[4 * q + j] = clsof<SMEM>(T, w[j] & 0xFF) | (clsof<SMEM>(T, (w[j] >> 8) & 0xFF) << 8) |
+                            (clsof<SMEM>(T, (w[j] >> 16) & 0xFF) << 16) | (clsof<SMEM>(T, w[j] >> 24) << 24);
+    }
+    auto cls_at = [&](int u) -> uint32_t { return (cw[u >> 2] >> (8 * (u & 3))) & 0xFFu; };
+    uint32_t f = p.w.FC[g];
+    uint32_t b = p.w.BC[g];                                    // B̂_64
+    if (f == kUnknown || b == kUnknown) { bad = true; f = 0; b = 0; }   // never index with the sentinel
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        if (i > 0) f = fnext<SMEM>(T, f, cls_at(i - 1));      // B_i
+        sF[i * BD] = (St)f;
+        b = bnext<SMEM>(T, b, cls_at(63 - i));                // B̂_{63-i}
+        sB[(31 - i) * BD] = (St)b;
+        asm volatile("" ::: "memory");                        // keep shared-memory traffic in its step
+    }
+    constexpr int CB = bytes_of(E);
+    constexpr int CPV = 16 / CB;                               // columns per 16-byte vector
+    uint4 *gout = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(p.out) + pos * CB);
+    uint32_t wf[4] = {0, 0, 0, 0}, wb[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int i = 32; i < 64; ++i) {
+        f = fnext<SMEM>(T, f, cls_at(i - 1));                 // B_i
+        b = bnext<SMEM>(T, b, cls_at(63 - i));                // B̂_{63-i}
+        const uint64_t vf = enc_col<SMEM, E>(e, f, sB[(i - 32) * BD], bad);                          // column i
+        const uint64_t vb = enc_col<SMEM, E>(e, sF[(63 - i) * BD], b, bad);                          // column 63-i
+        put_col<CB>(wf, i % CPV, vf);
+        if (i % CPV == CPV - 1) {
+            gout[i / CPV] = make_uint4(wf[0], wf[1], wf[2], wf[3]);
+            wf[0] = wf[1] = wf[2] = wf[3] = 0;
         }
+        put_col<CB>(wb, (63 - i) % CPV, vb);
+        if ((63 - i) % CPV == 0) {
+            gout[(63 - i) / CPV] = make_uint4(wb[0], wb[1], wb[2], wb[3]);
+            wb[0] = wb[1] = wb[2] = wb[3] = 0;
+        }
+        asm volatile("" ::: "memory");
     }
 }
 
@@ -163,10 +272,13 @@ __device__ void group_tail(const Params &p, const Tabs &T, const Enc &e, uint64_
 }
 
 template <bool SMEM, int E>
-__global__ void __launch_bounds__(kBlockThreads, 2) merge_kernel(Params p) {
+__global__ void __launch_bounds__(kBlockThreads, 3) merge_kernel(Params p) {
+    using St = typename std::conditional<SMEM, uint16_t, uint32_t>::type;
     extern __shared__ __align__(16) uint8_t sm[];
     Tabs T;
     uint8_t *rest = stage_tables<SMEM>(p, sm, T);
+    St *stage = reinterpret_cast<St *>(rest);                 // [2][32][blockDim] half-group states
+    rest += (2 * 32 * kBlockThreads * sizeof(St) + 15) & ~(size_t)15;
     Enc e{};
     const DevTables &t = p.t;
     e.nbd1 = t.nbd + 1; e.nfd = t.nfd; e.nbd = t.nbd;
@@ -204,7 +316,8 @@ __global__ void __launch_bounds__(kBlockThreads, 2) merge_kernel(Params p) {
             for (uint32_t u = 0; u < ncol; ++u) store_col<E>(p.out, pos + u, 0);
             continue;
         }
-        if (g * 64 + 64 <= p.n) group_full<SMEM, E>(p, T, e, g, bad);
+        if (g * 64 + 64 <= p.n)
+            group_full<SMEM, E, St>(p, T, e, g, bad, stage + threadIdx.x, stage + 32 * kBlockThreads + threadIdx.x);
         else group_tail<SMEM, E>(p, T, e, g, bad);
     }
     if (bad) atomicExch(p.status, RE_E_INTERNAL);
@@ -281,9 +394,10 @@ void fixup_one(const Params &p, cudaStream_t s, int sm_count) {
 
 size_t merge_extra_smem(const Params &p) {
     const DevTables &t = p.t;
+    const size_t stage = (2 * 32 * kBlockThreads * (p.smem_tables ? 2 : 4) + 15) & ~(size_t)15;
     if (p.kind == RE_SLPF_DICT)
-        return p.pt_in_smem ? (size_t)(t.nfd + 1) * (t.nbd + 1) * p.col_bytes : 0;
-    return (size_t)(t.nf + t.nb) * 8;
+        return stage + (p.pt_in_smem ? (size_t)(t.nfd + 1) * (t.nbd + 1) * p.col_bytes : 0);
+    return stage + (size_t)(t.nf + t.nb) * 8;
 }
 
 void launch_fixup(const Params &p, cudaStream_t s, int sm_count) {

@@ -10,12 +10,17 @@
 // Chunk 0 runs forward from I and chunk c-1 backward from F without
 // speculation (J_0 = I, Ĵ_{c+1} = F, Eq. joiner).
 //
-// Runs are compared at every 64-byte sub-chunk boundary.  Once all live runs
-// of a direction hold the same state they stay equal, so from there on the
-// common state is the exact state of the text for any live input: the thread
-// writes it as a checkpoint (FC / BC), keeps one run and remembers which slots
-// were live.  Outputs: end state per slot (R, R̂), checkpoints, and the first
-// (forward) / last (backward) boundary where the runs agreed.
+// Runs are kept distinct: at every 64-byte sub-chunk boundary dead runs are
+// dropped and runs in equal states are merged (equal states stay equal), each
+// run carrying the set of slots it stands for.  While several runs are live
+// the thread records, per boundary, the (state, slot set) of each run; the
+// fix-up later turns a record into the exact state by the union of Eq. joiner
+// over the slots its input enters.  Once one run is left its state is exact
+// for any input that enters a live slot, and the thread writes it as a
+// checkpoint (FC / BC).  At the end it writes the end state of every slot
+// (R, R̂) and the first (forward) / last (backward) boundary where a single
+// run was left.  Active runs drop fast after a few bytes (Sect. 4.3), so
+// most of every chunk runs with one run per direction.
 #include "kernels.cuh"
 
 namespace slpf {
@@ -57,26 +62,47 @@ __device__ __forceinline__ void walk_block(const Params &p, const Tabs &T, uint6
     }
 }
 
-// If all live runs agree, keep one run and record the live slots.
+// Drop dead runs and merge runs in equal states (their slot sets are joined).
+// All indexing is static so the run arrays stay in registers.
 template <int MS>
-__device__ __forceinline__ bool try_converge(uint32_t (&s)[MS], uint32_t &m, uint32_t (&live)[(MS + 31) / 32]) {
-    uint32_t rep = 0;
-    bool same = true;
+__device__ __forceinline__ void compact(uint32_t (&s)[MS], uint32_t (&mk)[MS], uint32_t &m) {
+    uint32_t ns[MS], nk[MS];
+    uint32_t cnt = 0;
 #pragma unroll
-    for (int j = 0; j < MS; ++j)
+    for (int j = 0; j < MS; ++j) { ns[j] = 0; nk[j] = 0; }
+#pragma unroll
+    for (int j = 0; j < MS; ++j) {
         if (j < (int)m && s[j]) {
-            if (!rep) rep = s[j];
-            else if (s[j] != rep) same = false;
-        }
-    if (!same) return false;
+            bool merged = false;
 #pragma unroll
-    for (int w = 0; w < (MS + 31) / 32; ++w) live[w] = 0;
+            for (int k = 0; k < j; ++k)
+                if (k < (int)cnt && ns[k] == s[j]) { nk[k] |= mk[j]; merged = true; }
+            if (!merged) {
+#pragma unroll
+                for (int k = 0; k <= j; ++k)
+                    if (k == (int)cnt) { ns[k] = s[j]; nk[k] = mk[j]; }
+                ++cnt;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < MS; ++j) { s[j] = ns[j]; mk[j] = nk[j]; }
+    m = cnt;
+}
+
+// Record the runs at one boundary (while more than one run is live).
+template <int MS>
+__device__ __forceinline__ void record(const Params &p, uint32_t *cnt_row, uint2 *ent_row, uint32_t &used,
+                                       uint32_t &nrec, bool &open, uint32_t slot, const uint32_t (&s)[MS],
+                                       const uint32_t (&mk)[MS], uint32_t m) {
+    if (!open) return;
+    if (slot >= kRecBounds || used + m > kRecEntries) { open = false; return; }
 #pragma unroll
     for (int j = 0; j < MS; ++j)
-        if (j < (int)m && s[j]) live[j >> 5] |= 1u << (j & 31);
-    s[0] = rep;
-    m = 1;
-    return true;
+        if (j < (int)m) ent_row[used + j] = make_uint2(s[j], mk[j]);
+    used += m;
+    cnt_row[slot] = m;
+    nrec = slot + 1;
 }
 
 template <bool SMEM, int MS>
@@ -86,48 +112,49 @@ __device__ void reach_chunk(const Params &p, const Tabs &T, uint32_t i) {
     const uint32_t len = chunk_len(p, i);
     const uint32_t nsub = (len + 63) / 64;
     const bool bwd = !p.recognize;
-    uint32_t sf[MS], sb[MS];
-    uint32_t livef[(MS + 31) / 32], liveb[(MS + 31) / 32];
+    uint32_t sf[MS], sb[MS], kf[MS], kb[MS];
 #pragma unroll
-    for (int j = 0; j < MS; ++j) { sf[j] = 0u; sb[j] = 0u; }
-    uint32_t mf, mf0, mb = 0, mb0 = 0;
+    for (int j = 0; j < MS; ++j) { sf[j] = 0u; sb[j] = 0u; kf[j] = 0u; kb[j] = 0u; }
+    uint32_t mf, mb = 0;
     int tstart, tlast = -1;
     if (i == 0) {
-        mf = 1; sf[0] = t.fI; tstart = 0;                  // J_0 = I
+        mf = 1; sf[0] = t.fI; kf[0] = 1; tstart = 0;      // J_0 = I
     } else {
         const uint32_t pr = clsof<SMEM>(T, __ldg(p.x + base - 1)) * t.ncls + clsof<SMEM>(T, __ldg(p.x + base));
         mf = __ldg(t.fSlotCount + pr);
 #pragma unroll
         for (int j = 0; j < MS; ++j)
-            if (j < (int)mf) sf[j] = __ldg(t.fSlotStart + pr * t.msf + j);
+            if (j < (int)mf) { sf[j] = __ldg(t.fSlotStart + pr * t.msf + j); kf[j] = 1u << j; }
         tstart = 1;                                        // slot states follow byte 0
     }
-    mf0 = mf;
     if (bwd) {
         if (i == p.c - 1) {
-            mb = 1; sb[0] = t.bF; tlast = (int)len - 1;    // Ĵ_{c+1} = F
+            mb = 1; sb[0] = t.bF; kb[0] = 1; tlast = (int)len - 1;   // Ĵ_{c+1} = F
         } else {
             const uint32_t pr = clsof<SMEM>(T, __ldg(p.x + base + len - 1)) * t.ncls +
                                 clsof<SMEM>(T, __ldg(p.x + base + len));
             mb = __ldg(t.bSlotCount + pr);
 #pragma unroll
             for (int j = 0; j < MS; ++j)
-                if (j < (int)mb) sb[j] = __ldg(t.bSlotStart + pr * t.msb + j);
+                if (j < (int)mb) { sb[j] = __ldg(t.bSlotStart + pr * t.msb + j); kb[j] = 1u << j; }
             tlast = (int)len - 2;                          // slot states precede the last byte
         }
-        mb0 = mb;
     }
-#pragma unroll
-    for (int w = 0; w < (MS + 31) / 32; ++w) { livef[w] = ~0u; liveb[w] = ~0u; }
-    bool fconv = false, bconv = false;
-    uint32_t fconv_sub = nsub, bconv_sub = 0;
-    if (mf <= 1) { fconv = true; fconv_sub = 1; }
-    if (mb <= 1) { bconv = true; bconv_sub = nsub - 1; }
+    bool fconv = mf <= 1, bconv = mb <= 1;
+    uint32_t fconv_sub = fconv ? 1 : nsub, bconv_sub = bconv ? nsub - 1 : 0;
+    uint32_t *fcnt = p.w.recFc + (size_t)i * kRecBounds, *bcnt = p.w.recBc + (size_t)i * kRecBounds;
+    uint2 *fent = p.w.recFe + (size_t)i * kRecEntries, *bent = p.w.recBe + (size_t)i * kRecEntries;
+    uint32_t fused = 0, bused = 0, fnrec = 0, bnrec = 0;
+    bool fopen = true, bopen = true;
 
     for (uint32_t blk = 0; blk < nsub; ++blk) {
         const uint32_t fb = blk, bb = nsub - 1 - blk;
         if (fb >= 1) {                                      // boundary before forward block fb
-            if (!fconv && try_converge<MS>(sf, mf, livef)) { fconv = true; fconv_sub = fb; }
+            if (!fconv) {
+                compact<MS>(sf, kf, mf);
+                if (mf <= 1) { fconv = true; fconv_sub = fb; }
+                else record<MS>(p, fcnt, fent, fused, fnrec, fopen, fb - 1, sf, kf, mf);
+            }
             p.w.FC[(uint64_t)i * p.S + fb] = fconv ? sf[0] : kUnknown;
         }
         const uint64_t fpos = base + 64ull * fb, bpos = base + 64ull * bb;
@@ -144,38 +171,36 @@ __device__ void reach_chunk(const Params &p, const Tabs &T, uint32_t i) {
             else walk_block<SMEM, MS, false, false>(p, T, fpos, bpos, sf, sb, mf, mb, bwd, 0, 64, 0, 63);
         }
         if (bwd && bb >= 1) {                               // boundary at the start of backward block bb
-            if (!bconv && try_converge<MS>(sb, mb, liveb)) { bconv = true; bconv_sub = bb; }
+            if (!bconv) {
+                compact<MS>(sb, kb, mb);
+                if (mb <= 1) { bconv = true; bconv_sub = bb; }
+                else record<MS>(p, bcnt, bent, bused, bnrec, bopen, nsub - 1 - bb, sb, kb, mb);
+            }
             p.w.BC[(uint64_t)i * p.S + bb - 1] = bconv ? sb[0] : kUnknown;
         }
     }
-    // end state of every original slot (a slot dead at convergence stays dead)
+    // end state of every slot: the state of the run standing for it (0 if none)
     const uint32_t msf = t.msf;
     for (uint32_t j = 0; j < msf; ++j) {
         uint32_t v = 0;
-        if (j < mf0) {
-            if (mf == 1 && mf0 > 1) v = ((livef[j >> 5] >> (j & 31)) & 1) ? sf[0] : 0u;
-            else {
 #pragma unroll
-                for (int jj = 0; jj < MS; ++jj) if (jj == (int)j) v = sf[jj];
-            }
-        }
+        for (int r = 0; r < MS; ++r)
+            if (r < (int)mf && ((kf[r] >> j) & 1)) v = sf[r];
         p.w.Rf[(size_t)i * msf + j] = v;
     }
     p.w.fconv[i] = fconv_sub;
+    p.w.fnrec[i] = fnrec;
     if (bwd) {
         const uint32_t msb = t.msb;
         for (uint32_t j = 0; j < msb; ++j) {
             uint32_t v = 0;
-            if (j < mb0) {
-                if (mb == 1 && mb0 > 1) v = ((liveb[j >> 5] >> (j & 31)) & 1) ? sb[0] : 0u;
-                else {
 #pragma unroll
-                    for (int jj = 0; jj < MS; ++jj) if (jj == (int)j) v = sb[jj];
-                }
-            }
+            for (int r = 0; r < MS; ++r)
+                if (r < (int)mb && ((kb[r] >> j) & 1)) v = sb[r];
             p.w.Rb[(size_t)i * msb + j] = v;
         }
         p.w.bconv[i] = bconv_sub;
+        p.w.bnrec[i] = bnrec;
     }
 }
 
@@ -198,8 +223,8 @@ void launch_one(const Params &p, cudaStream_t s, int sm_count) {
     }
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_kernel<SMEM, MS>, kBlockThreads, smem);
-    uint64_t want = (p.c + kBlockThreads - 1) / kBlockThreads;
-    uint64_t blocks = std::min<uint64_t>(want, (uint64_t)std::max(per_sm, 1) * sm_count);
+    const uint64_t want = (p.c + kBlockThreads - 1) / kBlockThreads;
+    const uint64_t blocks = std::min<uint64_t>(want, (uint64_t)std::max(per_sm, 1) * sm_count);
     reach_kernel<SMEM, MS><<<(uint32_t)std::max<uint64_t>(blocks, 1), kBlockThreads, smem, s>>>(p);
 }
 
