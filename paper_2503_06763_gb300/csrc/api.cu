@@ -27,6 +27,7 @@ re_status cuda_fail(cudaError_t e, const char *what) {
     } while (0)
 
 constexpr size_t kSmemTablesMax = 120 * 1024;   // both u16 transition tables + class map
+constexpr size_t kSmemPairMax = 48 * 1024;      // both two-byte tables + class map
 constexpr size_t kSmemMergeMax = 190 * 1024;    // plus the dictionary pair table
 
 int sm_count_of(int device) {
@@ -287,10 +288,12 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     p.col_bytes = cb; p.kind = kind; p.status = slpf->d_status;
     p.recognize = recognize ? 1u : 0u;
     const DevTables &t = h->dev;
-    const size_t tab = tables_smem_bytes(t);
-    p.smem_tables = (t.nf < 65536 && t.nb < 65536 && tab <= kSmemTablesMax) ? 1u : 0u;
-    p.pt_in_smem = (kind == RE_SLPF_DICT &&
-                    (p.smem_tables ? tab : 0) + (size_t)(t.nfd + 1) * (t.nbd + 1) * cb <= kSmemMergeMax) ? 1u : 0u;
+    const bool fit16 = t.nf < 65536 && t.nb < 65536;
+    if (fit16 && tables_smem_bytes(t, TM_PAIR) <= kSmemPairMax) p.tmode = TM_PAIR;
+    else if (fit16 && tables_smem_bytes(t, TM_SMEM) <= kSmemTablesMax) p.tmode = TM_SMEM;
+    else p.tmode = TM_GLOBAL;
+    const size_t tab = tables_smem_bytes(t, p.tmode);
+    p.pt_in_smem = (kind == RE_SLPF_DICT && tab + (size_t)(t.nfd + 1) * (t.nbd + 1) * cb <= kSmemMergeMax) ? 1u : 0u;
     auto mark = [&](int j) -> cudaError_t { return ev ? cudaEventRecord(ev[j], s) : cudaSuccess; };
     if (len == 0) {
         CUDA_TRY(mark(0), "event");

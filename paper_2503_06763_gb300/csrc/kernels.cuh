@@ -19,7 +19,8 @@
 namespace slpf {
 
 constexpr int kMaxW = 64;           // segments per column <= 4096
-constexpr uint32_t kBlockThreads = 256;
+constexpr uint32_t kBlockThreads = 256;     // build & merge
+constexpr uint32_t kChunkThreads = 128;     // reach and fix-up (one thread per chunk)
 constexpr uint32_t kRecBounds = 16;   // boundaries recorded per chunk and direction before runs meet
 constexpr uint32_t kRecEntries = 48;  // (state, slot set) entries recorded per chunk and direction
 
@@ -48,7 +49,7 @@ struct Params {
     uint32_t col_bytes, kind;       // output encoding (re_slpf_kind)
     int32_t *status;
     uint32_t recognize;             // forward reach + join only
-    uint32_t smem_tables;           // transition tables staged in shared memory (u16)
+    uint32_t tmode;                 // TM_GLOBAL / TM_SMEM / TM_PAIR (see Tabs)
     uint32_t pt_in_smem;            // dictionary pair table staged in shared memory
 };
 
@@ -79,65 +80,109 @@ __device__ __forceinline__ uint32_t byte_of(const uint4 &v, int u) {   // u in 0
 }
 
 // ---------------------------------------------------------------- tables
-// Transition tables, either staged in shared memory as u16 (SMEM) or read
-// from global memory as u32.  Row s, column = byte class.
+// Transition tables in one of three modes (template parameter TM):
+//   TM_GLOBAL: one-byte tables read from global memory (u32 states);
+//   TM_SMEM:   one-byte tables staged in shared memory as u16;
+//   TM_PAIR:   two-byte tables in shared memory, one 32-bit entry per
+//              (state, class pair): low half the state after the first byte
+//              consumed, high half after both (used when ncls^2 is small).
+// Row s, column = byte class (or class pair c1*ncls + c2 for the left and
+// right byte of the pair).  A forward pair consumes c1 then c2, a backward
+// pair c2 then c1.
+enum { TM_GLOBAL = 0, TM_SMEM = 1, TM_PAIR = 2 };
+
 struct Tabs {
     const uint8_t *cls;
     const uint16_t *f16, *b16;
     const uint32_t *f32, *b32;
-    uint32_t ncls;
+    const uint32_t *f2, *b2;
+    uint32_t ncls, nc2;
 };
 
-template <bool SMEM>
+template <int TM>
 __device__ __forceinline__ uint32_t fnext(const Tabs &T, uint32_t s, uint32_t c) {
-    if (SMEM) return T.f16[s * T.ncls + c];
+    if (TM == TM_SMEM) return T.f16[s * T.ncls + c];
+    if (TM == TM_PAIR) return T.f2[s * T.nc2 + c * T.ncls] & 0xFFFFu;
     return __ldg(T.f32 + (size_t)s * T.ncls + c);
 }
-template <bool SMEM>
+template <int TM>
 __device__ __forceinline__ uint32_t bnext(const Tabs &T, uint32_t s, uint32_t c) {
-    if (SMEM) return T.b16[s * T.ncls + c];
+    if (TM == TM_SMEM) return T.b16[s * T.ncls + c];
+    if (TM == TM_PAIR) return T.b2[s * T.nc2 + c] & 0xFFFFu;
     return __ldg(T.b32 + (size_t)s * T.ncls + c);
 }
-template <bool SMEM>
+__device__ __forceinline__ uint32_t fpair(const Tabs &T, uint32_t s, uint32_t cp) { return T.f2[s * T.nc2 + cp]; }
+__device__ __forceinline__ uint32_t bpair(const Tabs &T, uint32_t s, uint32_t cp) { return T.b2[s * T.nc2 + cp]; }
+
+template <int TM>
 __device__ __forceinline__ uint32_t clsof(const Tabs &T, uint32_t b) {
-    if (SMEM) return T.cls[b];
+    if (TM != TM_GLOBAL) return T.cls[b];
     return __ldg(T.cls + b);
 }
 
-// Bytes of shared memory used by stage_tables (tables only).
-__host__ __device__ inline size_t tables_smem_bytes(const DevTables &t) {
+// Bytes of shared memory used by stage_tables.
+__host__ __device__ inline size_t tables_smem_bytes(const DevTables &t, int tm) {
+    if (tm == TM_GLOBAL) return 0;
     size_t a = 256;
-    a += ((size_t)t.nf * t.ncls * 2 + 15) & ~(size_t)15;
-    a += ((size_t)t.nb * t.ncls * 2 + 15) & ~(size_t)15;
+    if (tm == TM_SMEM) {
+        a += ((size_t)t.nf * t.ncls * 2 + 15) & ~(size_t)15;
+        a += ((size_t)t.nb * t.ncls * 2 + 15) & ~(size_t)15;
+    } else {
+        a += (size_t)(t.nf + t.nb) * t.ncls * t.ncls * 4;
+        a = (a + 15) & ~(size_t)15;                  // keep the next area 16-byte aligned
+    }
     return a;
 }
 
-// Stage the byte-class map and both transition tables in shared memory
+// Stage the byte-class map and the transition tables in shared memory
 // (block-wide; ends with __syncthreads).  Returns the end of the used area.
-template <bool SMEM>
+template <int TM>
 __device__ uint8_t *stage_tables(const Params &p, uint8_t *sm, Tabs &T) {
     const DevTables &t = p.t;
     T.ncls = t.ncls;
+    T.nc2 = t.ncls * t.ncls;
     T.f32 = t.fT;
     T.b32 = t.bT;
-    if (!SMEM) {
+    T.f16 = T.b16 = nullptr;
+    T.f2 = T.b2 = nullptr;
+    if (TM == TM_GLOBAL) {
         T.cls = t.cls;
-        T.f16 = T.b16 = nullptr;
         return sm;
     }
     uint8_t *cls = sm;
-    uint16_t *f16 = reinterpret_cast<uint16_t *>(sm + 256);
-    size_t fsz = (size_t)t.nf * t.ncls;
-    uint16_t *b16 = reinterpret_cast<uint16_t *>(sm + 256 + ((fsz * 2 + 15) & ~(size_t)15));
-    size_t bsz = (size_t)t.nb * t.ncls;
     for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) cls[i] = __ldg(t.cls + i);
-    for (size_t i = threadIdx.x; i < fsz; i += blockDim.x) f16[i] = (uint16_t)__ldg(t.fT + i);
-    for (size_t i = threadIdx.x; i < bsz; i += blockDim.x) b16[i] = (uint16_t)__ldg(t.bT + i);
     T.cls = cls;
-    T.f16 = f16;
-    T.b16 = b16;
+    if (TM == TM_SMEM) {
+        uint16_t *f16 = reinterpret_cast<uint16_t *>(sm + 256);
+        const size_t fsz = (size_t)t.nf * t.ncls;
+        uint16_t *b16 = reinterpret_cast<uint16_t *>(sm + 256 + ((fsz * 2 + 15) & ~(size_t)15));
+        const size_t bsz = (size_t)t.nb * t.ncls;
+        for (size_t i = threadIdx.x; i < fsz; i += blockDim.x) f16[i] = (uint16_t)__ldg(t.fT + i);
+        for (size_t i = threadIdx.x; i < bsz; i += blockDim.x) b16[i] = (uint16_t)__ldg(t.bT + i);
+        T.f16 = f16;
+        T.b16 = b16;
+        __syncthreads();
+        return reinterpret_cast<uint8_t *>(b16) + ((bsz * 2 + 15) & ~(size_t)15);
+    }
+    const uint32_t nc = t.ncls, nc2 = nc * nc;
+    uint32_t *f2 = reinterpret_cast<uint32_t *>(sm + 256);
+    uint32_t *b2 = f2 + (size_t)t.nf * nc2;
+    for (size_t i = threadIdx.x; i < (size_t)t.nf * nc2; i += blockDim.x) {
+        const uint32_t s = (uint32_t)(i / nc2), r = (uint32_t)(i % nc2), c1 = r / nc, c2 = r % nc;
+        const uint32_t mid = __ldg(t.fT + (size_t)s * nc + c1);
+        f2[i] = mid | (__ldg(t.fT + (size_t)mid * nc + c2) << 16);
+    }
+    for (size_t i = threadIdx.x; i < (size_t)t.nb * nc2; i += blockDim.x) {
+        const uint32_t s = (uint32_t)(i / nc2), r = (uint32_t)(i % nc2), c1 = r / nc, c2 = r % nc;
+        const uint32_t mid = __ldg(t.bT + (size_t)s * nc + c2);
+        b2[i] = mid | (__ldg(t.bT + (size_t)mid * nc + c1) << 16);
+    }
+    T.f2 = f2;
+    T.b2 = b2;
     __syncthreads();
-    return reinterpret_cast<uint8_t *>(b16) + ((bsz * 2 + 15) & ~(size_t)15);
+    // end of the used area, rounded up to 16 bytes exactly as in tables_smem_bytes
+    const size_t used = (256 + (size_t)(t.nf + t.nb) * nc2 * 4 + 15) & ~(size_t)15;
+    return sm + used;
 }
 
 // ---------------------------------------------------------------- launchers

@@ -75,11 +75,11 @@ __device__ uint32_t hit_mask(const Params &p, bool fwd, uint32_t pr, uint32_t S)
     return H;
 }
 
-template <bool SMEM>
-__global__ void __launch_bounds__(kBlockThreads) fixup_kernel(Params p) {
+template <int TM>
+__global__ void __launch_bounds__(kChunkThreads) fixup_kernel(Params p) {
     extern __shared__ __align__(16) uint8_t sm[];
     Tabs T;
-    stage_tables<SMEM>(p, sm, T);
+    stage_tables<TM>(p, sm, T);
     if (*p.status != RE_OK) return;
     const DevTables &t = p.t;
     bool bad = false;
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kBlockThreads) fixup_kernel(Params p) {
         const uint32_t fcs = p.w.fconv[i];
         if (fcs > 1) {
             const uint32_t J = p.w.FJ[i];
-            const uint32_t pr = clsof<SMEM>(T, __ldg(p.x + base - 1)) * t.ncls + clsof<SMEM>(T, __ldg(p.x + base));
+            const uint32_t pr = clsof<TM>(T, __ldg(p.x + base - 1)) * t.ncls + clsof<TM>(T, __ldg(p.x + base));
             const uint32_t H = hit_mask(p, true, pr, J);
             const uint32_t nrec = p.w.fnrec[i];
             const uint32_t *cnt = p.w.recFc + (size_t)i * kRecBounds;
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kBlockThreads) fixup_kernel(Params p) {
                 p.w.FC[g0 + s] = exact;
             }
             for (uint32_t tt = 64 * (s - 1); s < fcs; ++tt) {       // walk the rest
-                exact = fnext<SMEM>(T, exact, clsof<SMEM>(T, __ldg(p.x + base + tt)));
+                exact = fnext<TM>(T, exact, clsof<TM>(T, __ldg(p.x + base + tt)));
                 if (((tt + 1) & 63) == 0) { p.w.FC[g0 + (tt + 1) / 64] = exact; ++s; }
             }
         }
@@ -117,8 +117,8 @@ __global__ void __launch_bounds__(kBlockThreads) fixup_kernel(Params p) {
             const uint32_t J = p.w.BJ[i + 1];
             uint32_t H = 0;
             if (i + 1 < p.c) {
-                const uint32_t pr = clsof<SMEM>(T, __ldg(p.x + base + len - 1)) * t.ncls +
-                                    clsof<SMEM>(T, __ldg(p.x + base + len));
+                const uint32_t pr = clsof<TM>(T, __ldg(p.x + base + len - 1)) * t.ncls +
+                                    clsof<TM>(T, __ldg(p.x + base + len));
                 H = hit_mask(p, false, pr, J);
             }
             const uint32_t nrec = p.w.bnrec[i];
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kBlockThreads) fixup_kernel(Params p) {
             if (bb > bcs) {                                           // walk the rest
                 int64_t tt = (r == 0) ? (int64_t)len - 1 : 64 * (int64_t)(bb + 1) - 1;
                 for (; bb > bcs; --tt) {
-                    exact = bnext<SMEM>(T, exact, clsof<SMEM>(T, __ldg(p.x + base + tt)));
+                    exact = bnext<TM>(T, exact, clsof<TM>(T, __ldg(p.x + base + tt)));
                     if ((tt & 63) == 0) { p.w.BC[g0 + tt / 64 - 1] = exact; --bb; }
                 }
             }
@@ -179,18 +179,18 @@ constexpr int bytes_of(int E) { return (E == ENC_X2) ? 2 : (E == ENC_X4) ? 4 : E
 // Put one column value into a 16-byte vector being assembled (slot k).
 template <int CB>
 __device__ __forceinline__ void put_col(uint32_t (&w4)[4], int k, uint64_t v) {
-    if (CB == 8) {
+    if constexpr (CB == 8) {
         w4[2 * k] = (uint32_t)v;
         w4[2 * k + 1] = (uint32_t)(v >> 32);
-    } else if (CB == 4) {
+    } else if constexpr (CB == 4) {
         w4[k] = (uint32_t)v;
     } else {
-        const uint32_t m = (1u << (8 * CB)) - 1;
+        constexpr uint32_t m = (1u << (8 * CB)) - 1;
         w4[(k * CB) >> 2] |= ((uint32_t)v & m) << (8 * ((k * CB) & 3));
     }
 }
 
-template <bool SMEM, int E>
+template <int TM, int E>
 __device__ __forceinline__ uint64_t enc_col(const Enc &e, uint32_t f, uint32_t b, bool &bad) {
     if (bytes_of(E) == 8) return enc_d8(e, f, b);
     return enc_lo<E>(e, f, b, bad);
@@ -199,7 +199,7 @@ __device__ __forceinline__ uint64_t enc_col(const Enc &e, uint32_t f, uint32_t b
 // Full group: 64 columns.  Forward states B_0..B_31 and backward states
 // B̂_32..B̂_63 go to this thread's column of sF / sB (stride blockDim), then
 // the two builders continue past the midpoint and merge.
-template <bool SMEM, int E, typename St>
+template <int TM, int E, typename St>
 __device__ __forceinline__ void group_full(const Params &p, const Tabs &T, const Enc &e, uint64_t g, bool &bad,
                                            St *sF, St *sB) {
     constexpr uint32_t BD = kBlockThreads;                     // compile-time stride: immediate offsets
@@ -212,8 +212,8 @@ __device__ __forceinline__ void group_full(const Params &p, const Tabs &T, const
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            cw[4 * q + j] = clsof<SMEM>(T, w[j] & 0xFF) | (clsof<SMEM>(T, (w[j] >> 8) & 0xFF) << 8) |
-                            (clsof<SMEM>(T, (w[j] >> 16) & 0xFF) << 16) | (clsof<SMEM>(T, w[j] >> 24) << 24);
+            cw[4 * q + j] = clsof<TM>(T, w[j] & 0xFF) | (clsof<TM>(T, (w[j] >> 8) & 0xFF) << 8) |
+                            (clsof<TM>(T, (w[j] >> 16) & 0xFF) << 16) | (clsof<TM>(T, w[j] >> 24) << 24);
     }
     auto cls_at = [&](int u) -> uint32_t { return (cw[u >> 2] >> (8 * (u & 3))) & 0xFFu; };
     uint32_t f = p.w.FC[g];
@@ -221,9 +221,9 @@ __device__ __forceinline__ void group_full(const Params &p, const Tabs &T, const
     if (f == kUnknown || b == kUnknown) { bad = true; f = 0; b = 0; }   // never index with the sentinel
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
-        if (i > 0) f = fnext<SMEM>(T, f, cls_at(i - 1));      // B_i
+        if (i > 0) f = fnext<TM>(T, f, cls_at(i - 1));      // B_i
         sF[i * BD] = (St)f;
-        b = bnext<SMEM>(T, b, cls_at(63 - i));                // B̂_{63-i}
+        b = bnext<TM>(T, b, cls_at(63 - i));                // B̂_{63-i}
         sB[(31 - i) * BD] = (St)b;
         asm volatile("" ::: "memory");                        // keep shared-memory traffic in its step
     }
@@ -233,10 +233,10 @@ __device__ __forceinline__ void group_full(const Params &p, const Tabs &T, const
     uint32_t wf[4] = {0, 0, 0, 0}, wb[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int i = 32; i < 64; ++i) {
-        f = fnext<SMEM>(T, f, cls_at(i - 1));                 // B_i
-        b = bnext<SMEM>(T, b, cls_at(63 - i));                // B̂_{63-i}
-        const uint64_t vf = enc_col<SMEM, E>(e, f, sB[(i - 32) * BD], bad);                          // column i
-        const uint64_t vb = enc_col<SMEM, E>(e, sF[(63 - i) * BD], b, bad);                          // column 63-i
+        f = fnext<TM>(T, f, cls_at(i - 1));                 // B_i
+        b = bnext<TM>(T, b, cls_at(63 - i));                // B̂_{63-i}
+        const uint64_t vf = enc_col<TM, E>(e, f, sB[(i - 32) * BD], bad);                          // column i
+        const uint64_t vb = enc_col<TM, E>(e, sF[(63 - i) * BD], b, bad);                          // column 63-i
         put_col<CB>(wf, i % CPV, vf);
         if (i % CPV == CPV - 1) {
             gout[i / CPV] = make_uint4(wf[0], wf[1], wf[2], wf[3]);
@@ -251,8 +251,77 @@ __device__ __forceinline__ void group_full(const Params &p, const Tabs &T, const
     }
 }
 
+// Full group with two-byte tables: pair j holds bytes 2j, 2j+1.  Forward:
+// B_{2j} -> (B_{2j+1}, B_{2j+2}); backward: B̂_{2j+2} -> (B̂_{2j+1}, B̂_{2j}).
+// Each stage word holds the two states of one pair.
+template <int E>
+__device__ __forceinline__ void group_full_pair(const Params &p, const Tabs &T, const Enc &e, uint64_t g, bool &bad,
+                                                uint32_t *sF, uint32_t *sB) {
+    constexpr uint32_t BD = kBlockThreads;
+    const uint64_t pos = g * 64;
+    uint32_t cp[32];                                           // class pair of every byte pair
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p.x + pos) + q);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            cp[8 * q + 2 * j] = clsof<TM_PAIR>(T, w[j] & 0xFF) * T.ncls + clsof<TM_PAIR>(T, (w[j] >> 8) & 0xFF);
+            cp[8 * q + 2 * j + 1] = clsof<TM_PAIR>(T, (w[j] >> 16) & 0xFF) * T.ncls + clsof<TM_PAIR>(T, w[j] >> 24);
+        }
+    }
+    uint32_t f = p.w.FC[g];                                    // B_0
+    uint32_t b = p.w.BC[g];                                    // B̂_64
+    if (f == kUnknown || b == kUnknown) { bad = true; f = 0; b = 0; }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const uint32_t ef = fpair(T, f, cp[i]);                // pair i: B_{2i+1}, B_{2i+2}
+        sF[i * BD] = f | (ef << 16);                           // B_{2i}, B_{2i+1}
+        f = ef >> 16;
+        const int jb = 31 - i;
+        const uint32_t eb = bpair(T, b, cp[jb]);               // pair jb: B̂_{2jb+1}, B̂_{2jb}
+        sB[i * BD] = (eb >> 16) | (eb << 16);                  // B̂_{2jb}, B̂_{2jb+1}
+        b = eb >> 16;
+        asm volatile("" ::: "memory");
+    }
+    constexpr int CB = bytes_of(E);
+    constexpr int CPV = 16 / CB;
+    uint4 *gout = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(p.out) + pos * CB);
+    uint32_t wf[4] = {0, 0, 0, 0}, wb[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int i = 16; i < 32; ++i) {
+        // forward pair i: columns 2i, 2i+1 (ascending) with B̂ from pair i's stage word
+        const uint32_t ef = fpair(T, f, cp[i]);
+        const uint32_t hb = sB[(31 - i) * BD];                 // stored at step 31-i: B̂_{2i} | B̂_{2i+1} << 16
+        const uint64_t v0 = enc_col<TM_PAIR, E>(e, f, hb & 0xFFFF, bad);
+        const uint64_t v1 = enc_col<TM_PAIR, E>(e, ef & 0xFFFF, hb >> 16, bad);
+        f = ef >> 16;
+        // backward pair jb = 31-i: columns 2jb+1, 2jb (descending) with B from pair jb's stage word
+        const int jb = 31 - i;
+        const uint32_t eb = bpair(T, b, cp[jb]);
+        const uint32_t hf = sF[jb * BD];                       // B_{2jb} | B_{2jb+1} << 16
+        const uint64_t u1 = enc_col<TM_PAIR, E>(e, hf >> 16, eb & 0xFFFF, bad);
+        const uint64_t u0 = enc_col<TM_PAIR, E>(e, hf & 0xFFFF, eb >> 16, bad);
+        b = eb >> 16;
+        const int c0 = 2 * i, d1 = 2 * jb + 1;
+        put_col<CB>(wf, c0 % CPV, v0);
+        put_col<CB>(wf, (c0 + 1) % CPV, v1);
+        if ((c0 + 1) % CPV == CPV - 1) {
+            gout[(c0 + 1) / CPV] = make_uint4(wf[0], wf[1], wf[2], wf[3]);
+            wf[0] = wf[1] = wf[2] = wf[3] = 0;
+        }
+        put_col<CB>(wb, d1 % CPV, u1);
+        put_col<CB>(wb, (d1 - 1) % CPV, u0);
+        if ((d1 - 1) % CPV == 0) {
+            gout[(d1 - 1) / CPV] = make_uint4(wb[0], wb[1], wb[2], wb[3]);
+            wb[0] = wb[1] = wb[2] = wb[3] = 0;
+        }
+        asm volatile("" ::: "memory");
+    }
+}
+
 // Last group (fewer than 64 columns or no byte after it): plain loops.
-template <bool SMEM, int E>
+template <int TM, int E>
 __device__ void group_tail(const Params &p, const Tabs &T, const Enc &e, uint64_t g, bool &bad) {
     const uint64_t pos = g * 64;
     const uint64_t nleft = p.n + 1 - pos;
@@ -261,24 +330,24 @@ __device__ void group_tail(const Params &p, const Tabs &T, const Enc &e, uint64_
     uint32_t f = p.w.FC[g], b = p.w.BC[g];
     if (f == kUnknown || b == kUnknown) { bad = true; f = 0; b = 0; }
     F[0] = f;
-    for (uint32_t u = 1; u < ncol; ++u) F[u] = fnext<SMEM>(T, F[u - 1], clsof<SMEM>(T, __ldg(p.x + pos + u - 1)));
-    if (pos + 64 <= p.n) b = bnext<SMEM>(T, b, clsof<SMEM>(T, __ldg(p.x + pos + 63)));
+    for (uint32_t u = 1; u < ncol; ++u) F[u] = fnext<TM>(T, F[u - 1], clsof<TM>(T, __ldg(p.x + pos + u - 1)));
+    if (pos + 64 <= p.n) b = bnext<TM>(T, b, clsof<TM>(T, __ldg(p.x + pos + 63)));
     B[ncol - 1] = b;
-    for (int u = (int)ncol - 2; u >= 0; --u) B[u] = bnext<SMEM>(T, B[u + 1], clsof<SMEM>(T, __ldg(p.x + pos + u)));
+    for (int u = (int)ncol - 2; u >= 0; --u) B[u] = bnext<TM>(T, B[u + 1], clsof<TM>(T, __ldg(p.x + pos + u)));
     for (uint32_t u = 0; u < ncol; ++u) {
         uint64_t v = bytes_of(E) == 8 ? enc_d8(e, F[u], B[u]) : (uint64_t)enc_lo<E>(e, F[u], B[u], bad);
         store_col<E>(p.out, pos + u, v);
     }
 }
 
-template <bool SMEM, int E>
+template <int TM, int E>
 __global__ void __launch_bounds__(kBlockThreads, 3) merge_kernel(Params p) {
-    using St = typename std::conditional<SMEM, uint16_t, uint32_t>::type;
+    using St = typename std::conditional<TM != TM_GLOBAL, uint16_t, uint32_t>::type;
     extern __shared__ __align__(16) uint8_t sm[];
     Tabs T;
-    uint8_t *rest = stage_tables<SMEM>(p, sm, T);
+    uint8_t *rest = stage_tables<TM>(p, sm, T);
     St *stage = reinterpret_cast<St *>(rest);                 // [2][32][blockDim] half-group states
-    rest += (2 * 32 * kBlockThreads * sizeof(St) + 15) & ~(size_t)15;
+    rest += (2 * 32 * kBlockThreads * (TM == TM_PAIR ? 2 : sizeof(St)) + 15) & ~(size_t)15;
     Enc e{};
     const DevTables &t = p.t;
     e.nbd1 = t.nbd + 1; e.nfd = t.nfd; e.nbd = t.nbd;
@@ -316,9 +385,15 @@ __global__ void __launch_bounds__(kBlockThreads, 3) merge_kernel(Params p) {
             for (uint32_t u = 0; u < ncol; ++u) store_col<E>(p.out, pos + u, 0);
             continue;
         }
-        if (g * 64 + 64 <= p.n)
-            group_full<SMEM, E, St>(p, T, e, g, bad, stage + threadIdx.x, stage + 32 * kBlockThreads + threadIdx.x);
-        else group_tail<SMEM, E>(p, T, e, g, bad);
+        if (g * 64 + 64 <= p.n) {
+            if constexpr (TM == TM_PAIR) {
+                uint32_t *st32 = reinterpret_cast<uint32_t *>(stage);
+                group_full_pair<E>(p, T, e, g, bad, st32 + threadIdx.x, st32 + 16 * kBlockThreads + threadIdx.x);
+            } else {
+                group_full<TM, E, St>(p, T, e, g, bad, stage + threadIdx.x, stage + 32 * kBlockThreads + threadIdx.x);
+            }
+        }
+        else group_tail<TM, E>(p, T, e, g, bad);
     }
     if (bad) atomicExch(p.status, RE_E_INTERNAL);
 }
@@ -346,68 +421,70 @@ __global__ void empty_text_kernel(Params p) {
 }
 
 template <typename K>
-int grid_for(K kernel, size_t smem, uint64_t items, int sm_count) {
+int grid_for(K kernel, size_t smem, uint64_t items, int sm_count, uint32_t threads) {
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlockThreads, smem);
-    const uint64_t want = (items + kBlockThreads - 1) / kBlockThreads;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    const uint64_t want = (items + threads - 1) / threads;
     return (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)std::max(per_sm, 1) * sm_count));
 }
 
-template <bool SMEM, int E>
+template <int TM, int E>
 void merge_one(const Params &p, cudaStream_t s, int sm_count) {
-    const size_t smem = (SMEM ? tables_smem_bytes(p.t) : 0) + merge_extra_smem(p);
+    const size_t smem = tables_smem_bytes(p.t, TM) + merge_extra_smem(p);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(merge_kernel<SMEM, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(merge_kernel<TM, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    merge_kernel<SMEM, E><<<grid_for(merge_kernel<SMEM, E>, smem, p.Gc, sm_count), kBlockThreads, smem, s>>>(p);
+    merge_kernel<TM, E><<<grid_for(merge_kernel<TM, E>, smem, p.Gc, sm_count, kBlockThreads), kBlockThreads, smem, s>>>(p);
 }
 
-template <bool SMEM>
+template <int TM>
 void merge_enc(const Params &p, cudaStream_t s, int sm_count) {
     if (p.kind == RE_SLPF_DICT) {
-        if (p.col_bytes == 2) merge_one<SMEM, ENC_X2>(p, s, sm_count);
-        else merge_one<SMEM, ENC_X4>(p, s, sm_count);
+        if (p.col_bytes == 2) merge_one<TM, ENC_X2>(p, s, sm_count);
+        else merge_one<TM, ENC_X4>(p, s, sm_count);
     } else {
         switch (p.col_bytes) {
-            case 1: merge_one<SMEM, ENC_D1>(p, s, sm_count); break;
-            case 2: merge_one<SMEM, ENC_D2>(p, s, sm_count); break;
-            case 4: merge_one<SMEM, ENC_D4>(p, s, sm_count); break;
-            default: merge_one<SMEM, ENC_D8>(p, s, sm_count); break;
+            case 1: merge_one<TM, ENC_D1>(p, s, sm_count); break;
+            case 2: merge_one<TM, ENC_D2>(p, s, sm_count); break;
+            case 4: merge_one<TM, ENC_D4>(p, s, sm_count); break;
+            default: merge_one<TM, ENC_D8>(p, s, sm_count); break;
         }
     }
 }
 
-template <bool SMEM>
+template <int TM>
 void fixup_one(const Params &p, cudaStream_t s, int sm_count) {
-    const size_t smem = SMEM ? tables_smem_bytes(p.t) : 0;
+    const size_t smem = tables_smem_bytes(p.t, TM);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(fixup_kernel<SMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(fixup_kernel<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    fixup_kernel<SMEM><<<grid_for(fixup_kernel<SMEM>, smem, p.c, sm_count), kBlockThreads, smem, s>>>(p);
+    fixup_kernel<TM><<<grid_for(fixup_kernel<TM>, smem, p.c, sm_count, kChunkThreads), kChunkThreads, smem, s>>>(p);
 }
 
 }  // namespace
 
 size_t merge_extra_smem(const Params &p) {
     const DevTables &t = p.t;
-    const size_t stage = (2 * 32 * kBlockThreads * (p.smem_tables ? 2 : 4) + 15) & ~(size_t)15;
+    const size_t stage = (2 * 32 * kBlockThreads * (p.tmode == TM_GLOBAL ? 4 : 2) + 15) & ~(size_t)15;
     if (p.kind == RE_SLPF_DICT)
         return stage + (p.pt_in_smem ? (size_t)(t.nfd + 1) * (t.nbd + 1) * p.col_bytes : 0);
     return stage + (size_t)(t.nf + t.nb) * 8;
 }
 
 void launch_fixup(const Params &p, cudaStream_t s, int sm_count) {
-    if (p.smem_tables) fixup_one<true>(p, s, sm_count);
-    else fixup_one<false>(p, s, sm_count);
+    if (p.tmode == TM_PAIR) fixup_one<TM_PAIR>(p, s, sm_count);
+    else if (p.tmode == TM_SMEM) fixup_one<TM_SMEM>(p, s, sm_count);
+    else fixup_one<TM_GLOBAL>(p, s, sm_count);
 }
 
 void launch_merge(const Params &p, cudaStream_t s, int sm_count) {
-    if (p.smem_tables) merge_enc<true>(p, s, sm_count);
-    else merge_enc<false>(p, s, sm_count);
+    if (p.tmode == TM_PAIR) merge_enc<TM_PAIR>(p, s, sm_count);
+    else if (p.tmode == TM_SMEM) merge_enc<TM_SMEM>(p, s, sm_count);
+    else merge_enc<TM_GLOBAL>(p, s, sm_count);
 }
 
 void launch_empty(const Params &p, cudaStream_t s) { empty_text_kernel<<<1, 1, 0, s>>>(p); }

@@ -26,7 +26,7 @@
 namespace slpf {
 namespace {
 
-template <bool SMEM, int MS, bool MULTI, bool EDGE>
+template <int TM, int MS, bool MULTI, bool EDGE>
 __device__ __forceinline__ void walk_block(const Params &p, const Tabs &T, uint64_t fpos, uint64_t bpos,
                                            uint32_t (&sf)[MS], uint32_t (&sb)[MS], uint32_t mf, uint32_t mb,
                                            bool bwd, int f_lo, int f_hi, int b_lo, int b_hi) {
@@ -35,29 +35,53 @@ __device__ __forceinline__ void walk_block(const Params &p, const Tabs &T, uint6
     for (int q = 0; q < 4; ++q) {
         const uint4 fx = load16(p.x, p.n, fpos + 16 * q);
         const uint4 bx = bwd ? load16(p.x, p.n, bpos + 16 * (3 - q)) : make_uint4(0, 0, 0, 0);
+        if (TM == TM_PAIR && !EDGE) {                 // two bytes per table lookup
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                const uint32_t cpf = clsof<TM>(T, byte_of(fx, 2 * v)) * T.ncls + clsof<TM>(T, byte_of(fx, 2 * v + 1));
+                if (MULTI) {
+#pragma unroll
+                    for (int j = 0; j < MS; ++j)
+                        if (j < (int)mf) sf[j] = fpair(T, sf[j], cpf) >> 16;
+                } else {
+                    sf[0] = fpair(T, sf[0], cpf) >> 16;
+                }
+                if (bwd) {
+                    const uint32_t cpb = clsof<TM>(T, byte_of(bx, 14 - 2 * v)) * T.ncls + clsof<TM>(T, byte_of(bx, 15 - 2 * v));
+                    if (MULTI) {
+#pragma unroll
+                        for (int j = 0; j < MS; ++j)
+                            if (j < (int)mb) sb[j] = bpair(T, sb[j], cpb) >> 16;
+                    } else {
+                        sb[0] = bpair(T, sb[0], cpb) >> 16;
+                    }
+                }
+            }
+        } else {
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
             const int tf = 16 * q + u, tb = 63 - tf;
             if (!EDGE || (tf >= f_lo && tf < f_hi)) {
-                const uint32_t c = clsof<SMEM>(T, byte_of(fx, u));
+                const uint32_t c = clsof<TM>(T, byte_of(fx, u));
                 if (MULTI) {
 #pragma unroll
                     for (int j = 0; j < MS; ++j)
-                        if (j < (int)mf) sf[j] = fnext<SMEM>(T, sf[j], c);
+                        if (j < (int)mf) sf[j] = fnext<TM>(T, sf[j], c);
                 } else {
-                    sf[0] = fnext<SMEM>(T, sf[0], c);
+                    sf[0] = fnext<TM>(T, sf[0], c);
                 }
             }
             if (bwd && (!EDGE || (tb >= b_lo && tb <= b_hi))) {
-                const uint32_t c = clsof<SMEM>(T, byte_of(bx, 15 - u));
+                const uint32_t c = clsof<TM>(T, byte_of(bx, 15 - u));
                 if (MULTI) {
 #pragma unroll
                     for (int j = 0; j < MS; ++j)
-                        if (j < (int)mb) sb[j] = bnext<SMEM>(T, sb[j], c);
+                        if (j < (int)mb) sb[j] = bnext<TM>(T, sb[j], c);
                 } else {
-                    sb[0] = bnext<SMEM>(T, sb[0], c);
+                    sb[0] = bnext<TM>(T, sb[0], c);
                 }
             }
+        }
         }
     }
 }
@@ -105,7 +129,7 @@ __device__ __forceinline__ void record(const Params &p, uint32_t *cnt_row, uint2
     nrec = slot + 1;
 }
 
-template <bool SMEM, int MS>
+template <int TM, int MS>
 __device__ void reach_chunk(const Params &p, const Tabs &T, uint32_t i) {
     const DevTables &t = p.t;
     const uint64_t base = (uint64_t)i * p.k;
@@ -120,7 +144,7 @@ __device__ void reach_chunk(const Params &p, const Tabs &T, uint32_t i) {
     if (i == 0) {
         mf = 1; sf[0] = t.fI; kf[0] = 1; tstart = 0;      // J_0 = I
     } else {
-        const uint32_t pr = clsof<SMEM>(T, __ldg(p.x + base - 1)) * t.ncls + clsof<SMEM>(T, __ldg(p.x + base));
+        const uint32_t pr = clsof<TM>(T, __ldg(p.x + base - 1)) * t.ncls + clsof<TM>(T, __ldg(p.x + base));
         mf = __ldg(t.fSlotCount + pr);
 #pragma unroll
         for (int j = 0; j < MS; ++j)
@@ -131,8 +155,8 @@ __device__ void reach_chunk(const Params &p, const Tabs &T, uint32_t i) {
         if (i == p.c - 1) {
             mb = 1; sb[0] = t.bF; kb[0] = 1; tlast = (int)len - 1;   // Ĵ_{c+1} = F
         } else {
-            const uint32_t pr = clsof<SMEM>(T, __ldg(p.x + base + len - 1)) * t.ncls +
-                                clsof<SMEM>(T, __ldg(p.x + base + len));
+            const uint32_t pr = clsof<TM>(T, __ldg(p.x + base + len - 1)) * t.ncls +
+                                clsof<TM>(T, __ldg(p.x + base + len));
             mb = __ldg(t.bSlotCount + pr);
 #pragma unroll
             for (int j = 0; j < MS; ++j)
@@ -164,11 +188,11 @@ __device__ void reach_chunk(const Params &p, const Tabs &T, uint32_t i) {
         const bool edge = f_lo != 0 || f_hi != 64 || (bwd && b_hi != 63);
         const bool multi = mf > 1 || mb > 1;
         if (edge) {
-            if (multi) walk_block<SMEM, MS, true, true>(p, T, fpos, bpos, sf, sb, mf, mb, bwd, f_lo, f_hi, 0, b_hi);
-            else walk_block<SMEM, MS, false, true>(p, T, fpos, bpos, sf, sb, mf, mb, bwd, f_lo, f_hi, 0, b_hi);
+            if (multi) walk_block<TM, MS, true, true>(p, T, fpos, bpos, sf, sb, mf, mb, bwd, f_lo, f_hi, 0, b_hi);
+            else walk_block<TM, MS, false, true>(p, T, fpos, bpos, sf, sb, mf, mb, bwd, f_lo, f_hi, 0, b_hi);
         } else {
-            if (multi) walk_block<SMEM, MS, true, false>(p, T, fpos, bpos, sf, sb, mf, mb, bwd, 0, 64, 0, 63);
-            else walk_block<SMEM, MS, false, false>(p, T, fpos, bpos, sf, sb, mf, mb, bwd, 0, 64, 0, 63);
+            if (multi) walk_block<TM, MS, true, false>(p, T, fpos, bpos, sf, sb, mf, mb, bwd, 0, 64, 0, 63);
+            else walk_block<TM, MS, false, false>(p, T, fpos, bpos, sf, sb, mf, mb, bwd, 0, 64, 0, 63);
         }
         if (bwd && bb >= 1) {                               // boundary at the start of backward block bb
             if (!bconv) {
@@ -204,37 +228,38 @@ __device__ void reach_chunk(const Params &p, const Tabs &T, uint32_t i) {
     }
 }
 
-template <bool SMEM, int MS>
-__global__ void __launch_bounds__(kBlockThreads) reach_kernel(Params p) {
+template <int TM, int MS>
+__global__ void __launch_bounds__(kChunkThreads) reach_kernel(Params p) {
     extern __shared__ __align__(16) uint8_t sm[];
     Tabs T;
-    stage_tables<SMEM>(p, sm, T);
+    stage_tables<TM>(p, sm, T);
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < p.c; i += stride) reach_chunk<SMEM, MS>(p, T, i);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < p.c; i += stride) reach_chunk<TM, MS>(p, T, i);
 }
 
-template <bool SMEM, int MS>
+template <int TM, int MS>
 void launch_one(const Params &p, cudaStream_t s, int sm_count) {
-    const size_t smem = SMEM ? tables_smem_bytes(p.t) : 0;
+    const size_t smem = tables_smem_bytes(p.t, TM);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(reach_kernel<SMEM, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(reach_kernel<TM, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_kernel<SMEM, MS>, kBlockThreads, smem);
-    const uint64_t want = (p.c + kBlockThreads - 1) / kBlockThreads;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_kernel<TM, MS>, kChunkThreads, smem);
+    const uint64_t want = (p.c + kChunkThreads - 1) / kChunkThreads;
     const uint64_t blocks = std::min<uint64_t>(want, (uint64_t)std::max(per_sm, 1) * sm_count);
-    reach_kernel<SMEM, MS><<<(uint32_t)std::max<uint64_t>(blocks, 1), kBlockThreads, smem, s>>>(p);
+    reach_kernel<TM, MS><<<(uint32_t)std::max<uint64_t>(blocks, 1), kChunkThreads, smem, s>>>(p);
 }
 
-template <bool SMEM>
+template <int TM>
 bool launch_ms(const Params &p, cudaStream_t s, uint32_t ms, int sm_count) {
-    if (SMEM && ms <= 2) launch_one<SMEM, 2>(p, s, sm_count);
-    else if (SMEM && ms <= 4) launch_one<SMEM, 4>(p, s, sm_count);
-    else if (ms <= 8) launch_one<SMEM, 8>(p, s, sm_count);
-    else if (SMEM && ms <= 16) launch_one<SMEM, 16>(p, s, sm_count);
-    else if (ms <= 32) launch_one<SMEM, 32>(p, s, sm_count);
+    constexpr bool FULL = TM != TM_GLOBAL;          // fewer instantiations for the rare global mode
+    if (FULL && ms <= 2) launch_one<TM, 2>(p, s, sm_count);
+    else if (FULL && ms <= 4) launch_one<TM, 4>(p, s, sm_count);
+    else if (ms <= 8) launch_one<TM, 8>(p, s, sm_count);
+    else if (FULL && ms <= 16) launch_one<TM, 16>(p, s, sm_count);
+    else if (ms <= 32) launch_one<TM, 32>(p, s, sm_count);
     else return false;
     return true;
 }
@@ -242,7 +267,9 @@ bool launch_ms(const Params &p, cudaStream_t s, uint32_t ms, int sm_count) {
 }  // namespace
 
 bool launch_reach(const Params &p, cudaStream_t s, uint32_t ms, int sm_count) {
-    return p.smem_tables ? launch_ms<true>(p, s, ms, sm_count) : launch_ms<false>(p, s, ms, sm_count);
+    if (p.tmode == TM_PAIR) return launch_ms<TM_PAIR>(p, s, ms, sm_count);
+    if (p.tmode == TM_SMEM) return launch_ms<TM_SMEM>(p, s, ms, sm_count);
+    return launch_ms<TM_GLOBAL>(p, s, ms, sm_count);
 }
 
 }  // namespace slpf
