@@ -1,6 +1,8 @@
 // C ABI of include/slpf_parser.h: compile (host tables -> one device
 // allocation), layout / workspace sizing, and the parse launcher that
 // enqueues reach -> join -> fix-up -> build & merge on the caller's stream.
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cstring>
 #include <string>
@@ -52,6 +54,36 @@ uint32_t choose_chunk(uint64_t n, int sms, const re_parse_opts *opts) {
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    }
+    return fn;
+}
+
+// Output viewed as rows of one 64-column group (64 * cb bytes), one box per
+// warp tile of 32 groups, swizzled to match the kernel's shared-memory tile.
+bool output_tensor_map(CUtensorMap &map, void *d_cols, uint32_t cb, uint64_t rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
+    if (!fn || rows == 0 || rows > 0xFFFFFFFFull || (cb != 1 && cb != 2)) return false;
+    const cuuint64_t dims[2] = {64ull * cb, rows};
+    const cuuint64_t strides[1] = {64ull * cb};
+    const cuuint32_t box[2] = {64u * cb, 32u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    const CUresult r = fn(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, d_cols, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, cb == 2 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
 
 constexpr int kArrays = 17;
 
@@ -289,10 +321,14 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     p.recognize = recognize ? 1u : 0u;
     const DevTables &t = h->dev;
     const bool fit16 = t.nf < 65536 && t.nb < 65536;
-    if (fit16 && tables_smem_bytes(t, TM_PAIR) <= kSmemPairMax) p.tmode = TM_PAIR;
+    if (fit16 && t.ncls <= 16 && tables_smem_bytes(t, TM_PAIR) <= kSmemPairMax) p.tmode = TM_PAIR;
     else if (fit16 && tables_smem_bytes(t, TM_SMEM) <= kSmemTablesMax) p.tmode = TM_SMEM;
     else p.tmode = TM_GLOBAL;
     const size_t tab = tables_smem_bytes(t, p.tmode);
+    p.Gfast = len / kSub;
+    alignas(64) CUtensorMap out_map;
+    std::memset(&out_map, 0, sizeof(out_map));
+    p.out_tma = (!recognize && output_tensor_map(out_map, slpf->d_cols, cb, p.Gfast)) ? 1u : 0u;
     p.pt_in_smem = (kind == RE_SLPF_DICT && tab + (size_t)(t.nfd + 1) * (t.nbd + 1) * cb <= kSmemMergeMax) ? 1u : 0u;
     auto mark = [&](int j) -> cudaError_t { return ev ? cudaEventRecord(ev[j], s) : cudaSuccess; };
     if (len == 0) {
@@ -324,7 +360,7 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     if (!recognize) {
         launch_fixup(p, s, sms);
         CUDA_TRY(mark(3), "event");
-        launch_merge(p, s, sms);
+        launch_merge(p, out_map, s, sms);
     } else {
         CUDA_TRY(mark(3), "event");
     }

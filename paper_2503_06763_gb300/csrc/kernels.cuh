@@ -12,6 +12,7 @@
 //                BC[g] = backward state B̂ at position min(64g+64, n).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "re_internal.h"
@@ -51,6 +52,8 @@ struct Params {
     uint32_t recognize;             // forward reach + join only
     uint32_t tmode;                 // TM_GLOBAL / TM_SMEM / TM_PAIR (see Tabs)
     uint32_t pt_in_smem;            // dictionary pair table staged in shared memory
+    uint32_t out_tma;               // full column groups leave through TMA tensor stores
+    uint64_t Gfast;                 // groups g with 64g + 64 <= n (computed on the fast path)
 };
 
 // ---------------------------------------------------------------- helpers
@@ -185,12 +188,29 @@ __device__ uint8_t *stage_tables(const Params &p, uint8_t *sm, Tabs &T) {
     return sm + used;
 }
 
+// ---------------------------------------------------------------- TMA (bulk async copies)
+__device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
+    return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+// Make this thread's generic-proxy shared-memory writes visible to the async proxy.
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// 2D tiled store shared -> global (box from the tensor map), coordinates {x, y}.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, uint32_t src, int32_t x, int32_t y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+                 :: "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(src) : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// The bulk groups of this thread have finished reading shared memory.
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// The bulk groups of this thread have completed.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // ---------------------------------------------------------------- launchers
 size_t merge_extra_smem(const Params &p);
 bool launch_reach(const Params &p, cudaStream_t s, uint32_t ms, int sm_count);
 void launch_join(const Params &p, cudaStream_t s);
 void launch_fixup(const Params &p, cudaStream_t s, int sm_count);
-void launch_merge(const Params &p, cudaStream_t s, int sm_count);
+void launch_merge(const Params &p, const CUtensorMap &out_map, cudaStream_t s, int sm_count);
 void launch_empty(const Params &p, cudaStream_t s);
 cudaError_t set_kernel_attributes();   // max dynamic shared memory, once per process
 

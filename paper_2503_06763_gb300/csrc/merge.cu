@@ -196,16 +196,34 @@ __device__ __forceinline__ uint64_t enc_col(const Enc &e, uint32_t f, uint32_t b
     return enc_lo<E>(e, f, b, bad);
 }
 
-// Full group: 64 columns.  Forward states B_0..B_31 and backward states
-// B̂_32..B̂_63 go to this thread's column of sF / sB (stride blockDim), then
-// the two builders continue past the midpoint and merge.
-template <int TM, int E, typename St>
+// Where a full group's 16-byte output vectors go: straight to global memory,
+// or into this lane's row of the warp's shared-memory tile, swizzled the way
+// the TMA tensor store reads it (SWIZZLE_128B for 128-byte rows, 64B for
+// 64-byte rows: 16-byte chunk j of row r sits at chunk j ^ f(r)).
+template <bool TMA, int CB>
+struct Sink {
+    uint4 *g;
+    uint8_t *row;
+    uint32_t lane;
+    __device__ __forceinline__ void put(int chunk, uint4 v) const {
+        if constexpr (TMA) {
+            const uint32_t sw = (CB == 2) ? ((uint32_t)chunk ^ (lane & 7)) : ((uint32_t)chunk ^ ((lane >> 1) & 3));
+            *reinterpret_cast<uint4 *>(row + (sw << 4)) = v;
+        } else {
+            g[chunk] = v;
+        }
+    }
+};
+
+// Full group (one-byte tables): forward states B_0..B_31 and backward states
+// B̂_32..B̂_63 go to this thread's column of sF / sB (stride kBlockThreads),
+// then the two builders continue past the midpoint and merge.
+template <int TM, int E, bool TMA, typename St>
 __device__ __forceinline__ void group_full(const Params &p, const Tabs &T, const Enc &e, uint64_t g, bool &bad,
-                                           St *sF, St *sB) {
+                                           St *sF, St *sB, const Sink<TMA, bytes_of(E)> &out) {
     constexpr uint32_t BD = kBlockThreads;                     // compile-time stride: immediate offsets
     const uint64_t pos = g * 64;
-    // byte classes of the group's 64 bytes, four 8-bit codes per register
-    uint32_t cw[16];
+    uint32_t cw[16];                                           // byte classes, four per register
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p.x + pos) + q);
@@ -221,30 +239,29 @@ __device__ __forceinline__ void group_full(const Params &p, const Tabs &T, const
     if (f == kUnknown || b == kUnknown) { bad = true; f = 0; b = 0; }   // never index with the sentinel
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
-        if (i > 0) f = fnext<TM>(T, f, cls_at(i - 1));      // B_i
+        if (i > 0) f = fnext<TM>(T, f, cls_at(i - 1));        // B_i
         sF[i * BD] = (St)f;
-        b = bnext<TM>(T, b, cls_at(63 - i));                // B̂_{63-i}
+        b = bnext<TM>(T, b, cls_at(63 - i));                  // B̂_{63-i}
         sB[(31 - i) * BD] = (St)b;
         asm volatile("" ::: "memory");                        // keep shared-memory traffic in its step
     }
     constexpr int CB = bytes_of(E);
     constexpr int CPV = 16 / CB;                               // columns per 16-byte vector
-    uint4 *gout = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(p.out) + pos * CB);
     uint32_t wf[4] = {0, 0, 0, 0}, wb[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int i = 32; i < 64; ++i) {
-        f = fnext<TM>(T, f, cls_at(i - 1));                 // B_i
-        b = bnext<TM>(T, b, cls_at(63 - i));                // B̂_{63-i}
-        const uint64_t vf = enc_col<TM, E>(e, f, sB[(i - 32) * BD], bad);                          // column i
-        const uint64_t vb = enc_col<TM, E>(e, sF[(63 - i) * BD], b, bad);                          // column 63-i
+        f = fnext<TM>(T, f, cls_at(i - 1));                   // B_i
+        b = bnext<TM>(T, b, cls_at(63 - i));                  // B̂_{63-i}
+        const uint64_t vf = enc_col<TM, E>(e, f, sB[(i - 32) * BD], bad);          // column i
+        const uint64_t vb = enc_col<TM, E>(e, sF[(63 - i) * BD], b, bad);          // column 63-i
         put_col<CB>(wf, i % CPV, vf);
         if (i % CPV == CPV - 1) {
-            gout[i / CPV] = make_uint4(wf[0], wf[1], wf[2], wf[3]);
+            out.put(i / CPV, make_uint4(wf[0], wf[1], wf[2], wf[3]));
             wf[0] = wf[1] = wf[2] = wf[3] = 0;
         }
         put_col<CB>(wb, (63 - i) % CPV, vb);
         if ((63 - i) % CPV == 0) {
-            gout[(63 - i) / CPV] = make_uint4(wb[0], wb[1], wb[2], wb[3]);
+            out.put((63 - i) / CPV, make_uint4(wb[0], wb[1], wb[2], wb[3]));
             wb[0] = wb[1] = wb[2] = wb[3] = 0;
         }
         asm volatile("" ::: "memory");
@@ -253,53 +270,57 @@ __device__ __forceinline__ void group_full(const Params &p, const Tabs &T, const
 
 // Full group with two-byte tables: pair j holds bytes 2j, 2j+1.  Forward:
 // B_{2j} -> (B_{2j+1}, B_{2j+2}); backward: B̂_{2j+2} -> (B̂_{2j+1}, B̂_{2j}).
-// Each stage word holds the two states of one pair.
-template <int E>
+// The first half of each direction stays in registers (two states per word).
+template <int E, bool TMA>
 __device__ __forceinline__ void group_full_pair(const Params &p, const Tabs &T, const Enc &e, uint64_t g, bool &bad,
-                                                uint32_t *sF, uint32_t *sB) {
-    constexpr uint32_t BD = kBlockThreads;
+                                                const Sink<TMA, bytes_of(E)> &out) {
     const uint64_t pos = g * 64;
-    uint32_t cp[32];                                           // class pair of every byte pair
+    uint32_t cpk[8];                                           // class pair of every byte pair, four per word
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p.x + pos) + q);
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        uint32_t lo = 0, hi = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            cp[8 * q + 2 * j] = clsof<TM_PAIR>(T, w[j] & 0xFF) * T.ncls + clsof<TM_PAIR>(T, (w[j] >> 8) & 0xFF);
-            cp[8 * q + 2 * j + 1] = clsof<TM_PAIR>(T, (w[j] >> 16) & 0xFF) * T.ncls + clsof<TM_PAIR>(T, w[j] >> 24);
+            const uint32_t c0 = clsof<TM_PAIR>(T, w[j] & 0xFF) * T.ncls + clsof<TM_PAIR>(T, (w[j] >> 8) & 0xFF);
+            const uint32_t c1 = clsof<TM_PAIR>(T, (w[j] >> 16) & 0xFF) * T.ncls + clsof<TM_PAIR>(T, w[j] >> 24);
+            const uint32_t two = c0 | (c1 << 8);
+            if (j < 2) lo |= two << (16 * j);
+            else hi |= two << (16 * (j - 2));
         }
+        cpk[2 * q] = lo;
+        cpk[2 * q + 1] = hi;
     }
+    auto cp_at = [&](int j) -> uint32_t { return (cpk[j >> 2] >> (8 * (j & 3))) & 0xFFu; };
     uint32_t f = p.w.FC[g];                                    // B_0
     uint32_t b = p.w.BC[g];                                    // B̂_64
     if (f == kUnknown || b == kUnknown) { bad = true; f = 0; b = 0; }
+    uint32_t sF[16], sB[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        const uint32_t ef = fpair(T, f, cp[i]);                // pair i: B_{2i+1}, B_{2i+2}
-        sF[i * BD] = f | (ef << 16);                           // B_{2i}, B_{2i+1}
+        const uint32_t ef = fpair(T, f, cp_at(i));             // pair i: B_{2i+1}, B_{2i+2}
+        sF[i] = f | (ef << 16);                                // B_{2i}, B_{2i+1}
         f = ef >> 16;
-        const int jb = 31 - i;
-        const uint32_t eb = bpair(T, b, cp[jb]);               // pair jb: B̂_{2jb+1}, B̂_{2jb}
-        sB[i * BD] = (eb >> 16) | (eb << 16);                  // B̂_{2jb}, B̂_{2jb+1}
+        const uint32_t eb = bpair(T, b, cp_at(31 - i));        // pair 31-i: B̂_{63-2i}, B̂_{62-2i}
+        sB[i] = (eb >> 16) | (eb << 16);                       // B̂_{62-2i}, B̂_{63-2i}
         b = eb >> 16;
-        asm volatile("" ::: "memory");
     }
     constexpr int CB = bytes_of(E);
     constexpr int CPV = 16 / CB;
-    uint4 *gout = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(p.out) + pos * CB);
     uint32_t wf[4] = {0, 0, 0, 0}, wb[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int i = 16; i < 32; ++i) {
-        // forward pair i: columns 2i, 2i+1 (ascending) with B̂ from pair i's stage word
-        const uint32_t ef = fpair(T, f, cp[i]);
-        const uint32_t hb = sB[(31 - i) * BD];                 // stored at step 31-i: B̂_{2i} | B̂_{2i+1} << 16
+        // forward pair i: columns 2i, 2i+1 (ascending); their B̂ were stored at step 31-i
+        const uint32_t ef = fpair(T, f, cp_at(i));
+        const uint32_t hb = sB[31 - i];
         const uint64_t v0 = enc_col<TM_PAIR, E>(e, f, hb & 0xFFFF, bad);
         const uint64_t v1 = enc_col<TM_PAIR, E>(e, ef & 0xFFFF, hb >> 16, bad);
         f = ef >> 16;
-        // backward pair jb = 31-i: columns 2jb+1, 2jb (descending) with B from pair jb's stage word
+        // backward pair jb = 31-i: columns 2jb+1, 2jb (descending); their B were stored at step jb
         const int jb = 31 - i;
-        const uint32_t eb = bpair(T, b, cp[jb]);
-        const uint32_t hf = sF[jb * BD];                       // B_{2jb} | B_{2jb+1} << 16
+        const uint32_t eb = bpair(T, b, cp_at(jb));
+        const uint32_t hf = sF[jb];
         const uint64_t u1 = enc_col<TM_PAIR, E>(e, hf >> 16, eb & 0xFFFF, bad);
         const uint64_t u0 = enc_col<TM_PAIR, E>(e, hf & 0xFFFF, eb >> 16, bad);
         b = eb >> 16;
@@ -307,16 +328,15 @@ __device__ __forceinline__ void group_full_pair(const Params &p, const Tabs &T, 
         put_col<CB>(wf, c0 % CPV, v0);
         put_col<CB>(wf, (c0 + 1) % CPV, v1);
         if ((c0 + 1) % CPV == CPV - 1) {
-            gout[(c0 + 1) / CPV] = make_uint4(wf[0], wf[1], wf[2], wf[3]);
+            out.put((c0 + 1) / CPV, make_uint4(wf[0], wf[1], wf[2], wf[3]));
             wf[0] = wf[1] = wf[2] = wf[3] = 0;
         }
         put_col<CB>(wb, d1 % CPV, u1);
         put_col<CB>(wb, (d1 - 1) % CPV, u0);
         if ((d1 - 1) % CPV == 0) {
-            gout[(d1 - 1) / CPV] = make_uint4(wb[0], wb[1], wb[2], wb[3]);
+            out.put((d1 - 1) / CPV, make_uint4(wb[0], wb[1], wb[2], wb[3]));
             wb[0] = wb[1] = wb[2] = wb[3] = 0;
         }
-        asm volatile("" ::: "memory");
     }
 }
 
@@ -335,19 +355,33 @@ __device__ void group_tail(const Params &p, const Tabs &T, const Enc &e, uint64_
     B[ncol - 1] = b;
     for (int u = (int)ncol - 2; u >= 0; --u) B[u] = bnext<TM>(T, B[u + 1], clsof<TM>(T, __ldg(p.x + pos + u)));
     for (uint32_t u = 0; u < ncol; ++u) {
-        uint64_t v = bytes_of(E) == 8 ? enc_d8(e, F[u], B[u]) : (uint64_t)enc_lo<E>(e, F[u], B[u], bad);
+        const uint64_t v = bytes_of(E) == 8 ? enc_d8(e, F[u], B[u]) : (uint64_t)enc_lo<E>(e, F[u], B[u], bad);
         store_col<E>(p.out, pos + u, v);
     }
 }
 
-template <int TM, int E>
-__global__ void __launch_bounds__(kBlockThreads, 3) merge_kernel(Params p) {
+// Persistent grid: each warp takes tiles of 32 consecutive column groups
+// (lane = group).  With TMA the warp's tile of outputs is written to shared
+// memory and stored with one tensor-store per tile.
+template <int TM, int E, bool TMA>
+__global__ void __launch_bounds__(kBlockThreads, 3)
+    merge_kernel(const __grid_constant__ Params p, const __grid_constant__ CUtensorMap out_map) {
     using St = typename std::conditional<TM != TM_GLOBAL, uint16_t, uint32_t>::type;
+    constexpr int CB = bytes_of(E);
+    constexpr uint32_t ROWB = 64 * CB;                        // output bytes of one group
+    constexpr uint32_t WPB = kBlockThreads / 32;
     extern __shared__ __align__(16) uint8_t sm[];
+    uint8_t *base = sm;
+    uint8_t *tiles = nullptr;
+    if constexpr (TMA) {                                      // warp tiles, 1024-byte aligned for the swizzle
+        const uint32_t a = smem_u32(sm);
+        tiles = sm + ((1024 - (a & 1023)) & 1023);
+        base = tiles + WPB * 32 * ROWB;
+    }
     Tabs T;
-    uint8_t *rest = stage_tables<TM>(p, sm, T);
-    St *stage = reinterpret_cast<St *>(rest);                 // [2][32][blockDim] half-group states
-    rest += (2 * 32 * kBlockThreads * (TM == TM_PAIR ? 2 : sizeof(St)) + 15) & ~(size_t)15;
+    uint8_t *rest = stage_tables<TM>(p, base, T);
+    St *stage = reinterpret_cast<St *>(rest);                 // [2][32][kBlockThreads] (one-byte tables)
+    if (TM != TM_PAIR) rest += (2 * 32 * kBlockThreads * sizeof(St) + 15) & ~(size_t)15;
     Enc e{};
     const DevTables &t = p.t;
     e.nbd1 = t.nbd + 1; e.nfd = t.nfd; e.nbd = t.nbd;
@@ -376,25 +410,48 @@ __global__ void __launch_bounds__(kBlockThreads, 3) merge_kernel(Params p) {
     __syncthreads();
     const bool ok = *p.status == RE_OK;
     bool bad = false;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < p.Gc; g += stride) {
-        if (!ok) {                                           // rejected text: every column is empty
-            const uint64_t pos = g * 64;
-            const uint64_t nleft = p.n + 1 - pos;
-    const uint32_t ncol = nleft < 64 ? (uint32_t)nleft : 64u;
-            for (uint32_t u = 0; u < ncol; ++u) store_col<E>(p.out, pos + u, 0);
-            continue;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint8_t *tile = TMA ? tiles + warp * 32 * ROWB : nullptr;
+    const uint64_t gw = (uint64_t)blockIdx.x * WPB + warp, nw = (uint64_t)gridDim.x * WPB;
+    for (uint64_t gb = gw * 32; gb < p.Gc; gb += nw * 32) {
+        const uint64_t g = gb + lane;
+        if (TMA && gb != gw * 32) {                           // previous tile read by its store?
+            if (lane == 0) bulk_wait_read_all();
+            __syncwarp();
         }
-        if (g * 64 + 64 <= p.n) {
-            if constexpr (TM == TM_PAIR) {
-                uint32_t *st32 = reinterpret_cast<uint32_t *>(stage);
-                group_full_pair<E>(p, T, e, g, bad, st32 + threadIdx.x, st32 + 16 * kBlockThreads + threadIdx.x);
+        Sink<TMA, CB> out{reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(p.out) + g * ROWB),
+                          TMA ? tile + lane * ROWB : nullptr, lane};
+        if (g < p.Gc) {
+            if (!ok) {                                        // rejected text: every column is empty
+                if (TMA && g < p.Gfast) {
+#pragma unroll
+                    for (int v = 0; v < (int)(ROWB / 16); ++v) out.put(v, make_uint4(0, 0, 0, 0));
+                } else {
+                    const uint64_t pos = g * 64;
+                    const uint64_t nleft = p.n + 1 - pos;
+                    const uint32_t ncol = nleft < 64 ? (uint32_t)nleft : 64u;
+                    for (uint32_t u = 0; u < ncol; ++u) store_col<E>(p.out, pos + u, 0);
+                }
+            } else if (g < p.Gfast) {
+                if constexpr (TM == TM_PAIR)
+                    group_full_pair<E, TMA>(p, T, e, g, bad, out);
+                else
+                    group_full<TM, E, TMA, St>(p, T, e, g, bad, stage + threadIdx.x,
+                                               stage + 32 * kBlockThreads + threadIdx.x, out);
             } else {
-                group_full<TM, E, St>(p, T, e, g, bad, stage + threadIdx.x, stage + 32 * kBlockThreads + threadIdx.x);
+                group_tail<TM, E>(p, T, e, g, bad);
             }
         }
-        else group_tail<TM, E>(p, T, e, g, bad);
+        if constexpr (TMA) {
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0 && gb < p.Gfast) {                  // rows past Gfast are clipped by the map
+                tma_store_2d(&out_map, smem_u32(tile), 0, (int32_t)gb);
+                bulk_commit();
+            }
+        }
     }
+    if (TMA && lane == 0) bulk_wait_all();
     if (bad) atomicExch(p.status, RE_E_INTERNAL);
 }
 
@@ -428,28 +485,38 @@ int grid_for(K kernel, size_t smem, uint64_t items, int sm_count, uint32_t threa
     return (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)std::max(per_sm, 1) * sm_count));
 }
 
-template <int TM, int E>
-void merge_one(const Params &p, cudaStream_t s, int sm_count) {
+template <int TM, int E, bool TMA>
+void merge_one(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
     const size_t smem = tables_smem_bytes(p.t, TM) + merge_extra_smem(p);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(merge_kernel<TM, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(merge_kernel<TM, E, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    merge_kernel<TM, E><<<grid_for(merge_kernel<TM, E>, smem, p.Gc, sm_count, kBlockThreads), kBlockThreads, smem, s>>>(p);
+    const int blocks = grid_for(merge_kernel<TM, E, TMA>, smem, p.Gc, sm_count, kBlockThreads);
+    merge_kernel<TM, E, TMA><<<blocks, kBlockThreads, smem, s>>>(p, map);
+}
+
+template <int TM, int E>
+void merge_tma(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
+    constexpr int CB = bytes_of(E);
+    if constexpr (CB <= 2) {
+        if (p.out_tma) { merge_one<TM, E, true>(p, map, s, sm_count); return; }
+    }
+    merge_one<TM, E, false>(p, map, s, sm_count);
 }
 
 template <int TM>
-void merge_enc(const Params &p, cudaStream_t s, int sm_count) {
+void merge_enc(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
     if (p.kind == RE_SLPF_DICT) {
-        if (p.col_bytes == 2) merge_one<TM, ENC_X2>(p, s, sm_count);
-        else merge_one<TM, ENC_X4>(p, s, sm_count);
+        if (p.col_bytes == 2) merge_tma<TM, ENC_X2>(p, map, s, sm_count);
+        else merge_tma<TM, ENC_X4>(p, map, s, sm_count);
     } else {
         switch (p.col_bytes) {
-            case 1: merge_one<TM, ENC_D1>(p, s, sm_count); break;
-            case 2: merge_one<TM, ENC_D2>(p, s, sm_count); break;
-            case 4: merge_one<TM, ENC_D4>(p, s, sm_count); break;
-            default: merge_one<TM, ENC_D8>(p, s, sm_count); break;
+            case 1: merge_tma<TM, ENC_D1>(p, map, s, sm_count); break;
+            case 2: merge_tma<TM, ENC_D2>(p, map, s, sm_count); break;
+            case 4: merge_tma<TM, ENC_D4>(p, map, s, sm_count); break;
+            default: merge_tma<TM, ENC_D8>(p, map, s, sm_count); break;
         }
     }
 }
@@ -469,10 +536,11 @@ void fixup_one(const Params &p, cudaStream_t s, int sm_count) {
 
 size_t merge_extra_smem(const Params &p) {
     const DevTables &t = p.t;
-    const size_t stage = (2 * 32 * kBlockThreads * (p.tmode == TM_GLOBAL ? 4 : 2) + 15) & ~(size_t)15;
-    if (p.kind == RE_SLPF_DICT)
-        return stage + (p.pt_in_smem ? (size_t)(t.nfd + 1) * (t.nbd + 1) * p.col_bytes : 0);
-    return stage + (size_t)(t.nf + t.nb) * 8;
+    size_t a = 0;
+    if (p.out_tma) a += 1024 + (size_t)(kBlockThreads / 32) * 32 * 64 * p.col_bytes;   // warp tiles + alignment
+    if (p.tmode != TM_PAIR) a += (2 * 32 * kBlockThreads * (p.tmode == TM_GLOBAL ? 4 : 2) + 15) & ~(size_t)15;
+    if (p.kind == RE_SLPF_DICT) return a + (p.pt_in_smem ? (size_t)(t.nfd + 1) * (t.nbd + 1) * p.col_bytes : 0);
+    return a + (size_t)(t.nf + t.nb) * 8;
 }
 
 void launch_fixup(const Params &p, cudaStream_t s, int sm_count) {
@@ -481,10 +549,10 @@ void launch_fixup(const Params &p, cudaStream_t s, int sm_count) {
     else fixup_one<TM_GLOBAL>(p, s, sm_count);
 }
 
-void launch_merge(const Params &p, cudaStream_t s, int sm_count) {
-    if (p.tmode == TM_PAIR) merge_enc<TM_PAIR>(p, s, sm_count);
-    else if (p.tmode == TM_SMEM) merge_enc<TM_SMEM>(p, s, sm_count);
-    else merge_enc<TM_GLOBAL>(p, s, sm_count);
+void launch_merge(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
+    if (p.tmode == TM_PAIR) merge_enc<TM_PAIR>(p, map, s, sm_count);
+    else if (p.tmode == TM_SMEM) merge_enc<TM_SMEM>(p, map, s, sm_count);
+    else merge_enc<TM_GLOBAL>(p, map, s, sm_count);
 }
 
 void launch_empty(const Params &p, cudaStream_t s) { empty_text_kernel<<<1, 1, 0, s>>>(p); }
