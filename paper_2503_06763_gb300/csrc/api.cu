@@ -85,7 +85,7 @@ bool output_tensor_map(CUtensorMap &map, void *d_cols, uint32_t cb, uint64_t row
     return r == CUDA_SUCCESS;
 }
 
-constexpr int kArrays = 17;
+constexpr int kArrays = 19;
 
 struct Layout {
     uint32_t k, c, S;
@@ -107,6 +107,7 @@ Layout layout_for(const re_handle *h, uint64_t n, uint32_t k) {
         (size_t)L.Gc * 4, (size_t)L.Gc * 4,               // FC, BC
         c * 4, c * 4, c * 4, c * 4,                       // fconv, bconv, fkind, bkind
         c * 4, c * 4,                                     // fnrec, bnrec
+        c * 4, c * 4,                                     // fhit, bhit
         c * kRecBounds * 4, c * kRecBounds * 4,           // recFc, recBc
         c * kRecEntries * 8, c * kRecEntries * 8,         // recFe, recBe
         FLAG_COUNT * 4};
@@ -345,9 +346,10 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     p.w.fconv = (uint32_t *)(w + L.off[6]); p.w.bconv = (uint32_t *)(w + L.off[7]);
     p.w.fkind = (uint32_t *)(w + L.off[8]); p.w.bkind = (uint32_t *)(w + L.off[9]);
     p.w.fnrec = (uint32_t *)(w + L.off[10]); p.w.bnrec = (uint32_t *)(w + L.off[11]);
-    p.w.recFc = (uint32_t *)(w + L.off[12]); p.w.recBc = (uint32_t *)(w + L.off[13]);
-    p.w.recFe = (uint2 *)(w + L.off[14]); p.w.recBe = (uint2 *)(w + L.off[15]);
-    p.w.flags = (int32_t *)(w + L.off[16]);
+    p.w.fhit = (uint32_t *)(w + L.off[12]); p.w.bhit = (uint32_t *)(w + L.off[13]);
+    p.w.recFc = (uint32_t *)(w + L.off[14]); p.w.recBc = (uint32_t *)(w + L.off[15]);
+    p.w.recFe = (uint2 *)(w + L.off[16]); p.w.recBe = (uint2 *)(w + L.off[17]);
+    p.w.flags = (int32_t *)(w + L.off[18]);
     CUDA_TRY(mark(0), "event");
     launch_flags_init(p, s);
     if (!launch_reach(p, s, std::max(t.msf, recognize ? 1u : t.msb), sms)) {

@@ -137,28 +137,33 @@ __global__ void join_chain_kernel(Params p) {
     if (bad) atomicExch(&p.w.flags[FLAG_INTERNAL], 1);
 }
 
-// Does input state S enter a live slot of chunk i?
-__device__ bool hits_live(const Params &p, bool fwd, uint32_t i, uint32_t S) {
+// Live slots of chunk i (their end state is not the empty set).
+__device__ uint32_t live_slots(const Params &p, bool fwd, uint32_t i, uint32_t pr) {
     const DevTables &t = p.t;
-    const uint32_t W = t.W;
-    const uint32_t pr = fwd ? pair_fwd(p, i) : pair_bwd(p, i);
     const uint32_t m = __ldg((fwd ? t.fSlotCount : t.bSlotCount) + pr);
     const uint32_t ms = fwd ? t.msf : t.msb;
     const uint32_t *R = (fwd ? p.w.Rf : p.w.Rb) + (size_t)i * ms;
-    const uint64_t *mask = (fwd ? t.fSlotMask : t.bSlotMask) + (size_t)pr * ms * W;
-    const uint64_t *sb = (fwd ? t.fBits : t.bBits) + (size_t)S * W;
+    uint32_t L = 0;
     for (uint32_t s = 0; s < m; ++s)
-        if (R[s] && any_and(sb, mask + (size_t)s * W, W)) return true;
-    return false;
+        if (R[s]) L |= 1u << s;
+    return L;
 }
 
+// Check each chunk's guessed output against its (now known) input and keep
+// the slots that input enters for the fix-up.
 __global__ void join_verify_kernel(Params p) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= p.c) return;
     {   // forward: input FJ[i] -> output FJ[i+1]
         const uint32_t in = p.w.FJ[i], out = p.w.FJ[i + 1];
         bool fail = in == 0 || out == 0;
-        if (!fail && i > 0 && p.w.fkind[i] == 0) fail = !hits_live(p, true, i, in);
+        uint32_t H = 0;
+        if (i > 0 && in != 0) {
+            const uint32_t pr = pair_fwd(p, i);
+            H = slot_hits(p.t, true, pr, in);
+            if (!fail && p.w.fkind[i] == 0) fail = (H & live_slots(p, true, i, pr)) == 0;
+        }
+        p.w.fhit[i] = H;
         if (fail) atomicMin(&p.w.flags[FLAG_FFAIL], (int32_t)i);
         p.w.FC[(uint64_t)i * p.S] = in;                              // position i*k
         if (i == p.c - 1 && (p.n & 63) == 0) p.w.FC[p.n >> 6] = p.w.FJ[p.c];   // position n
@@ -167,7 +172,13 @@ __global__ void join_verify_kernel(Params p) {
     {   // backward: input BJ[i+1] -> output BJ[i]
         const uint32_t in = p.w.BJ[i + 1], out = p.w.BJ[i];
         bool fail = in == 0 || out == 0;
-        if (!fail && i < p.c - 1 && p.w.bkind[i] == 0) fail = !hits_live(p, false, i, in);
+        uint32_t H = 0;
+        if (i < p.c - 1 && in != 0) {
+            const uint32_t pr = pair_bwd(p, i);
+            H = slot_hits(p.t, false, pr, in);
+            if (!fail && p.w.bkind[i] == 0) fail = (H & live_slots(p, false, i, pr)) == 0;
+        }
+        p.w.bhit[i] = H;
         if (fail) atomicMin(&p.w.flags[FLAG_BFAIL], (int32_t)i);
         if (i + 1 < p.c) {
             p.w.BC[(uint64_t)(i + 1) * p.S - 1] = in;                // position (i+1)*k

@@ -34,6 +34,7 @@ struct Work {                       // device workspace, carved from the caller'
     uint32_t *fconv, *bconv;        // [c] first / last sub-chunk boundary the reach runs agree on
     uint32_t *fkind, *bkind;        // [c] 0: every live slot ends in one state, 1: several
     uint32_t *fnrec, *bnrec;        // [c] boundaries recorded (from the chunk's start / end)
+    uint32_t *fhit, *bhit;          // [c] slots the exact input state J_{i-1} / Ĵ_{i+1} enters
     uint32_t *recFc, *recBc;        // [c][kRecBounds] runs recorded at each boundary
     uint2 *recFe, *recBe;           // [c][kRecEntries] (state, slot set) of those runs
     int32_t *flags;                 // [FLAG_COUNT]
@@ -66,6 +67,19 @@ __device__ __forceinline__ bool any_and(const uint64_t *a, const uint64_t *b, ui
     for (uint32_t w = 0; w < W; ++w)
         if (__ldg(a + w) & __ldg(b + w)) return true;
     return false;
+}
+
+// Slots of the class pair pr that input state S enters (bit j: slot j).
+__device__ __forceinline__ uint32_t slot_hits(const DevTables &t, bool fwd, uint32_t pr, uint32_t S) {
+    const uint32_t W = t.W;
+    const uint32_t m = __ldg((fwd ? t.fSlotCount : t.bSlotCount) + pr);
+    const uint32_t ms = fwd ? t.msf : t.msb;
+    const uint64_t *mask = (fwd ? t.fSlotMask : t.bSlotMask) + (size_t)pr * ms * W;
+    const uint64_t *sb = (fwd ? t.fBits : t.bBits) + (size_t)S * W;
+    uint32_t H = 0;
+    for (uint32_t j = 0; j < m; ++j)
+        if (any_and(sb, mask + (size_t)j * W, W)) H |= 1u << j;
+    return H;
 }
 
 // 16 text bytes from x[at..at+16); bytes at or past n read as 0.

@@ -61,79 +61,73 @@ __device__ uint32_t record_union(const Params &p, bool fwd, const uint2 *ent, ui
     return id;
 }
 
-// Slots of the chunk's boundary class pair that input state S enters.
-__device__ uint32_t hit_mask(const Params &p, bool fwd, uint32_t pr, uint32_t S) {
-    const DevTables &t = p.t;
-    const uint32_t W = t.W;
-    const uint32_t m = __ldg((fwd ? t.fSlotCount : t.bSlotCount) + pr);
-    const uint32_t ms = fwd ? t.msf : t.msb;
-    const uint64_t *mask = (fwd ? t.fSlotMask : t.bSlotMask) + (size_t)pr * ms * W;
-    const uint64_t *sb = (fwd ? t.fBits : t.bBits) + (size_t)S * W;
-    uint32_t H = 0;
-    for (uint32_t j = 0; j < m; ++j)
-        if (any_and(sb, mask + (size_t)j * W, W)) H |= 1u << j;
-    return H;
-}
-
+// One warp per chunk: lane r turns record r into the exact checkpoint; a
+// single lane walks the boundaries past the record, if any.
 template <int TM>
 __global__ void __launch_bounds__(kChunkThreads) fixup_kernel(Params p) {
     extern __shared__ __align__(16) uint8_t sm[];
     Tabs T;
     stage_tables<TM>(p, sm, T);
     if (*p.status != RE_OK) return;
-    const DevTables &t = p.t;
     bool bad = false;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < p.c; i += stride) {
-        const uint64_t base = (uint64_t)i * p.k;
-        const uint32_t len = chunk_len(p, i);
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t wpb = blockDim.x / 32;
+    const uint64_t nw = (uint64_t)gridDim.x * wpb;
+    for (uint64_t i = (uint64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < p.c; i += nw) {
+        const uint64_t base = i * p.k;
+        const uint32_t len = chunk_len(p, (uint32_t)i);
         const uint32_t nsub = (len + 63) / 64;
-        const uint64_t g0 = (uint64_t)i * p.S;
-        // forward: boundaries 1 .. fconv-1
+        const uint64_t g0 = i * p.S;
+        // ---- forward: boundaries 1 .. fconv-1; record r is boundary r+1
         const uint32_t fcs = p.w.fconv[i];
         if (fcs > 1) {
-            const uint32_t J = p.w.FJ[i];
-            const uint32_t pr = clsof<TM>(T, __ldg(p.x + base - 1)) * t.ncls + clsof<TM>(T, __ldg(p.x + base));
-            const uint32_t H = hit_mask(p, true, pr, J);
-            const uint32_t nrec = p.w.fnrec[i];
-            const uint32_t *cnt = p.w.recFc + (size_t)i * kRecBounds;
-            const uint2 *ent = p.w.recFe + (size_t)i * kRecEntries;
-            uint32_t exact = J, s = 1, off = 0;
-            for (; s < fcs && s - 1 < nrec; ++s) {
-                const uint32_t m = cnt[s - 1];
-                exact = record_union(p, true, ent + off, m, H, bad);
-                off += m;
-                p.w.FC[g0 + s] = exact;
+            const uint32_t nrec = p.w.fnrec[i], H = p.w.fhit[i];
+            const uint32_t cnt = lane < nrec ? p.w.recFc[i * kRecBounds + lane] : 0u;
+            uint32_t off = cnt;                                           // inclusive scan -> exclusive
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, off, d);
+                if ((int)lane >= d) off += v;
             }
-            for (uint32_t tt = 64 * (s - 1); s < fcs; ++tt) {       // walk the rest
-                exact = fnext<TM>(T, exact, clsof<TM>(T, __ldg(p.x + base + tt)));
-                if (((tt + 1) & 63) == 0) { p.w.FC[g0 + (tt + 1) / 64] = exact; ++s; }
+            off -= cnt;
+            uint32_t st = 0;
+            if (lane < nrec) {
+                st = record_union(p, true, p.w.recFe + i * kRecEntries + off, cnt, H, bad);
+                p.w.FC[g0 + lane + 1] = st;
+            }
+            const uint32_t from = __shfl_sync(0xFFFFFFFFu, st, nrec > 0 ? nrec - 1 : 0);
+            if (nrec + 1 <= fcs - 1 && lane == 0) {                      // walk the rest
+                uint32_t exact = nrec == 0 ? p.w.FJ[i] : from;
+                for (uint32_t tt = 64 * nrec, s = nrec + 1; s < fcs; ++tt) {
+                    exact = fnext<TM>(T, exact, clsof<TM>(T, __ldg(p.x + base + tt)));
+                    if (((tt + 1) & 63) == 0) { p.w.FC[g0 + (tt + 1) / 64] = exact; ++s; }
+                }
             }
         }
         if (p.recognize) continue;
-        // backward: boundaries nsub-1 down to bconv+1
+        // ---- backward: boundaries nsub-1 down to bconv+1; record r is boundary nsub-1-r
         const uint32_t bcs = p.w.bconv[i];
         if (nsub >= 2 && bcs + 1 <= nsub - 1) {
-            const uint32_t J = p.w.BJ[i + 1];
-            uint32_t H = 0;
-            if (i + 1 < p.c) {
-                const uint32_t pr = clsof<TM>(T, __ldg(p.x + base + len - 1)) * t.ncls +
-                                    clsof<TM>(T, __ldg(p.x + base + len));
-                H = hit_mask(p, false, pr, J);
+            const uint32_t nrec = p.w.bnrec[i], H = p.w.bhit[i];
+            const uint32_t cnt = lane < nrec ? p.w.recBc[i * kRecBounds + lane] : 0u;
+            uint32_t off = cnt;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, off, d);
+                if ((int)lane >= d) off += v;
             }
-            const uint32_t nrec = p.w.bnrec[i];
-            const uint32_t *cnt = p.w.recBc + (size_t)i * kRecBounds;
-            const uint2 *ent = p.w.recBe + (size_t)i * kRecEntries;
-            uint32_t exact = J, bb = nsub - 1, r = 0, off = 0;
-            for (; bb > bcs && r < nrec; --bb, ++r) {
-                const uint32_t m = cnt[r];
-                exact = record_union(p, false, ent + off, m, H, bad);
-                off += m;
-                p.w.BC[g0 + bb - 1] = exact;
+            off -= cnt;
+            uint32_t st = 0;
+            if (lane < nrec) {
+                st = record_union(p, false, p.w.recBe + i * kRecEntries + off, cnt, H, bad);
+                p.w.BC[g0 + (nsub - 1 - lane) - 1] = st;
             }
-            if (bb > bcs) {                                           // walk the rest
-                int64_t tt = (r == 0) ? (int64_t)len - 1 : 64 * (int64_t)(bb + 1) - 1;
-                for (; bb > bcs; --tt) {
+            const uint32_t from = __shfl_sync(0xFFFFFFFFu, st, nrec > 0 ? nrec - 1 : 0);
+            const uint32_t bb_first = nsub - 1 - nrec;                   // first boundary not recorded
+            if (bb_first > bcs && lane == 0) {                           // walk the rest
+                uint32_t exact = nrec == 0 ? p.w.BJ[i + 1] : from;
+                int64_t tt = nrec == 0 ? (int64_t)len - 1 : 64 * (int64_t)(bb_first + 1) - 1;
+                for (uint32_t bb = bb_first; bb > bcs; --tt) {
                     exact = bnext<TM>(T, exact, clsof<TM>(T, __ldg(p.x + base + tt)));
                     if ((tt & 63) == 0) { p.w.BC[g0 + tt / 64 - 1] = exact; --bb; }
                 }
@@ -529,7 +523,8 @@ void fixup_one(const Params &p, cudaStream_t s, int sm_count) {
         cudaFuncSetAttribute(fixup_kernel<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    fixup_kernel<TM><<<grid_for(fixup_kernel<TM>, smem, p.c, sm_count, kChunkThreads), kChunkThreads, smem, s>>>(p);
+    fixup_kernel<TM><<<grid_for(fixup_kernel<TM>, smem, (uint64_t)p.c * 32, sm_count, kChunkThreads), kChunkThreads,
+                       smem, s>>>(p);
 }
 
 }  // namespace
