@@ -70,6 +70,21 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
+// Text viewed as rows of full chunks (k bytes), one box = 32 chunks x 64
+// bytes, SWIZZLE_64B to match the reach kernel's tile reads.
+bool text_tensor_map(CUtensorMap &map, const uint8_t *d_text, uint32_t k, uint64_t rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
+    if (!fn || rows < 32 || rows > 0xFFFFFFFFull || (k % 64) != 0) return false;
+    const cuuint64_t dims[2] = {k, rows};
+    const cuuint64_t strides[1] = {k};
+    const cuuint32_t box[2] = {64u, 32u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    const CUresult r = fn(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(d_text), dims, strides, box,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 // Output viewed as rows of one 64-column group (64 * cb bytes), one box per
 // warp tile of 32 groups, swizzled to match the kernel's shared-memory tile.
 bool output_tensor_map(CUtensorMap &map, void *d_cols, uint32_t cb, uint64_t rows) {
@@ -192,6 +207,7 @@ re_status re_compile(const char *pattern, size_t len, const re_compile_opts *opt
     const size_t i_bSM = add(C.bSlotMask.data(), C.bSlotMask.size() * 8);
     const size_t i_bSC = add(C.bSlotCount.data(), C.bSlotCount.size() * 4);
     const size_t i_pt = add(C.pt.data(), C.pt.size() * 4);
+    const size_t i_f2 = add(C.f2.data(), C.f2.size() * 4), i_b2 = add(C.b2.data(), C.b2.size() * 4);
     DevTables &t = h->dev;
     t.fHashMask = C.fHashMask; t.bHashMask = C.bHashMask;
     t.ncls = C.ncls; t.W = C.W; t.ell = C.ell;
@@ -218,6 +234,8 @@ re_status re_compile(const char *pattern, size_t len, const re_compile_opts *opt
     t.bSlotStart = (const uint32_t *)(b + pc[i_bSS].off); t.bSlotMask = (const uint64_t *)(b + pc[i_bSM].off);
     t.bSlotCount = (const uint32_t *)(b + pc[i_bSC].off);
     t.pt = (const uint32_t *)(b + pc[i_pt].off);
+    t.f2 = C.f2.empty() ? nullptr : (const uint32_t *)(b + pc[i_f2].off);
+    t.b2 = C.b2.empty() ? nullptr : (const uint32_t *)(b + pc[i_b2].off);
     *out = h;
     return RE_OK;
 }
@@ -322,7 +340,7 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     p.recognize = recognize ? 1u : 0u;
     const DevTables &t = h->dev;
     const bool fit16 = t.nf < 65536 && t.nb < 65536;
-    if (fit16 && t.ncls <= 16 && tables_smem_bytes(t, TM_PAIR) <= kSmemPairMax) p.tmode = TM_PAIR;
+    if (t.f2 && t.b2 && tables_smem_bytes(t, TM_PAIR) <= kSmemPairMax) p.tmode = TM_PAIR;
     else if (fit16 && tables_smem_bytes(t, TM_SMEM) <= kSmemTablesMax) p.tmode = TM_SMEM;
     else p.tmode = TM_GLOBAL;
     const size_t tab = tables_smem_bytes(t, p.tmode);
@@ -330,6 +348,10 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     alignas(64) CUtensorMap out_map;
     std::memset(&out_map, 0, sizeof(out_map));
     p.out_tma = (!recognize && output_tensor_map(out_map, slpf->d_cols, cb, p.Gfast)) ? 1u : 0u;
+    alignas(64) CUtensorMap text_map;
+    std::memset(&text_map, 0, sizeof(text_map));
+    p.c_full = (uint32_t)(len / k);
+    p.text_tma = text_tensor_map(text_map, d_text, k, p.c_full) ? 1u : 0u;
     p.pt_in_smem = (kind == RE_SLPF_DICT && tab + (size_t)(t.nfd + 1) * (t.nbd + 1) * cb <= kSmemMergeMax) ? 1u : 0u;
     auto mark = [&](int j) -> cudaError_t { return ev ? cudaEventRecord(ev[j], s) : cudaSuccess; };
     if (len == 0) {
@@ -352,7 +374,7 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     p.w.flags = (int32_t *)(w + L.off[18]);
     CUDA_TRY(mark(0), "event");
     launch_flags_init(p, s);
-    if (!launch_reach(p, s, std::max(t.msf, recognize ? 1u : t.msb), sms)) {
+    if (!launch_reach(p, text_map, s, std::max(t.msf, recognize ? 1u : t.msb), sms)) {
         set_error("too many speculative starts");
         return RE_E_INTERNAL;
     }

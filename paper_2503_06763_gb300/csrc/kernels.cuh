@@ -54,6 +54,8 @@ struct Params {
     uint32_t tmode;                 // TM_GLOBAL / TM_SMEM / TM_PAIR (see Tabs)
     uint32_t pt_in_smem;            // dictionary pair table staged in shared memory
     uint32_t out_tma;               // full column groups leave through TMA tensor stores
+    uint32_t text_tma;              // reach reads full chunks through TMA tiles
+    uint32_t c_full;                // chunks of exactly k bytes (rows of the text tensor map)
     uint64_t Gfast;                 // groups g with 64g + 64 <= n (computed on the fast path)
 };
 
@@ -181,18 +183,20 @@ __device__ uint8_t *stage_tables(const Params &p, uint8_t *sm, Tabs &T) {
         __syncthreads();
         return reinterpret_cast<uint8_t *>(b16) + ((bsz * 2 + 15) & ~(size_t)15);
     }
-    const uint32_t nc = t.ncls, nc2 = nc * nc;
+    const uint32_t nc2 = t.ncls * t.ncls;
     uint32_t *f2 = reinterpret_cast<uint32_t *>(sm + 256);
     uint32_t *b2 = f2 + (size_t)t.nf * nc2;
-    for (size_t i = threadIdx.x; i < (size_t)t.nf * nc2; i += blockDim.x) {
-        const uint32_t s = (uint32_t)(i / nc2), r = (uint32_t)(i % nc2), c1 = r / nc, c2 = r % nc;
-        const uint32_t mid = __ldg(t.fT + (size_t)s * nc + c1);
-        f2[i] = mid | (__ldg(t.fT + (size_t)mid * nc + c2) << 16);
-    }
-    for (size_t i = threadIdx.x; i < (size_t)t.nb * nc2; i += blockDim.x) {
-        const uint32_t s = (uint32_t)(i / nc2), r = (uint32_t)(i % nc2), c1 = r / nc, c2 = r % nc;
-        const uint32_t mid = __ldg(t.bT + (size_t)s * nc + c2);
-        b2[i] = mid | (__ldg(t.bT + (size_t)mid * nc + c1) << 16);
+    // copy the two-byte tables built at compile time (16-byte vectors where possible)
+    const size_t nwords = (size_t)(t.nf + t.nb) * nc2;
+    const bool contiguous = t.b2 == t.f2 + (size_t)t.nf * nc2;
+    if (contiguous && ((reinterpret_cast<uintptr_t>(t.f2) & 15) == 0)) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(t.f2);
+        uint4 *dst = reinterpret_cast<uint4 *>(f2);
+        for (size_t i = threadIdx.x; i < nwords / 4; i += blockDim.x) dst[i] = __ldg(src + i);
+        for (size_t i = (nwords / 4) * 4 + threadIdx.x; i < nwords; i += blockDim.x) f2[i] = __ldg(t.f2 + i);
+    } else {
+        for (size_t i = threadIdx.x; i < (size_t)t.nf * nc2; i += blockDim.x) f2[i] = __ldg(t.f2 + i);
+        for (size_t i = threadIdx.x; i < (size_t)t.nb * nc2; i += blockDim.x) b2[i] = __ldg(t.b2 + i);
     }
     T.f2 = f2;
     T.b2 = b2;
@@ -214,6 +218,28 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, uint32_t sr
                  :: "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(src) : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// 2D tiled load global -> shared, completion counted on an mbarrier (bytes).
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int32_t x, int32_t y, uint32_t bar) {
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                 :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+}
+// One bounded wait on phase parity `ph`: true once that phase has completed.
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t ph) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(bar), "r"(ph) : "memory");
+    return ok != 0;
+}
+constexpr uint32_t kWaitLimit = 1u << 22;   // try_wait rounds before a wait is declared lost
 // The bulk groups of this thread have finished reading shared memory.
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 // The bulk groups of this thread have completed.
@@ -221,7 +247,7 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 
 // ---------------------------------------------------------------- launchers
 size_t merge_extra_smem(const Params &p);
-bool launch_reach(const Params &p, cudaStream_t s, uint32_t ms, int sm_count);
+bool launch_reach(const Params &p, const CUtensorMap &text_map, cudaStream_t s, uint32_t ms, int sm_count);
 void launch_join(const Params &p, cudaStream_t s);
 void launch_fixup(const Params &p, cudaStream_t s, int sm_count);
 void launch_merge(const Params &p, const CUtensorMap &out_map, cudaStream_t s, int sm_count);

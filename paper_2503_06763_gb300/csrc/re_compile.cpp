@@ -699,6 +699,28 @@ re_status compile_pattern(const char *pattern, size_t len, const re_compile_opts
     }
 
     // ---- device probe tables
+    // ---- two-byte tables for small class alphabets: one lookup per byte pair.
+    // Forward entry (s, c1, c2): mid = δ(s, c1), end = δ(mid, c2); backward
+    // entry: mid = δ̂(s, c2), end = δ̂(mid, c1) (the right byte is read first).
+    C.f2.clear(); C.b2.clear();
+    if (ncls <= 16 && C.nf < 65536 && C.nb < 65536 &&
+        (uint64_t)(C.nf + C.nb) * ncls * ncls * 4 <= 48 * 1024) {
+        const uint32_t nc2 = ncls * ncls;
+        C.f2.resize((size_t)C.nf * nc2);
+        C.b2.resize((size_t)C.nb * nc2);
+        for (uint32_t st = 0; st < C.nf; ++st)
+            for (uint32_t c1 = 0; c1 < ncls; ++c1)
+                for (uint32_t c2 = 0; c2 < ncls; ++c2) {
+                    const uint32_t mid = C.fT[(size_t)st * ncls + c1];
+                    C.f2[(size_t)st * nc2 + c1 * ncls + c2] = mid | (C.fT[(size_t)mid * ncls + c2] << 16);
+                }
+        for (uint32_t st = 0; st < C.nb; ++st)
+            for (uint32_t c1 = 0; c1 < ncls; ++c1)
+                for (uint32_t c2 = 0; c2 < ncls; ++c2) {
+                    const uint32_t mid = C.bT[(size_t)st * ncls + c2];
+                    C.b2[(size_t)st * nc2 + c1 * ncls + c2] = mid | (C.bT[(size_t)mid * ncls + c1] << 16);
+                }
+    }
     C.fHash = build_device_hash(C.fBits, C.nf, W, C.fHashMask);
     C.bHash = build_device_hash(C.bBits, C.nb, W, C.bHashMask);
     return RE_OK;

@@ -47,6 +47,7 @@ struct DevTables {
     const uint64_t *bSlotMask;   // [ncls][ncls][msb][W] segments whose first symbol is a key
     const uint32_t *bSlotCount;  // [ncls][ncls]
     const uint32_t *pt;          // [(nfd+1)][(nbd+1)] dictionary index of B ∩ B̂ (DICT)
+    const uint32_t *f2, *b2;     // [n][ncls^2] two-byte tables (mid | end << 16), or null
     uint32_t fHashMask, bHashMask;
     uint32_t ncls, W, ell;
     uint32_t nf, nb, nfd, nbd;   // states incl. empty row 0; nfd/nbd = classic DFA states
@@ -62,6 +63,7 @@ struct Compiled {
     uint8_t cls[256];
     uint32_t nf = 0, nb = 0, nfd = 0, nbd = 0, msf = 0, msb = 0;
     std::vector<uint32_t> fT, bT;             // [n][ncls]
+    std::vector<uint32_t> f2, b2;             // [n][ncls^2] two-byte tables (empty when too large)
     std::vector<uint64_t> fBits, bBits;       // [n][W]
     std::vector<uint32_t> fHash, bHash;
     uint32_t fHashMask = 0, bHashMask = 0;

@@ -1,0 +1,17 @@
+// Reach kernels for the global table mode (see reach_impl.cuh).
+#include "reach_impl.cuh"
+
+namespace slpf {
+bool launch_reach_global(const Params &p, const CUtensorMap &map, cudaStream_t s, uint32_t ms, int sm_count) {
+    return reach::launch_ms<TM_GLOBAL>(p, map, s, ms, sm_count);
+}
+
+bool launch_reach_pair(const Params &p, const CUtensorMap &map, cudaStream_t s, uint32_t ms, int sm_count);
+bool launch_reach_smem(const Params &p, const CUtensorMap &map, cudaStream_t s, uint32_t ms, int sm_count);
+
+bool launch_reach(const Params &p, const CUtensorMap &map, cudaStream_t s, uint32_t ms, int sm_count) {
+    if (p.tmode == TM_PAIR) return launch_reach_pair(p, map, s, ms, sm_count);
+    if (p.tmode == TM_SMEM) return launch_reach_smem(p, map, s, ms, sm_count);
+    return launch_reach_global(p, map, s, ms, sm_count);
+}
+}  // namespace slpf

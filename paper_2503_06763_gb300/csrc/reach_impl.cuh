@@ -1,0 +1,371 @@
+// Reach phase, shared implementation included by reach_pair.cu, reach_smem.cu
+// and reach_global.cu (one translation unit per table mode).
+//
+// Reach phase (arXiv 2503.06763, Eq. reacher; Sect. 4.1 fuses the forward and
+// backward reacher of a chunk into one task, as here).
+//
+// One thread per chunk y_i runs, in the same loop, the forward ME-DFA from
+// every speculation slot of the chunk left to right and the reverse ME-DFA
+// from every backward slot right to left: two independent dependency chains.
+// Slots are the distinct start sets after the boundary byte (a run from a
+// singleton {q} reaches D_end(q) after one byte), restricted by the class of
+// the byte before the boundary (the last-character filter of Sect. 6).
+// Chunk 0 runs forward from I and chunk c-1 backward from F without
+// speculation (J_0 = I, Ĵ_{c+1} = F, Eq. joiner).
+//
+// Runs are kept distinct: at every 64-byte sub-chunk boundary dead runs are
+// dropped and runs in equal states are merged (equal states stay equal), each
+// run carrying the set of slots it stands for.  While several runs are live
+// the thread records, per boundary, the (state, slot set) of each run; the
+// fix-up later turns a record into the exact state by the union of Eq. joiner
+// over the slots its input enters.  Once one run is left its state is exact
+// for any input that enters a live slot, and the thread writes it as a
+// checkpoint (FC / BC).  At the end it writes the end state of every slot
+// (R, R̂) and the first (forward) / last (backward) boundary where a single
+// run was left.  Active runs drop fast after a few bytes (Sect. 4.3), so
+// most of every chunk runs with one run per direction.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace slpf {
+namespace reach {
+
+// One 64-byte block of both directions.  Runs j < wm (the warp's largest
+// run count, so the loop bound is warp-uniform) are stepped; a lane with
+// fewer runs steps empty states, which stay empty (row 0 of every table).
+// Bytes come from this lane's row of the warp's forward / backward tile
+// (64-byte rows, SWIZZLE_64B layout: 16-byte chunk q of row r sits at chunk
+// q ^ ((r >> 1) & 3)), filled by TMA or, for warps TMA cannot serve, by the
+// lanes themselves.
+template <int TM, int MS, bool EDGE>
+__device__ __forceinline__ void walk_block(const Params &p, const Tabs &T, const uint8_t *frow, const uint8_t *brow,
+                                           uint32_t (&sf)[MS], uint32_t (&sb)[MS], uint32_t wmf, uint32_t wmb,
+                                           bool bwd, int f_lo, int f_hi, int b_lo, int b_hi) {
+    const uint32_t swz = ((threadIdx.x & 31) >> 1) & 3;
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+        const uint4 fx = *reinterpret_cast<const uint4 *>(frow + (((uint32_t)q ^ swz) << 4));
+        const uint4 bx = bwd ? *reinterpret_cast<const uint4 *>(brow + (((uint32_t)(3 - q) ^ swz) << 4))
+                             : make_uint4(0, 0, 0, 0);
+        if (TM == TM_PAIR && !EDGE) {                 // two bytes per table lookup
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                const uint32_t cpf = clsof<TM>(T, byte_of(fx, 2 * v)) * T.ncls + clsof<TM>(T, byte_of(fx, 2 * v + 1));
+#pragma unroll
+                for (int j = 0; j < MS; ++j)
+                    if (j < (int)wmf) sf[j] = fpair(T, sf[j], cpf) >> 16;
+                if (bwd) {
+                    const uint32_t cpb = clsof<TM>(T, byte_of(bx, 14 - 2 * v)) * T.ncls + clsof<TM>(T, byte_of(bx, 15 - 2 * v));
+#pragma unroll
+                    for (int j = 0; j < MS; ++j)
+                        if (j < (int)wmb) sb[j] = bpair(T, sb[j], cpb) >> 16;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int tf = 16 * q + u, tb = 63 - tf;
+                if (!EDGE || (tf >= f_lo && tf < f_hi)) {
+                    const uint32_t c = clsof<TM>(T, byte_of(fx, u));
+#pragma unroll
+                    for (int j = 0; j < MS; ++j)
+                        if (j < (int)wmf) sf[j] = fnext<TM>(T, sf[j], c);
+                }
+                if (bwd && (!EDGE || (tb >= b_lo && tb <= b_hi))) {
+                    const uint32_t c = clsof<TM>(T, byte_of(bx, 15 - u));
+#pragma unroll
+                    for (int j = 0; j < MS; ++j)
+                        if (j < (int)wmb) sb[j] = bnext<TM>(T, sb[j], c);
+                }
+            }
+        }
+    }
+}
+
+// Per-warp ring of TMA tiles: kStages stages of a forward and a backward tile
+// (32 chunk rows x 64 bytes each) and one mbarrier per stage.
+constexpr int kStages = 3;
+constexpr uint32_t kTileBytes = 32 * 64;
+struct Ring {
+    uint8_t *tiles;       // [kStages][2][kTileBytes], 1024-byte aligned
+    uint32_t bars;        // shared address of kStages mbarriers
+    uint32_t phase;       // bit s: parity of the next completion of stage s
+};
+
+__device__ __forceinline__ void ring_issue(const Params &p, const CUtensorMap &map, const Ring &r, int s,
+                                           uint32_t i0, uint32_t fb, uint32_t bb, bool bwd) {
+    const uint32_t bar = r.bars + 8 * s;
+    mbar_expect_tx(bar, bwd ? 2 * kTileBytes : kTileBytes);
+    tma_load_2d(smem_u32(r.tiles + (2 * s) * kTileBytes), &map, 64 * fb, (int32_t)i0, bar);
+    if (bwd) tma_load_2d(smem_u32(r.tiles + (2 * s + 1) * kTileBytes), &map, 64 * bb, (int32_t)i0, bar);
+}
+
+// Fill this lane's rows of stage s with plain loads (warps TMA cannot serve:
+// the text's last, shorter chunk, or no tensor map).  Bytes past n read as 0.
+__device__ __forceinline__ void ring_fill_plain(const Params &p, const Ring &r, int s, uint64_t fpos, uint64_t bpos,
+                                                bool bwd) {
+    const uint32_t lane = threadIdx.x & 31, swz = (lane >> 1) & 3;
+    uint8_t *frow = r.tiles + (2 * s) * kTileBytes + lane * 64;
+    uint8_t *brow = r.tiles + (2 * s + 1) * kTileBytes + lane * 64;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        *reinterpret_cast<uint4 *>(frow + (((uint32_t)q ^ swz) << 4)) = load16(p.x, p.n, fpos + 16 * q);
+        if (bwd) *reinterpret_cast<uint4 *>(brow + (((uint32_t)q ^ swz) << 4)) = load16(p.x, p.n, bpos + 16 * q);
+    }
+}
+
+// Wait for stage s (every lane waits, so every lane acquires the tile data).
+__device__ __forceinline__ bool ring_wait(Ring &r, int s) {
+    const uint32_t bar = r.bars + 8 * s, ph = (r.phase >> s) & 1u;
+    bool ok = false;
+    for (uint32_t it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(bar, ph);
+    r.phase ^= 1u << s;
+    return __all_sync(0xFFFFFFFFu, ok);
+}
+
+// Drop dead runs and merge runs in equal states (their slot sets are joined).
+// All indexing is static so the run arrays stay in registers.
+template <int MS>
+__device__ __forceinline__ void compact(uint32_t (&s)[MS], uint32_t (&mk)[MS], uint32_t &m) {
+    uint32_t ns[MS], nk[MS];
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int j = 0; j < MS; ++j) { ns[j] = 0; nk[j] = 0; }
+#pragma unroll
+    for (int j = 0; j < MS; ++j) {
+        if (j < (int)m && s[j]) {
+            bool merged = false;
+#pragma unroll
+            for (int k = 0; k < j; ++k)
+                if (k < (int)cnt && ns[k] == s[j]) { nk[k] |= mk[j]; merged = true; }
+            if (!merged) {
+#pragma unroll
+                for (int k = 0; k <= j; ++k)
+                    if (k == (int)cnt) { ns[k] = s[j]; nk[k] = mk[j]; }
+                ++cnt;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < MS; ++j) { s[j] = ns[j]; mk[j] = nk[j]; }
+    m = cnt;
+}
+
+// Record the runs at one boundary (while more than one run is live).
+template <int MS>
+__device__ __forceinline__ void record(const Params &p, uint32_t *cnt_row, uint2 *ent_row, uint32_t &used,
+                                       uint32_t &nrec, bool &open, uint32_t slot, const uint32_t (&s)[MS],
+                                       const uint32_t (&mk)[MS], uint32_t m) {
+    if (!open) return;
+    if (slot >= kRecBounds || used + m > kRecEntries) { open = false; return; }
+#pragma unroll
+    for (int j = 0; j < MS; ++j)
+        if (j < (int)m) ent_row[used + j] = make_uint2(s[j], mk[j]);
+    used += m;
+    cnt_row[slot] = m;
+    nrec = slot + 1;
+}
+
+// Lanes of this warp that process block blk: chunk i = i0 + lane with
+// i0 = i - lane (chunks are consecutive across a warp).  Full chunks have
+// the same number of blocks; only the last chunk of the text may be shorter.
+__device__ __forceinline__ unsigned block_lanes(const Params &p, uint32_t i, uint32_t blk) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t i0 = i - lane;
+    const uint32_t last = p.c - 1;
+    unsigned mask = 0;
+    if (last > i0) {
+        const uint32_t full = last - i0;                  // lanes holding chunks i0 .. c-2
+        mask = full >= 32 ? 0xFFFFFFFFu : ((1u << full) - 1);
+    }
+    if (last - i0 < 32) {                                  // this warp holds the last chunk
+        const uint32_t nsub_last = (uint32_t)((p.n - (uint64_t)last * p.k + 63) / 64);
+        if (blk < nsub_last) mask |= 1u << (last - i0);
+    }
+    return mask;
+}
+
+template <int TM, int MS>
+__device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CUtensorMap &map, Ring &ring,
+                            bool tma) {
+    const DevTables &t = p.t;
+    const uint64_t base = (uint64_t)i * p.k;
+    const uint32_t len = chunk_len(p, i);
+    const uint32_t nsub = (len + 63) / 64;
+    const bool bwd = !p.recognize;
+    uint32_t sf[MS], sb[MS], kf[MS], kb[MS];
+#pragma unroll
+    for (int j = 0; j < MS; ++j) { sf[j] = 0u; sb[j] = 0u; kf[j] = 0u; kb[j] = 0u; }
+    uint32_t mf, mb = 0;
+    int tstart, tlast = -1;
+    if (i == 0) {
+        mf = 1; sf[0] = t.fI; kf[0] = 1; tstart = 0;      // J_0 = I
+    } else {
+        const uint32_t pr = clsof<TM>(T, __ldg(p.x + base - 1)) * t.ncls + clsof<TM>(T, __ldg(p.x + base));
+        mf = __ldg(t.fSlotCount + pr);
+#pragma unroll
+        for (int j = 0; j < MS; ++j)
+            if (j < (int)mf) { sf[j] = __ldg(t.fSlotStart + pr * t.msf + j); kf[j] = 1u << j; }
+        tstart = 1;                                        // slot states follow byte 0
+    }
+    if (bwd) {
+        if (i == p.c - 1) {
+            mb = 1; sb[0] = t.bF; kb[0] = 1; tlast = (int)len - 1;   // Ĵ_{c+1} = F
+        } else {
+            const uint32_t pr = clsof<TM>(T, __ldg(p.x + base + len - 1)) * t.ncls +
+                                clsof<TM>(T, __ldg(p.x + base + len));
+            mb = __ldg(t.bSlotCount + pr);
+#pragma unroll
+            for (int j = 0; j < MS; ++j)
+                if (j < (int)mb) { sb[j] = __ldg(t.bSlotStart + pr * t.msb + j); kb[j] = 1u << j; }
+            tlast = (int)len - 2;                          // slot states precede the last byte
+        }
+    }
+    bool fconv = mf <= 1, bconv = mb <= 1;
+    uint32_t fconv_sub = fconv ? 1 : nsub, bconv_sub = bconv ? nsub - 1 : 0;
+    uint32_t *fcnt = p.w.recFc + (size_t)i * kRecBounds, *bcnt = p.w.recBc + (size_t)i * kRecBounds;
+    uint2 *fent = p.w.recFe + (size_t)i * kRecEntries, *bent = p.w.recBe + (size_t)i * kRecEntries;
+    uint32_t fused = 0, bused = 0, fnrec = 0, bnrec = 0;
+    bool fopen = true, bopen = true;
+
+    const uint32_t lane = threadIdx.x & 31, i0 = i - lane;
+    if (tma && lane == 0)                                     // prologue: first stages in flight
+        for (uint32_t b = 0; b < (uint32_t)kStages && b < nsub; ++b) ring_issue(p, map, ring, b, i0, b, nsub - 1 - b, bwd);
+    for (uint32_t blk = 0; blk < nsub; ++blk) {
+        const uint32_t fb = blk, bb = nsub - 1 - blk;
+        const int stage = (int)(blk % kStages);
+        if (fb >= 1) {                                      // boundary before forward block fb
+            if (!fconv) {
+                compact<MS>(sf, kf, mf);
+                if (mf <= 1) { fconv = true; fconv_sub = fb; }
+                else record<MS>(p, fcnt, fent, fused, fnrec, fopen, fb - 1, sf, kf, mf);
+            }
+            p.w.FC[(uint64_t)i * p.S + fb] = fconv ? sf[0] : kUnknown;
+        }
+        const uint64_t fpos = base + 64ull * fb, bpos = base + 64ull * bb;
+        const int f_lo = fb == 0 ? tstart : 0;
+        const int f_hi = (int)min(64u, len - 64 * fb);
+        const int b_hi = min(63, tlast - (int)(64 * bb));
+        const bool edge = f_lo != 0 || f_hi != 64 || (bwd && b_hi != 63);
+        const unsigned act = block_lanes(p, i, blk);
+        const uint32_t wmf = __reduce_max_sync(act, mf), wmb = __reduce_max_sync(act, mb);
+        if (tma) {
+            if (!ring_wait(ring, stage)) return false;        // lost TMA completion: give up this chunk tile
+        } else {
+            ring_fill_plain(p, ring, stage, fpos, bpos, bwd);
+            __syncwarp(act);
+        }
+        const uint8_t *frow = ring.tiles + (2 * stage) * kTileBytes + lane * 64;
+        const uint8_t *brow = ring.tiles + (2 * stage + 1) * kTileBytes + lane * 64;
+        if (edge) walk_block<TM, MS, true>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, f_lo, f_hi, 0, b_hi);
+        else walk_block<TM, MS, false>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
+        if (tma) {
+            __syncwarp();                                     // every lane has read this stage
+            if (lane == 0 && blk + kStages < nsub)
+                ring_issue(p, map, ring, stage, i0, blk + kStages, nsub - 1 - (blk + kStages), bwd);
+        } else {
+            __syncwarp(act);                                  // stage read before the next fill
+        }
+        if (bwd && bb >= 1) {                               // boundary at the start of backward block bb
+            if (!bconv) {
+                compact<MS>(sb, kb, mb);
+                if (mb <= 1) { bconv = true; bconv_sub = bb; }
+                else record<MS>(p, bcnt, bent, bused, bnrec, bopen, nsub - 1 - bb, sb, kb, mb);
+            }
+            p.w.BC[(uint64_t)i * p.S + bb - 1] = bconv ? sb[0] : kUnknown;
+        }
+    }
+    // end state of every slot: the state of the run standing for it (0 if none)
+    const uint32_t msf = t.msf;
+    for (uint32_t j = 0; j < msf; ++j) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int r = 0; r < MS; ++r)
+            if (r < (int)mf && ((kf[r] >> j) & 1)) v = sf[r];
+        p.w.Rf[(size_t)i * msf + j] = v;
+    }
+    p.w.fconv[i] = fconv_sub;
+    p.w.fnrec[i] = fnrec;
+    if (bwd) {
+        const uint32_t msb = t.msb;
+        for (uint32_t j = 0; j < msb; ++j) {
+            uint32_t v = 0;
+#pragma unroll
+            for (int r = 0; r < MS; ++r)
+                if (r < (int)mb && ((kb[r] >> j) & 1)) v = sb[r];
+            p.w.Rb[(size_t)i * msb + j] = v;
+        }
+        p.w.bconv[i] = bconv_sub;
+        p.w.bnrec[i] = bnrec;
+    }
+    return true;
+}
+
+template <int TM, int MS>
+__global__ void __launch_bounds__(kChunkThreads)
+    reach_kernel(const __grid_constant__ Params p, const __grid_constant__ CUtensorMap map) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    Tabs T;
+    uint8_t *rest = stage_tables<TM>(p, sm, T);
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x / 32;
+    Ring ring{};
+    {
+        const uint32_t a = smem_u32(rest);
+        uint8_t *aligned = rest + ((1024 - (a & 1023)) & 1023);
+        ring.tiles = aligned + warp * (kStages * 2 * kTileBytes);
+        ring.bars = smem_u32(aligned + wpb * (kStages * 2 * kTileBytes)) + warp * kStages * 8;
+        ring.phase = 0;
+        if (p.text_tma && lane == 0) {
+            for (int st = 0; st < kStages; ++st) mbar_init(ring.bars + 8 * st, 1);
+            mbar_init_fence();
+        }
+        __syncwarp();
+    }
+    // warps take tiles of 32 consecutive chunks
+    const uint64_t nw = (uint64_t)gridDim.x * wpb;
+    for (uint64_t t = (uint64_t)blockIdx.x * wpb + warp; t * 32 < p.c; t += nw) {
+        const uint32_t i = (uint32_t)(t * 32) + lane;
+        const bool tma = p.text_tma && t * 32 + 32 <= p.c_full;
+        if (i >= p.c) continue;                               // lanes past the text (plain path only)
+        if (!reach_chunk<TM, MS>(p, T, i, map, ring, tma)) {
+            atomicExch(p.status, RE_E_INTERNAL);
+            atomicExch(&p.w.flags[FLAG_INTERNAL], 1);
+            for (int st = 0; st < kStages; ++st) {            // drain: bounded wait on every stage
+                bool ok = false;
+                for (uint32_t it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(ring.bars + 8 * st, (ring.phase >> st) & 1u);
+            }
+            return;
+        }
+    }
+}
+
+template <int TM, int MS>
+void launch_one(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
+    const size_t smem = tables_smem_bytes(p.t, TM) + 1024 + (kChunkThreads / 32) * (kStages * 2 * kTileBytes + kStages * 8);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(reach_kernel<TM, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_kernel<TM, MS>, kChunkThreads, smem);
+    const uint64_t want = (p.c + kChunkThreads - 1) / kChunkThreads;
+    const uint64_t blocks = std::min<uint64_t>(want, (uint64_t)std::max(per_sm, 1) * sm_count);
+    reach_kernel<TM, MS><<<(uint32_t)std::max<uint64_t>(blocks, 1), kChunkThreads, smem, s>>>(p, map);
+}
+
+template <int TM>
+bool launch_ms(const Params &p, const CUtensorMap &map, cudaStream_t s, uint32_t ms, int sm_count) {
+    constexpr bool FULL = TM != TM_GLOBAL;          // fewer instantiations for the rare global mode
+    if (FULL && ms <= 2) launch_one<TM, 2>(p, map, s, sm_count);
+    else if (FULL && ms <= 4) launch_one<TM, 4>(p, map, s, sm_count);
+    else if (ms <= 8) launch_one<TM, 8>(p, map, s, sm_count);
+    else if (FULL && ms <= 16) launch_one<TM, 16>(p, map, s, sm_count);
+    else if (ms <= 32) launch_one<TM, 32>(p, map, s, sm_count);
+    else return false;
+    return true;
+}
+
+}  // namespace reach
+}  // namespace slpf

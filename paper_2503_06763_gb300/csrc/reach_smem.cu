@@ -1,0 +1,8 @@
+// Reach kernels for the smem table mode (see reach_impl.cuh).
+#include "reach_impl.cuh"
+
+namespace slpf {
+bool launch_reach_smem(const Params &p, const CUtensorMap &map, cudaStream_t s, uint32_t ms, int sm_count) {
+    return reach::launch_ms<TM_SMEM>(p, map, s, ms, sm_count);
+}
+}  // namespace slpf
