@@ -47,7 +47,7 @@ int sm_count_of(int device) {
 // scheduler, chunks long enough that speculative runs meet early in them.
 uint32_t choose_chunk(uint64_t n, int sms, const re_parse_opts *opts) {
     if (opts && opts->chunk_len) return opts->chunk_len;
-    const uint64_t target = (uint64_t)sms * 512;
+    const uint64_t target = (uint64_t)sms * 384;
     uint64_t k = (n + target - 1) / target;
     k = (k + kSub - 1) / kSub * kSub;
     return (uint32_t)std::min<uint64_t>(std::max<uint64_t>(k, 256), 1u << 20);

@@ -31,14 +31,15 @@
 namespace slpf {
 namespace reach {
 
-// One 64-byte block of both directions.  Runs j < wm (the warp's largest
-// run count, so the loop bound is warp-uniform) are stepped; a lane with
-// fewer runs steps empty states, which stay empty (row 0 of every table).
+// One 64-byte block of both directions.  Runs j < W are stepped, W a
+// compile-time width chosen per block from the warp's largest run count (so
+// the loops are fully unrolled without predication); a lane with fewer runs
+// steps empty states, which stay empty (row 0 of every table).
 // Bytes come from this lane's row of the warp's forward / backward tile
 // (64-byte rows, SWIZZLE_64B layout: 16-byte chunk q of row r sits at chunk
 // q ^ ((r >> 1) & 3)), filled by TMA or, for warps TMA cannot serve, by the
 // lanes themselves.
-template <int TM, int MS, bool EDGE>
+template <int TM, int MS, bool EDGE, int W>
 __device__ __forceinline__ void walk_block(const Params &p, const Tabs &T, const uint8_t *frow, const uint8_t *brow,
                                            uint32_t (&sf)[MS], uint32_t (&sb)[MS], uint32_t wmf, uint32_t wmb,
                                            bool bwd, int f_lo, int f_hi, int b_lo, int b_hi) {
@@ -53,13 +54,11 @@ __device__ __forceinline__ void walk_block(const Params &p, const Tabs &T, const
             for (int v = 0; v < 8; ++v) {
                 const uint32_t cpf = clsof<TM>(T, byte_of(fx, 2 * v)) * T.ncls + clsof<TM>(T, byte_of(fx, 2 * v + 1));
 #pragma unroll
-                for (int j = 0; j < MS; ++j)
-                    if (j < (int)wmf) sf[j] = fpair(T, sf[j], cpf) >> 16;
+                for (int j = 0; j < W; ++j) sf[j] = fpair(T, sf[j], cpf) >> 16;
                 if (bwd) {
                     const uint32_t cpb = clsof<TM>(T, byte_of(bx, 14 - 2 * v)) * T.ncls + clsof<TM>(T, byte_of(bx, 15 - 2 * v));
 #pragma unroll
-                    for (int j = 0; j < MS; ++j)
-                        if (j < (int)wmb) sb[j] = bpair(T, sb[j], cpb) >> 16;
+                    for (int j = 0; j < W; ++j) sb[j] = bpair(T, sb[j], cpb) >> 16;
                 }
             }
         } else {
@@ -69,14 +68,12 @@ __device__ __forceinline__ void walk_block(const Params &p, const Tabs &T, const
                 if (!EDGE || (tf >= f_lo && tf < f_hi)) {
                     const uint32_t c = clsof<TM>(T, byte_of(fx, u));
 #pragma unroll
-                    for (int j = 0; j < MS; ++j)
-                        if (j < (int)wmf) sf[j] = fnext<TM>(T, sf[j], c);
+                    for (int j = 0; j < W; ++j) sf[j] = fnext<TM>(T, sf[j], c);
                 }
                 if (bwd && (!EDGE || (tb >= b_lo && tb <= b_hi))) {
                     const uint32_t c = clsof<TM>(T, byte_of(bx, 15 - u));
 #pragma unroll
-                    for (int j = 0; j < MS; ++j)
-                        if (j < (int)wmb) sb[j] = bnext<TM>(T, sb[j], c);
+                    for (int j = 0; j < W; ++j) sb[j] = bnext<TM>(T, sb[j], c);
                 }
             }
         }
@@ -258,8 +255,12 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
         }
         const uint8_t *frow = ring.tiles + (2 * stage) * kTileBytes + lane * 64;
         const uint8_t *brow = ring.tiles + (2 * stage + 1) * kTileBytes + lane * 64;
-        if (edge) walk_block<TM, MS, true>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, f_lo, f_hi, 0, b_hi);
-        else walk_block<TM, MS, false>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
+        const uint32_t wm = max(wmf, wmb);
+        if (edge) walk_block<TM, MS, true, MS>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, f_lo, f_hi, 0, b_hi);
+        else if (wm <= 1) walk_block<TM, MS, false, 1>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
+        else if (MS > 2 && wm <= 2) walk_block<TM, MS, false, (MS > 2 ? 2 : MS)>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
+        else if (MS > 4 && wm <= 4) walk_block<TM, MS, false, (MS > 4 ? 4 : MS)>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
+        else walk_block<TM, MS, false, MS>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
         if (tma) {
             __syncwarp();                                     // every lane has read this stage
             if (lane == 0 && blk + kStages < nsub)
