@@ -22,8 +22,8 @@ namespace slpf {
 constexpr int kMaxW = 64;           // segments per column <= 4096
 constexpr uint32_t kBlockThreads = 256;     // build & merge
 constexpr uint32_t kChunkThreads = 128;     // reach and fix-up (one thread per chunk)
-constexpr uint32_t kRecBounds = 16;   // boundaries recorded per chunk and direction before runs meet
-constexpr uint32_t kRecEntries = 48;  // (state, slot set) entries recorded per chunk and direction
+constexpr uint32_t kRecBounds = 32;   // boundaries recorded per chunk and direction before runs meet
+constexpr uint32_t kRecEntries = 96;  // (state, slot set) entries recorded per chunk and direction
 
 enum Flag { FLAG_FFAIL = 0, FLAG_BFAIL = 1, FLAG_INTERNAL = 2, FLAG_COUNT = 4 };
 

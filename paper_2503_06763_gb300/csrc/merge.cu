@@ -39,20 +39,43 @@ __device__ uint32_t probe_state(const uint32_t *hash, uint32_t mask, const uint6
 }
 
 // Exact state at a recorded boundary: union of the runs whose slots H enters.
+// The entries are loaded up front (independent loads); the union of W <= 2
+// words stays in registers.
 __device__ uint32_t record_union(const Params &p, bool fwd, const uint2 *ent, uint32_t cnt, uint32_t H, bool &bad) {
     const DevTables &t = p.t;
     const uint32_t W = t.W;
     const uint64_t *bits = fwd ? t.fBits : t.bBits;
+    uint2 r[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) r[e] = (e < (int)cnt) ? ent[e] : make_uint2(0u, 0u);
     uint32_t single = 0;
     bool multi = false;
+    if (W <= 2 && cnt <= 8) {
+        uint64_t a0 = 0, a1 = 0;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            if (!(r[e].y & H)) continue;                         // empty entries have no slots
+            const uint32_t st = r[e].x;
+            if (!single) single = st;
+            else if (st != single) multi = true;
+            a0 |= __ldg(bits + (size_t)st * W);
+            if (W == 2) a1 |= __ldg(bits + (size_t)st * W + 1);
+        }
+        if (!multi) return single;
+        const uint64_t key[2] = {a0, a1};
+        const uint32_t id = fwd ? probe_state(t.fHash, t.fHashMask, t.fBits, W, key)
+                                : probe_state(t.bHash, t.bHashMask, t.bBits, W, key);
+        if (!id) bad = true;
+        return id;
+    }
     uint64_t acc[kMaxW];
     for (uint32_t w = 0; w < W; ++w) acc[w] = 0;
     for (uint32_t e = 0; e < cnt; ++e) {
-        const uint2 r = ent[e];
-        if (!(r.y & H)) continue;
-        if (!single) single = r.x;
-        else if (r.x != single) multi = true;
-        for (uint32_t w = 0; w < W; ++w) acc[w] |= __ldg(bits + (size_t)r.x * W + w);
+        const uint2 q = e < 8 ? r[e] : ent[e];
+        if (!(q.y & H)) continue;
+        if (!single) single = q.x;
+        else if (q.x != single) multi = true;
+        for (uint32_t w = 0; w < W; ++w) acc[w] |= __ldg(bits + (size_t)q.x * W + w);
     }
     if (!multi) return single;
     const uint32_t id = fwd ? probe_state(t.fHash, t.fHashMask, t.fBits, W, acc)
@@ -61,8 +84,69 @@ __device__ uint32_t record_union(const Params &p, bool fwd, const uint2 *ent, ui
     return id;
 }
 
-// One warp per chunk: lane r turns record r into the exact checkpoint; a
-// single lane walks the boundaries past the record, if any.
+// Fast walk of bytes [t0, t1) of a chunk (forward) with the staged tables:
+// two bytes per lookup where pair tables exist.  Calls at(tt+1, state) after
+// every byte tt whose successor boundary (tt+1) is a multiple of 64.
+template <int TM, typename F>
+__device__ __forceinline__ uint32_t walk_fwd(const Params &p, const Tabs &T, uint64_t base, uint32_t t0, uint32_t t1,
+                                             uint32_t st, F at) {
+    uint32_t tt = t0;
+    for (; tt < t1 && (tt & 15); ++tt) {                          // to a 16-byte boundary
+        st = fnext<TM>(T, st, clsof<TM>(T, __ldg(p.x + base + tt)));
+        if (((tt + 1) & 63) == 0) at(tt + 1, st);
+    }
+    for (; tt + 16 <= t1; tt += 16) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p.x + base + tt));
+        if (TM == TM_PAIR) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                st = fpair(T, st, clsof<TM>(T, byte_of(v, 2 * j)) * T.ncls + clsof<TM>(T, byte_of(v, 2 * j + 1))) >> 16;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) st = fnext<TM>(T, st, clsof<TM>(T, byte_of(v, j)));
+        }
+        if (((tt + 16) & 63) == 0) at(tt + 16, st);
+    }
+    for (; tt < t1; ++tt) {
+        st = fnext<TM>(T, st, clsof<TM>(T, __ldg(p.x + base + tt)));
+        if (((tt + 1) & 63) == 0) at(tt + 1, st);
+    }
+    return st;
+}
+
+// Backward walk of bytes t1-1 down to t0 (t0, t1 multiples of 64 or t1 = len);
+// calls at(tt, state) after every byte tt that is a multiple of 64.
+template <int TM, typename F>
+__device__ __forceinline__ uint32_t walk_bwd(const Params &p, const Tabs &T, uint64_t base, uint32_t t0, uint32_t t1,
+                                             uint32_t st, F at) {
+    int64_t tt = (int64_t)t1 - 1;
+    for (; tt >= (int64_t)t0 && ((tt + 1) & 15); --tt) {          // down to a 16-byte boundary
+        st = bnext<TM>(T, st, clsof<TM>(T, __ldg(p.x + base + tt)));
+        if ((tt & 63) == 0) at((uint32_t)tt, st);
+    }
+    for (; tt - 15 >= (int64_t)t0; tt -= 16) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p.x + base + tt - 15));
+        if (TM == TM_PAIR) {
+#pragma unroll
+            for (int j = 7; j >= 0; --j)
+                st = bpair(T, st, clsof<TM>(T, byte_of(v, 2 * j)) * T.ncls + clsof<TM>(T, byte_of(v, 2 * j + 1))) >> 16;
+        } else {
+#pragma unroll
+            for (int j = 15; j >= 0; --j) st = bnext<TM>(T, st, clsof<TM>(T, byte_of(v, j)));
+        }
+        if (((tt - 15) & 63) == 0) at((uint32_t)(tt - 15), st);
+    }
+    for (; tt >= (int64_t)t0; --tt) {
+        st = bnext<TM>(T, st, clsof<TM>(T, __ldg(p.x + base + tt)));
+        if ((tt & 63) == 0) at((uint32_t)tt, st);
+    }
+    return st;
+}
+
+// One warp per chunk and direction pair: lanes 0-15 take the forward
+// direction, lanes 16-31 the backward one; lane r of a half turns records r
+// and r+16 into exact checkpoints; one lane per half walks any boundaries
+// past the record with the staged tables.
 template <int TM>
 __global__ void __launch_bounds__(kChunkThreads) fixup_kernel(Params p) {
     extern __shared__ __align__(16) uint8_t sm[];
@@ -70,7 +154,8 @@ __global__ void __launch_bounds__(kChunkThreads) fixup_kernel(Params p) {
     stage_tables<TM>(p, sm, T);
     if (*p.status != RE_OK) return;
     bool bad = false;
-    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t lane = threadIdx.x & 31, half = lane >> 4, r = lane & 15;
+    const bool fwd = half == 0;
     const uint32_t wpb = blockDim.x / 32;
     const uint64_t nw = (uint64_t)gridDim.x * wpb;
     for (uint64_t i = (uint64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < p.c; i += nw) {
@@ -78,59 +163,64 @@ __global__ void __launch_bounds__(kChunkThreads) fixup_kernel(Params p) {
         const uint32_t len = chunk_len(p, (uint32_t)i);
         const uint32_t nsub = (len + 63) / 64;
         const uint64_t g0 = i * p.S;
-        // ---- forward: boundaries 1 .. fconv-1; record r is boundary r+1
-        const uint32_t fcs = p.w.fconv[i];
-        if (fcs > 1) {
-            const uint32_t nrec = p.w.fnrec[i], H = p.w.fhit[i];
-            const uint32_t cnt = lane < nrec ? p.w.recFc[i * kRecBounds + lane] : 0u;
-            uint32_t off = cnt;                                           // inclusive scan -> exclusive
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, off, d);
-                if ((int)lane >= d) off += v;
-            }
-            off -= cnt;
-            uint32_t st = 0;
-            if (lane < nrec) {
-                st = record_union(p, true, p.w.recFe + i * kRecEntries + off, cnt, H, bad);
-                p.w.FC[g0 + lane + 1] = st;
-            }
-            const uint32_t from = __shfl_sync(0xFFFFFFFFu, st, nrec > 0 ? nrec - 1 : 0);
-            if (nrec + 1 <= fcs - 1 && lane == 0) {                      // walk the rest
-                uint32_t exact = nrec == 0 ? p.w.FJ[i] : from;
-                for (uint32_t tt = 64 * nrec, s = nrec + 1; s < fcs; ++tt) {
-                    exact = fnext<TM>(T, exact, clsof<TM>(T, __ldg(p.x + base + tt)));
-                    if (((tt + 1) & 63) == 0) { p.w.FC[g0 + (tt + 1) / 64] = exact; ++s; }
-                }
-            }
+        uint32_t conv, nrec, H;
+        bool active;
+        if (fwd) {
+            conv = p.w.fconv[i];
+            active = conv > 1;                                    // boundaries 1 .. conv-1
+            nrec = p.w.fnrec[i]; H = p.w.fhit[i];
+        } else {
+            conv = p.w.bconv[i];
+            active = !p.recognize && nsub >= 2 && conv + 1 <= nsub - 1;   // boundaries nsub-1 .. conv+1
+            nrec = p.w.bnrec[i]; H = p.w.bhit[i];
         }
-        if (p.recognize) continue;
-        // ---- backward: boundaries nsub-1 down to bconv+1; record r is boundary nsub-1-r
-        const uint32_t bcs = p.w.bconv[i];
-        if (nsub >= 2 && bcs + 1 <= nsub - 1) {
-            const uint32_t nrec = p.w.bnrec[i], H = p.w.bhit[i];
-            const uint32_t cnt = lane < nrec ? p.w.recBc[i * kRecBounds + lane] : 0u;
-            uint32_t off = cnt;
+        if (!active) nrec = 0;
+        const uint32_t *cnt_row = (fwd ? p.w.recFc : p.w.recBc) + i * kRecBounds;
+        const uint32_t c0 = r < nrec ? cnt_row[r] : 0u, c1 = r + 16 < nrec ? cnt_row[r + 16] : 0u;
+        uint32_t off0 = c0, tot = c0 + c1;                        // scans within the half
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, off, d);
-                if ((int)lane >= d) off += v;
+        for (int d = 1; d < 16; d <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, off0, d, 16);
+            if ((int)r >= d) off0 += v;
+        }
+        const uint32_t sum0 = __shfl_sync(0xFFFFFFFFu, off0, 15, 16);   // entries of records 0..15
+        uint32_t off1 = c1;
+#pragma unroll
+        for (int d = 1; d < 16; d <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, off1, d, 16);
+            if ((int)r >= d) off1 += v;
+        }
+        off0 -= c0;
+        off1 = sum0 + off1 - c1;
+        (void)tot;
+        const uint2 *ent = (fwd ? p.w.recFe : p.w.recBe) + i * kRecEntries;
+        uint32_t st0 = 0, st1 = 0;
+        if (r < nrec) {
+            st0 = record_union(p, fwd, ent + off0, c0, H, bad);
+            if (fwd) p.w.FC[g0 + r + 1] = st0;                    // record r: boundary r+1
+            else p.w.BC[g0 + (nsub - 1 - r) - 1] = st0;           // record r: boundary nsub-1-r
+        }
+        if (r + 16 < nrec) {
+            st1 = record_union(p, fwd, ent + off1, c1, H, bad);
+            if (fwd) p.w.FC[g0 + r + 17] = st1;
+            else p.w.BC[g0 + (nsub - 17 - r) - 1] = st1;
+        }
+        const uint32_t lastr = nrec > 0 ? nrec - 1 : 0;           // last record: lane lastr % 16
+        const uint32_t from = __shfl_sync(0xFFFFFFFFu, lastr >= 16 ? st1 : st0, (lastr & 15) + 16 * half, 32);
+        if (!active || r != 0) continue;
+        if (fwd) {
+            if (nrec + 1 <= conv - 1) {                           // walk boundaries nrec+1 .. conv-1
+                const uint32_t start = nrec == 0 ? p.w.FJ[i] : from;
+                walk_fwd<TM>(p, T, base, 64 * nrec, 64 * (conv - 1), start,
+                             [&](uint32_t b, uint32_t s2) { p.w.FC[g0 + b / 64] = s2; });
             }
-            off -= cnt;
-            uint32_t st = 0;
-            if (lane < nrec) {
-                st = record_union(p, false, p.w.recBe + i * kRecEntries + off, cnt, H, bad);
-                p.w.BC[g0 + (nsub - 1 - lane) - 1] = st;
-            }
-            const uint32_t from = __shfl_sync(0xFFFFFFFFu, st, nrec > 0 ? nrec - 1 : 0);
-            const uint32_t bb_first = nsub - 1 - nrec;                   // first boundary not recorded
-            if (bb_first > bcs && lane == 0) {                           // walk the rest
-                uint32_t exact = nrec == 0 ? p.w.BJ[i + 1] : from;
-                int64_t tt = nrec == 0 ? (int64_t)len - 1 : 64 * (int64_t)(bb_first + 1) - 1;
-                for (uint32_t bb = bb_first; bb > bcs; --tt) {
-                    exact = bnext<TM>(T, exact, clsof<TM>(T, __ldg(p.x + base + tt)));
-                    if ((tt & 63) == 0) { p.w.BC[g0 + tt / 64 - 1] = exact; --bb; }
-                }
+        } else {
+            const uint32_t bb_first = nsub - 1 - nrec;            // first boundary not recorded
+            if (bb_first > conv) {                                // walk boundaries bb_first .. conv+1
+                const uint32_t start = nrec == 0 ? p.w.BJ[i + 1] : from;
+                const uint32_t t1 = nrec == 0 ? len : 64 * (bb_first + 1);
+                walk_bwd<TM>(p, T, base, 64 * (conv + 1), t1, start,
+                             [&](uint32_t b, uint32_t s2) { p.w.BC[g0 + b / 64 - 1] = s2; });
             }
         }
     }
@@ -144,17 +234,14 @@ struct Enc {
     const uint64_t *fbits, *bbits;   // DENSE: segment set of each state (W == 1)
     const uint16_t *pt16;            // DICT: pair table in shared memory (u16)
     const uint32_t *pt32;            // DICT: pair table (u32; shared or global)
-    uint32_t nbd1, nfd, nbd;
+    uint32_t nb;
 };
 
 template <int E>
 __device__ __forceinline__ uint32_t enc_lo(const Enc &e, uint32_t f, uint32_t b, bool &bad) {
     if (E == ENC_X2 || E == ENC_X4) {
-        bad |= (f > e.nfd) | (b > e.nbd);
-        f = min(f, e.nfd);
-        b = min(b, e.nbd);
-        const uint32_t at = f * e.nbd1 + b;
-        return e.pt16 ? (uint32_t)e.pt16[at] : (e.pt32 == nullptr ? 0u : e.pt32[at]);
+        const uint32_t at = f * e.nb + b;                 // the pair table spans every state pair
+        return e.pt16 ? (uint32_t)e.pt16[at] : e.pt32[at];
     }
     return (uint32_t)(e.fbits[f] & e.bbits[b]);
 }
@@ -378,10 +465,10 @@ __global__ void __launch_bounds__(kBlockThreads, 3)
     if (TM != TM_PAIR) rest += (2 * 32 * kBlockThreads * sizeof(St) + 15) & ~(size_t)15;
     Enc e{};
     const DevTables &t = p.t;
-    e.nbd1 = t.nbd + 1; e.nfd = t.nfd; e.nbd = t.nbd;
+    e.nb = t.nb;
     if (E == ENC_X2 || E == ENC_X4) {
         if (p.pt_in_smem) {
-            const size_t cnt = (size_t)(t.nfd + 1) * (t.nbd + 1);
+            const size_t cnt = (size_t)t.nf * t.nb;
             if (E == ENC_X2) {
                 uint16_t *pt = reinterpret_cast<uint16_t *>(rest);
                 for (size_t i = threadIdx.x; i < cnt; i += blockDim.x) pt[i] = (uint16_t)__ldg(t.pt + i);
@@ -458,7 +545,7 @@ __global__ void empty_text_kernel(Params p) {
     *p.status = meet ? RE_OK : RE_REJECTED;
     if (!p.out) return;
     if (p.kind == RE_SLPF_DICT) {
-        const uint32_t d = meet ? t.pt[(size_t)t.fI * (t.nbd + 1) + t.bF] : 0u;
+        const uint32_t d = meet ? t.pt[(size_t)t.fI * t.nb + t.bF] : 0u;
         if (p.col_bytes == 2) reinterpret_cast<uint16_t *>(p.out)[0] = (uint16_t)d;
         else reinterpret_cast<uint32_t *>(p.out)[0] = d;
     } else {
@@ -534,7 +621,7 @@ size_t merge_extra_smem(const Params &p) {
     size_t a = 0;
     if (p.out_tma) a += 1024 + (size_t)(kBlockThreads / 32) * 32 * 64 * p.col_bytes;   // warp tiles + alignment
     if (p.tmode != TM_PAIR) a += (2 * 32 * kBlockThreads * (p.tmode == TM_GLOBAL ? 4 : 2) + 15) & ~(size_t)15;
-    if (p.kind == RE_SLPF_DICT) return a + (p.pt_in_smem ? (size_t)(t.nfd + 1) * (t.nbd + 1) * p.col_bytes : 0);
+    if (p.kind == RE_SLPF_DICT) return a + (p.pt_in_smem ? (size_t)t.nf * t.nb * p.col_bytes : 0);
     return a + (size_t)(t.nf + t.nb) * 8;
 }
 

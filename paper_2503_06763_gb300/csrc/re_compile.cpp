@@ -653,15 +653,19 @@ re_status compile_pattern(const char *pattern, size_t len, const re_compile_opts
     // ---- column dictionary: every non-empty B ∩ B̂ over classic-DFA state pairs
     C.has_dict = false;
     C.dict.clear(); C.pt.clear(); C.dict_size = 0;
-    if ((uint64_t)(nfd + 1) * (nbd + 1) <= max_dict) {
+    if ((uint64_t)C.nf * C.nb <= max_dict) {
         StateTable cols(W);
-        std::vector<uint32_t> raw((size_t)(nfd + 1) * (nbd + 1), 0);
+        // raw pair table over all states; pairs the parse can produce are
+        // (DFA state reachable from I, reverse DFA state reachable from F)
+        std::vector<uint32_t> raw((size_t)C.nf * C.nb, 0xFFFFFFFFu);
         std::vector<uint64_t> tmp(W);
-        for (uint32_t f = 1; f <= nfd; ++f)
-            for (uint32_t b = 1; b <= nbd; ++b) {
+        for (uint32_t f = 0; f < C.nf; ++f)
+            for (uint32_t b = 0; b < C.nb; ++b) {
+                if (f == 0 || b == 0) { raw[(size_t)f * C.nb + b] = 0; continue; }   // an empty side
+                if (f > nfd || b > nbd) continue;                                  // never produced
                 for (uint32_t w = 0; w < W; ++w) tmp[w] = ftab.row(f)[w] & btab.row(b)[w];
                 bool ins;
-                raw[(size_t)f * (nbd + 1) + b] = cols.intern(tmp.data(), ins);
+                raw[(size_t)f * C.nb + b] = cols.intern(tmp.data(), ins);
             }
         uint32_t D0 = cols.size() - 1;
         if (D0 < 0xFFFFFFF0u) {
@@ -690,7 +694,7 @@ re_status compile_pattern(const char *pattern, size_t len, const re_compile_opts
             std::vector<uint32_t> rank(D0 + 1, 0);
             for (uint32_t i = 0; i < D0; ++i) rank[order[i]] = i + 1;
             C.pt.resize(raw.size());
-            for (size_t i = 0; i < raw.size(); ++i) C.pt[i] = rank[raw[i]];
+            for (size_t i = 0; i < raw.size(); ++i) C.pt[i] = raw[i] == 0xFFFFFFFFu ? 0xFFFFFFFFu : rank[raw[i]];
             C.dict.resize((size_t)D0 * W);
             for (uint32_t i = 0; i < D0; ++i) std::copy(cols.row(order[i]), cols.row(order[i]) + W, &C.dict[(size_t)i * W]);
             C.dict_size = D0;

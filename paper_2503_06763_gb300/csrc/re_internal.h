@@ -46,7 +46,8 @@ struct DevTables {
     const uint32_t *bSlotStart;  // [ncls][ncls][msb] start state after the chunk's last byte
     const uint64_t *bSlotMask;   // [ncls][ncls][msb][W] segments whose first symbol is a key
     const uint32_t *bSlotCount;  // [ncls][ncls]
-    const uint32_t *pt;          // [(nfd+1)][(nbd+1)] dictionary index of B ∩ B̂ (DICT)
+    const uint32_t *pt;          // [nf][nb] dictionary index of B ∩ B̂ (DICT); pairs the
+                                 // parse never produces hold 0xFFFFFFFF
     const uint32_t *f2, *b2;     // [n][ncls^2] two-byte tables (mid | end << 16), or null
     uint32_t fHashMask, bHashMask;
     uint32_t ncls, W, ell;
@@ -69,7 +70,7 @@ struct Compiled {
     uint32_t fHashMask = 0, bHashMask = 0;
     std::vector<uint32_t> fSlotStart, fSlotCount, bSlotStart, bSlotCount;
     std::vector<uint64_t> fSlotMask, bSlotMask;
-    std::vector<uint32_t> pt;                 // [(nfd+1)][(nbd+1)]
+    std::vector<uint32_t> pt;                 // [nf][nb]
     std::vector<uint64_t> dict;               // [dict_size][W]
     uint32_t dict_size = 0;
     bool has_dict = false;
