@@ -143,6 +143,17 @@ def cpu_baseline(text_host, pattern):
                       f"{dt:.1f} s, host {os.uname().machine} nproc={os.cpu_count()}"}
 
 
+def csrc_hash() -> str:
+    """SHA-256 over every CUDA source of the library, in name order."""
+    d = os.path.join(ROOT, "paper_2503_06763_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()
+
+
 def traffic_for(kernel: str, n: int):
     """ncu DRAM bytes of the dominant kernel, scaled per text byte, if the
     committed capture matches the current kernel source."""
@@ -150,9 +161,7 @@ def traffic_for(kernel: str, n: int):
     try:
         with open(path) as f:
             d = json.load(f)
-        src = b"".join(open(os.path.join(ROOT, "paper_2503_06763_gb300", "csrc", f), "rb").read()
-                       for f in ("kernels.cuh", "reach.cu", "merge.cu"))
-        if d.get("csrc_sha256") != hashlib.sha256(src).hexdigest():
+        if d.get("csrc_sha256") != csrc_hash():
             return None
         per = d.get("dram_bytes_per_text_byte", {}).get(kernel)
         return None if per is None else per * n

@@ -348,12 +348,13 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     alignas(64) CUtensorMap out_map;
     std::memset(&out_map, 0, sizeof(out_map));
     p.out_tma = (!recognize && output_tensor_map(out_map, slpf->d_cols, cb, p.Gfast)) ? 1u : 0u;
+    // Stage the dictionary pair table in shared memory when the merge's whole
+    // footprint (tables, stage, output tiles and the table) still fits.
     if (kind == RE_SLPF_DICT && tab + merge_extra_smem(p) + (size_t)t.nf * t.nb * cb <= kSmemMergeMax) p.pt_in_smem = 1;
     alignas(64) CUtensorMap text_map;
     std::memset(&text_map, 0, sizeof(text_map));
     p.c_full = (uint32_t)(len / k);
     p.text_tma = text_tensor_map(text_map, d_text, k, p.c_full) ? 1u : 0u;
-    p.pt_in_smem = 0;                     // decided below, once the merge's other shared memory is known
     auto mark = [&](int j) -> cudaError_t { return ev ? cudaEventRecord(ev[j], s) : cudaSuccess; };
     if (len == 0) {
         CUDA_TRY(mark(0), "event");

@@ -211,6 +211,11 @@ __device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
     return (uint32_t)__cvta_generic_to_shared(ptr);
 }
 // Make this thread's generic-proxy shared-memory writes visible to the async proxy.
+// Bring the 128-byte line holding addr into L2 (no register result).
+__device__ __forceinline__ void prefetch_l2(const void *addr) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(addr));
+}
+
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 // 2D tiled store shared -> global (box from the tensor map), coordinates {x, y}.
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, uint32_t src, int32_t x, int32_t y) {

@@ -496,6 +496,11 @@ __global__ void __launch_bounds__(kBlockThreads, 3)
     const uint64_t gw = (uint64_t)blockIdx.x * WPB + warp, nw = (uint64_t)gridDim.x * WPB;
     for (uint64_t gb = gw * 32; gb < p.Gc; gb += nw * 32) {
         const uint64_t g = gb + lane;
+        {                                                     // next tile's text and checkpoints into L2
+            const uint64_t gn = gb + nw * 32;
+            if (gn + lane < p.Gfast) prefetch_l2(p.x + (gn + lane) * 64);
+            if (lane < 2 && gn < p.Gc) prefetch_l2((lane ? p.w.BC : p.w.FC) + gn);
+        }
         if (TMA && gb != gw * 32) {                           // previous tile read by its store?
             if (lane == 0) bulk_wait_read_all();
             __syncwarp();

@@ -1,5 +1,5 @@
 // Internal definitions shared by the host compiler (re_compile.cpp) and the
-// device parse path (parse_kernels.cu).  Not part of the public ABI.
+// device parse path (the .cu files).  Not part of the public ABI.
 #pragma once
 
 #include <stdint.h>
