@@ -159,6 +159,35 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
                    re_slpf *slpf, void *d_workspace, uint64_t workspace_bytes,
                    const re_parse_opts *opts);
 
+/* Size of the library-owned device scratch used by re_parse_static: 64 MiB,
+ * enough for texts up to about 8 MiB with automatic chunking (about 0.54
+ * byte of workspace per text byte for texts of 256 MiB, more for short ones,
+ * whose chunks are shorter; re_workspace_size gives the exact figure).      */
+#define RE_STATIC_SCRATCH_BYTES (64u << 20)
+
+/* re_parse without a caller workspace and without any allocation.  The paper
+ * has no counterpart: this is a deployment variant of re_parse, for callers
+ * that cannot allocate device memory when they parse -- a C host program with
+ * no device allocator of its own, or a request loop that must not call
+ * cudaMalloc / cudaFree between launches, since those may synchronise the
+ * whole device and stall every other stream.
+ *
+ * The workspace is one fixed device array of RE_STATIC_SCRATCH_BYTES per
+ * device, owned by the library.  Arguments, results and errors are those of
+ * re_parse, plus:
+ *   - RE_E_CAPACITY (nothing enqueued) when re_workspace_size(h, len, opts)
+ *     exceeds RE_STATIC_SCRATCH_BYTES; re_last_error() gives both sizes;
+ *   - RE_E_CUDA when the scratch address cannot be resolved.
+ * The first call on each device resolves that address (cudaGetSymbolAddress)
+ * with the device current; make that first call before any stream capture.
+ * Every call on a device shares the one scratch: calls whose work can overlap
+ * on the device (different streams with no ordering between them, or several
+ * host threads) race and corrupt each other's results.  Successive calls on
+ * one stream are ordered and safe.  The scratch needs no clearing between
+ * calls.                                                                    */
+re_status re_parse_static(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream stream,
+                          re_slpf *slpf, const re_parse_opts *opts);
+
 /* Thread-local description of the last error returned on this thread.     */
 const char *re_last_error(void);
 

@@ -23,7 +23,8 @@ RE_COMPILE_HOST_ONLY = 1
 RE_PARSE_RECOGNIZE_ONLY = 1
 
 EXPORTS = ["re_compile", "re_free", "re_get_info", "re_segment_name", "re_dict_copy",
-           "re_slpf_layout", "re_workspace_size", "re_parse", "re_last_error"]
+           "re_slpf_layout", "re_workspace_size", "re_parse", "re_parse_static", "re_last_error"]
+RE_STATIC_SCRATCH_BYTES = 64 << 20
 
 
 class ReError(RuntimeError):
@@ -85,6 +86,8 @@ def load():
     lib.re_workspace_size.restype = i32
     lib.re_parse.argtypes = [vp, vp, u64, vp, ctypes.POINTER(Slpf), vp, u64, ctypes.POINTER(ParseOpts)]
     lib.re_parse.restype = i32
+    lib.re_parse_static.argtypes = [vp, vp, u64, vp, ctypes.POINTER(Slpf), ctypes.POINTER(ParseOpts)]
+    lib.re_parse_static.restype = i32
     lib.re_last_error.argtypes = []
     lib.re_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -191,6 +194,28 @@ class Regex:
             opts.n_events, opts.events = RE_PHASE_EVENTS, ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p))
         check(load().re_parse(self._h, text.data_ptr() if n else None, n, ctypes.c_void_p(s.cuda_stream),
                               ctypes.byref(slpf), workspace.data_ptr(), workspace.numel(), ctypes.byref(opts)))
+        return out, status, kname
+
+    def parse_static(self, text, kind: str = "auto", chunk_len: int = 0, stream=None, out=None, status=None):
+        """Like ``parse`` but through re_parse_static: the library's fixed device
+        scratch serves as workspace, so only the output tensors are allocated
+        here (pass ``out`` and ``status`` to allocate nothing)."""
+        import torch
+        if not (isinstance(text, torch.Tensor) and text.is_cuda and text.dtype == torch.uint8):
+            raise TypeError("text must be a CUDA uint8 tensor")
+        text = text.contiguous()
+        n = text.numel()
+        kname, cb, _ = self.layout(n, kind)
+        dt = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}[cb]
+        if out is None:
+            out = torch.empty(n + 1, dtype=dt, device=text.device)
+        if status is None:
+            status = torch.empty(1, dtype=torch.int32, device=text.device)
+        s = stream if stream is not None else torch.cuda.current_stream(text.device)
+        slpf = Slpf(KINDS[kname], cb, 0, out.data_ptr(), out.numel() * out.element_size(), status.data_ptr())
+        opts = ParseOpts(KINDS[kname], chunk_len, 0, 0, None)
+        check(load().re_parse_static(self._h, text.data_ptr() if n else None, n, ctypes.c_void_p(s.cuda_stream),
+                                     ctypes.byref(slpf), ctypes.byref(opts)))
         return out, status, kname
 
     # ------------------------------------------------------------------ decoding
