@@ -159,6 +159,54 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
                    re_slpf *slpf, void *d_workspace, uint64_t workspace_bytes,
                    const re_parse_opts *opts);
 
+/* ---------------------------------------------------------------- batches
+ * Many texts, each under its own compiled RE, parsed together: the texts
+ * that share a handle form a group, and every phase of a group is one kernel
+ * launch over all its texts (reach tiles of 32 chunks, chunks, and merge
+ * tiles of 32 column groups, handed out by device work counters), instead of
+ * one launch per phase and text.  Results are those of re_parse on each text
+ * (Sect. 3.2); the chunk length of each text is chosen from its length and
+ * its group's total length (re_batch_chunk_len reports it).
+ *
+ * Use: re_batch_plan (host only; sizes, chunk lengths, a pinned descriptor
+ * buffer) -> re_batch_workspace_size -> re_parse_batch (binds text, output
+ * and workspace pointers, uploads the descriptors, enqueues the kernels) ->
+ * re_batch_run to parse the same bound buffers again (kernels only, nothing
+ * copied) -> re_batch_free.                                                 */
+typedef struct re_batch re_batch;       /* opaque: a planned batch */
+
+/* Plan count texts: text j has lens[j] bytes and is parsed under hs[j] (all
+ * handles on the current device).  opts->kind is the encoding for every text
+ * (AUTO resolved per handle); opts->chunk_len, if not 0, fixes every chunk
+ * length; RE_PARSE_RECOGNIZE_ONLY is honoured; phase events are not.
+ * *out owns a pinned host buffer until re_batch_free.                       */
+re_status re_batch_plan(re_handle *const *hs, const uint64_t *lens, uint32_t count, const re_parse_opts *opts,
+                        re_batch **out);
+
+/* Device workspace the batch needs (descriptors + every text's workspace). */
+re_status re_batch_workspace_size(const re_batch *b, uint64_t *bytes);
+
+/* Chunk length chosen for text j.                                          */
+re_status re_batch_chunk_len(const re_batch *b, uint32_t j, uint32_t *k);
+
+/* Enqueue the parse of every text: d_texts[j] (16-byte aligned device bytes
+ * of lens[j]), outs[j] laid out like re_parse's output (kind = the planned
+ * encoding, col_bytes from re_slpf_layout, a status word per text).  The
+ * workspace (256-byte aligned, re_batch_workspace_size bytes) is caller
+ * owned and bound to the batch until the next re_parse_batch.  Copies the
+ * descriptors from the plan's pinned buffer on the stream; a later call on the
+ * same plan first waits for that copy.  Asynchronous otherwise.              */
+re_status re_parse_batch(re_batch *b, const uint8_t *const *d_texts, re_slpf *outs, void *d_workspace,
+                         uint64_t workspace_bytes, re_stream stream);
+
+/* Enqueue the kernels of the last re_parse_batch again, over the same bound
+ * text, output and workspace buffers (their contents may have changed).
+ * Only kernel launches: no copy, no allocation, no host synchronisation.    */
+re_status re_batch_run(re_batch *b, re_stream stream);
+
+/* Free the plan (waits for its last descriptor copy).                      */
+void re_batch_free(re_batch *b);
+
 /* Size of the library-owned device scratch used by re_parse_static: 64 MiB,
  * enough for texts up to about 8 MiB with automatic chunking (about 0.54
  * byte of workspace per text byte for texts of 256 MiB, more for short ones,

@@ -5,6 +5,6 @@ sm_103a CUDA kernels behind the C ABI of ``include/slpf_parser.h``), its build
 script and a thin ctypes binding.  ``Regex(pattern).parse(text)`` returns the
 clean SLPF of a device-resident text.
 """
-from .native import KINDS, RE_OK, RE_REJECTED, STATUS_NAMES, Regex, ReError, load  # noqa: F401
+from .native import KINDS, RE_OK, RE_REJECTED, STATUS_NAMES, Batch, Regex, ReError, load  # noqa: F401
 
-__all__ = ["Regex", "ReError", "load", "KINDS", "RE_OK", "RE_REJECTED", "STATUS_NAMES"]
+__all__ = ["Regex", "Batch", "ReError", "load", "KINDS", "RE_OK", "RE_REJECTED", "STATUS_NAMES"]

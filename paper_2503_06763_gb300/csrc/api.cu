@@ -1,11 +1,15 @@
 // C ABI of include/slpf_parser.h: compile (host tables -> one device
-// allocation), layout / workspace sizing, and the parse launcher that
-// enqueues reach -> join -> fix-up -> build & merge on the caller's stream.
+// allocation), layout / workspace sizing, the parse launcher that enqueues
+// reach -> join -> fix-up -> build & merge on the caller's stream, and the
+// batch planner / launcher (many texts, one launch per phase and RE).
 #include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <memory>
 #include <string>
+#include <vector>
 
 #include "kernels.cuh"
 
@@ -154,6 +158,35 @@ re_status resolve_kind(const re_handle *h, re_slpf_kind kind, re_slpf_kind &out,
         return RE_E_INVALID_ARG;
     }
     out = kind;
+    return RE_OK;
+}
+
+uint32_t table_mode(const DevTables &t) {
+    const bool fit16 = t.nf < 65536 && t.nb < 65536;
+    if (t.f2 && t.b2 && tables_smem_bytes(t, TM_PAIR) <= kSmemPairMax) return TM_PAIR;
+    if (fit16 && tables_smem_bytes(t, TM_SMEM) <= kSmemTablesMax) return TM_SMEM;
+    return TM_GLOBAL;
+}
+
+// Point the workspace arrays of p at their places in w (layout L).
+void carve(Params &p, const Layout &L, uint8_t *w) {
+    p.w.Rf = (uint32_t *)(w + L.off[0]); p.w.Rb = (uint32_t *)(w + L.off[1]);
+    p.w.FJ = (uint32_t *)(w + L.off[2]); p.w.BJ = (uint32_t *)(w + L.off[3]);
+    p.w.FC = (uint32_t *)(w + L.off[4]); p.w.BC = (uint32_t *)(w + L.off[5]);
+    p.w.fconv = (uint32_t *)(w + L.off[6]); p.w.bconv = (uint32_t *)(w + L.off[7]);
+    p.w.fkind = (uint32_t *)(w + L.off[8]); p.w.bkind = (uint32_t *)(w + L.off[9]);
+    p.w.fnrec = (uint32_t *)(w + L.off[10]); p.w.bnrec = (uint32_t *)(w + L.off[11]);
+    p.w.fhit = (uint32_t *)(w + L.off[12]); p.w.bhit = (uint32_t *)(w + L.off[13]);
+    p.w.recFc = (uint32_t *)(w + L.off[14]); p.w.recBc = (uint32_t *)(w + L.off[15]);
+    p.w.recFe = (uint2 *)(w + L.off[16]); p.w.recBe = (uint2 *)(w + L.off[17]);
+    p.w.flags = (int32_t *)(w + L.off[18]);
+}
+
+// Check one output descriptor against the resolved encoding.
+re_status check_output(const re_slpf *slpf, uint64_t len, uint32_t cb) {
+    if (slpf->col_bytes != cb) { set_error("slpf->col_bytes does not match the layout"); return RE_E_INVALID_ARG; }
+    if (!slpf->d_cols || slpf->cols_cap_bytes < (len + 1) * cb) { set_error("SLPF buffer too small"); return RE_E_CAPACITY; }
+    if ((uintptr_t)slpf->d_cols & 15) { set_error("d_cols must be 16-byte aligned"); return RE_E_INVALID_ARG; }
     return RE_OK;
 }
 
@@ -314,9 +347,8 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     if (!recognize || slpf->d_cols) {
         const re_status st = resolve_kind(h, slpf->kind, kind, cb);
         if (st != RE_OK) return st;
-        if (slpf->col_bytes != cb) { set_error("slpf->col_bytes does not match the layout"); return RE_E_INVALID_ARG; }
-        if (!slpf->d_cols || slpf->cols_cap_bytes < (len + 1) * cb) { set_error("SLPF buffer too small"); return RE_E_CAPACITY; }
-        if ((uintptr_t)slpf->d_cols & 15) { set_error("d_cols must be 16-byte aligned"); return RE_E_INVALID_ARG; }
+        const re_status so = check_output(slpf, len, cb);
+        if (so != RE_OK) return so;
     }
     int dev_now = 0;
     cudaGetDevice(&dev_now);
@@ -339,10 +371,7 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     p.col_bytes = cb; p.kind = kind; p.status = slpf->d_status;
     p.recognize = recognize ? 1u : 0u;
     const DevTables &t = h->dev;
-    const bool fit16 = t.nf < 65536 && t.nb < 65536;
-    if (t.f2 && t.b2 && tables_smem_bytes(t, TM_PAIR) <= kSmemPairMax) p.tmode = TM_PAIR;
-    else if (fit16 && tables_smem_bytes(t, TM_SMEM) <= kSmemTablesMax) p.tmode = TM_SMEM;
-    else p.tmode = TM_GLOBAL;
+    p.tmode = table_mode(t);
     const size_t tab = tables_smem_bytes(t, p.tmode);
     p.Gfast = len / kSub;
     alignas(64) CUtensorMap out_map;
@@ -363,17 +392,7 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
         CUDA_TRY(cudaGetLastError(), "launch");
         return RE_OK;
     }
-    uint8_t *w = (uint8_t *)d_workspace;
-    p.w.Rf = (uint32_t *)(w + L.off[0]); p.w.Rb = (uint32_t *)(w + L.off[1]);
-    p.w.FJ = (uint32_t *)(w + L.off[2]); p.w.BJ = (uint32_t *)(w + L.off[3]);
-    p.w.FC = (uint32_t *)(w + L.off[4]); p.w.BC = (uint32_t *)(w + L.off[5]);
-    p.w.fconv = (uint32_t *)(w + L.off[6]); p.w.bconv = (uint32_t *)(w + L.off[7]);
-    p.w.fkind = (uint32_t *)(w + L.off[8]); p.w.bkind = (uint32_t *)(w + L.off[9]);
-    p.w.fnrec = (uint32_t *)(w + L.off[10]); p.w.bnrec = (uint32_t *)(w + L.off[11]);
-    p.w.fhit = (uint32_t *)(w + L.off[12]); p.w.bhit = (uint32_t *)(w + L.off[13]);
-    p.w.recFc = (uint32_t *)(w + L.off[14]); p.w.recBc = (uint32_t *)(w + L.off[15]);
-    p.w.recFe = (uint2 *)(w + L.off[16]); p.w.recBe = (uint2 *)(w + L.off[17]);
-    p.w.flags = (int32_t *)(w + L.off[18]);
+    carve(p, L, (uint8_t *)d_workspace);
     CUDA_TRY(mark(0), "event");
     launch_flags_init(p, s);
     if (!launch_reach(p, text_map, s, std::max(t.msf, recognize ? 1u : t.msb), sms)) {
@@ -393,6 +412,288 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     CUDA_TRY(mark(4), "event");
     CUDA_TRY(cudaGetLastError(), "launch");
     return RE_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batch
+// A planned batch: per text its group (compiled RE), chunk length and
+// workspace layout; per group the table mode, encoding and unit counts.  The
+// descriptor area at the start of the workspace holds every text's Params,
+// the per-group prefix sums and work counters; it is written from a pinned
+// host copy by re_parse_batch and only read by the kernels afterwards.
+struct re_batch {
+    struct Text {
+        uint32_t group = 0, slot = 0;   // slot: index of its Params in the descriptor area
+        uint64_t len = 0;
+        uint32_t k = 0;
+        Layout L{};
+        size_t ws_off = 0;
+    };
+    struct Group {
+        re_handle *h = nullptr;
+        uint32_t tmode = 0, ms = 0, pt_in_smem = 0, cb = 1;
+        re_slpf_kind kind = RE_SLPF_DENSE;
+        std::vector<uint32_t> members;  // caller indices, longest chunks first
+        size_t params_off = 0, cbase_off = 0, rbase_off = 0, mbase_off = 0;
+        uint64_t chunks = 0, n_reach = 0, n_merge = 0;
+    };
+    int device = 0, sms = 152;
+    bool recognize = false;
+    std::vector<Text> texts;
+    std::vector<Group> groups;
+    size_t queue_off = 0, desc_bytes = 0, total = 0;
+    uint8_t *pinned = nullptr;
+    cudaEvent_t uploaded = nullptr;
+    bool pending = false;
+    uint8_t *d_ws = nullptr;
+};
+
+namespace slpf {
+namespace {
+
+// Chunk length of one text of a batch: the single-text rule applied to the
+// group's total bytes (one reach lane per chunk, about one wave of lanes for
+// the whole group), but short enough that the text spans a warp tile of 32
+// chunks where it can.
+uint32_t batch_chunk(uint64_t len, uint64_t group_bytes, int sms, const re_parse_opts *opts) {
+    if (opts && opts->chunk_len) return opts->chunk_len;
+    const uint32_t kg = choose_chunk(group_bytes, sms, nullptr);
+    uint64_t kt = (len + 31) / 32;
+    kt = (kt + kSub - 1) / kSub * kSub;
+    return (uint32_t)std::max<uint64_t>(256, std::min<uint64_t>(kg, kt));
+}
+
+Params group_like(const re_batch::Group &g, bool recognize) {
+    Params q{};
+    q.t = g.h->dev;
+    q.tmode = g.tmode;
+    q.kind = g.kind;
+    q.col_bytes = g.cb;
+    q.recognize = recognize ? 1u : 0u;
+    q.pt_in_smem = g.pt_in_smem;
+    return q;
+}
+
+re_status batch_run(re_batch *b, cudaStream_t s) {
+    uint8_t *w = b->d_ws;
+    launch_batch_init(reinterpret_cast<const Params *>(w), (uint32_t)b->texts.size(),
+                      reinterpret_cast<uint32_t *>(w + b->queue_off), (uint32_t)b->groups.size() * kQueues, s);
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        const re_batch::Group &g = b->groups[gi];
+        BatchGroup bg{};
+        bg.t = g.h->dev;
+        bg.texts = reinterpret_cast<const Params *>(w + g.params_off);
+        bg.chunk_base = reinterpret_cast<const uint64_t *>(w + g.cbase_off);
+        bg.rtile_base = reinterpret_cast<const uint64_t *>(w + g.rbase_off);
+        bg.mtile_base = reinterpret_cast<const uint64_t *>(w + g.mbase_off);
+        bg.queue = reinterpret_cast<uint32_t *>(w + b->queue_off) + gi * kQueues;
+        bg.chunks = g.chunks; bg.n_reach = g.n_reach; bg.n_merge = g.n_merge;
+        bg.nt = (uint32_t)g.members.size();
+        bg.recognize = b->recognize ? 1u : 0u;
+        if (g.n_reach && !launch_reach_batch(bg, g.tmode, g.ms, s, b->sms)) {
+            set_error("too many speculative starts");
+            return RE_E_INTERNAL;
+        }
+        launch_join_batch(bg, s);
+        launch_fixup_batch(bg, g.tmode, s, b->sms);
+        launch_merge_batch(bg, group_like(g, b->recognize), s, b->sms);
+    }
+    CUDA_TRY(cudaGetLastError(), "batch launch");
+    return RE_OK;
+}
+
+}  // namespace
+}  // namespace slpf
+
+extern "C" {
+
+re_status re_batch_plan(re_handle *const *hs, const uint64_t *lens, uint32_t count, const re_parse_opts *opts,
+                        re_batch **out) {
+    if (!out || (count && (!hs || !lens))) { set_error("null argument"); return RE_E_INVALID_ARG; }
+    *out = nullptr;
+    if (opts && (opts->flags & ~RE_PARSE_RECOGNIZE_ONLY)) { set_error("unknown parse flags"); return RE_E_INVALID_ARG; }
+    if (opts && opts->n_events) { set_error("batch parses record no phase events"); return RE_E_INVALID_ARG; }
+    if (opts && opts->chunk_len && opts->chunk_len % kSub) {
+        set_error("chunk_len must be a positive multiple of 64");
+        return RE_E_INVALID_ARG;
+    }
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    std::unique_ptr<re_batch> b(new (std::nothrow) re_batch());
+    if (!b) { set_error("host allocation failed"); return RE_E_NOMEM; }
+    b->device = dev;
+    b->sms = sm_count_of(dev);
+    b->recognize = opts && (opts->flags & RE_PARSE_RECOGNIZE_ONLY);
+    b->texts.resize(count);
+    std::map<re_handle *, uint32_t> gid;
+    std::vector<uint64_t> gbytes;
+    for (uint32_t j = 0; j < count; ++j) {
+        re_handle *h = hs[j];
+        if (!h) { set_error("null handle in batch"); return RE_E_INVALID_ARG; }
+        if (h->host_only) { set_error("handle was compiled with RE_COMPILE_HOST_ONLY"); return RE_E_INVALID_ARG; }
+        if (h->device != dev) { set_error("current device differs from a handle's device"); return RE_E_INVALID_ARG; }
+        auto it = gid.find(h);
+        if (it == gid.end()) {
+            it = gid.emplace(h, (uint32_t)b->groups.size()).first;
+            re_batch::Group g;
+            g.h = h;
+            g.tmode = table_mode(h->dev);
+            g.ms = std::max(h->host.msf, b->recognize ? 1u : h->host.msb);
+            if (!b->recognize) {
+                const re_status st = resolve_kind(h, opts ? opts->kind : RE_SLPF_AUTO, g.kind, g.cb);
+                if (st != RE_OK) return st;
+            }
+            b->groups.push_back(std::move(g));
+            gbytes.push_back(0);
+        }
+        b->texts[j].group = it->second;
+        b->texts[j].len = lens[j];
+        b->groups[it->second].members.push_back(j);
+        gbytes[it->second] += lens[j];
+    }
+    // chunk lengths, then members longest chunks first
+    for (uint32_t j = 0; j < count; ++j) {
+        re_batch::Text &t = b->texts[j];
+        t.k = batch_chunk(t.len, gbytes[t.group], b->sms, opts);
+        if (t.len / t.k >= 0xFFFFFFF0ull) { set_error("text too long for this chunk length"); return RE_E_INVALID_ARG; }
+        if (t.len) t.L = layout_for(b->groups[t.group].h, t.len, t.k);
+    }
+    uint32_t slot = 0;                                       // every text's Params, group after group
+    for (auto &g : b->groups) {
+        std::stable_sort(g.members.begin(), g.members.end(), [&](uint32_t a, uint32_t c) {
+            return b->texts[a].k > b->texts[c].k;
+        });
+        g.params_off = (size_t)slot * sizeof(Params);
+        for (uint32_t j : g.members) b->texts[j].slot = slot++;
+    }
+    size_t off = align256((size_t)count * sizeof(Params));
+    for (auto &g : b->groups) {
+        const size_t arr = (g.members.size() + 1) * sizeof(uint64_t);
+        g.cbase_off = off; off = align256(off + arr);
+        g.rbase_off = off; off = align256(off + arr);
+        g.mbase_off = off; off = align256(off + arr);
+        Params q = group_like(g, b->recognize);
+        const size_t tab = tables_smem_bytes(g.h->dev, g.tmode);
+        if (!b->recognize && g.kind == RE_SLPF_DICT &&
+            tab + merge_extra_smem(q) + (size_t)g.h->dev.nf * g.h->dev.nb * g.cb <= kSmemMergeMax)
+            g.pt_in_smem = 1;
+    }
+    b->queue_off = off;
+    off = align256(off + b->groups.size() * kQueues * sizeof(uint32_t));
+    b->desc_bytes = off;
+    for (uint32_t j = 0; j < count; ++j) {
+        re_batch::Text &t = b->texts[j];
+        if (!t.len) continue;
+        t.ws_off = off;
+        off += align256(t.L.total);
+    }
+    b->total = std::max<size_t>(off, 256);
+    CUDA_TRY(cudaHostAlloc((void **)&b->pinned, b->desc_bytes, cudaHostAllocDefault), "batch descriptor buffer");
+    std::memset(b->pinned, 0, b->desc_bytes);
+    for (auto &g : b->groups) {                              // prefix sums of the units of each kind
+        uint64_t *cb = reinterpret_cast<uint64_t *>(b->pinned + g.cbase_off);
+        uint64_t *rb = reinterpret_cast<uint64_t *>(b->pinned + g.rbase_off);
+        uint64_t *mb = reinterpret_cast<uint64_t *>(b->pinned + g.mbase_off);
+        cb[0] = rb[0] = mb[0] = 0;
+        for (size_t m = 0; m < g.members.size(); ++m) {
+            const re_batch::Text &t = b->texts[g.members[m]];
+            const uint64_t c = t.len ? t.L.c : 0;
+            const uint64_t groups = (t.len && !b->recognize) ? t.L.Gc : 0;
+            cb[m + 1] = cb[m] + c;
+            rb[m + 1] = rb[m] + (c + 31) / 32;
+            mb[m + 1] = mb[m] + (groups + 31) / 32;
+        }
+        g.chunks = cb[g.members.size()];
+        g.n_reach = rb[g.members.size()];
+        g.n_merge = mb[g.members.size()];
+        if (g.n_reach >= 0xFFFFFFFFull || g.n_merge >= 0xFFFFFFFFull) {
+            set_error("batch too large for one launch per phase");
+            return RE_E_INVALID_ARG;
+        }
+    }
+    CUDA_TRY(cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming), "batch event");
+    *out = b.release();
+    return RE_OK;
+}
+
+re_status re_batch_workspace_size(const re_batch *b, uint64_t *bytes) {
+    if (!b || !bytes) { set_error("null argument"); return RE_E_INVALID_ARG; }
+    *bytes = b->total;
+    return RE_OK;
+}
+
+re_status re_batch_chunk_len(const re_batch *b, uint32_t j, uint32_t *k) {
+    if (!b || !k || j >= b->texts.size()) { set_error("bad argument"); return RE_E_INVALID_ARG; }
+    *k = b->texts[j].k;
+    return RE_OK;
+}
+
+re_status re_parse_batch(re_batch *b, const uint8_t *const *d_texts, re_slpf *outs, void *d_workspace,
+                         uint64_t workspace_bytes, re_stream stream) {
+    const uint32_t count = b ? (uint32_t)b->texts.size() : 0;
+    if (!b || (count && (!d_texts || !outs))) { set_error("null argument"); return RE_E_INVALID_ARG; }
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != b->device) { set_error("current device differs from the batch's device"); return RE_E_INVALID_ARG; }
+    if (!d_workspace || workspace_bytes < b->total || ((uintptr_t)d_workspace & 255)) {
+        set_error("workspace missing, too small or not 256-byte aligned");
+        return RE_E_CAPACITY;
+    }
+    for (uint32_t j = 0; j < count; ++j) {
+        const re_batch::Text &t = b->texts[j];
+        const re_batch::Group &g = b->groups[t.group];
+        if (!outs[j].d_status || (t.len && !d_texts[j])) { set_error("null text or status in batch"); return RE_E_INVALID_ARG; }
+        if (t.len && ((uintptr_t)d_texts[j] & 15)) { set_error("batch text must be 16-byte aligned"); return RE_E_INVALID_ARG; }
+        if (!b->recognize) {
+            if (outs[j].kind != g.kind) { set_error("slpf->kind differs from the planned encoding"); return RE_E_INVALID_ARG; }
+            const re_status so = check_output(&outs[j], t.len, g.cb);
+            if (so != RE_OK) return so;
+        }
+    }
+    if (b->pending) CUDA_TRY(cudaEventSynchronize(b->uploaded), "batch descriptor upload");
+    uint8_t *w = (uint8_t *)d_workspace;
+    for (uint32_t j = 0; j < count; ++j) {
+        const re_batch::Text &t = b->texts[j];
+        const re_batch::Group &g = b->groups[t.group];
+        Params p = group_like(g, b->recognize);
+        p.x = d_texts[j];
+        p.n = t.len;
+        p.k = t.k;
+        p.c = t.len ? t.L.c : 0;
+        p.S = t.k / kSub;
+        p.Gc = t.len / kSub + 1;
+        p.out = b->recognize ? nullptr : outs[j].d_cols;
+        p.status = outs[j].d_status;
+        p.Gfast = t.len / kSub;
+        p.c_full = (uint32_t)(t.len / t.k);
+        if (t.len) carve(p, t.L, w + t.ws_off);
+        std::memcpy(b->pinned + (size_t)t.slot * sizeof(Params), &p, sizeof(Params));
+        outs[j].n_cols = t.len + 1;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(w, b->pinned, b->desc_bytes, cudaMemcpyHostToDevice, s), "batch descriptor upload");
+    CUDA_TRY(cudaEventRecord(b->uploaded, s), "batch event");
+    b->pending = true;
+    b->d_ws = w;
+    return batch_run(b, s);
+}
+
+re_status re_batch_run(re_batch *b, re_stream stream) {
+    if (!b) { set_error("null argument"); return RE_E_INVALID_ARG; }
+    if (!b->d_ws) { set_error("batch not bound: call re_parse_batch first"); return RE_E_INVALID_ARG; }
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != b->device) { set_error("current device differs from the batch's device"); return RE_E_INVALID_ARG; }
+    return batch_run(b, (cudaStream_t)stream);
+}
+
+void re_batch_free(re_batch *b) {
+    if (!b) return;
+    if (b->pending) cudaEventSynchronize(b->uploaded);
+    if (b->uploaded) cudaEventDestroy(b->uploaded);
+    if (b->pinned) cudaFreeHost(b->pinned);
+    delete b;
 }
 
 }  // extern "C"

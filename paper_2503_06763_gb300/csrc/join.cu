@@ -96,9 +96,7 @@ __device__ void classify(const Params &p, bool fwd, uint32_t i) {
     }
 }
 
-__global__ void join_classify_kernel(Params p) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.c) return;
+__device__ void classify_at(const Params &p, uint32_t i) {
     if (i == 0) {
         p.w.FJ[0] = p.t.fI;
         p.w.FJ[1] = p.w.Rf[0];
@@ -116,9 +114,9 @@ __global__ void join_classify_kernel(Params p) {
     }
 }
 
-__global__ void join_chain_kernel(Params p) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.c) return;
+// Chains of general chunks, evaluated in order from their known neighbour
+// (started by the chunk just after / before the neighbour).
+__device__ void chain_at(const Params &p, uint32_t i) {
     bool bad = false;
     if (p.w.fkind[i] == 1 && p.w.fkind[i - 1] == 0) {     // i >= 1: fkind[0] == 0
         uint32_t cur = p.w.FJ[i];
@@ -137,6 +135,16 @@ __global__ void join_chain_kernel(Params p) {
     if (bad) atomicExch(&p.w.flags[FLAG_INTERNAL], 1);
 }
 
+__global__ void join_classify_kernel(Params p) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < p.c) classify_at(p, i);
+}
+
+__global__ void join_chain_kernel(Params p) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < p.c) chain_at(p, i);
+}
+
 // Live slots of chunk i (their end state is not the empty set).
 __device__ uint32_t live_slots(const Params &p, bool fwd, uint32_t i, uint32_t pr) {
     const DevTables &t = p.t;
@@ -151,9 +159,7 @@ __device__ uint32_t live_slots(const Params &p, bool fwd, uint32_t i, uint32_t p
 
 // Check each chunk's guessed output against its (now known) input and keep
 // the slots that input enters for the fix-up.
-__global__ void join_verify_kernel(Params p) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.c) return;
+__device__ void verify_at(const Params &p, uint32_t i) {
     {   // forward: input FJ[i] -> output FJ[i+1]
         const uint32_t in = p.w.FJ[i], out = p.w.FJ[i + 1];
         bool fail = in == 0 || out == 0;
@@ -190,7 +196,7 @@ __global__ void join_verify_kernel(Params p) {
 
 // Accept iff both joins ran through and C_0 = I ∩ Ĵ_1 is not empty
 // (recognizer: iff the forward join ran through and J_c ∩ F is not empty).
-__global__ void status_kernel(Params p) {
+__device__ void status_of(const Params &p) {
     const DevTables &t = p.t;
     int32_t st = RE_OK;
     if (p.w.flags[FLAG_FFAIL] < (int32_t)p.c || (!p.recognize && p.w.flags[FLAG_BFAIL] < (int32_t)p.c)) {
@@ -206,8 +212,51 @@ __global__ void status_kernel(Params p) {
     *p.status = st;
 }
 
+__global__ void join_verify_kernel(Params p) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < p.c) verify_at(p, i);
+}
+
+__global__ void status_kernel(Params p) { status_of(p); }
+
 __global__ void flags_init_kernel(Params p) {
     if (threadIdx.x < FLAG_COUNT) p.w.flags[threadIdx.x] = threadIdx.x < 2 ? (int32_t)p.c : 0;
+}
+
+// ------------------------------------------------------------------ batch
+// The same steps over every chunk of every text of a group: thread j takes
+// flat chunk j (its text by binary search on the chunk prefix sums).
+enum BatchStep { B_CLASSIFY = 0, B_CHAIN = 1, B_VERIFY = 2 };
+
+template <int STEP>
+__global__ void join_batch_kernel(const __grid_constant__ BatchGroup b) {
+    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= b.chunks) return;
+    const uint32_t ti = text_of(b.chunk_base, b.nt, j);
+    const Params &p = b.texts[ti];
+    const uint32_t i = (uint32_t)(j - b.chunk_base[ti]);
+    if (STEP == B_CLASSIFY) classify_at(p, i);
+    else if (STEP == B_CHAIN) chain_at(p, i);
+    else verify_at(p, i);
+}
+
+// Status of every text; an empty text has the single column C_0 = I ∩ F.
+__global__ void status_batch_kernel(const __grid_constant__ BatchGroup b) {
+    const uint32_t ti = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ti >= b.nt) return;
+    const Params &p = b.texts[ti];
+    if (p.n == 0) empty_text(p);
+    else status_of(p);
+}
+
+// Work counters of every group and the join flags of every text.
+__global__ void batch_init_kernel(const Params *texts, uint32_t nt, uint32_t *queues, uint32_t nq) {
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < nq) queues[j] = 0;
+    if (j < nt && texts[j].n) {
+        int32_t *f = texts[j].w.flags;
+        for (uint32_t q = 0; q < FLAG_COUNT; ++q) f[q] = q < 2 ? (int32_t)texts[j].c : 0;
+    }
 }
 
 }  // namespace
@@ -221,5 +270,20 @@ void launch_join(const Params &p, cudaStream_t s) {
 }
 
 void launch_flags_init(const Params &p, cudaStream_t s) { flags_init_kernel<<<1, 32, 0, s>>>(p); }
+
+void launch_batch_init(const Params *texts, uint32_t nt, uint32_t *queues, uint32_t nq, cudaStream_t s) {
+    const uint32_t n = nt > nq ? nt : nq;
+    batch_init_kernel<<<(n + kBlockThreads - 1) / kBlockThreads, kBlockThreads, 0, s>>>(texts, nt, queues, nq);
+}
+
+void launch_join_batch(const BatchGroup &b, cudaStream_t s) {
+    if (b.chunks) {
+        const uint32_t blocks = (uint32_t)((b.chunks + kBlockThreads - 1) / kBlockThreads);
+        join_batch_kernel<B_CLASSIFY><<<blocks, kBlockThreads, 0, s>>>(b);
+        join_batch_kernel<B_CHAIN><<<blocks, kBlockThreads, 0, s>>>(b);
+        join_batch_kernel<B_VERIFY><<<blocks, kBlockThreads, 0, s>>>(b);
+    }
+    status_batch_kernel<<<(b.nt + kBlockThreads - 1) / kBlockThreads, kBlockThreads, 0, s>>>(b);
+}
 
 }  // namespace slpf

@@ -1,5 +1,5 @@
-// Device-side definitions shared by the parse kernels (reach.cu, join.cu,
-// merge.cu) and the host launcher (api.cu).
+// Device-side definitions shared by the parse kernels (reach_*.cu, join.cu,
+// merge.cu) and the host launchers (api.cu, batch.cu).
 //
 // Geometry of one parse (arXiv 2503.06763, Sect. 3.2, split phase):
 //   text x[0..n), n >= 1; chunks y_i = x[i*k, min((i+1)*k, n)), k a multiple of
@@ -59,6 +59,37 @@ struct Params {
     uint64_t Gfast;                 // groups g with 64g + 64 <= n (computed on the fast path)
 };
 
+// Texts of one batch that share one compiled RE (re_parse_batch).  Every
+// phase kernel of the group takes its units of work -- 32-chunk reach tiles,
+// chunks, 32-group merge tiles -- in one flat index space per kind: the
+// prefix sums below give each text's first unit, and a unit finds its text
+// by binary search.  Reach and merge tiles are handed out by atomic work
+// counters; texts come longest chunks first, so the longest reach tiles
+// start first.  A text's parameters (geometry, text, workspace and output
+// pointers) are a Params in device memory.  The group shares tables, table
+// mode and output encoding, so each block stages the tables once.
+struct BatchGroup {
+    DevTables t;
+    const Params *texts;            // [nt]
+    const uint64_t *chunk_base;     // [nt+1] chunks before each text
+    const uint64_t *rtile_base;     // [nt+1] reach tiles (32 chunks) before each text
+    const uint64_t *mtile_base;     // [nt+1] merge tiles (32 column groups) before each text
+    uint32_t *queue;                // [kQueues] work counters, zeroed before the group runs
+    uint64_t chunks, n_reach, n_merge;
+    uint32_t nt, recognize;
+};
+enum Queue { Q_REACH = 0, Q_MERGE = 1, kQueues = 4 };
+
+// The text owning flat unit j: the last text whose first unit is <= j.
+__device__ __forceinline__ uint32_t text_of(const uint64_t *base, uint32_t nt, uint64_t j) {
+    uint32_t lo = 0, hi = nt;                    // base[lo] <= j < base[hi]
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (__ldg(base + mid) <= j) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ uint32_t chunk_len(const Params &p, uint32_t i) {
     uint64_t rest = p.n - (uint64_t)i * p.k;
@@ -96,6 +127,28 @@ __device__ __forceinline__ uint4 load16(const uint8_t *x, uint64_t n, uint64_t a
 __device__ __forceinline__ uint32_t byte_of(const uint4 &v, int u) {   // u in 0..15, unrolled
     uint32_t w = (u < 4) ? v.x : (u < 8) ? v.y : (u < 12) ? v.z : v.w;
     return (w >> (8 * (u & 3))) & 0xFFu;
+}
+
+// Empty text: one column C_0 = I ∩ F, and the status.
+__device__ inline void empty_text(const Params &p) {
+    const DevTables &t = p.t;
+    const uint64_t v = t.fBits[(size_t)t.fI * t.W] & t.bBits[(size_t)t.bF * t.W];
+    bool meet = false;
+    for (uint32_t w = 0; w < t.W; ++w) meet |= (t.fBits[(size_t)t.fI * t.W + w] & t.bBits[(size_t)t.bF * t.W + w]) != 0;
+    *p.status = meet ? RE_OK : RE_REJECTED;
+    if (!p.out) return;
+    if (p.kind == RE_SLPF_DICT) {
+        const uint32_t d = meet ? t.pt[(size_t)t.fI * t.nb + t.bF] : 0u;
+        if (p.col_bytes == 2) reinterpret_cast<uint16_t *>(p.out)[0] = (uint16_t)d;
+        else reinterpret_cast<uint32_t *>(p.out)[0] = d;
+    } else {
+        switch (p.col_bytes) {
+            case 1: reinterpret_cast<uint8_t *>(p.out)[0] = (uint8_t)v; break;
+            case 2: reinterpret_cast<uint16_t *>(p.out)[0] = (uint16_t)v; break;
+            case 4: reinterpret_cast<uint32_t *>(p.out)[0] = (uint32_t)v; break;
+            default: reinterpret_cast<uint64_t *>(p.out)[0] = v; break;
+        }
+    }
 }
 
 // ---------------------------------------------------------------- tables
@@ -156,8 +209,7 @@ __host__ __device__ inline size_t tables_smem_bytes(const DevTables &t, int tm) 
 // Stage the byte-class map and the transition tables in shared memory
 // (block-wide; ends with __syncthreads).  Returns the end of the used area.
 template <int TM>
-__device__ uint8_t *stage_tables(const Params &p, uint8_t *sm, Tabs &T) {
-    const DevTables &t = p.t;
+__device__ uint8_t *stage_tables(const DevTables &t, uint8_t *sm, Tabs &T) {
     T.ncls = t.ncls;
     T.nc2 = t.ncls * t.ncls;
     T.f32 = t.fT;
@@ -210,12 +262,12 @@ __device__ uint8_t *stage_tables(const Params &p, uint8_t *sm, Tabs &T) {
 __device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
     return (uint32_t)__cvta_generic_to_shared(ptr);
 }
-// Make this thread's generic-proxy shared-memory writes visible to the async proxy.
 // Bring the 128-byte line holding addr into L2 (no register result).
 __device__ __forceinline__ void prefetch_l2(const void *addr) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(addr));
 }
 
+// Make this thread's generic-proxy shared-memory writes visible to the async proxy.
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 // 2D tiled store shared -> global (box from the tensor map), coordinates {x, y}.
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, uint32_t src, int32_t x, int32_t y) {
@@ -258,5 +310,12 @@ void launch_fixup(const Params &p, cudaStream_t s, int sm_count);
 void launch_merge(const Params &p, const CUtensorMap &out_map, cudaStream_t s, int sm_count);
 void launch_empty(const Params &p, cudaStream_t s);
 cudaError_t set_kernel_attributes();   // max dynamic shared memory, once per process
+
+// Batch launchers: one launch per phase for every text of the group.
+void launch_batch_init(const Params *texts, uint32_t nt, uint32_t *queues, uint32_t nq, cudaStream_t s);
+bool launch_reach_batch(const BatchGroup &b, uint32_t tmode, uint32_t ms, cudaStream_t s, int sm_count);
+void launch_join_batch(const BatchGroup &b, cudaStream_t s);
+void launch_fixup_batch(const BatchGroup &b, uint32_t tmode, cudaStream_t s, int sm_count);
+void launch_merge_batch(const BatchGroup &b, const Params &like, cudaStream_t s, int sm_count);
 
 }  // namespace slpf

@@ -146,85 +146,106 @@ __device__ __forceinline__ uint32_t walk_bwd(const Params &p, const Tabs &T, uin
 // One warp per chunk and direction pair: lanes 0-15 take the forward
 // direction, lanes 16-31 the backward one; lane r of a half turns records r
 // and r+16 into exact checkpoints; one lane per half walks any boundaries
-// past the record with the staged tables.
+// past the record with the staged tables.  Called by the whole warp.
+template <int TM>
+__device__ void fixup_chunk(const Params &p, const Tabs &T, uint64_t i, bool &bad) {
+    const uint32_t lane = threadIdx.x & 31, half = lane >> 4, r = lane & 15;
+    const bool fwd = half == 0;
+    const uint64_t base = i * p.k;
+    const uint32_t len = chunk_len(p, (uint32_t)i);
+    const uint32_t nsub = (len + 63) / 64;
+    const uint64_t g0 = i * p.S;
+    uint32_t conv, nrec, H;
+    bool active;
+    if (fwd) {
+        conv = p.w.fconv[i];
+        active = conv > 1;                                    // boundaries 1 .. conv-1
+        nrec = p.w.fnrec[i]; H = p.w.fhit[i];
+    } else {
+        conv = p.w.bconv[i];
+        active = !p.recognize && nsub >= 2 && conv + 1 <= nsub - 1;   // boundaries nsub-1 .. conv+1
+        nrec = p.w.bnrec[i]; H = p.w.bhit[i];
+    }
+    if (!active) nrec = 0;
+    const uint32_t *cnt_row = (fwd ? p.w.recFc : p.w.recBc) + i * kRecBounds;
+    const uint32_t c0 = r < nrec ? cnt_row[r] : 0u, c1 = r + 16 < nrec ? cnt_row[r + 16] : 0u;
+    uint32_t off0 = c0, tot = c0 + c1;                        // scans within the half
+#pragma unroll
+    for (int d = 1; d < 16; d <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, off0, d, 16);
+        if ((int)r >= d) off0 += v;
+    }
+    const uint32_t sum0 = __shfl_sync(0xFFFFFFFFu, off0, 15, 16);   // entries of records 0..15
+    uint32_t off1 = c1;
+#pragma unroll
+    for (int d = 1; d < 16; d <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, off1, d, 16);
+        if ((int)r >= d) off1 += v;
+    }
+    off0 -= c0;
+    off1 = sum0 + off1 - c1;
+    (void)tot;
+    const uint2 *ent = (fwd ? p.w.recFe : p.w.recBe) + i * kRecEntries;
+    uint32_t st0 = 0, st1 = 0;
+    if (r < nrec) {
+        st0 = record_union(p, fwd, ent + off0, c0, H, bad);
+        if (fwd) p.w.FC[g0 + r + 1] = st0;                    // record r: boundary r+1
+        else p.w.BC[g0 + (nsub - 1 - r) - 1] = st0;           // record r: boundary nsub-1-r
+    }
+    if (r + 16 < nrec) {
+        st1 = record_union(p, fwd, ent + off1, c1, H, bad);
+        if (fwd) p.w.FC[g0 + r + 17] = st1;
+        else p.w.BC[g0 + (nsub - 17 - r) - 1] = st1;
+    }
+    const uint32_t lastr = nrec > 0 ? nrec - 1 : 0;           // last record: lane lastr % 16
+    const uint32_t from = __shfl_sync(0xFFFFFFFFu, lastr >= 16 ? st1 : st0, (lastr & 15) + 16 * half, 32);
+    if (!active || r != 0) return;
+    if (fwd) {
+        if (nrec + 1 <= conv - 1) {                           // walk boundaries nrec+1 .. conv-1
+            const uint32_t start = nrec == 0 ? p.w.FJ[i] : from;
+            walk_fwd<TM>(p, T, base, 64 * nrec, 64 * (conv - 1), start,
+                         [&](uint32_t b, uint32_t s2) { p.w.FC[g0 + b / 64] = s2; });
+        }
+    } else {
+        const uint32_t bb_first = nsub - 1 - nrec;            // first boundary not recorded
+        if (bb_first > conv) {                                // walk boundaries bb_first .. conv+1
+            const uint32_t start = nrec == 0 ? p.w.BJ[i + 1] : from;
+            const uint32_t t1 = nrec == 0 ? len : 64 * (bb_first + 1);
+            walk_bwd<TM>(p, T, base, 64 * (conv + 1), t1, start,
+                         [&](uint32_t b, uint32_t s2) { p.w.BC[g0 + b / 64 - 1] = s2; });
+        }
+    }
+}
+
 template <int TM>
 __global__ void __launch_bounds__(kChunkThreads) fixup_kernel(Params p) {
     extern __shared__ __align__(16) uint8_t sm[];
     Tabs T;
-    stage_tables<TM>(p, sm, T);
+    stage_tables<TM>(p.t, sm, T);
     if (*p.status != RE_OK) return;
     bool bad = false;
-    const uint32_t lane = threadIdx.x & 31, half = lane >> 4, r = lane & 15;
-    const bool fwd = half == 0;
     const uint32_t wpb = blockDim.x / 32;
     const uint64_t nw = (uint64_t)gridDim.x * wpb;
-    for (uint64_t i = (uint64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < p.c; i += nw) {
-        const uint64_t base = i * p.k;
-        const uint32_t len = chunk_len(p, (uint32_t)i);
-        const uint32_t nsub = (len + 63) / 64;
-        const uint64_t g0 = i * p.S;
-        uint32_t conv, nrec, H;
-        bool active;
-        if (fwd) {
-            conv = p.w.fconv[i];
-            active = conv > 1;                                    // boundaries 1 .. conv-1
-            nrec = p.w.fnrec[i]; H = p.w.fhit[i];
-        } else {
-            conv = p.w.bconv[i];
-            active = !p.recognize && nsub >= 2 && conv + 1 <= nsub - 1;   // boundaries nsub-1 .. conv+1
-            nrec = p.w.bnrec[i]; H = p.w.bhit[i];
-        }
-        if (!active) nrec = 0;
-        const uint32_t *cnt_row = (fwd ? p.w.recFc : p.w.recBc) + i * kRecBounds;
-        const uint32_t c0 = r < nrec ? cnt_row[r] : 0u, c1 = r + 16 < nrec ? cnt_row[r + 16] : 0u;
-        uint32_t off0 = c0, tot = c0 + c1;                        // scans within the half
-#pragma unroll
-        for (int d = 1; d < 16; d <<= 1) {
-            const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, off0, d, 16);
-            if ((int)r >= d) off0 += v;
-        }
-        const uint32_t sum0 = __shfl_sync(0xFFFFFFFFu, off0, 15, 16);   // entries of records 0..15
-        uint32_t off1 = c1;
-#pragma unroll
-        for (int d = 1; d < 16; d <<= 1) {
-            const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, off1, d, 16);
-            if ((int)r >= d) off1 += v;
-        }
-        off0 -= c0;
-        off1 = sum0 + off1 - c1;
-        (void)tot;
-        const uint2 *ent = (fwd ? p.w.recFe : p.w.recBe) + i * kRecEntries;
-        uint32_t st0 = 0, st1 = 0;
-        if (r < nrec) {
-            st0 = record_union(p, fwd, ent + off0, c0, H, bad);
-            if (fwd) p.w.FC[g0 + r + 1] = st0;                    // record r: boundary r+1
-            else p.w.BC[g0 + (nsub - 1 - r) - 1] = st0;           // record r: boundary nsub-1-r
-        }
-        if (r + 16 < nrec) {
-            st1 = record_union(p, fwd, ent + off1, c1, H, bad);
-            if (fwd) p.w.FC[g0 + r + 17] = st1;
-            else p.w.BC[g0 + (nsub - 17 - r) - 1] = st1;
-        }
-        const uint32_t lastr = nrec > 0 ? nrec - 1 : 0;           // last record: lane lastr % 16
-        const uint32_t from = __shfl_sync(0xFFFFFFFFu, lastr >= 16 ? st1 : st0, (lastr & 15) + 16 * half, 32);
-        if (!active || r != 0) continue;
-        if (fwd) {
-            if (nrec + 1 <= conv - 1) {                           // walk boundaries nrec+1 .. conv-1
-                const uint32_t start = nrec == 0 ? p.w.FJ[i] : from;
-                walk_fwd<TM>(p, T, base, 64 * nrec, 64 * (conv - 1), start,
-                             [&](uint32_t b, uint32_t s2) { p.w.FC[g0 + b / 64] = s2; });
-            }
-        } else {
-            const uint32_t bb_first = nsub - 1 - nrec;            // first boundary not recorded
-            if (bb_first > conv) {                                // walk boundaries bb_first .. conv+1
-                const uint32_t start = nrec == 0 ? p.w.BJ[i + 1] : from;
-                const uint32_t t1 = nrec == 0 ? len : 64 * (bb_first + 1);
-                walk_bwd<TM>(p, T, base, 64 * (conv + 1), t1, start,
-                             [&](uint32_t b, uint32_t s2) { p.w.BC[g0 + b / 64 - 1] = s2; });
-            }
-        }
-    }
+    for (uint64_t i = (uint64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < p.c; i += nw) fixup_chunk<TM>(p, T, i, bad);
     if (bad) atomicExch(p.status, RE_E_INTERNAL);
+}
+
+// Batch: warps take the flat chunks of every text of the group in turn.
+template <int TM>
+__global__ void __launch_bounds__(kChunkThreads) fixup_batch_kernel(const __grid_constant__ BatchGroup b) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    Tabs T;
+    stage_tables<TM>(b.t, sm, T);
+    const uint32_t wpb = blockDim.x / 32;
+    const uint64_t nw = (uint64_t)gridDim.x * wpb;
+    for (uint64_t j = (uint64_t)blockIdx.x * wpb + (threadIdx.x >> 5); j < b.chunks; j += nw) {
+        const uint32_t ti = text_of(b.chunk_base, b.nt, j);
+        const Params &p = b.texts[ti];
+        if (*p.status != RE_OK) continue;                         // warp-uniform: one text per warp
+        bool bad = false;
+        fixup_chunk<TM>(p, T, j - b.chunk_base[ti], bad);
+        if (bad) atomicExch(p.status, RE_E_INTERNAL);
+    }
 }
 
 // ------------------------------------------------------------------ encodings
@@ -441,33 +462,17 @@ __device__ void group_tail(const Params &p, const Tabs &T, const Enc &e, uint64_
     }
 }
 
-// Persistent grid: each warp takes tiles of 32 consecutive column groups
-// (lane = group).  With TMA the warp's tile of outputs is written to shared
-// memory and stored with one tensor-store per tile.
-template <int TM, int E, bool TMA>
-__global__ void __launch_bounds__(kBlockThreads, 3)
-    merge_kernel(const __grid_constant__ Params p, const __grid_constant__ CUtensorMap out_map) {
-    using St = typename std::conditional<TM != TM_GLOBAL, uint16_t, uint32_t>::type;
-    constexpr int CB = bytes_of(E);
-    constexpr uint32_t ROWB = 64 * CB;                        // output bytes of one group
-    constexpr uint32_t WPB = kBlockThreads / 32;
-    extern __shared__ __align__(16) uint8_t sm[];
-    uint8_t *base = sm;
-    uint8_t *tiles = nullptr;
-    if constexpr (TMA) {                                      // warp tiles, 1024-byte aligned for the swizzle
-        const uint32_t a = smem_u32(sm);
-        tiles = sm + ((1024 - (a & 1023)) & 1023);
-        base = tiles + WPB * 32 * ROWB;
-    }
-    Tabs T;
-    uint8_t *rest = stage_tables<TM>(p, base, T);
-    St *stage = reinterpret_cast<St *>(rest);                 // [2][32][kBlockThreads] (one-byte tables)
+// Shared-memory set-up of a merge block: staged tables, the per-thread state
+// stage (one-byte tables) and the encoder (pair table or segment bitsets).
+template <int TM, int E, typename St>
+__device__ void merge_setup(const DevTables &t, uint32_t pt_in_smem, uint8_t *base, Tabs &T, St *&stage, Enc &e) {
+    uint8_t *rest = stage_tables<TM>(t, base, T);
+    stage = reinterpret_cast<St *>(rest);                     // [2][32][kBlockThreads] (one-byte tables)
     if (TM != TM_PAIR) rest += (2 * 32 * kBlockThreads * sizeof(St) + 15) & ~(size_t)15;
-    Enc e{};
-    const DevTables &t = p.t;
+    e = Enc{};
     e.nb = t.nb;
     if (E == ENC_X2 || E == ENC_X4) {
-        if (p.pt_in_smem) {
+        if (pt_in_smem) {
             const size_t cnt = (size_t)t.nf * t.nb;
             if (E == ENC_X2) {
                 uint16_t *pt = reinterpret_cast<uint16_t *>(rest);
@@ -489,6 +494,60 @@ __global__ void __launch_bounds__(kBlockThreads, 3)
         e.fbits = fb; e.bbits = bb;
     }
     __syncthreads();
+}
+
+// Columns of group g of one text (this lane's group of its warp's tile).
+template <int TM, int E, bool TMA, typename St>
+__device__ __forceinline__ void merge_group(const Params &p, const Tabs &T, const Enc &e, St *stage, uint64_t g,
+                                            bool ok, bool &bad, const Sink<TMA, bytes_of(E)> &out) {
+    constexpr uint32_t ROWB = 64 * bytes_of(E);
+    if (g >= p.Gc) return;
+    if (!ok) {                                                // rejected text: every column is empty
+        if (TMA && g < p.Gfast) {
+#pragma unroll
+            for (int v = 0; v < (int)(ROWB / 16); ++v) out.put(v, make_uint4(0, 0, 0, 0));
+        } else {
+            const uint64_t pos = g * 64;
+            const uint64_t nleft = p.n + 1 - pos;
+            const uint32_t ncol = nleft < 64 ? (uint32_t)nleft : 64u;
+            for (uint32_t u = 0; u < ncol; ++u) store_col<E>(p.out, pos + u, 0);
+        }
+    } else if (g < p.Gfast) {
+        if constexpr (TM == TM_PAIR)
+            group_full_pair<E, TMA>(p, T, e, g, bad, out);
+        else
+            group_full<TM, E, TMA, St>(p, T, e, g, bad, stage + threadIdx.x, stage + 32 * kBlockThreads + threadIdx.x,
+                                       out);
+    } else {
+        group_tail<TM, E>(p, T, e, g, bad);
+    }
+}
+
+template <int TM>
+using StOf = typename std::conditional<TM != TM_GLOBAL, uint16_t, uint32_t>::type;
+
+// Persistent grid: each warp takes tiles of 32 consecutive column groups
+// (lane = group).  With TMA the warp's tile of outputs is written to shared
+// memory and stored with one tensor-store per tile.
+template <int TM, int E, bool TMA>
+__global__ void __launch_bounds__(kBlockThreads, 3)
+    merge_kernel(const __grid_constant__ Params p, const __grid_constant__ CUtensorMap out_map) {
+    using St = StOf<TM>;
+    constexpr int CB = bytes_of(E);
+    constexpr uint32_t ROWB = 64 * CB;                        // output bytes of one group
+    constexpr uint32_t WPB = kBlockThreads / 32;
+    extern __shared__ __align__(16) uint8_t sm[];
+    uint8_t *base = sm;
+    uint8_t *tiles = nullptr;
+    if constexpr (TMA) {                                      // warp tiles, 1024-byte aligned for the swizzle
+        const uint32_t a = smem_u32(sm);
+        tiles = sm + ((1024 - (a & 1023)) & 1023);
+        base = tiles + WPB * 32 * ROWB;
+    }
+    Tabs T;
+    St *stage;
+    Enc e;
+    merge_setup<TM, E, St>(p.t, p.pt_in_smem, base, T, stage, e);
     const bool ok = *p.status == RE_OK;
     bool bad = false;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -507,27 +566,7 @@ __global__ void __launch_bounds__(kBlockThreads, 3)
         }
         Sink<TMA, CB> out{reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(p.out) + g * ROWB),
                           TMA ? tile + lane * ROWB : nullptr, lane};
-        if (g < p.Gc) {
-            if (!ok) {                                        // rejected text: every column is empty
-                if (TMA && g < p.Gfast) {
-#pragma unroll
-                    for (int v = 0; v < (int)(ROWB / 16); ++v) out.put(v, make_uint4(0, 0, 0, 0));
-                } else {
-                    const uint64_t pos = g * 64;
-                    const uint64_t nleft = p.n + 1 - pos;
-                    const uint32_t ncol = nleft < 64 ? (uint32_t)nleft : 64u;
-                    for (uint32_t u = 0; u < ncol; ++u) store_col<E>(p.out, pos + u, 0);
-                }
-            } else if (g < p.Gfast) {
-                if constexpr (TM == TM_PAIR)
-                    group_full_pair<E, TMA>(p, T, e, g, bad, out);
-                else
-                    group_full<TM, E, TMA, St>(p, T, e, g, bad, stage + threadIdx.x,
-                                               stage + 32 * kBlockThreads + threadIdx.x, out);
-            } else {
-                group_tail<TM, E>(p, T, e, g, bad);
-            }
-        }
+        merge_group<TM, E, TMA, St>(p, T, e, stage, g, ok, bad, out);
         if constexpr (TMA) {
             fence_async_smem();
             __syncwarp();
@@ -541,27 +580,37 @@ __global__ void __launch_bounds__(kBlockThreads, 3)
     if (bad) atomicExch(p.status, RE_E_INTERNAL);
 }
 
-// Empty text: one column C_0 = I ∩ F.
-__global__ void empty_text_kernel(Params p) {
-    const DevTables &t = p.t;
-    const uint64_t v = t.fBits[(size_t)t.fI * t.W] & t.bBits[(size_t)t.bF * t.W];
-    bool meet = false;
-    for (uint32_t w = 0; w < t.W; ++w) meet |= (t.fBits[(size_t)t.fI * t.W + w] & t.bBits[(size_t)t.bF * t.W + w]) != 0;
-    *p.status = meet ? RE_OK : RE_REJECTED;
-    if (!p.out) return;
-    if (p.kind == RE_SLPF_DICT) {
-        const uint32_t d = meet ? t.pt[(size_t)t.fI * t.nb + t.bF] : 0u;
-        if (p.col_bytes == 2) reinterpret_cast<uint16_t *>(p.out)[0] = (uint16_t)d;
-        else reinterpret_cast<uint32_t *>(p.out)[0] = d;
-    } else {
-        switch (p.col_bytes) {
-            case 1: reinterpret_cast<uint8_t *>(p.out)[0] = (uint8_t)v; break;
-            case 2: reinterpret_cast<uint16_t *>(p.out)[0] = (uint16_t)v; break;
-            case 4: reinterpret_cast<uint32_t *>(p.out)[0] = (uint32_t)v; break;
-            default: reinterpret_cast<uint64_t *>(p.out)[0] = v; break;
-        }
+// Batch: warps take 32-group tiles of any text of the group from the work
+// list; outputs leave through plain 16-byte stores.
+template <int TM, int E>
+__global__ void __launch_bounds__(kBlockThreads, 3) merge_batch_kernel(const __grid_constant__ BatchGroup b,
+                                                                       uint32_t pt_in_smem) {
+    using St = StOf<TM>;
+    constexpr uint32_t ROWB = 64 * bytes_of(E);
+    extern __shared__ __align__(16) uint8_t sm[];
+    Tabs T;
+    St *stage;
+    Enc e;
+    merge_setup<TM, E, St>(b.t, pt_in_smem, sm, T, stage, e);
+    const uint32_t lane = threadIdx.x & 31;
+    for (;;) {
+        uint32_t tile = 0;
+        if (lane == 0) tile = atomicAdd(b.queue + Q_MERGE, 1u);
+        tile = __shfl_sync(0xFFFFFFFFu, tile, 0);
+        if (tile >= b.n_merge) break;
+        const uint32_t ti = text_of(b.mtile_base, b.nt, tile);
+        const Params &p = b.texts[ti];
+        const bool ok = *p.status == RE_OK;
+        const uint64_t g = (tile - b.mtile_base[ti]) * 32 + lane;
+        bool bad = false;
+        Sink<false, bytes_of(E)> out{reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(p.out) + g * ROWB), nullptr,
+                                     lane};
+        merge_group<TM, E, false, St>(p, T, e, stage, g, ok, bad, out);
+        if (bad) atomicExch(p.status, RE_E_INTERNAL);
     }
 }
+
+__global__ void empty_text_kernel(Params p) { empty_text(p); }
 
 template <typename K>
 int grid_for(K kernel, size_t smem, uint64_t items, int sm_count, uint32_t threads) {
@@ -607,6 +656,47 @@ void merge_enc(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_c
     }
 }
 
+template <int TM, int E>
+void merge_batch_one(const BatchGroup &b, const Params &like, cudaStream_t s, int sm_count) {
+    Params q = like;
+    q.out_tma = 0;
+    const size_t smem = tables_smem_bytes(b.t, TM) + merge_extra_smem(q);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(merge_batch_kernel<TM, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    const int blocks = grid_for(merge_batch_kernel<TM, E>, smem, (uint64_t)b.n_merge * 32, sm_count, kBlockThreads);
+    merge_batch_kernel<TM, E><<<blocks, kBlockThreads, smem, s>>>(b, q.pt_in_smem);
+}
+
+template <int TM>
+void merge_batch_enc(const BatchGroup &b, const Params &like, cudaStream_t s, int sm_count) {
+    if (like.kind == RE_SLPF_DICT) {
+        if (like.col_bytes == 2) merge_batch_one<TM, ENC_X2>(b, like, s, sm_count);
+        else merge_batch_one<TM, ENC_X4>(b, like, s, sm_count);
+    } else {
+        switch (like.col_bytes) {
+            case 1: merge_batch_one<TM, ENC_D1>(b, like, s, sm_count); break;
+            case 2: merge_batch_one<TM, ENC_D2>(b, like, s, sm_count); break;
+            case 4: merge_batch_one<TM, ENC_D4>(b, like, s, sm_count); break;
+            default: merge_batch_one<TM, ENC_D8>(b, like, s, sm_count); break;
+        }
+    }
+}
+
+template <int TM>
+void fixup_batch_one(const BatchGroup &b, cudaStream_t s, int sm_count) {
+    const size_t smem = tables_smem_bytes(b.t, TM);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(fixup_batch_kernel<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    fixup_batch_kernel<TM><<<grid_for(fixup_batch_kernel<TM>, smem, b.chunks * 32, sm_count, kChunkThreads),
+                             kChunkThreads, smem, s>>>(b);
+}
+
 template <int TM>
 void fixup_one(const Params &p, cudaStream_t s, int sm_count) {
     const size_t smem = tables_smem_bytes(p.t, TM);
@@ -643,5 +733,19 @@ void launch_merge(const Params &p, const CUtensorMap &map, cudaStream_t s, int s
 }
 
 void launch_empty(const Params &p, cudaStream_t s) { empty_text_kernel<<<1, 1, 0, s>>>(p); }
+
+void launch_fixup_batch(const BatchGroup &b, uint32_t tmode, cudaStream_t s, int sm_count) {
+    if (b.recognize || !b.chunks) return;
+    if (tmode == TM_PAIR) fixup_batch_one<TM_PAIR>(b, s, sm_count);
+    else if (tmode == TM_SMEM) fixup_batch_one<TM_SMEM>(b, s, sm_count);
+    else fixup_batch_one<TM_GLOBAL>(b, s, sm_count);
+}
+
+void launch_merge_batch(const BatchGroup &b, const Params &like, cudaStream_t s, int sm_count) {
+    if (b.recognize || !b.n_merge) return;
+    if (like.tmode == TM_PAIR) merge_batch_enc<TM_PAIR>(b, like, s, sm_count);
+    else if (like.tmode == TM_SMEM) merge_batch_enc<TM_SMEM>(b, like, s, sm_count);
+    else merge_batch_enc<TM_GLOBAL>(b, like, s, sm_count);
+}
 
 }  // namespace slpf

@@ -6,12 +6,24 @@ bool launch_reach_global(const Params &p, const CUtensorMap &map, cudaStream_t s
     return reach::launch_ms<TM_GLOBAL>(p, map, s, ms, sm_count);
 }
 
+bool launch_reach_batch_global(const BatchGroup &b, cudaStream_t s, uint32_t ms, int sm_count) {
+    return reach::launch_ms_batch<TM_GLOBAL>(b, s, ms, sm_count);
+}
+
 bool launch_reach_pair(const Params &p, const CUtensorMap &map, cudaStream_t s, uint32_t ms, int sm_count);
+bool launch_reach_batch_pair(const BatchGroup &b, cudaStream_t s, uint32_t ms, int sm_count);
+bool launch_reach_batch_smem(const BatchGroup &b, cudaStream_t s, uint32_t ms, int sm_count);
 bool launch_reach_smem(const Params &p, const CUtensorMap &map, cudaStream_t s, uint32_t ms, int sm_count);
 
 bool launch_reach(const Params &p, const CUtensorMap &map, cudaStream_t s, uint32_t ms, int sm_count) {
     if (p.tmode == TM_PAIR) return launch_reach_pair(p, map, s, ms, sm_count);
     if (p.tmode == TM_SMEM) return launch_reach_smem(p, map, s, ms, sm_count);
     return launch_reach_global(p, map, s, ms, sm_count);
+}
+
+bool launch_reach_batch(const BatchGroup &b, uint32_t tmode, uint32_t ms, cudaStream_t s, int sm_count) {
+    if (tmode == TM_PAIR) return launch_reach_batch_pair(b, s, ms, sm_count);
+    if (tmode == TM_SMEM) return launch_reach_batch_smem(b, s, ms, sm_count);
+    return launch_reach_batch_global(b, s, ms, sm_count);
 }
 }  // namespace slpf

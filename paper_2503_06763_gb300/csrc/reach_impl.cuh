@@ -90,12 +90,12 @@ struct Ring {
     uint32_t phase;       // bit s: parity of the next completion of stage s
 };
 
-__device__ __forceinline__ void ring_issue(const Params &p, const CUtensorMap &map, const Ring &r, int s,
+__device__ __forceinline__ void ring_issue(const Params &p, const CUtensorMap *map, const Ring &r, int s,
                                            uint32_t i0, uint32_t fb, uint32_t bb, bool bwd) {
     const uint32_t bar = r.bars + 8 * s;
     mbar_expect_tx(bar, bwd ? 2 * kTileBytes : kTileBytes);
-    tma_load_2d(smem_u32(r.tiles + (2 * s) * kTileBytes), &map, 64 * fb, (int32_t)i0, bar);
-    if (bwd) tma_load_2d(smem_u32(r.tiles + (2 * s + 1) * kTileBytes), &map, 64 * bb, (int32_t)i0, bar);
+    tma_load_2d(smem_u32(r.tiles + (2 * s) * kTileBytes), map, 64 * fb, (int32_t)i0, bar);
+    if (bwd) tma_load_2d(smem_u32(r.tiles + (2 * s + 1) * kTileBytes), map, 64 * bb, (int32_t)i0, bar);
 }
 
 // Fill this lane's rows of stage s with plain loads (warps TMA cannot serve:
@@ -184,7 +184,7 @@ __device__ __forceinline__ unsigned block_lanes(const Params &p, uint32_t i, uin
 }
 
 template <int TM, int MS>
-__device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CUtensorMap &map, Ring &ring,
+__device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CUtensorMap *map, Ring &ring,
                             bool tma) {
     const DevTables &t = p.t;
     const uint64_t base = (uint64_t)i * p.k;
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kChunkThreads)
     reach_kernel(const __grid_constant__ Params p, const __grid_constant__ CUtensorMap map) {
     extern __shared__ __align__(16) uint8_t sm[];
     Tabs T;
-    uint8_t *rest = stage_tables<TM>(p, sm, T);
+    uint8_t *rest = stage_tables<TM>(p.t, sm, T);
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x / 32;
     Ring ring{};
     {
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(kChunkThreads)
         const uint32_t i = (uint32_t)(t * 32) + lane;
         const bool tma = p.text_tma && t * 32 + 32 <= p.c_full;
         if (i >= p.c) continue;                               // lanes past the text (plain path only)
-        if (!reach_chunk<TM, MS>(p, T, i, map, ring, tma)) {
+        if (!reach_chunk<TM, MS>(p, T, i, &map, ring, tma)) {
             atomicExch(p.status, RE_E_INTERNAL);
             atomicExch(&p.w.flags[FLAG_INTERNAL], 1);
             for (int st = 0; st < kStages; ++st) {            // drain: bounded wait on every stage
@@ -341,9 +341,69 @@ __global__ void __launch_bounds__(kChunkThreads)
     }
 }
 
+// Batch: warps take 32-chunk tiles of any text of the group from the work
+// list (an atomic counter); text bytes come in by plain loads.  Lanes past
+// their text's last chunk skip the tile and meet the others at the closing
+// __syncwarp, so no lane waits in a collective that the others do not run.
+template <int TM, int MS>
+__global__ void __launch_bounds__(kChunkThreads) reach_batch_kernel(const __grid_constant__ BatchGroup b) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    Tabs T;
+    uint8_t *rest = stage_tables<TM>(b.t, sm, T);
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    Ring ring{};
+    {
+        const uint32_t a = smem_u32(rest);
+        uint8_t *aligned = rest + ((1024 - (a & 1023)) & 1023);
+        ring.tiles = aligned + warp * (kStages * 2 * kTileBytes);
+    }
+    for (;;) {
+        uint32_t tile = 0;
+        if (lane == 0) tile = atomicAdd(b.queue + Q_REACH, 1u);
+        tile = __shfl_sync(0xFFFFFFFFu, tile, 0);
+        if (tile >= b.n_reach) break;
+        const uint32_t ti = text_of(b.rtile_base, b.nt, tile);
+        const Params &p = b.texts[ti];
+        const uint32_t i = (uint32_t)(tile - b.rtile_base[ti]) * 32 + lane;
+        if (i < p.c && !reach_chunk<TM, MS>(p, T, i, nullptr, ring, false)) atomicExch(&p.w.flags[FLAG_INTERNAL], 1);
+        __syncwarp();
+    }
+}
+
+inline size_t reach_smem(const DevTables &t, int tm) {
+    return tables_smem_bytes(t, tm) + 1024 + (kChunkThreads / 32) * (kStages * 2 * kTileBytes + kStages * 8);
+}
+
+template <int TM, int MS>
+void launch_batch_one(const BatchGroup &b, cudaStream_t s, int sm_count) {
+    const size_t smem = reach_smem(b.t, TM);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(reach_batch_kernel<TM, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_batch_kernel<TM, MS>, kChunkThreads, smem);
+    const uint64_t want = ((uint64_t)b.n_reach + kChunkThreads / 32 - 1) / (kChunkThreads / 32);
+    const uint64_t blocks = std::min<uint64_t>(want, (uint64_t)std::max(per_sm, 1) * sm_count);
+    reach_batch_kernel<TM, MS><<<(uint32_t)std::max<uint64_t>(blocks, 1), kChunkThreads, smem, s>>>(b);
+}
+
+template <int TM>
+bool launch_ms_batch(const BatchGroup &b, cudaStream_t s, uint32_t ms, int sm_count) {
+    constexpr bool FULL = TM != TM_GLOBAL;
+    if (FULL && ms <= 2) launch_batch_one<TM, 2>(b, s, sm_count);
+    else if (FULL && ms <= 4) launch_batch_one<TM, 4>(b, s, sm_count);
+    else if (ms <= 8) launch_batch_one<TM, 8>(b, s, sm_count);
+    else if (FULL && ms <= 16) launch_batch_one<TM, 16>(b, s, sm_count);
+    else if (ms <= 32) launch_batch_one<TM, 32>(b, s, sm_count);
+    else return false;
+    return true;
+}
+
 template <int TM, int MS>
 void launch_one(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
-    const size_t smem = tables_smem_bytes(p.t, TM) + 1024 + (kChunkThreads / 32) * (kStages * 2 * kTileBytes + kStages * 8);
+    const size_t smem = reach_smem(p.t, TM);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(reach_kernel<TM, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -5,4 +5,7 @@ namespace slpf {
 bool launch_reach_pair(const Params &p, const CUtensorMap &map, cudaStream_t s, uint32_t ms, int sm_count) {
     return reach::launch_ms<TM_PAIR>(p, map, s, ms, sm_count);
 }
+bool launch_reach_batch_pair(const BatchGroup &b, cudaStream_t s, uint32_t ms, int sm_count) {
+    return reach::launch_ms_batch<TM_PAIR>(b, s, ms, sm_count);
+}
 }  // namespace slpf

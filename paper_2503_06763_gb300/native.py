@@ -23,7 +23,9 @@ RE_COMPILE_HOST_ONLY = 1
 RE_PARSE_RECOGNIZE_ONLY = 1
 
 EXPORTS = ["re_compile", "re_free", "re_get_info", "re_segment_name", "re_dict_copy",
-           "re_slpf_layout", "re_workspace_size", "re_parse", "re_parse_static", "re_last_error"]
+           "re_slpf_layout", "re_workspace_size", "re_parse", "re_batch_plan", "re_batch_workspace_size",
+           "re_batch_chunk_len", "re_parse_batch", "re_batch_run", "re_batch_free", "re_parse_static",
+           "re_last_error"]
 RE_STATIC_SCRATCH_BYTES = 64 << 20
 
 
@@ -86,6 +88,19 @@ def load():
     lib.re_workspace_size.restype = i32
     lib.re_parse.argtypes = [vp, vp, u64, vp, ctypes.POINTER(Slpf), vp, u64, ctypes.POINTER(ParseOpts)]
     lib.re_parse.restype = i32
+    lib.re_batch_plan.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(u64), u32, ctypes.POINTER(ParseOpts),
+                                  ctypes.POINTER(vp)]
+    lib.re_batch_plan.restype = i32
+    lib.re_batch_workspace_size.argtypes = [vp, ctypes.POINTER(u64)]
+    lib.re_batch_workspace_size.restype = i32
+    lib.re_batch_chunk_len.argtypes = [vp, u32, ctypes.POINTER(u32)]
+    lib.re_batch_chunk_len.restype = i32
+    lib.re_parse_batch.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(Slpf), vp, u64, vp]
+    lib.re_parse_batch.restype = i32
+    lib.re_batch_run.argtypes = [vp, vp]
+    lib.re_batch_run.restype = i32
+    lib.re_batch_free.argtypes = [vp]
+    lib.re_batch_free.restype = None
     lib.re_parse_static.argtypes = [vp, vp, u64, vp, ctypes.POINTER(Slpf), ctypes.POINTER(ParseOpts)]
     lib.re_parse_static.restype = i32
     lib.re_last_error.argtypes = []
@@ -230,3 +245,92 @@ class Regex:
         d = self.dictionary()
         table = np.concatenate([np.zeros((1, self.words), dtype=np.uint64), d], axis=0)
         return table[idx]
+
+
+class Batch:
+    """A planned batch (re_batch_plan): texts j of lens[j] bytes, each under
+    regexes[j].  ``parse`` binds CUDA tensors and enqueues every phase as one
+    launch per RE; ``run`` re-enqueues the kernels over the same buffers."""
+
+    def __init__(self, regexes, lens, kind: str = "auto", chunk_len: int = 0, recognize_only: bool = False):
+        self.regexes = list(regexes)
+        self.lens = [int(n) for n in lens]
+        if len(self.regexes) != len(self.lens):
+            raise ValueError("one length per regex")
+        self.count = len(self.lens)
+        self.recognize_only = recognize_only
+        self.kind = kind
+        hs = (ctypes.c_void_p * max(self.count, 1))(*[r._h for r in self.regexes])
+        ls = (ctypes.c_uint64 * max(self.count, 1))(*self.lens)
+        flags = RE_PARSE_RECOGNIZE_ONLY if recognize_only else 0
+        opts = ParseOpts(KINDS[kind], chunk_len, flags, 0, None)
+        b = ctypes.c_void_p()
+        check(load().re_batch_plan(hs, ls, self.count, ctypes.byref(opts), ctypes.byref(b)))
+        self._b = b
+        w = ctypes.c_uint64()
+        check(load().re_batch_workspace_size(self._b, ctypes.byref(w)))
+        self.workspace_size = w.value
+        self._keep = None
+
+    def chunk_len(self, j: int) -> int:
+        k = ctypes.c_uint32()
+        check(load().re_batch_chunk_len(self._b, j, ctypes.byref(k)))
+        return k.value
+
+    def parse(self, texts, outs=None, status=None, workspace=None, stream=None):
+        """texts: CUDA uint8 tensors (16-byte aligned).  Returns (outs, status,
+        kinds): per text a column tensor (None in recognizer mode), one int32
+        status word per text, and the encoding name per text."""
+        import torch
+        if len(texts) != self.count:
+            raise ValueError("one text per planned length")
+        dev = texts[0].device if self.count else torch.device("cuda", torch.cuda.current_device())
+        kinds, specs = [], []
+        for rx, n, t in zip(self.regexes, self.lens, texts):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.uint8 and t.numel() == n):
+                raise TypeError("each text must be a CUDA uint8 tensor of its planned length")
+            if self.recognize_only:
+                kinds.append(None)
+                specs.append((0, 1))
+            else:
+                kname, cb, _ = rx.layout(n, self.kind)
+                kinds.append(kname)
+                specs.append((KINDS[kname], cb))
+        if outs is None:
+            dts = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}
+            outs = [None if self.recognize_only else torch.empty(n + 1, dtype=dts[cb], device=dev)
+                    for n, (_, cb) in zip(self.lens, specs)]
+        if status is None:
+            status = torch.empty(max(self.count, 1), dtype=torch.int32, device=dev)
+        if workspace is None or workspace.numel() < self.workspace_size:
+            workspace = torch.empty(max(self.workspace_size, 256), dtype=torch.uint8, device=dev)
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        arr = (Slpf * max(self.count, 1))()
+        ptrs = (ctypes.c_void_p * max(self.count, 1))()
+        for j in range(self.count):
+            o = outs[j]
+            k, cb = specs[j]
+            arr[j] = Slpf(k, cb, 0, o.data_ptr() if o is not None else None,
+                          o.numel() * o.element_size() if o is not None else 0, status.data_ptr() + 4 * j)
+            ptrs[j] = texts[j].data_ptr() if self.lens[j] else None
+        check(load().re_parse_batch(self._b, ptrs, arr, workspace.data_ptr(), workspace.numel(),
+                                    ctypes.c_void_p(s.cuda_stream)))
+        self._keep = (list(texts), outs, status, workspace)     # bound buffers stay alive with the batch
+        return outs, status, kinds
+
+    def run(self, stream=None):
+        """Enqueue the kernels again over the buffers bound by ``parse``."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        check(load().re_batch_run(self._b, ctypes.c_void_p(s.cuda_stream)))
+
+    def close(self):
+        if getattr(self, "_b", None):
+            load().re_batch_free(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
