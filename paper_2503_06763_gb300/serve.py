@@ -1,0 +1,230 @@
+"""Serving loop: continuous batching of parse requests on one GPU.
+
+Compiled automata stay resident on the device (one ``Regex`` per RE).
+Requests -- (RE index, text bytes) -- are admitted as they arrive into the
+next free *slot*.  A slot owns a CUDA stream, a device arena and pinned host
+staging buffers, all allocated once when the server starts.  A request joins
+a slot's batch only if its device footprint fits in the slot's arena:
+
+    text + SLPF columns + its share of the batch workspace.
+
+So the device memory a request's SLPF output needs is what admits it.  Each
+slot runs one ``re_parse_batch`` over its requests:
+
+    one host->device copy of all their texts,
+    the batch kernels (one launch per phase and RE),
+    one device->host copy of all their columns and status words.
+
+While a slot is on the GPU, requests that arrive meanwhile fill the other
+slots.  Their work overlaps on the device, and a slot is reused as soon as
+its event completes.
+
+Every request gets back the same bytes as ``Regex.parse`` on its text alone:
+the batch kernels compute each text independently.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .native import Batch, Regex
+
+
+def _align(v: int, a: int = 256) -> int:
+    return (v + a - 1) // a * a
+
+
+@dataclass
+class Request:
+    rid: int
+    re_index: int
+    text: np.ndarray                 # host bytes (uint8)
+    arrival: float = 0.0             # seconds on the server clock
+    done: float = 0.0
+    status: int = -100
+    cols: np.ndarray | None = None   # host copy of the SLPF columns
+    kind: str = ""
+
+
+@dataclass
+class _Slot:
+    stream: object
+    arena: object                    # device uint8
+    pin_in: object                   # pinned host uint8 (texts)
+    pin_out: object                  # pinned host uint8 (columns + status words)
+    event: object = None
+    reqs: list = field(default_factory=list)
+    batch: Batch | None = None
+    views: list = field(default_factory=list)
+
+
+class Server:
+    """Continuous-batching request loop over resident compiled REs."""
+
+    def __init__(self, patterns, slots: int = 4, arena_bytes: int = 2 << 30, max_batch: int = 4096,
+                 device=None):
+        import torch
+        self.torch = torch
+        self.dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.regexes = [p if isinstance(p, Regex) else Regex(p) for p in patterns]
+        self.max_batch = max_batch
+        self.arena_bytes = arena_bytes
+        self.slots = []
+        for _ in range(slots):
+            self.slots.append(_Slot(
+                stream=torch.cuda.Stream(self.dev),
+                arena=torch.empty(arena_bytes, dtype=torch.uint8, device=self.dev),
+                pin_in=torch.empty(arena_bytes // 4, dtype=torch.uint8).pin_memory(),
+                pin_out=torch.empty(arena_bytes // 2, dtype=torch.uint8).pin_memory()))
+        self.stats = {"batches": 0, "requests": 0, "max_batch": 0, "max_inflight": 0}
+
+    # ------------------------------------------------------------------ sizing
+    def _layout(self, re_index: int, n: int):
+        rx = self.regexes[re_index]
+        kname, cb, nbytes = rx.layout(n, "auto")
+        return kname, cb, nbytes
+
+    def footprint(self, req: Request) -> tuple[int, int, int]:
+        """(device bytes, pinned-in bytes, pinned-out bytes) a request needs,
+        with an upper bound on its workspace share (the single-text size)."""
+        n = len(req.text)
+        _, cb, nbytes = self._layout(req.re_index, n)
+        ws = self.regexes[req.re_index].workspace_size(n)
+        # the batch descriptors (parameters and prefix sums) take under 1 KiB a text
+        return _align(n) + _align(nbytes) + _align(ws) + 1024, _align(n), _align(nbytes)
+
+    def fits_alone(self, req: Request) -> bool:
+        d, i, o = self.footprint(req)
+        s = self.slots[0]
+        return d + (1 << 20) <= self.arena_bytes and i <= s.pin_in.numel() and o + 4096 <= s.pin_out.numel()
+
+    # ------------------------------------------------------------------ one slot
+    def _launch(self, slot: _Slot, reqs: list):
+        torch = self.torch
+        lens = [len(r.text) for r in reqs]
+        b = Batch([self.regexes[r.re_index] for r in reqs], lens)
+        # arena: [texts][columns][status words][workspace]
+        offs_t, o = [], 0
+        for n in lens:
+            offs_t.append(o)
+            o += _align(n)
+        text_end = o
+        offs_c, kinds, cbs = [], [], []
+        for r, n in zip(reqs, lens):
+            kname, cb, nbytes = self._layout(r.re_index, n)
+            offs_c.append(o)
+            kinds.append(kname)
+            cbs.append(cb)
+            o += _align(nbytes)
+        st_off = o
+        o += _align(4 * len(reqs))
+        out_end = o
+        ws_off = o
+        if ws_off + b.workspace_size > self.arena_bytes or text_end > slot.pin_in.numel() \
+                or out_end - text_end > slot.pin_out.numel():
+            b.close()
+            raise RuntimeError("slot arena too small for the admitted batch")
+        # texts into pinned staging, one copy to the device
+        pin_in = slot.pin_in.numpy()
+        for r, ot in zip(reqs, offs_t):
+            pin_in[ot:ot + len(r.text)] = r.text
+        dt = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}
+        A = slot.arena
+        texts = [A[ot:ot + n] for ot, n in zip(offs_t, lens)]
+        outs = [A[oc:oc + (n + 1) * cb].view(dt[cb]) for oc, n, cb in zip(offs_c, lens, cbs)]
+        status = A[st_off:st_off + 4 * len(reqs)].view(torch.int32)
+        ws = A[ws_off:ws_off + max(b.workspace_size, 256)]
+        with torch.cuda.stream(slot.stream):
+            if text_end:
+                A[:text_end].copy_(slot.pin_in[:text_end], non_blocking=True)
+            b.parse(texts, outs=outs, status=status, workspace=ws, stream=slot.stream)
+            slot.pin_out[:out_end - text_end].copy_(A[text_end:out_end], non_blocking=True)
+            slot.event = torch.cuda.Event()
+            slot.event.record(slot.stream)
+        slot.reqs = reqs
+        slot.batch = b
+        slot.views = [(oc - text_end, n, cb, k) for oc, n, cb, k in zip(offs_c, lens, cbs, kinds)] + \
+                     [st_off - text_end]
+
+    def _retire(self, slot: _Slot, now: float, keep_cols: bool):
+        out = slot.pin_out.numpy()
+        st_rel = slot.views[-1]
+        status = out[st_rel:st_rel + 4 * len(slot.reqs)].view(np.int32)
+        dt = {1: np.uint8, 2: np.uint16, 4: np.uint32, 8: np.uint64}
+        for j, (r, (oc, n, cb, k)) in enumerate(zip(slot.reqs, slot.views[:-1])):
+            r.status = int(status[j])
+            r.kind = k
+            r.done = now
+            if keep_cols:
+                r.cols = out[oc:oc + (n + 1) * cb].view(dt[cb]).copy()
+        slot.batch.close()
+        slot.batch, slot.reqs, slot.event, slot.views = None, [], None, []
+
+    # ------------------------------------------------------------------ loop
+    def run(self, requests: list, realtime: bool = True, keep_cols: bool = False, poll_sleep: float = 20e-6):
+        """Serve ``requests`` (sorted by arrival, seconds from start).  With
+        realtime=False every request is available at once (offline).  Fills
+        each request's status / done (and cols with keep_cols); returns the
+        wall time the loop took."""
+        for r in requests:
+            if not self.fits_alone(r):
+                raise ValueError(f"request {r.rid} ({len(r.text)} bytes) exceeds a slot's arena")
+        waiting = deque()
+        nxt = 0
+        t0 = time.perf_counter()
+        pending = len(requests)
+        while pending:
+            now = time.perf_counter() - t0
+            while nxt < len(requests) and (not realtime or requests[nxt].arrival <= now):
+                waiting.append(requests[nxt])
+                nxt += 1
+            progressed = False
+            for s in self.slots:                                   # retire finished slots
+                if s.event is not None and s.event.query():
+                    pending -= len(s.reqs)
+                    self._retire(s, time.perf_counter() - t0, keep_cols)
+                    progressed = True
+            for s in self.slots:                                   # admit into free slots
+                if not waiting:
+                    break
+                if s.event is not None:
+                    continue
+                take, dev_used, in_used, out_used = [], 1 << 20, 0, 4096
+                while waiting and len(take) < self.max_batch:
+                    d, i, o = self.footprint(waiting[0])
+                    if take and (dev_used + d > self.arena_bytes or in_used + i > s.pin_in.numel()
+                                 or out_used + o > s.pin_out.numel()):
+                        break
+                    take.append(waiting.popleft())
+                    dev_used, in_used, out_used = dev_used + d, in_used + i, out_used + o
+                self._launch(s, take)
+                self.stats["batches"] += 1
+                self.stats["requests"] += len(take)
+                self.stats["max_batch"] = max(self.stats["max_batch"], len(take))
+                self.stats["max_inflight"] = max(self.stats["max_inflight"],
+                                                 sum(1 for q in self.slots if q.event is not None))
+                progressed = True
+            if not progressed:
+                if nxt < len(requests) and realtime and not waiting:
+                    gap = requests[nxt].arrival - (time.perf_counter() - t0)
+                    if gap > 0:
+                        time.sleep(min(gap, 1e-3))
+                else:
+                    time.sleep(poll_sleep)
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.torch.cuda.synchronize(self.dev)
+        for s in self.slots:
+            if s.batch is not None:
+                s.batch.close()
+        self.slots = []
+
+
+def latency_summary(requests: list) -> dict:
+    lat = np.array([r.done - r.arrival for r in requests]) * 1e3
+    return {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "mean_ms": round(float(lat.mean()), 3), "max_ms": round(float(lat.max()), 3)}

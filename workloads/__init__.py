@@ -244,3 +244,50 @@ def sample_text(tree: _Tree, n: int, seed: int) -> np.ndarray:
         pieces.append(s)
         total += len(s)
     return np.frombuffer(b"".join(pieces), dtype=np.uint8).copy()
+
+
+class PiecePool:
+    """Valid iterations of the top-level star of a random RE (see random_re),
+    drawn once from random syntax trees of its body; long valid texts are
+    then random sequences of whole pieces, assembled with numpy."""
+
+    def __init__(self, tree: _Tree, seed: int, count: int = 2048):
+        rng = rng_for(seed)
+        body = tree.kids[0]
+        pieces = []
+        for _ in range(count):
+            part: list = []
+            _emit(body, rng, part, 1 << 16)
+            pieces.append(b"".join(part))
+        self.lens = np.array([len(p) for p in pieces], dtype=np.int64)
+        self.starts = np.concatenate([[0], np.cumsum(self.lens)[:-1]]).astype(np.int64)
+        self.data = np.frombuffer(b"".join(pieces), dtype=np.uint8)
+
+    def text(self, n: int, seed: int) -> np.ndarray:
+        """A valid text of at most n bytes: whole pieces while they fit."""
+        rng = rng_for(seed)
+        mean = max(1.0, float(self.lens.mean()))
+        idx = rng.integers(0, len(self.lens), size=int(n / mean * 1.2) + 16)
+        ln = self.lens[idx]
+        cum = np.cumsum(ln)
+        while cum[-1] < n:                       # rare: draw more pieces
+            more = rng.integers(0, len(self.lens), size=len(idx))
+            idx = np.concatenate([idx, more])
+            ln = self.lens[idx]
+            cum = np.cumsum(ln)
+        q = int(np.searchsorted(cum, n, side="right"))   # pieces 0..q-1 fit in n bytes
+        idx, ln = idx[:q], ln[:q]
+        total = int(ln.sum())
+        if total == 0:
+            return np.zeros(0, dtype=np.uint8)
+        before = np.concatenate([[0], np.cumsum(ln)[:-1]])
+        src = np.repeat(self.starts[idx] - before, ln) + np.arange(total, dtype=np.int64)
+        return self.data[src]
+
+
+def batch_lengths(n_texts: int, seed: int, lo: int = 1 << 10, hi: int = 4 << 20):
+    """Text lengths log-uniform in [lo, hi] and an RE index in 0..7 per text."""
+    rng = rng_for(seed)
+    lens = np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_texts)).astype(np.int64)
+    which = rng.integers(0, 8, size=n_texts)
+    return lens, which
