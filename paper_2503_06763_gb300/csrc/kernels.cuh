@@ -169,6 +169,7 @@ struct Tabs {
     const uint32_t *f32, *b32;
     const uint32_t *f2, *b2;
     uint32_t ncls, nc2;
+    uint32_t rowb, nf, magic;       // reach in pair mode: run-state encoding (see reach_impl.cuh)
 };
 
 template <int TM>

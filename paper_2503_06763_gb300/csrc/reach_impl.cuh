@@ -31,6 +31,86 @@
 namespace slpf {
 namespace reach {
 
+// ------------------------------------------------------------------ pair-mode layout
+// In pair mode (at most 16 byte classes) the reach keeps every run state as
+// the byte offset of its row in one shared-memory array of two-byte
+// transition rows, forward rows first:
+//     forward state s  -> s * rowb,        backward state s -> (nf + s) * rowb,
+// rowb = ncls^2 * 4.  An entry of row s, column (c1, c2), is the offset of the
+// state after the byte pair, so one step is an add and a load:
+//     run = *(u32 *)(sm + kRows + run + cp4),  cp4 = 4 * (c1 * ncls + c2),
+// and cp4 comes from two byte-indexed class tables, H[b] = c(b) * ncls and
+// L[b] = 4 * c(b), as (H[b1] << 2) + L[b2].  The run's state id is needed only
+// at 64-byte boundaries (records, checkpoints, end states) and is the offset
+// divided by rowb (a multiply-high by a reciprocal: offsets are exact
+// multiples of rowb and small).  Blocks that start or end inside a chunk's
+// edge step one byte at a time on state ids with the one-byte tables.
+//   [0, 256) H    [256, 512) L    [512, 768) byte -> class
+//   [kRows, kRows + (nf + nb) * rowb) rows, then one-byte tables (u16)
+constexpr uint32_t kClsH = 0, kClsL = 256, kCls = 512, kRows = 1024;
+
+__host__ __device__ inline size_t reach_pair_smem(const DevTables &t) {
+    const size_t rows = (size_t)(t.nf + t.nb) * t.ncls * t.ncls * 4;
+    return kRows + ((rows + 15) & ~(size_t)15) + (((size_t)t.nf * t.ncls * 2 + 15) & ~(size_t)15) +
+           (((size_t)t.nb * t.ncls * 2 + 15) & ~(size_t)15);
+}
+
+// Stage the pair-mode layout (block-wide; ends with __syncthreads).
+__device__ inline uint8_t *stage_reach_pair(const DevTables &t, uint8_t *sm, Tabs &T) {
+    const uint32_t ncls = t.ncls, nc2 = ncls * ncls, rowb = nc2 * 4;
+    for (uint32_t b = threadIdx.x; b < 256; b += blockDim.x) {
+        const uint32_t c = __ldg(t.cls + b);
+        sm[kClsH + b] = (uint8_t)(c * ncls);
+        sm[kClsL + b] = (uint8_t)(4 * c);
+        sm[kCls + b] = (uint8_t)c;
+    }
+    uint32_t *rows = reinterpret_cast<uint32_t *>(sm + kRows);
+    const size_t nfw = (size_t)t.nf * nc2, nbw = (size_t)t.nb * nc2;
+    for (size_t i = threadIdx.x; i < nfw; i += blockDim.x) rows[i] = (__ldg(t.f2 + i) >> 16) * rowb;
+    for (size_t i = threadIdx.x; i < nbw; i += blockDim.x) rows[nfw + i] = (t.nf + (__ldg(t.b2 + i) >> 16)) * rowb;
+    uint8_t *after = sm + kRows + (((nfw + nbw) * 4 + 15) & ~(size_t)15);
+    uint16_t *f16 = reinterpret_cast<uint16_t *>(after);
+    const size_t fsz = (size_t)t.nf * ncls, bsz = (size_t)t.nb * ncls;
+    uint16_t *b16 = reinterpret_cast<uint16_t *>(after + ((fsz * 2 + 15) & ~(size_t)15));
+    for (size_t i = threadIdx.x; i < fsz; i += blockDim.x) f16[i] = (uint16_t)__ldg(t.fT + i);
+    for (size_t i = threadIdx.x; i < bsz; i += blockDim.x) b16[i] = (uint16_t)__ldg(t.bT + i);
+    T.cls = sm + kCls;
+    T.f16 = f16;
+    T.b16 = b16;
+    T.f32 = t.fT;
+    T.b32 = t.bT;
+    T.f2 = T.b2 = nullptr;
+    T.ncls = ncls;
+    T.nc2 = nc2;
+    T.rowb = rowb;
+    T.nf = t.nf;
+    T.magic = 0xFFFFFFFFu / rowb + 1u;
+    __syncthreads();
+    return reinterpret_cast<uint8_t *>(b16) + ((bsz * 2 + 15) & ~(size_t)15);
+}
+
+// Run state <-> state id (identity outside pair mode).
+template <int TM> __device__ __forceinline__ uint32_t enc_f(const Tabs &T, uint32_t id) {
+    return TM == TM_PAIR ? id * T.rowb : id;
+}
+template <int TM> __device__ __forceinline__ uint32_t enc_b(const Tabs &T, uint32_t id) {
+    return TM == TM_PAIR ? (T.nf + id) * T.rowb : id;
+}
+template <int TM> __device__ __forceinline__ uint32_t dec_f(const Tabs &T, uint32_t e) {
+    return TM == TM_PAIR ? __umulhi(e, T.magic) : e;
+}
+template <int TM> __device__ __forceinline__ uint32_t dec_b(const Tabs &T, uint32_t e) {
+    return TM == TM_PAIR ? __umulhi(e, T.magic) - T.nf : e;
+}
+
+// Byte k (0..3) of w, zero-extended (one byte permute).
+__device__ __forceinline__ uint32_t byte_k(uint32_t w, int k) { return __byte_perm(w, 0u, 0x4440u | (uint32_t)k); }
+
+// 4 * class pair of bytes (lo, hi) of w at positions k, k+1 in pair mode.
+__device__ __forceinline__ uint32_t cp4_of(const uint8_t *sm, uint32_t w, int k) {
+    return ((uint32_t)sm[kClsH + byte_k(w, k)] << 2) + sm[kClsL + byte_k(w, k + 1)];
+}
+
 // One 64-byte block of both directions.  Runs j < W are stepped, W a
 // compile-time width chosen per block from the warp's largest run count (so
 // the loops are fully unrolled without predication); a lane with fewer runs
@@ -49,16 +129,18 @@ __device__ __forceinline__ void walk_block(const Params &p, const Tabs &T, const
         const uint4 fx = *reinterpret_cast<const uint4 *>(frow + (((uint32_t)q ^ swz) << 4));
         const uint4 bx = bwd ? *reinterpret_cast<const uint4 *>(brow + (((uint32_t)(3 - q) ^ swz) << 4))
                              : make_uint4(0, 0, 0, 0);
-        if (TM == TM_PAIR && !EDGE) {                 // two bytes per table lookup
+        if (TM == TM_PAIR && !EDGE) {                 // two bytes per table lookup (run states are row offsets)
+            extern __shared__ __align__(16) uint8_t sm[];
+            const uint32_t fw[4] = {fx.x, fx.y, fx.z, fx.w}, bw[4] = {bx.x, bx.y, bx.z, bx.w};
 #pragma unroll
             for (int v = 0; v < 8; ++v) {
-                const uint32_t cpf = clsof<TM>(T, byte_of(fx, 2 * v)) * T.ncls + clsof<TM>(T, byte_of(fx, 2 * v + 1));
+                const uint32_t cpf = cp4_of(sm, fw[v >> 1], 2 * (v & 1));
 #pragma unroll
-                for (int j = 0; j < W; ++j) sf[j] = fpair(T, sf[j], cpf) >> 16;
-                if (bwd) {
-                    const uint32_t cpb = clsof<TM>(T, byte_of(bx, 14 - 2 * v)) * T.ncls + clsof<TM>(T, byte_of(bx, 15 - 2 * v));
+                for (int j = 0; j < W; ++j) sf[j] = *reinterpret_cast<const uint32_t *>(sm + kRows + sf[j] + cpf);
+                if (bwd) {                            // pair (14-2v, 15-2v), consumed right to left
+                    const uint32_t cpb = cp4_of(sm, bw[(7 - v) >> 1], 2 * ((7 - v) & 1));
 #pragma unroll
-                    for (int j = 0; j < W; ++j) sb[j] = bpair(T, sb[j], cpb) >> 16;
+                    for (int j = 0; j < W; ++j) sb[j] = *reinterpret_cast<const uint32_t *>(sm + kRows + sb[j] + cpb);
                 }
             }
         } else {
@@ -124,14 +206,14 @@ __device__ __forceinline__ bool ring_wait(Ring &r, int s) {
 // Drop dead runs and merge runs in equal states (their slot sets are joined).
 // All indexing is static so the run arrays stay in registers.
 template <int MS>
-__device__ __forceinline__ void compact(uint32_t (&s)[MS], uint32_t (&mk)[MS], uint32_t &m) {
+__device__ __forceinline__ void compact(uint32_t (&s)[MS], uint32_t (&mk)[MS], uint32_t &m, uint32_t dead) {
     uint32_t ns[MS], nk[MS];
     uint32_t cnt = 0;
 #pragma unroll
-    for (int j = 0; j < MS; ++j) { ns[j] = 0; nk[j] = 0; }
+    for (int j = 0; j < MS; ++j) { ns[j] = dead; nk[j] = 0; }   // unused runs hold the empty state
 #pragma unroll
     for (int j = 0; j < MS; ++j) {
-        if (j < (int)m && s[j]) {
+        if (j < (int)m && s[j] != dead) {
             bool merged = false;
 #pragma unroll
             for (int k = 0; k < j; ++k)
@@ -150,15 +232,15 @@ __device__ __forceinline__ void compact(uint32_t (&s)[MS], uint32_t (&mk)[MS], u
 }
 
 // Record the runs at one boundary (while more than one run is live).
-template <int MS>
-__device__ __forceinline__ void record(const Params &p, uint32_t *cnt_row, uint2 *ent_row, uint32_t &used,
-                                       uint32_t &nrec, bool &open, uint32_t slot, const uint32_t (&s)[MS],
-                                       const uint32_t (&mk)[MS], uint32_t m) {
+template <int TM, int MS, bool FWD>
+__device__ __forceinline__ void record(const Params &p, const Tabs &T, uint32_t *cnt_row, uint2 *ent_row,
+                                       uint32_t &used, uint32_t &nrec, bool &open, uint32_t slot,
+                                       const uint32_t (&s)[MS], const uint32_t (&mk)[MS], uint32_t m) {
     if (!open) return;
     if (slot >= kRecBounds || used + m > kRecEntries) { open = false; return; }
 #pragma unroll
     for (int j = 0; j < MS; ++j)
-        if (j < (int)m) ent_row[used + j] = make_uint2(s[j], mk[j]);
+        if (j < (int)m) ent_row[used + j] = make_uint2(FWD ? dec_f<TM>(T, s[j]) : dec_b<TM>(T, s[j]), mk[j]);
     used += m;
     cnt_row[slot] = m;
     nrec = slot + 1;
@@ -193,29 +275,31 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
     const bool bwd = !p.recognize;
     uint32_t sf[MS], sb[MS], kf[MS], kb[MS];
 #pragma unroll
-    for (int j = 0; j < MS; ++j) { sf[j] = 0u; sb[j] = 0u; kf[j] = 0u; kb[j] = 0u; }
+    const uint32_t dead_f = enc_f<TM>(T, 0), dead_b = enc_b<TM>(T, 0);
+#pragma unroll
+    for (int j = 0; j < MS; ++j) { sf[j] = dead_f; sb[j] = dead_b; kf[j] = 0u; kb[j] = 0u; }
     uint32_t mf, mb = 0;
     int tstart, tlast = -1;
     if (i == 0) {
-        mf = 1; sf[0] = t.fI; kf[0] = 1; tstart = 0;      // J_0 = I
+        mf = 1; sf[0] = enc_f<TM>(T, t.fI); kf[0] = 1; tstart = 0;      // J_0 = I
     } else {
         const uint32_t pr = clsof<TM>(T, __ldg(p.x + base - 1)) * t.ncls + clsof<TM>(T, __ldg(p.x + base));
         mf = __ldg(t.fSlotCount + pr);
 #pragma unroll
         for (int j = 0; j < MS; ++j)
-            if (j < (int)mf) { sf[j] = __ldg(t.fSlotStart + pr * t.msf + j); kf[j] = 1u << j; }
+            if (j < (int)mf) { sf[j] = enc_f<TM>(T, __ldg(t.fSlotStart + pr * t.msf + j)); kf[j] = 1u << j; }
         tstart = 1;                                        // slot states follow byte 0
     }
     if (bwd) {
         if (i == p.c - 1) {
-            mb = 1; sb[0] = t.bF; kb[0] = 1; tlast = (int)len - 1;   // Ĵ_{c+1} = F
+            mb = 1; sb[0] = enc_b<TM>(T, t.bF); kb[0] = 1; tlast = (int)len - 1;   // Ĵ_{c+1} = F
         } else {
             const uint32_t pr = clsof<TM>(T, __ldg(p.x + base + len - 1)) * t.ncls +
                                 clsof<TM>(T, __ldg(p.x + base + len));
             mb = __ldg(t.bSlotCount + pr);
 #pragma unroll
             for (int j = 0; j < MS; ++j)
-                if (j < (int)mb) { sb[j] = __ldg(t.bSlotStart + pr * t.msb + j); kb[j] = 1u << j; }
+                if (j < (int)mb) { sb[j] = enc_b<TM>(T, __ldg(t.bSlotStart + pr * t.msb + j)); kb[j] = 1u << j; }
             tlast = (int)len - 2;                          // slot states precede the last byte
         }
     }
@@ -234,11 +318,11 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
         const int stage = (int)(blk % kStages);
         if (fb >= 1) {                                      // boundary before forward block fb
             if (!fconv) {
-                compact<MS>(sf, kf, mf);
+                compact<MS>(sf, kf, mf, dead_f);
                 if (mf <= 1) { fconv = true; fconv_sub = fb; }
-                else record<MS>(p, fcnt, fent, fused, fnrec, fopen, fb - 1, sf, kf, mf);
+                else record<TM, MS, true>(p, T, fcnt, fent, fused, fnrec, fopen, fb - 1, sf, kf, mf);
             }
-            p.w.FC[(uint64_t)i * p.S + fb] = fconv ? sf[0] : kUnknown;
+            p.w.FC[(uint64_t)i * p.S + fb] = fconv ? dec_f<TM>(T, sf[0]) : kUnknown;
         }
         const uint64_t fpos = base + 64ull * fb, bpos = base + 64ull * bb;
         const int f_lo = fb == 0 ? tstart : 0;
@@ -256,7 +340,17 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
         const uint8_t *frow = ring.tiles + (2 * stage) * kTileBytes + lane * 64;
         const uint8_t *brow = ring.tiles + (2 * stage + 1) * kTileBytes + lane * 64;
         const uint32_t wm = max(wmf, wmb);
-        if (edge) walk_block<TM, MS, true, MS>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, f_lo, f_hi, 0, b_hi);
+        if (edge) {
+            if constexpr (TM == TM_PAIR) {              // one byte at a time on state ids
+#pragma unroll
+                for (int j = 0; j < MS; ++j) { sf[j] = dec_f<TM>(T, sf[j]); sb[j] = dec_b<TM>(T, sb[j]); }
+                walk_block<TM_SMEM, MS, true, MS>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, f_lo, f_hi, 0, b_hi);
+#pragma unroll
+                for (int j = 0; j < MS; ++j) { sf[j] = enc_f<TM>(T, sf[j]); sb[j] = enc_b<TM>(T, sb[j]); }
+            } else {
+                walk_block<TM, MS, true, MS>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, f_lo, f_hi, 0, b_hi);
+            }
+        }
         else if (wm <= 1) walk_block<TM, MS, false, 1>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
         else if (MS > 2 && wm <= 2) walk_block<TM, MS, false, (MS > 2 ? 2 : MS)>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
         else if (MS > 4 && wm <= 4) walk_block<TM, MS, false, (MS > 4 ? 4 : MS)>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
@@ -270,11 +364,11 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
         }
         if (bwd && bb >= 1) {                               // boundary at the start of backward block bb
             if (!bconv) {
-                compact<MS>(sb, kb, mb);
+                compact<MS>(sb, kb, mb, dead_b);
                 if (mb <= 1) { bconv = true; bconv_sub = bb; }
-                else record<MS>(p, bcnt, bent, bused, bnrec, bopen, nsub - 1 - bb, sb, kb, mb);
+                else record<TM, MS, false>(p, T, bcnt, bent, bused, bnrec, bopen, nsub - 1 - bb, sb, kb, mb);
             }
-            p.w.BC[(uint64_t)i * p.S + bb - 1] = bconv ? sb[0] : kUnknown;
+            p.w.BC[(uint64_t)i * p.S + bb - 1] = bconv ? dec_b<TM>(T, sb[0]) : kUnknown;
         }
     }
     // end state of every slot: the state of the run standing for it (0 if none)
@@ -283,7 +377,7 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
         uint32_t v = 0;
 #pragma unroll
         for (int r = 0; r < MS; ++r)
-            if (r < (int)mf && ((kf[r] >> j) & 1)) v = sf[r];
+            if (r < (int)mf && ((kf[r] >> j) & 1)) v = dec_f<TM>(T, sf[r]);
         p.w.Rf[(size_t)i * msf + j] = v;
     }
     p.w.fconv[i] = fconv_sub;
@@ -294,7 +388,7 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
             uint32_t v = 0;
 #pragma unroll
             for (int r = 0; r < MS; ++r)
-                if (r < (int)mb && ((kb[r] >> j) & 1)) v = sb[r];
+                if (r < (int)mb && ((kb[r] >> j) & 1)) v = dec_b<TM>(T, sb[r]);
             p.w.Rb[(size_t)i * msb + j] = v;
         }
         p.w.bconv[i] = bconv_sub;
@@ -308,7 +402,7 @@ __global__ void __launch_bounds__(kChunkThreads)
     reach_kernel(const __grid_constant__ Params p, const __grid_constant__ CUtensorMap map) {
     extern __shared__ __align__(16) uint8_t sm[];
     Tabs T;
-    uint8_t *rest = stage_tables<TM>(p.t, sm, T);
+    uint8_t *rest = TM == TM_PAIR ? stage_reach_pair(p.t, sm, T) : stage_tables<TM>(p.t, sm, T);
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x / 32;
     Ring ring{};
     {
@@ -349,7 +443,7 @@ template <int TM, int MS>
 __global__ void __launch_bounds__(kChunkThreads) reach_batch_kernel(const __grid_constant__ BatchGroup b) {
     extern __shared__ __align__(16) uint8_t sm[];
     Tabs T;
-    uint8_t *rest = stage_tables<TM>(b.t, sm, T);
+    uint8_t *rest = TM == TM_PAIR ? stage_reach_pair(b.t, sm, T) : stage_tables<TM>(b.t, sm, T);
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Ring ring{};
     {
@@ -371,7 +465,8 @@ __global__ void __launch_bounds__(kChunkThreads) reach_batch_kernel(const __grid
 }
 
 inline size_t reach_smem(const DevTables &t, int tm) {
-    return tables_smem_bytes(t, tm) + 1024 + (kChunkThreads / 32) * (kStages * 2 * kTileBytes + kStages * 8);
+    const size_t tab = tm == TM_PAIR ? reach_pair_smem(t) : tables_smem_bytes(t, tm);
+    return tab + 1024 + (kChunkThreads / 32) * (kStages * 2 * kTileBytes + kStages * 8);
 }
 
 template <int TM, int MS>
