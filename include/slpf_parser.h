@@ -236,6 +236,20 @@ void re_batch_free(re_batch *b);
 re_status re_parse_static(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream stream,
                           re_slpf *slpf, const re_parse_opts *opts);
 
+/* re_parse for a text in host memory: enqueue on stream the copy of
+ * text[0..len) into d_text, the parse (as re_parse, into the device buffers
+ * of *slpf and d_workspace), and the copies of the len + 1 columns into
+ * host_cols and of the status word into *host_status.  Asynchronous: the
+ * host buffers must stay valid until the stream reaches them, and should be
+ * pinned (page-locked) for the copies to overlap other work; the host
+ * results are valid once the stream has been synchronised.  Calls on
+ * different streams with separate buffers overlap one text's copies with
+ * another's kernels.  d_text: device, >= len bytes, 16-byte aligned;
+ * host_cols: (len + 1) * slpf->col_bytes bytes, NULL in recognizer mode.    */
+re_status re_parse_host(re_handle *h, const uint8_t *text, uint64_t len, void *host_cols, int32_t *host_status,
+                        uint8_t *d_text, re_slpf *slpf, void *d_workspace, uint64_t workspace_bytes,
+                        re_stream stream, const re_parse_opts *opts);
+
 /* Thread-local description of the last error returned on this thread.     */
 const char *re_last_error(void);
 

@@ -416,6 +416,26 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
 
 }  // extern "C"
 
+extern "C" re_status re_parse_host(re_handle *h, const uint8_t *text, uint64_t len, void *host_cols,
+                                   int32_t *host_status, uint8_t *d_text, re_slpf *slpf, void *d_workspace,
+                                   uint64_t workspace_bytes, re_stream stream, const re_parse_opts *opts) {
+    const bool recognize = opts && (opts->flags & RE_PARSE_RECOGNIZE_ONLY);
+    if (!h || !slpf || !host_status || (len && (!text || !d_text)) || (!recognize && !host_cols)) {
+        set_error("null argument");
+        return RE_E_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (len) CUDA_TRY(cudaMemcpyAsync(d_text, text, len, cudaMemcpyHostToDevice, s), "text to device");
+    const re_status st = re_parse(h, d_text, len, stream, slpf, d_workspace, workspace_bytes, opts);
+    if (st != RE_OK) return st;
+    if (!recognize)
+        CUDA_TRY(cudaMemcpyAsync(host_cols, slpf->d_cols, (len + 1) * slpf->col_bytes, cudaMemcpyDeviceToHost, s),
+                 "columns to host");
+    CUDA_TRY(cudaMemcpyAsync(host_status, slpf->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+             "status to host");
+    return RE_OK;
+}
+
 // ------------------------------------------------------------------ batch
 // A planned batch: per text its group (compiled RE), chunk length and
 // workspace layout; per group the table mode, encoding and unit counts.  The

@@ -24,7 +24,7 @@ RE_PARSE_RECOGNIZE_ONLY = 1
 
 EXPORTS = ["re_compile", "re_free", "re_get_info", "re_segment_name", "re_dict_copy",
            "re_slpf_layout", "re_workspace_size", "re_parse", "re_batch_plan", "re_batch_workspace_size",
-           "re_batch_chunk_len", "re_parse_batch", "re_batch_run", "re_batch_free", "re_parse_static",
+           "re_batch_chunk_len", "re_parse_batch", "re_batch_run", "re_batch_free", "re_parse_host", "re_parse_static",
            "re_last_error"]
 RE_STATIC_SCRATCH_BYTES = 64 << 20
 
@@ -101,6 +101,8 @@ def load():
     lib.re_batch_run.restype = i32
     lib.re_batch_free.argtypes = [vp]
     lib.re_batch_free.restype = None
+    lib.re_parse_host.argtypes = [vp, vp, u64, vp, vp, vp, ctypes.POINTER(Slpf), vp, u64, vp, ctypes.POINTER(ParseOpts)]
+    lib.re_parse_host.restype = i32
     lib.re_parse_static.argtypes = [vp, vp, u64, vp, ctypes.POINTER(Slpf), ctypes.POINTER(ParseOpts)]
     lib.re_parse_static.restype = i32
     lib.re_last_error.argtypes = []
@@ -232,6 +234,23 @@ class Regex:
         check(load().re_parse_static(self._h, text.data_ptr() if n else None, n, ctypes.c_void_p(s.cuda_stream),
                                      ctypes.byref(slpf), ctypes.byref(opts)))
         return out, status, kname
+
+    def parse_host(self, text, cols, status, d_text, d_cols, d_status, workspace, stream=None, kind: str = "auto",
+                   chunk_len: int = 0):
+        """re_parse_host: ``text`` / ``cols`` / ``status`` are host tensors
+        (pinned for overlap), ``d_*`` and ``workspace`` device tensors.
+        Enqueues copy-in, parse and copy-back on the stream; nothing waits."""
+        import torch
+        n = text.numel()
+        kname, cb, _ = self.layout(n, kind)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        slpf = Slpf(KINDS[kname], cb, 0, d_cols.data_ptr(), d_cols.numel() * d_cols.element_size(),
+                    d_status.data_ptr())
+        opts = ParseOpts(KINDS[kname], chunk_len, 0, 0, None)
+        check(load().re_parse_host(self._h, text.data_ptr() if n else None, n, cols.data_ptr(), status.data_ptr(),
+                                   d_text.data_ptr() if n else None, ctypes.byref(slpf), workspace.data_ptr(),
+                                   workspace.numel(), ctypes.c_void_p(s.cuda_stream), ctypes.byref(opts)))
+        return kname
 
     # ------------------------------------------------------------------ decoding
     def decode(self, cols, kind: str):
