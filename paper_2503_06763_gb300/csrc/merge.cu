@@ -530,7 +530,7 @@ using StOf = typename std::conditional<TM != TM_GLOBAL, uint16_t, uint32_t>::typ
 // (lane = group).  With TMA the warp's tile of outputs is written to shared
 // memory and stored with one tensor-store per tile.
 template <int TM, int E, bool TMA>
-__global__ void __launch_bounds__(kBlockThreads, 3)
+__global__ void __launch_bounds__(kBlockThreads, TM == TM_PAIR ? 2 : 3)
     merge_kernel(const __grid_constant__ Params p, const __grid_constant__ CUtensorMap out_map) {
     using St = StOf<TM>;
     constexpr int CB = bytes_of(E);
