@@ -223,6 +223,10 @@ def main():
     rx = Regex(W.DNA_RE)
     dev = torch.device("cuda", local)
     text = torch.from_numpy(host).to(dev)
+    tuned = None
+    if args.chunk_len == 0:                 # re_autotune on this text; later parses use its choice
+        tuned = rx.autotune(text)
+        torch.cuda.empty_cache()
     kind, cb, out_bytes = rx.layout(n, "auto")
     dt = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}[cb]
     out = torch.empty(n + 1, dtype=dt, device=dev)
@@ -327,7 +331,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": WORKLOAD, "text_bytes_per_gpu": n, "encoding": f"{kind}-{8 * cb}bit",
-                   "chunk_len": args.chunk_len or "auto", "segments": rx.ell,
+                   "chunk_len": args.chunk_len or tuned, "chunk_len_from": "fixed" if args.chunk_len else "re_autotune", "segments": rx.ell,
                    "l2": "text 256 MiB > 129 MB L2 (no flush needed)",
                    "parallelism": f"independent texts per GPU x{world}"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

@@ -236,6 +236,18 @@ void re_batch_free(re_batch *b);
 re_status re_parse_static(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream stream,
                           re_slpf *slpf, const re_parse_opts *opts);
 
+/* Chunk-length autotuner (no counterpart in the paper, which fixes c to the
+ * thread count).  Parses d_text[0..len) with candidate chunk lengths around
+ * the built-in rule's choice (1/2x to 2x, multiples of 64, those whose
+ * workspace fits workspace_bytes), one warm-up and two timed runs each on
+ * stream, and keeps the fastest for this handle, the length bucket
+ * floor(log2(len)) and recognizer mode: later re_parse / re_workspace_size
+ * calls with chunk_len 0 use it (re_parse falls back to the rule's length if
+ * the workspace given is too small for it).  Blocks until the timing runs
+ * finish; *slpf is overwritten.  *chunk_len receives the choice.            */
+re_status re_autotune(re_handle *h, const uint8_t *d_text, uint64_t len, re_slpf *slpf, void *d_workspace,
+                      uint64_t workspace_bytes, re_stream stream, const re_parse_opts *opts, uint32_t *chunk_len);
+
 /* re_parse for a text in host memory: enqueue on stream the copy of
  * text[0..len) into d_text, the parse (as re_parse, into the device buffers
  * of *slpf and d_workspace), and the copies of the len + 1 columns into

@@ -57,6 +57,21 @@ uint32_t choose_chunk(uint64_t n, int sms, const re_parse_opts *opts) {
     return (uint32_t)std::min<uint64_t>(std::max<uint64_t>(k, 256), 1u << 20);
 }
 
+int length_bucket(uint64_t n) {
+    int b = 0;
+    while (n > 1) { n >>= 1; ++b; }
+    return b;
+}
+
+// The chunk length re_autotune chose for this length bucket, or 0.
+uint32_t tuned_chunk(re_handle *h, uint64_t n, const re_parse_opts *opts) {
+    if (opts && opts->chunk_len) return 0;
+    const int rec = (opts && (opts->flags & RE_PARSE_RECOGNIZE_ONLY)) ? 1 : 0;
+    std::lock_guard<std::mutex> g(h->tune_lock);
+    auto it = h->tuned.find({length_bucket(n), rec});
+    return it == h->tuned.end() ? 0u : it->second;
+}
+
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda).
@@ -324,7 +339,8 @@ re_status re_slpf_layout(const re_handle *h, uint64_t len, re_slpf_kind kind, re
 
 re_status re_workspace_size(const re_handle *h, uint64_t len, const re_parse_opts *opts, uint64_t *bytes) {
     if (!h || !bytes) { set_error("null argument"); return RE_E_INVALID_ARG; }
-    const uint32_t k = choose_chunk(len, sm_count_of(h->device), opts);
+    const uint32_t kt = tuned_chunk(const_cast<re_handle *>(h), len, opts);
+    const uint32_t k = kt ? kt : choose_chunk(len, sm_count_of(h->device), opts);
     if (k % kSub || k == 0) { set_error("chunk_len must be a positive multiple of 64"); return RE_E_INVALID_ARG; }
     *bytes = layout_for(h, len, k).total;
     return RE_OK;
@@ -354,7 +370,10 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     cudaGetDevice(&dev_now);
     if (dev_now != h->device) { set_error("current device differs from the handle's device"); return RE_E_INVALID_ARG; }
     const int sms = sm_count_of(h->device);
-    const uint32_t k = choose_chunk(len, sms, opts);
+    uint32_t k = choose_chunk(len, sms, opts);
+    if (const uint32_t kt = tuned_chunk(h, len, opts)) {      // tuned length, if the workspace holds it
+        if (!len || layout_for(h, len, kt).total <= workspace_bytes) k = kt;
+    }
     if (k % kSub || k == 0) { set_error("chunk_len must be a positive multiple of 64"); return RE_E_INVALID_ARG; }
     if (len / k >= 0xFFFFFFF0ull) { set_error("text too long for this chunk length"); return RE_E_INVALID_ARG; }
     const Layout L = layout_for(h, len, k);
@@ -415,6 +434,61 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
 }
 
 }  // extern "C"
+
+// Time candidate chunk lengths around the rule's choice on the caller's text
+// and keep the fastest for this handle and length bucket.
+extern "C" re_status re_autotune(re_handle *h, const uint8_t *d_text, uint64_t len, re_slpf *slpf,
+                                 void *d_workspace, uint64_t workspace_bytes, re_stream stream,
+                                 const re_parse_opts *opts, uint32_t *chunk_len) {
+    if (!h || !chunk_len || !len) { set_error("null argument or empty text"); return RE_E_INVALID_ARG; }
+    if (opts && opts->chunk_len) { set_error("autotune chooses chunk_len: pass 0"); return RE_E_INVALID_ARG; }
+    if (opts && opts->n_events) { set_error("autotune records its own events"); return RE_E_INVALID_ARG; }
+    const uint32_t k0 = choose_chunk(len, sm_count_of(h->device), nullptr);
+    std::vector<uint32_t> cand;
+    for (uint32_t num : {2u, 3u, 4u, 5u, 6u, 8u}) {            // k0 * num / 4, multiples of 64, >= 256
+        uint64_t k = (uint64_t)k0 * num / 4;
+        k = std::max<uint64_t>(256, (k + kSub - 1) / kSub * kSub);
+        if (k > (1u << 20) || std::find(cand.begin(), cand.end(), (uint32_t)k) != cand.end()) continue;
+        if (layout_for(h, len, (uint32_t)k).total > workspace_bytes) continue;
+        cand.push_back((uint32_t)k);
+    }
+    if (cand.empty()) { set_error("workspace too small for any candidate chunk length"); return RE_E_CAPACITY; }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0), "event");
+    CUDA_TRY(cudaEventCreate(&e1), "event");
+    uint32_t best = cand[0];
+    float best_ms = 1e30f;
+    re_status st = RE_OK;
+    for (uint32_t k : cand) {
+        re_parse_opts o = opts ? *opts : re_parse_opts{};
+        o.chunk_len = k;
+        o.n_events = 0;
+        o.events = nullptr;
+        float ms = 0.f;
+        for (int rep = 0; rep < 3 && st == RE_OK; ++rep) {   // one warm-up, two timed
+            cudaEventRecord(e0, s);
+            st = re_parse(h, d_text, len, stream, slpf, d_workspace, workspace_bytes, &o);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { st = cuda_fail(cudaGetLastError(), "autotune"); break; }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep) ms += t;
+        }
+        if (st != RE_OK) break;
+        if (ms < best_ms) { best_ms = ms; best = k; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != RE_OK) return st;
+    const int rec = (opts && (opts->flags & RE_PARSE_RECOGNIZE_ONLY)) ? 1 : 0;
+    {
+        std::lock_guard<std::mutex> g(h->tune_lock);
+        h->tuned[{length_bucket(len), rec}] = best;
+    }
+    *chunk_len = best;
+    return RE_OK;
+}
 
 extern "C" re_status re_parse_host(re_handle *h, const uint8_t *text, uint64_t len, void *host_cols,
                                    int32_t *host_status, uint8_t *d_text, re_slpf *slpf, void *d_workspace,

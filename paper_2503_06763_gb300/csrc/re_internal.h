@@ -3,6 +3,8 @@
 #pragma once
 
 #include <stdint.h>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -91,4 +93,7 @@ struct re_handle {
     size_t d_bytes = 0;
     int device = 0;
     bool host_only = false;
+    // chunk lengths chosen by re_autotune: key = (floor(log2(len)), recognizer)
+    std::mutex tune_lock;
+    std::map<std::pair<int, int>, uint32_t> tuned;
 };

@@ -24,7 +24,8 @@ RE_PARSE_RECOGNIZE_ONLY = 1
 
 EXPORTS = ["re_compile", "re_free", "re_get_info", "re_segment_name", "re_dict_copy",
            "re_slpf_layout", "re_workspace_size", "re_parse", "re_batch_plan", "re_batch_workspace_size",
-           "re_batch_chunk_len", "re_parse_batch", "re_batch_run", "re_batch_free", "re_parse_host", "re_parse_static",
+           "re_batch_chunk_len", "re_parse_batch", "re_batch_run", "re_batch_free", "re_autotune", "re_parse_host",
+           "re_parse_static",
            "re_last_error"]
 RE_STATIC_SCRATCH_BYTES = 64 << 20
 
@@ -101,6 +102,9 @@ def load():
     lib.re_batch_run.restype = i32
     lib.re_batch_free.argtypes = [vp]
     lib.re_batch_free.restype = None
+    lib.re_autotune.argtypes = [vp, vp, u64, ctypes.POINTER(Slpf), vp, u64, vp, ctypes.POINTER(ParseOpts),
+                                ctypes.POINTER(u32)]
+    lib.re_autotune.restype = i32
     lib.re_parse_host.argtypes = [vp, vp, u64, vp, vp, vp, ctypes.POINTER(Slpf), vp, u64, vp, ctypes.POINTER(ParseOpts)]
     lib.re_parse_host.restype = i32
     lib.re_parse_static.argtypes = [vp, vp, u64, vp, ctypes.POINTER(Slpf), ctypes.POINTER(ParseOpts)]
@@ -234,6 +238,26 @@ class Regex:
         check(load().re_parse_static(self._h, text.data_ptr() if n else None, n, ctypes.c_void_p(s.cuda_stream),
                                      ctypes.byref(slpf), ctypes.byref(opts)))
         return out, status, kname
+
+    def autotune(self, text, kind: str = "auto", workspace=None, stream=None) -> int:
+        """re_autotune on a CUDA uint8 tensor: returns the chunk length chosen
+        (and kept for texts of this length bucket)."""
+        import torch
+        n = text.numel()
+        kname, cb, _ = self.layout(n, kind)
+        dt = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}[cb]
+        out = torch.empty(n + 1, dtype=dt, device=text.device)
+        status = torch.empty(1, dtype=torch.int32, device=text.device)
+        if workspace is None:                   # room for every candidate (the shortest chunks need the most)
+            workspace = torch.empty(self.workspace_size(n, chunk_len=256), dtype=torch.uint8, device=text.device)
+        s = stream if stream is not None else torch.cuda.current_stream(text.device)
+        slpf = Slpf(KINDS[kname], cb, 0, out.data_ptr(), out.numel() * out.element_size(), status.data_ptr())
+        opts = ParseOpts(KINDS[kname], 0, 0, 0, None)
+        k = ctypes.c_uint32()
+        check(load().re_autotune(self._h, text.data_ptr(), n, ctypes.byref(slpf), workspace.data_ptr(),
+                                 workspace.numel(), ctypes.c_void_p(s.cuda_stream), ctypes.byref(opts),
+                                 ctypes.byref(k)))
+        return k.value
 
     def parse_host(self, text, cols, status, d_text, d_cols, d_status, workspace, stream=None, kind: str = "auto",
                    chunk_len: int = 0):

@@ -1,0 +1,45 @@
+"""re_autotune: the chosen chunk length is kept per handle and length bucket,
+used by later parses and workspace queries, and never changes the result."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import serial
+from oracle.re_front import compile_re
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2503_06763_gb300 import Regex
+    return Regex
+
+
+def test_autotune_keeps_choice_and_result(lib):
+    Regex = lib
+    n = 3 << 20
+    host = W.dna_text(n, seed=41)
+    t = torch.from_numpy(host).cuda()
+    fresh = Regex(W.DNA_RE)
+    rx = Regex(W.DNA_RE)
+    rule_ws = fresh.workspace_size(n)
+    k = rx.autotune(t)
+    assert k >= 256 and k % 64 == 0
+    assert rx.workspace_size(n) == rx.workspace_size(n, chunk_len=k)
+    assert rx.workspace_size(n + 12345) == rx.workspace_size(n + 12345, chunk_len=k)   # same length bucket
+    assert fresh.workspace_size(n) == rule_ws                                           # per handle
+    want = serial.parse(compile_re(W.DNA_RE), host)
+    cols, st, kind = rx.parse(t)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    assert np.array_equal(rx.decode(cols.cpu().numpy(), kind), want)
+    # a workspace sized by the rule: the parse falls back to the rule's chunk length
+    small = torch.empty(rule_ws, dtype=torch.uint8, device="cuda")
+    cols2, st2, _ = rx.parse(t, workspace=small)
+    torch.cuda.synchronize()
+    assert int(st2.item()) == 0 and torch.equal(cols2, cols)
