@@ -277,6 +277,20 @@ def main():
                 "phase_ms": {k: round(v, 4) for k, v in phase_ms.items()},
                 "whole_step_frac": round((n + (n + 1) * cb) / (ms / 1e3) / 1e9 / hbm, 4)}
 
+    # recognizer mode (forward reach + join only, Sect. 4.2), same text
+    rec_ws = torch.empty(rx.workspace_size(n, args.chunk_len, 1), dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        rx.parse(text, chunk_len=args.chunk_len, status=status, workspace=rec_ws, recognize_only=True)
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for _ in range(args.steps):
+        rx.parse(text, chunk_len=args.chunk_len, status=status, workspace=rec_ws, recognize_only=True)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    recognizer = {"value": round(n / (r0.elapsed_time(r1) / args.steps / 1e3) / 1e9, 3), "unit": "GB/s",
+                  "status": int(status.item())}
+    del rec_ws
+
     # end to end through re_parse_host: pinned host text in, columns and status
     # back to pinned host memory, every step.  Two streams with their own device
     # buffers take alternate steps, so one step's copies overlap the other's
@@ -334,7 +348,7 @@ def main():
                    "chunk_len": args.chunk_len or tuned, "chunk_len_from": "fixed" if args.chunk_len else "re_autotune", "segments": rx.ell,
                    "l2": "text 256 MiB > 129 MB L2 (no flush needed)",
                    "parallelism": f"independent texts per GPU x{world}"},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "recognizer": recognizer,
         "gpu_launches": 8 * args.steps, "clocks": clocks,
     }
     print(json.dumps(line))

@@ -196,7 +196,7 @@ class Regex:
         n = text.numel()
         kname, cb, nbytes = self.layout(n, kind)
         dt = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}[cb]
-        if out is None:
+        if out is None and not recognize_only:  # the recognizer writes no columns
             out = torch.empty(n + 1, dtype=dt, device=text.device)
         if status is None:
             status = torch.empty(1, dtype=torch.int32, device=text.device)
@@ -205,7 +205,8 @@ class Regex:
         if workspace is None or workspace.numel() < wsz:
             workspace = torch.empty(max(wsz, 256), dtype=torch.uint8, device=text.device)
         s = stream if stream is not None else torch.cuda.current_stream(text.device)
-        slpf = Slpf(KINDS[kname], cb, 0, out.data_ptr(), out.numel() * out.element_size(), status.data_ptr())
+        slpf = Slpf(KINDS[kname], cb, 0, out.data_ptr() if out is not None else None,
+                    out.numel() * out.element_size() if out is not None else 0, status.data_ptr())
         opts = ParseOpts(KINDS[kname], chunk_len, flags, 0, None)
         if events is not None:          # RE_PHASE_EVENTS torch.cuda.Event objects
             for e in events:

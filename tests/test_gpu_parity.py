@@ -125,3 +125,26 @@ def test_epsilon_and_single_terminal(lib):
                           ("()", b"x"), ("(a|b)?", b"")):
         rx = lib(pattern)
         check(rx, pattern, np.frombuffer(text, dtype=np.uint8).copy())
+
+
+@pytest.mark.parametrize("chunk_len", [64, 128, 0])
+def test_recognizer_matches_oracle_acceptance(lib, chunk_len):
+    """Recognizer mode (Sect. 4.2): forward reach + join only; the status word
+    must be the oracle's accept / reject, for valid and corrupted texts."""
+    rng = np.random.Generator(np.random.PCG64(17))
+    cases = [(W.DNA_RE, W.dna_text(50_000, seed=3)), (W.AB_RE, W.ab_text(20_001, seed=4))]
+    for s in range(4):
+        pat, tree, _ = W.random_re(800 + s, 10, 80)
+        cases.append((pat, W.sample_text(tree, 6000, seed=s)))
+    for pat, host in cases:
+        rx = lib(pat)
+        for corrupt in (False, True):
+            h = np.array(host, dtype=np.uint8, copy=True)
+            if corrupt and len(h):
+                j = int(rng.integers(0, len(h)))
+                h[j] = (int(h[j]) + 1 + int(rng.integers(0, 254))) % 256
+            t = torch.from_numpy(h).cuda()
+            _, st, _ = rx.parse(t, chunk_len=chunk_len, recognize_only=True)
+            torch.cuda.synchronize()
+            want = serial.accepted(oracle_cols(pat, h.tobytes()))
+            assert int(st.item()) == (0 if want else 1), (pat[:30], corrupt, len(h))
