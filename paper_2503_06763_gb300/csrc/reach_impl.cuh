@@ -119,14 +119,15 @@ __device__ __forceinline__ uint32_t cp4_of(const uint8_t *sm, uint32_t w, int k)
 // (64-byte rows, SWIZZLE_64B layout: 16-byte chunk q of row r sits at chunk
 // q ^ ((r >> 1) & 3)), filled by TMA or, for warps TMA cannot serve, by the
 // lanes themselves.
-template <int TM, int MS, bool EDGE, int W>
+template <int TM, int MS, bool EDGE, int W, bool FW = true>
 __device__ __forceinline__ void walk_block(const Params &p, const Tabs &T, const uint8_t *frow, const uint8_t *brow,
                                            uint32_t (&sf)[MS], uint32_t (&sb)[MS], uint32_t wmf, uint32_t wmb,
                                            bool bwd, int f_lo, int f_hi, int b_lo, int b_hi) {
     const uint32_t swz = ((threadIdx.x & 31) >> 1) & 3;
 #pragma unroll 1
     for (int q = 0; q < 4; ++q) {
-        const uint4 fx = *reinterpret_cast<const uint4 *>(frow + (((uint32_t)q ^ swz) << 4));
+        const uint4 fx = FW ? *reinterpret_cast<const uint4 *>(frow + (((uint32_t)q ^ swz) << 4))
+                            : make_uint4(0, 0, 0, 0);
         const uint4 bx = bwd ? *reinterpret_cast<const uint4 *>(brow + (((uint32_t)(3 - q) ^ swz) << 4))
                              : make_uint4(0, 0, 0, 0);
         if (TM == TM_PAIR && !EDGE) {                 // two bytes per table lookup (run states are row offsets)
@@ -134,9 +135,11 @@ __device__ __forceinline__ void walk_block(const Params &p, const Tabs &T, const
             const uint32_t fw[4] = {fx.x, fx.y, fx.z, fx.w}, bw[4] = {bx.x, bx.y, bx.z, bx.w};
 #pragma unroll
             for (int v = 0; v < 8; ++v) {
-                const uint32_t cpf = cp4_of(sm, fw[v >> 1], 2 * (v & 1));
+                if (FW) {
+                    const uint32_t cpf = cp4_of(sm, fw[v >> 1], 2 * (v & 1));
 #pragma unroll
-                for (int j = 0; j < W; ++j) sf[j] = *reinterpret_cast<const uint32_t *>(sm + kRows + sf[j] + cpf);
+                    for (int j = 0; j < W; ++j) sf[j] = *reinterpret_cast<const uint32_t *>(sm + kRows + sf[j] + cpf);
+                }
                 if (bwd) {                            // pair (14-2v, 15-2v), consumed right to left
                     const uint32_t cpb = cp4_of(sm, bw[(7 - v) >> 1], 2 * ((7 - v) & 1));
 #pragma unroll
@@ -147,7 +150,7 @@ __device__ __forceinline__ void walk_block(const Params &p, const Tabs &T, const
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
                 const int tf = 16 * q + u, tb = 63 - tf;
-                if (!EDGE || (tf >= f_lo && tf < f_hi)) {
+                if (FW && (!EDGE || (tf >= f_lo && tf < f_hi))) {
                     const uint32_t c = clsof<TM>(T, byte_of(fx, u));
 #pragma unroll
                     for (int j = 0; j < W; ++j) sf[j] = fnext<TM>(T, sf[j], c);
@@ -172,24 +175,36 @@ struct Ring {
     uint32_t phase;       // bit s: parity of the next completion of stage s
 };
 
+// Directions a warp walks: both (one lane per chunk), or one of them (the
+// forward and the backward walk of a chunk in two warps).
+enum { DIR_BOTH = 0, DIR_F = 1, DIR_B = 2 };
+template <int DIR> __device__ __forceinline__ uint8_t *tile_f(const Ring &r, int s) {
+    return r.tiles + (DIR == DIR_BOTH ? 2 * s : s) * kTileBytes;
+}
+template <int DIR> __device__ __forceinline__ uint8_t *tile_b(const Ring &r, int s) {
+    return r.tiles + (DIR == DIR_BOTH ? 2 * s + 1 : s) * kTileBytes;
+}
+
+template <int DIR>
 __device__ __forceinline__ void ring_issue(const Params &p, const CUtensorMap *map, const Ring &r, int s,
-                                           uint32_t i0, uint32_t fb, uint32_t bb, bool bwd) {
+                                           uint32_t i0, uint32_t fb, uint32_t bb, bool fwd, bool bwd) {
     const uint32_t bar = r.bars + 8 * s;
-    mbar_expect_tx(bar, bwd ? 2 * kTileBytes : kTileBytes);
-    tma_load_2d(smem_u32(r.tiles + (2 * s) * kTileBytes), map, 64 * fb, (int32_t)i0, bar);
-    if (bwd) tma_load_2d(smem_u32(r.tiles + (2 * s + 1) * kTileBytes), map, 64 * bb, (int32_t)i0, bar);
+    mbar_expect_tx(bar, ((fwd ? 1u : 0u) + (bwd ? 1u : 0u)) * kTileBytes);
+    if (fwd) tma_load_2d(smem_u32(tile_f<DIR>(r, s)), map, 64 * fb, (int32_t)i0, bar);
+    if (bwd) tma_load_2d(smem_u32(tile_b<DIR>(r, s)), map, 64 * bb, (int32_t)i0, bar);
 }
 
 // Fill this lane's rows of stage s with plain loads (warps TMA cannot serve:
 // the text's last, shorter chunk, or no tensor map).  Bytes past n read as 0.
+template <int DIR>
 __device__ __forceinline__ void ring_fill_plain(const Params &p, const Ring &r, int s, uint64_t fpos, uint64_t bpos,
-                                                bool bwd) {
+                                                bool fwd, bool bwd) {
     const uint32_t lane = threadIdx.x & 31, swz = (lane >> 1) & 3;
-    uint8_t *frow = r.tiles + (2 * s) * kTileBytes + lane * 64;
-    uint8_t *brow = r.tiles + (2 * s + 1) * kTileBytes + lane * 64;
+    uint8_t *frow = tile_f<DIR>(r, s) + lane * 64;
+    uint8_t *brow = tile_b<DIR>(r, s) + lane * 64;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        *reinterpret_cast<uint4 *>(frow + (((uint32_t)q ^ swz) << 4)) = load16(p.x, p.n, fpos + 16 * q);
+        if (fwd) *reinterpret_cast<uint4 *>(frow + (((uint32_t)q ^ swz) << 4)) = load16(p.x, p.n, fpos + 16 * q);
         if (bwd) *reinterpret_cast<uint4 *>(brow + (((uint32_t)q ^ swz) << 4)) = load16(p.x, p.n, bpos + 16 * q);
     }
 }
@@ -265,22 +280,23 @@ __device__ __forceinline__ unsigned block_lanes(const Params &p, uint32_t i, uin
     return mask;
 }
 
-template <int TM, int MS>
+template <int TM, int MS, int DIR = DIR_BOTH>
 __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CUtensorMap *map, Ring &ring,
                             bool tma) {
+    constexpr bool FW = DIR != DIR_B;
     const DevTables &t = p.t;
     const uint64_t base = (uint64_t)i * p.k;
     const uint32_t len = chunk_len(p, i);
     const uint32_t nsub = (len + 63) / 64;
-    const bool bwd = !p.recognize;
+    const bool bwd = DIR != DIR_F && !p.recognize;
     uint32_t sf[MS], sb[MS], kf[MS], kb[MS];
-#pragma unroll
     const uint32_t dead_f = enc_f<TM>(T, 0), dead_b = enc_b<TM>(T, 0);
 #pragma unroll
     for (int j = 0; j < MS; ++j) { sf[j] = dead_f; sb[j] = dead_b; kf[j] = 0u; kb[j] = 0u; }
-    uint32_t mf, mb = 0;
-    int tstart, tlast = -1;
-    if (i == 0) {
+    uint32_t mf = 0, mb = 0;
+    int tstart = 0, tlast = -1;
+    if (!FW) {
+    } else if (i == 0) {
         mf = 1; sf[0] = enc_f<TM>(T, t.fI); kf[0] = 1; tstart = 0;      // J_0 = I
     } else {
         const uint32_t pr = clsof<TM>(T, __ldg(p.x + base - 1)) * t.ncls + clsof<TM>(T, __ldg(p.x + base));
@@ -312,11 +328,12 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
 
     const uint32_t lane = threadIdx.x & 31, i0 = i - lane;
     if (tma && lane == 0)                                     // prologue: first stages in flight
-        for (uint32_t b = 0; b < (uint32_t)kStages && b < nsub; ++b) ring_issue(p, map, ring, b, i0, b, nsub - 1 - b, bwd);
+        for (uint32_t b = 0; b < (uint32_t)kStages && b < nsub; ++b)
+            ring_issue<DIR>(p, map, ring, b, i0, b, nsub - 1 - b, FW, bwd);
     for (uint32_t blk = 0; blk < nsub; ++blk) {
         const uint32_t fb = blk, bb = nsub - 1 - blk;
         const int stage = (int)(blk % kStages);
-        if (fb >= 1) {                                      // boundary before forward block fb
+        if (FW && fb >= 1) {                                // boundary before forward block fb
             if (!fconv) {
                 compact<MS>(sf, kf, mf, dead_f);
                 if (mf <= 1) { fconv = true; fconv_sub = fb; }
@@ -328,37 +345,37 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
         const int f_lo = fb == 0 ? tstart : 0;
         const int f_hi = (int)min(64u, len - 64 * fb);
         const int b_hi = min(63, tlast - (int)(64 * bb));
-        const bool edge = f_lo != 0 || f_hi != 64 || (bwd && b_hi != 63);
+        const bool edge = (FW && (f_lo != 0 || f_hi != 64)) || (bwd && b_hi != 63);
         const unsigned act = block_lanes(p, i, blk);
         const uint32_t wmf = __reduce_max_sync(act, mf), wmb = __reduce_max_sync(act, mb);
         if (tma) {
             if (!ring_wait(ring, stage)) return false;        // lost TMA completion: give up this chunk tile
         } else {
-            ring_fill_plain(p, ring, stage, fpos, bpos, bwd);
+            ring_fill_plain<DIR>(p, ring, stage, fpos, bpos, FW, bwd);
             __syncwarp(act);
         }
-        const uint8_t *frow = ring.tiles + (2 * stage) * kTileBytes + lane * 64;
-        const uint8_t *brow = ring.tiles + (2 * stage + 1) * kTileBytes + lane * 64;
+        const uint8_t *frow = tile_f<DIR>(ring, stage) + lane * 64;
+        const uint8_t *brow = tile_b<DIR>(ring, stage) + lane * 64;
         const uint32_t wm = max(wmf, wmb);
         if (edge) {
             if constexpr (TM == TM_PAIR) {              // one byte at a time on state ids
 #pragma unroll
                 for (int j = 0; j < MS; ++j) { sf[j] = dec_f<TM>(T, sf[j]); sb[j] = dec_b<TM>(T, sb[j]); }
-                walk_block<TM_SMEM, MS, true, MS>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, f_lo, f_hi, 0, b_hi);
+                walk_block<TM_SMEM, MS, true, MS, FW>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, f_lo, f_hi, 0, b_hi);
 #pragma unroll
                 for (int j = 0; j < MS; ++j) { sf[j] = enc_f<TM>(T, sf[j]); sb[j] = enc_b<TM>(T, sb[j]); }
             } else {
-                walk_block<TM, MS, true, MS>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, f_lo, f_hi, 0, b_hi);
+                walk_block<TM, MS, true, MS, FW>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, f_lo, f_hi, 0, b_hi);
             }
         }
-        else if (wm <= 1) walk_block<TM, MS, false, 1>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
-        else if (MS > 2 && wm <= 2) walk_block<TM, MS, false, (MS > 2 ? 2 : MS)>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
-        else if (MS > 4 && wm <= 4) walk_block<TM, MS, false, (MS > 4 ? 4 : MS)>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
-        else walk_block<TM, MS, false, MS>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
+        else if (wm <= 1) walk_block<TM, MS, false, 1, FW>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
+        else if (MS > 2 && wm <= 2) walk_block<TM, MS, false, (MS > 2 ? 2 : MS), FW>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
+        else if (MS > 4 && wm <= 4) walk_block<TM, MS, false, (MS > 4 ? 4 : MS), FW>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
+        else walk_block<TM, MS, false, MS, FW>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
         if (tma) {
             __syncwarp();                                     // every lane has read this stage
             if (lane == 0 && blk + kStages < nsub)
-                ring_issue(p, map, ring, stage, i0, blk + kStages, nsub - 1 - (blk + kStages), bwd);
+                ring_issue<DIR>(p, map, ring, stage, i0, blk + kStages, nsub - 1 - (blk + kStages), FW, bwd);
         } else {
             __syncwarp(act);                                  // stage read before the next fill
         }
@@ -372,16 +389,18 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
         }
     }
     // end state of every slot: the state of the run standing for it (0 if none)
-    const uint32_t msf = t.msf;
-    for (uint32_t j = 0; j < msf; ++j) {
-        uint32_t v = 0;
+    if (FW) {
+        const uint32_t msf = t.msf;
+        for (uint32_t j = 0; j < msf; ++j) {
+            uint32_t v = 0;
 #pragma unroll
-        for (int r = 0; r < MS; ++r)
-            if (r < (int)mf && ((kf[r] >> j) & 1)) v = dec_f<TM>(T, sf[r]);
-        p.w.Rf[(size_t)i * msf + j] = v;
+            for (int r = 0; r < MS; ++r)
+                if (r < (int)mf && ((kf[r] >> j) & 1)) v = dec_f<TM>(T, sf[r]);
+            p.w.Rf[(size_t)i * msf + j] = v;
+        }
+        p.w.fconv[i] = fconv_sub;
+        p.w.fnrec[i] = fnrec;
     }
-    p.w.fconv[i] = fconv_sub;
-    p.w.fnrec[i] = fnrec;
     if (bwd) {
         const uint32_t msb = t.msb;
         for (uint32_t j = 0; j < msb; ++j) {
@@ -397,10 +416,20 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
     return true;
 }
 
-template <int TM, int MS>
-__global__ void __launch_bounds__(kChunkThreads)
+// Warps per block of the split parse kernel: four 32-chunk tiles, each walked
+// forward by one warp and backward by another, sharing one copy of the tables.
+constexpr uint32_t kSplitThreads = 256;
+
+// One parse.  SPLIT: warp pairs take 32-chunk tiles, the even warp walking
+// the chunks forward and the odd one backward (each with a one-direction TMA
+// ring), which doubles the warps in flight for the same shared memory.
+// Otherwise (recognizer mode: forward only) every warp walks its tile in the
+// directions needed.
+template <int TM, int MS, bool SPLIT>
+__global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
     reach_kernel(const __grid_constant__ Params p, const __grid_constant__ CUtensorMap map) {
     extern __shared__ __align__(16) uint8_t sm[];
+    constexpr int TILES = SPLIT ? 1 : 2;                      // tiles per ring stage
     Tabs T;
     uint8_t *rest = TM == TM_PAIR ? stage_reach_pair(p.t, sm, T) : stage_tables<TM>(p.t, sm, T);
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x / 32;
@@ -408,8 +437,8 @@ __global__ void __launch_bounds__(kChunkThreads)
     {
         const uint32_t a = smem_u32(rest);
         uint8_t *aligned = rest + ((1024 - (a & 1023)) & 1023);
-        ring.tiles = aligned + warp * (kStages * 2 * kTileBytes);
-        ring.bars = smem_u32(aligned + wpb * (kStages * 2 * kTileBytes)) + warp * kStages * 8;
+        ring.tiles = aligned + warp * (kStages * TILES * kTileBytes);
+        ring.bars = smem_u32(aligned + wpb * (kStages * TILES * kTileBytes)) + warp * kStages * 8;
         ring.phase = 0;
         if (p.text_tma && lane == 0) {
             for (int st = 0; st < kStages; ++st) mbar_init(ring.bars + 8 * st, 1);
@@ -417,18 +446,24 @@ __global__ void __launch_bounds__(kChunkThreads)
         }
         __syncwarp();
     }
-    // warps take tiles of 32 consecutive chunks
-    const uint64_t nw = (uint64_t)gridDim.x * wpb;
-    for (uint64_t t = (uint64_t)blockIdx.x * wpb + warp; t * 32 < p.c; t += nw) {
+    const uint64_t gw = (uint64_t)blockIdx.x * wpb + warp, nw = (uint64_t)gridDim.x * wpb;
+    const uint64_t t0 = SPLIT ? gw >> 1 : gw, tstep = SPLIT ? nw >> 1 : nw;
+    const bool backward_warp = SPLIT && (gw & 1);
+    for (uint64_t t = t0; t * 32 < p.c; t += tstep) {
         const uint32_t i = (uint32_t)(t * 32) + lane;
         const bool tma = p.text_tma && t * 32 + 32 <= p.c_full;
         if (i >= p.c) continue;                               // lanes past the text (plain path only)
-        if (!reach_chunk<TM, MS>(p, T, i, &map, ring, tma)) {
+        bool ok;
+        if (!SPLIT) ok = reach_chunk<TM, MS, DIR_BOTH>(p, T, i, &map, ring, tma);
+        else if (backward_warp) ok = reach_chunk<TM, MS, DIR_B>(p, T, i, &map, ring, tma);
+        else ok = reach_chunk<TM, MS, DIR_F>(p, T, i, &map, ring, tma);
+        if (!ok) {
             atomicExch(p.status, RE_E_INTERNAL);
             atomicExch(&p.w.flags[FLAG_INTERNAL], 1);
             for (int st = 0; st < kStages; ++st) {            // drain: bounded wait on every stage
-                bool ok = false;
-                for (uint32_t it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(ring.bars + 8 * st, (ring.phase >> st) & 1u);
+                bool done = false;
+                for (uint32_t it = 0; it < kWaitLimit && !done; ++it)
+                    done = mbar_try_wait(ring.bars + 8 * st, (ring.phase >> st) & 1u);
             }
             return;
         }
@@ -464,9 +499,9 @@ __global__ void __launch_bounds__(kChunkThreads) reach_batch_kernel(const __grid
     }
 }
 
-inline size_t reach_smem(const DevTables &t, int tm) {
+inline size_t reach_smem(const DevTables &t, int tm, uint32_t threads = kChunkThreads, int tiles = 2) {
     const size_t tab = tm == TM_PAIR ? reach_pair_smem(t) : tables_smem_bytes(t, tm);
-    return tab + 1024 + (kChunkThreads / 32) * (kStages * 2 * kTileBytes + kStages * 8);
+    return tab + 1024 + (threads / 32) * (kStages * tiles * kTileBytes + kStages * 8);
 }
 
 template <int TM, int MS>
@@ -496,19 +531,27 @@ bool launch_ms_batch(const BatchGroup &b, cudaStream_t s, uint32_t ms, int sm_co
     return true;
 }
 
-template <int TM, int MS>
-void launch_one(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
-    const size_t smem = reach_smem(p.t, TM);
+template <int TM, int MS, bool SPLIT>
+void launch_split(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
+    const uint32_t threads = SPLIT ? kSplitThreads : kChunkThreads;
+    const size_t smem = reach_smem(p.t, TM, threads, SPLIT ? 1 : 2);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(reach_kernel<TM, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(reach_kernel<TM, MS, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_kernel<TM, MS>, kChunkThreads, smem);
-    const uint64_t want = (p.c + kChunkThreads - 1) / kChunkThreads;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_kernel<TM, MS, SPLIT>, threads, smem);
+    const uint64_t warps = ((uint64_t)p.c + 31) / 32 * (SPLIT ? 2 : 1);
+    const uint64_t want = (warps + threads / 32 - 1) / (threads / 32);
     const uint64_t blocks = std::min<uint64_t>(want, (uint64_t)std::max(per_sm, 1) * sm_count);
-    reach_kernel<TM, MS><<<(uint32_t)std::max<uint64_t>(blocks, 1), kChunkThreads, smem, s>>>(p, map);
+    reach_kernel<TM, MS, SPLIT><<<(uint32_t)std::max<uint64_t>(blocks, 1), threads, smem, s>>>(p, map);
+}
+
+template <int TM, int MS>
+void launch_one(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
+    if (p.recognize) launch_split<TM, MS, false>(p, map, s, sm_count);
+    else launch_split<TM, MS, true>(p, map, s, sm_count);
 }
 
 template <int TM>
