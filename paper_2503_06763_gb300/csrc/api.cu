@@ -93,7 +93,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // bytes, SWIZZLE_64B to match the reach kernel's tile reads.
 bool text_tensor_map(CUtensorMap &map, const uint8_t *d_text, uint32_t k, uint64_t rows) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
-    if (!fn || rows < 32 || rows > 0xFFFFFFFFull || (k % 64) != 0) return false;
+    if (!fn || rows < 32 || rows > 0x7FFFFFFFull || (k % 64) != 0) return false;   // int32 row coordinates
     const cuuint64_t dims[2] = {k, rows};
     const cuuint64_t strides[1] = {k};
     const cuuint32_t box[2] = {64u, 32u};
@@ -108,7 +108,7 @@ bool text_tensor_map(CUtensorMap &map, const uint8_t *d_text, uint32_t k, uint64
 // warp tile of 32 groups, swizzled to match the kernel's shared-memory tile.
 bool output_tensor_map(CUtensorMap &map, void *d_cols, uint32_t cb, uint64_t rows) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
-    if (!fn || rows == 0 || rows > 0xFFFFFFFFull || (cb != 1 && cb != 2)) return false;
+    if (!fn || rows == 0 || rows > 0x7FFFFFFFull || (cb != 1 && cb != 2)) return false;   // int32 row coordinates
     const cuuint64_t dims[2] = {64ull * cb, rows};
     const cuuint64_t strides[1] = {64ull * cb};
     const cuuint32_t box[2] = {64u * cb, 32u};

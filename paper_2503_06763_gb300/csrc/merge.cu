@@ -720,11 +720,10 @@ size_t merge_extra_smem(const Params &p) {
     return a + (size_t)(t.nf + t.nb) * 8;
 }
 
-void launch_fixup(const Params &p, cudaStream_t s, int sm_count) {
-    if (p.tmode == TM_PAIR) fixup_one<TM_PAIR>(p, s, sm_count);
-    else if (p.tmode == TM_SMEM) fixup_one<TM_SMEM>(p, s, sm_count);
-    else fixup_one<TM_GLOBAL>(p, s, sm_count);
-}
+// The fix-up reads its tables from global memory: walks past the records are
+// rare, and no staged tables means no shared memory, so more warps hide the
+// latency of the record loads.
+void launch_fixup(const Params &p, cudaStream_t s, int sm_count) { fixup_one<TM_GLOBAL>(p, s, sm_count); }
 
 void launch_merge(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
     if (p.tmode == TM_PAIR) merge_enc<TM_PAIR>(p, map, s, sm_count);
@@ -735,10 +734,9 @@ void launch_merge(const Params &p, const CUtensorMap &map, cudaStream_t s, int s
 void launch_empty(const Params &p, cudaStream_t s) { empty_text_kernel<<<1, 1, 0, s>>>(p); }
 
 void launch_fixup_batch(const BatchGroup &b, uint32_t tmode, cudaStream_t s, int sm_count) {
+    (void)tmode;
     if (b.recognize || !b.chunks) return;
-    if (tmode == TM_PAIR) fixup_batch_one<TM_PAIR>(b, s, sm_count);
-    else if (tmode == TM_SMEM) fixup_batch_one<TM_SMEM>(b, s, sm_count);
-    else fixup_batch_one<TM_GLOBAL>(b, s, sm_count);
+    fixup_batch_one<TM_GLOBAL>(b, s, sm_count);
 }
 
 void launch_merge_batch(const BatchGroup &b, const Params &like, cudaStream_t s, int sm_count) {
