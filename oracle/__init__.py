@@ -19,6 +19,8 @@ What is here, and the passage of the paper each part follows
 * ``trees``     -- brute-force enumeration of all syntax trees of a text
   (Sect. 2.1, Example 1), their LSTs (Prop. 1) and their factoring into
   segments (Sect. 2.3.2): an independent definition of the clean SLPF.
+* ``matches``   -- match extraction (Sect. 4.2, getMatches): the spans of a
+  group, from enumerated trees and from a visit of the clean SLPF.
 * ``parallel_equations`` -- the parallel algorithm's Eqs. reacher, joiner,
   builder and merger (Sect. 3.2) with DFA / ME-DFA transition functions
   computed on segment sets (Sect. 3.1), used for the Example 6 pins and
