@@ -236,6 +236,29 @@ void re_batch_free(re_batch *b);
 re_status re_parse_static(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream stream,
                           re_slpf *slpf, const re_parse_opts *opts);
 
+/* ---------------------------------------------------------------- matches
+ * Match extraction (Sect. 4.2, "Match extraction", getMatches): the spans of
+ * a group.  A group is an operator node k of the numbered RE (its pair k( )k
+ * in segment names); a match is a pair (i, j), i <= j, such that in some
+ * syntax tree of the text the node k spans text[i:j] (bytes i .. j-1).
+ * Computed from the clean SLPF by a visit along FolSeg arcs.
+ *
+ * re_matches reads the columns of a finished re_parse of a text of len
+ * bytes (*slpf as given to that parse; its status word decides: a rejected
+ * text has no matches) and writes up to cap_pairs pairs to d_pairs as
+ * {i, j} uint64 pairs sorted by (i, j), and the total number of matches to
+ * *d_count (device; it may exceed cap_pairs: call again with more room).
+ * Enqueued on stream, asynchronous.  Supports at most 512 segments.
+ * The visit from a start column follows the group until it closes, so a
+ * group inside an ambiguous iteration (an ORF whose codon star also matches
+ * stop codons) can have a number of matches, and a cost, quadratic in the
+ * text length.
+ * d_workspace: re_match_workspace_size bytes, 256-byte aligned.            */
+re_status re_match_workspace_size(const re_handle *h, uint64_t len, uint64_t *bytes);
+re_status re_matches(re_handle *h, const re_slpf *slpf, uint64_t len, uint32_t group, uint64_t *d_pairs,
+                     uint64_t cap_pairs, uint64_t *d_count, void *d_workspace, uint64_t workspace_bytes,
+                     re_stream stream);
+
 /* Chunk-length autotuner (no counterpart in the paper, which fixes c to the
  * thread count).  Parses d_text[0..len) with candidate chunk lengths around
  * the built-in rule's choice (1/2x to 2x, multiples of 64, those whose

@@ -256,6 +256,7 @@ re_status re_compile(const char *pattern, size_t len, const re_compile_opts *opt
     const size_t i_bSC = add(C.bSlotCount.data(), C.bSlotCount.size() * 4);
     const size_t i_pt = add(C.pt.data(), C.pt.size() * 4);
     const size_t i_f2 = add(C.f2.data(), C.f2.size() * 4), i_b2 = add(C.b2.data(), C.b2.size() * 4);
+    const size_t i_fs = add(C.folseg.data(), C.folseg.size() * 8), i_dc = add(C.dict.data(), C.dict.size() * 8);
     DevTables &t = h->dev;
     t.fHashMask = C.fHashMask; t.bHashMask = C.bHashMask;
     t.ncls = C.ncls; t.W = C.W; t.ell = C.ell;
@@ -284,6 +285,8 @@ re_status re_compile(const char *pattern, size_t len, const re_compile_opts *opt
     t.pt = (const uint32_t *)(b + pc[i_pt].off);
     t.f2 = C.f2.empty() ? nullptr : (const uint32_t *)(b + pc[i_f2].off);
     t.b2 = C.b2.empty() ? nullptr : (const uint32_t *)(b + pc[i_b2].off);
+    t.folseg = (const uint64_t *)(b + pc[i_fs].off);
+    t.dict = C.dict.empty() ? nullptr : (const uint64_t *)(b + pc[i_dc].off);
     *out = h;
     return RE_OK;
 }
@@ -507,6 +510,71 @@ extern "C" re_status re_parse_host(re_handle *h, const uint8_t *text, uint64_t l
                  "columns to host");
     CUDA_TRY(cudaMemcpyAsync(host_status, slpf->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
              "status to host");
+    return RE_OK;
+}
+
+// ------------------------------------------------------------------ match extraction
+extern "C" re_status re_match_workspace_size(const re_handle *h, uint64_t len, uint64_t *bytes) {
+    if (!h || !bytes) { set_error("null argument"); return RE_E_INVALID_ARG; }
+    *bytes = match_workspace_bytes(len);
+    return RE_OK;
+}
+
+extern "C" re_status re_matches(re_handle *h, const re_slpf *slpf, uint64_t len, uint32_t group, uint64_t *d_pairs,
+                                uint64_t cap_pairs, uint64_t *d_count, void *d_workspace, uint64_t workspace_bytes,
+                                re_stream stream) {
+    if (!h || !slpf || !d_count || !slpf->d_cols || !slpf->d_status || (cap_pairs && !d_pairs)) {
+        set_error("null argument");
+        return RE_E_INVALID_ARG;
+    }
+    if (h->host_only) { set_error("handle was compiled with RE_COMPILE_HOST_ONLY"); return RE_E_INVALID_ARG; }
+    const Compiled &C = h->host;
+    re_slpf_kind kind;
+    uint32_t cb;
+    const re_status st = resolve_kind(h, slpf->kind, kind, cb);
+    if (st != RE_OK) return st;
+    if (slpf->kind == RE_SLPF_AUTO || slpf->col_bytes != cb || slpf->cols_cap_bytes < (len + 1) * cb) {
+        set_error("slpf does not describe the columns of a text of this length");
+        return RE_E_INVALID_ARG;
+    }
+    if (C.W > (uint32_t)kMatchW) { set_error("match extraction supports at most 512 segments"); return RE_E_CAPACITY; }
+    if (kind == RE_SLPF_DICT && !h->dev.dict) { set_error("no dictionary on the device"); return RE_E_INTERNAL; }
+    MatchArgs a{};
+    bool is_group = false;
+    for (uint32_t q = 0; q < C.ell; ++q) {
+        std::vector<int> kp;                                 // +1: k(, -1: )k, in order
+        for (int32_t v : C.parens[q])
+            if ((uint32_t)(v < 0 ? -v : v) == group) kp.push_back(v > 0 ? 1 : -1);
+        const uint64_t bit = 1ull << (q & 63);
+        const uint32_t w = q >> 6;
+        if (kp.empty()) { a.none[w] |= bit; continue; }
+        is_group = true;
+        if (kp.back() == 1) a.open[w] |= bit;
+        if (kp.front() == -1) a.close_first[w] |= bit;
+        for (size_t x = 0; x < kp.size(); ++x)
+            if (kp[x] == 1 && std::find(kp.begin() + x + 1, kp.end(), -1) != kp.end()) { a.whole[w] |= bit; break; }
+    }
+    if (!group || !is_group) { set_error("no group with this number (an operator node of the numbered RE)"); return RE_E_INVALID_ARG; }
+    if (!d_workspace || workspace_bytes < match_workspace_bytes(len) || ((uintptr_t)d_workspace & 255)) {
+        set_error("workspace missing, too small or not 256-byte aligned");
+        return RE_E_CAPACITY;
+    }
+    int dev_now = 0;
+    cudaGetDevice(&dev_now);
+    if (dev_now != h->device) { set_error("current device differs from the handle's device"); return RE_E_INVALID_ARG; }
+    a.cols = slpf->d_cols;
+    a.col_bytes = cb;
+    a.kind = kind;
+    a.W = C.W;
+    a.n = len;
+    a.folseg = h->dev.folseg;
+    a.dict = h->dev.dict;
+    a.status = slpf->d_status;
+    a.pairs = d_pairs;
+    a.cap = cap_pairs;
+    a.count = d_count;
+    launch_matches(a, d_workspace, (cudaStream_t)stream);
+    CUDA_TRY(cudaGetLastError(), "match launch");
     return RE_OK;
 }
 

@@ -312,6 +312,28 @@ void launch_merge(const Params &p, const CUtensorMap &out_map, cudaStream_t s, i
 void launch_empty(const Params &p, cudaStream_t s);
 cudaError_t set_kernel_attributes();   // max dynamic shared memory, once per process
 
+// Match extraction (matches.cu).
+constexpr int kMatchW = 8;                    // segment words supported (ell <= 512)
+
+struct MatchArgs {
+    const void *cols;                         // SLPF columns C_0 .. C_n
+    uint32_t col_bytes, kind, W;
+    uint64_t n;                               // text length (columns n + 1)
+    const uint64_t *folseg;                   // [ell][W]
+    const uint64_t *dict;                     // [dict_size][W] (DICT)
+    uint64_t open[kMatchW], close_first[kMatchW], whole[kMatchW], none[kMatchW];
+    const int32_t *status;                    // parse status: anything but RE_OK gives no matches
+    uint64_t *cnt;                            // [G] pairs per range, then their exclusive offsets
+    uint64_t *bsum;                           // [ceil(G / kScanBlock)] block totals, then offsets
+    uint64_t G;
+    uint64_t *pairs;                          // [cap][2]
+    uint64_t cap;
+    uint64_t *count;
+};
+
+size_t match_workspace_bytes(uint64_t n);
+void launch_matches(MatchArgs a, void *ws, cudaStream_t s);
+
 // Batch launchers: one launch per phase for every text of the group.
 void launch_batch_init(const Params *texts, uint32_t nt, uint32_t *queues, uint32_t nq, cudaStream_t s);
 bool launch_reach_batch(const BatchGroup &b, uint32_t tmode, uint32_t ms, cudaStream_t s, int sm_count);

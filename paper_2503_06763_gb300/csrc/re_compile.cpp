@@ -447,6 +447,14 @@ re_status compile_pattern(const char *pattern, size_t len, const re_compile_opts
             }
         }
         C.names.push_back(nm);
+        std::vector<int32_t> pr;
+        for (int sy : sg) {
+            const Sym &y = syms[sy];
+            if (y.kind == OPEN) pr.push_back(y.num);
+            else if (y.kind == CLOSE) pr.push_back(-y.num);
+            if (y.kind == OPEN || y.kind == CLOSE) C.max_group = std::max<uint32_t>(C.max_group, y.num);
+        }
+        C.parens.push_back(std::move(pr));
     }
 
     // ---- positions (numbered terminals) and byte classes (App. A)
@@ -495,6 +503,11 @@ re_status compile_pattern(const char *pattern, size_t len, const re_compile_opts
         for (int nx : fol[pos_sym[p]]) f[nx] = 1;
         for (uint32_t q = 0; q < ell; ++q) if (f[seg_first[q]]) Bits::set(&D[(size_t)p * W], q);
     }
+    // FolSeg(q) = D_end(q) (Eq. folsegdef); a segment ending in ⊣ has no follower
+    C.folseg.assign((size_t)ell * W, 0);
+    for (uint32_t q = 0; q < ell; ++q)
+        if (seg_end_pos[q] >= 0)
+            std::copy(&D[(size_t)seg_end_pos[q] * W], &D[(size_t)seg_end_pos[q] * W] + W, &C.folseg[(size_t)q * W]);
     std::vector<std::vector<uint32_t>> match_pos(ncls);
     for (uint32_t c = 0; c < ncls; ++c)
         for (uint32_t p = 0; p < P; ++p) if (pos_match[(size_t)p * ncls + c]) match_pos[c].push_back(p);

@@ -57,6 +57,8 @@ struct DevTables {
     uint32_t msf, msb;           // slot capacity per class pair
     uint32_t fI, bF;             // state ids of I (forward) and F (reverse)
     uint32_t dict_size;
+    const uint64_t *folseg;      // [ell][W] FolSeg of each segment (match extraction)
+    const uint64_t *dict;        // [dict_size][W] DICT columns, entry d at row d-1 (match extraction)
 };
 
 // Host-side compiled RE.
@@ -76,6 +78,9 @@ struct Compiled {
     std::vector<uint64_t> dict;               // [dict_size][W]
     uint32_t dict_size = 0;
     bool has_dict = false;
+    std::vector<uint64_t> folseg;             // [ell][W] FolSeg(q) (Eq. folsegdef)
+    std::vector<std::vector<int32_t>> parens; // per segment, in order: +k for k(, -k for )k
+    uint32_t max_group = 0;                   // largest operator number
 };
 
 // Compile; returns RE_OK or an error with a message in err.

@@ -24,7 +24,8 @@ RE_PARSE_RECOGNIZE_ONLY = 1
 
 EXPORTS = ["re_compile", "re_free", "re_get_info", "re_segment_name", "re_dict_copy",
            "re_slpf_layout", "re_workspace_size", "re_parse", "re_batch_plan", "re_batch_workspace_size",
-           "re_batch_chunk_len", "re_parse_batch", "re_batch_run", "re_batch_free", "re_autotune", "re_parse_host",
+           "re_batch_chunk_len", "re_parse_batch", "re_batch_run", "re_batch_free", "re_match_workspace_size",
+           "re_matches", "re_autotune", "re_parse_host",
            "re_parse_static",
            "re_last_error"]
 RE_STATIC_SCRATCH_BYTES = 64 << 20
@@ -102,6 +103,10 @@ def load():
     lib.re_batch_run.restype = i32
     lib.re_batch_free.argtypes = [vp]
     lib.re_batch_free.restype = None
+    lib.re_match_workspace_size.argtypes = [vp, u64, ctypes.POINTER(u64)]
+    lib.re_match_workspace_size.restype = i32
+    lib.re_matches.argtypes = [vp, ctypes.POINTER(Slpf), u64, u32, vp, u64, vp, vp, u64, vp]
+    lib.re_matches.restype = i32
     lib.re_autotune.argtypes = [vp, vp, u64, ctypes.POINTER(Slpf), vp, u64, vp, ctypes.POINTER(ParseOpts),
                                 ctypes.POINTER(u32)]
     lib.re_autotune.restype = i32
@@ -239,6 +244,29 @@ class Regex:
         check(load().re_parse_static(self._h, text.data_ptr() if n else None, n, ctypes.c_void_p(s.cuda_stream),
                                      ctypes.byref(slpf), ctypes.byref(opts)))
         return out, status, kname
+
+    def matches(self, cols, status, n: int, group: int, kind: str, cap=None, stream=None):
+        """re_matches over the columns of a parse of an n-byte text: returns
+        an int64 [m, 2] CUDA tensor of (i, j) spans of group ``group`` in
+        (i, j) order.  With cap=None a first call counts the matches."""
+        import torch
+        dev = cols.device
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        cb = cols.element_size()
+        slpf = Slpf(KINDS[kind], cb, n + 1, cols.data_ptr(), cols.numel() * cb, status.data_ptr())
+        w = ctypes.c_uint64()
+        check(load().re_match_workspace_size(self._h, n, ctypes.byref(w)))
+        ws = torch.empty(max(w.value, 256), dtype=torch.uint8, device=dev)
+        count = torch.zeros(1, dtype=torch.int64, device=dev)
+        if cap is None:
+            check(load().re_matches(self._h, ctypes.byref(slpf), n, group, None, 0, count.data_ptr(),
+                                    ws.data_ptr(), ws.numel(), ctypes.c_void_p(s.cuda_stream)))
+            cap = int(count.item())
+        pairs = torch.empty((max(cap, 1), 2), dtype=torch.int64, device=dev)
+        check(load().re_matches(self._h, ctypes.byref(slpf), n, group, pairs.data_ptr(), cap, count.data_ptr(),
+                                ws.data_ptr(), ws.numel(), ctypes.c_void_p(s.cuda_stream)))
+        total = int(count.item())
+        return pairs[:min(total, cap)], total
 
     def autotune(self, text, kind: str = "auto", workspace=None, stream=None) -> int:
         """re_autotune on a CUDA uint8 tensor: returns the chunk length chosen
