@@ -48,7 +48,7 @@ def parse_args():
     ap.add_argument("--bytes", type=int, default=N_BYTES, help="text size (default 256 MiB)")
     ap.add_argument("--chunk-len", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"],
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "matches"],
                     help="single: one 256 MiB text (default); batch: 4096 texts under 8 random REs; "
                          "serve: Poisson request stream")
     ap.add_argument("--texts", type=int, default=4096, help="batch mode: number of texts")
@@ -207,6 +207,8 @@ def main():
         return batch_mode(args, rank, world, local)
     if args.mode == "serve":
         return serve_mode(args, rank, world, local)
+    if args.mode == "matches":
+        return matches_mode(args, rank, world, local)
 
     import torch
     torch.cuda.set_device(local)
@@ -501,6 +503,55 @@ def serve_mode(args, rank, world, local):
                    "segments": [r[2].ell for r in res]},
         "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"], "rates": results,
     }
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def matches_mode(args, rank, world, local):
+    """Match extraction (re_matches) after a parse of the DNA workload: the
+    stop codons that close an ORF (group 13), as text GB/s of columns
+    visited; the oracle's forest visit on a 1 MiB prefix beside it."""
+    import torch
+    import workloads as W
+    from paper_2503_06763_gb300 import Regex
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.bytes
+    host = W.dna_text(n, seed=rank_seed(1, rank))
+    rx = Regex(W.DNA_RE)
+    text = torch.from_numpy(host).to(dev)
+    cols, st, kind = rx.parse(text)
+    torch.cuda.synchronize()
+    group = 13
+    pairs, total = rx.matches(cols, st, n, group, kind)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 3)):
+        rx.matches(cols, st, n, group, kind, cap=total)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        rx.matches(cols, st, n, group, kind, cap=total)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import matches as M
+        from oracle import serial
+        from oracle.re_front import compile_re
+        c = compile_re(W.DNA_RE)
+        sample = host[:1 << 20].tobytes()
+        colsets = [serial.from_bits(row) for row in serial.parse(c, sample)]
+        t0 = time.perf_counter()
+        M.matches_by_slpf(c, sample, group, colsets)
+        dt = time.perf_counter() - t0
+        cpu = {"value": round(len(sample) / dt / 1e9, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": "first 1 MiB: forest visit of the oracle's own SLPF (columns given)"}
+    line = {"metric": "match extraction GB/s of text (re_matches: count, scan, write)", "value": round(n / (ms / 1e3) / 1e9, 3),
+            "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "group": "13 (stop codon closing an ORF)", "matches": total},
+            "cpu_baseline": cpu}
     if rank == 0:
         print(json.dumps(line))
 

@@ -135,12 +135,12 @@ __device__ void chain_at(const Params &p, uint32_t i) {
     if (bad) atomicExch(&p.w.flags[FLAG_INTERNAL], 1);
 }
 
-__global__ void join_classify_kernel(Params p) {
+__global__ void join_classify_kernel(const __grid_constant__ Params p) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < p.c) classify_at(p, i);
 }
 
-__global__ void join_chain_kernel(Params p) {
+__global__ void join_chain_kernel(const __grid_constant__ Params p) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < p.c) chain_at(p, i);
 }
@@ -212,14 +212,14 @@ __device__ void status_of(const Params &p) {
     *p.status = st;
 }
 
-__global__ void join_verify_kernel(Params p) {
+__global__ void join_verify_kernel(const __grid_constant__ Params p) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < p.c) verify_at(p, i);
 }
 
-__global__ void status_kernel(Params p) { status_of(p); }
+__global__ void status_kernel(const __grid_constant__ Params p) { status_of(p); }
 
-__global__ void flags_init_kernel(Params p) {
+__global__ void flags_init_kernel(const __grid_constant__ Params p) {
     if (threadIdx.x < FLAG_COUNT) p.w.flags[threadIdx.x] = threadIdx.x < 2 ? (int32_t)p.c : 0;
 }
 

@@ -323,7 +323,7 @@ struct MatchArgs {
     const uint64_t *dict;                     // [dict_size][W] (DICT)
     uint64_t open[kMatchW], close_first[kMatchW], whole[kMatchW], none[kMatchW];
     const int32_t *status;                    // parse status: anything but RE_OK gives no matches
-    uint64_t *cnt;                            // [G] pairs per range, then their exclusive offsets
+    uint64_t *cnt;                            // [G] pairs per warp range, then their exclusive offsets
     uint64_t *bsum;                           // [ceil(G / kScanBlock)] block totals, then offsets
     uint64_t G;
     uint64_t *pairs;                          // [cap][2]

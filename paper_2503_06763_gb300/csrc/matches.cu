@@ -9,9 +9,13 @@
 // open, and a segment whose first k-parenthesis is )k at column j closes it,
 // giving (i, j).  The SLPF is clean, so each such path lies on a whole tree.
 //
-// One thread per range of 64 start columns.  A count pass, an exclusive scan
-// of the counts and a write pass put the pairs in (i, j) order with no
-// atomics; the total is reported even when the caller's buffer is smaller.
+// One warp per range of 2048 start columns, 32 consecutive ones per step,
+// holding 64 columns in registers so that visits read their first 32 columns
+// by shuffle.  A count pass, an exclusive scan of the per-warp counts and a
+// write pass put the pairs in (i, j) order with no atomics; the total is
+// reported even when the caller's buffer is smaller.
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace slpf {
@@ -20,12 +24,13 @@ constexpr uint32_t kScanBlock = 1024;
 
 namespace {
 
-__device__ __forceinline__ void load_column(const MatchArgs &a, uint64_t r, uint64_t (&v)[kMatchW]) {
+template <int W>
+__device__ __forceinline__ void load_column(const MatchArgs &a, uint64_t r, uint64_t (&v)[W]) {
     if (a.kind == RE_SLPF_DICT) {
         const uint32_t id = a.col_bytes == 2 ? __ldg(reinterpret_cast<const uint16_t *>(a.cols) + r)
                                              : __ldg(reinterpret_cast<const uint32_t *>(a.cols) + r);
 #pragma unroll
-        for (int w = 0; w < kMatchW; ++w)
+        for (int w = 0; w < W; ++w)                          // W rounds a.W up: the rows have stride a.W
             v[w] = (w < (int)a.W && id) ? __ldg(a.dict + (size_t)(id - 1) * a.W + w) : 0ull;
     } else {
         uint64_t x;
@@ -37,45 +42,55 @@ __device__ __forceinline__ void load_column(const MatchArgs &a, uint64_t r, uint
         }
         v[0] = x;
 #pragma unroll
-        for (int w = 1; w < kMatchW; ++w) v[w] = 0;
+        for (int w = 1; w < W; ++w) v[w] = 0;
     }
 }
 
-// Visit from start column i; emit(j) for every match (i, j), j increasing.
-template <typename F>
-__device__ void visit(const MatchArgs &a, uint64_t i, F emit) {
-    uint64_t C[kMatchW], S[kMatchW];
-    load_column(a, i, C);
-    bool whole = false, live = false;
+// Columns per warp: the warp takes 32 consecutive start columns per step, so
+// its column loads are coalesced; warp-level scans keep the (i, j) order.
+constexpr uint32_t kWarpCols = 2048;
+
+__device__ __forceinline__ uint64_t warp_exclusive(uint64_t c, uint64_t &total) {
+    const uint32_t lane = threadIdx.x & 31;
+    uint64_t s = c;
 #pragma unroll
-    for (int w = 0; w < kMatchW; ++w) {
-        whole |= (C[w] & a.whole[w]) != 0;
-        S[w] = C[w] & a.open[w];
-        live |= S[w] != 0;
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, s, d);
+        if ((int)lane >= d) s += y;
     }
-    if (whole) emit(i);
-    uint64_t r = i;
+    total = __shfl_sync(0xFFFFFFFFu, s, 31);
+    return s - c;
+}
+
+// One step of a warp: lane l starts the visit at column i = base + l.  The
+// warp holds columns base .. base + 63 in registers (c0: base + lane, c1:
+// base + 32 + lane), so the first 32 columns of every visit come by shuffle;
+// a visit still open after them goes on with loads (visit_from).  Called by
+// the whole warp; emit(j) gets the matches (i, j) of this lane in j order.
+template <int W, typename F>
+__device__ void visit_from(const MatchArgs &a, uint64_t i, uint64_t r, uint64_t (&S)[W], F emit) {
+    bool live = true;
     while (live && r < a.n) {
-        uint64_t N[kMatchW];
+        uint64_t N[W], C[W];
 #pragma unroll
-        for (int w = 0; w < kMatchW; ++w) N[w] = 0;
+        for (int w = 0; w < W; ++w) N[w] = 0;
 #pragma unroll
-        for (int w = 0; w < kMatchW; ++w) {
+        for (int w = 0; w < W; ++w) {
             uint64_t m = S[w];
             while (m) {
                 const uint32_t q = 64 * w + (uint32_t)__ffsll((long long)m) - 1;
                 m &= m - 1;
 #pragma unroll
-                for (int w2 = 0; w2 < kMatchW; ++w2)
-                    if (w2 < (int)a.W) N[w2] |= __ldg(a.folseg + (size_t)q * a.W + w2);
+                for (int w2 = 0; w2 < W; ++w2)
+                        if (w2 < (int)a.W) N[w2] |= __ldg(a.folseg + (size_t)q * a.W + w2);
             }
         }
         ++r;
-        load_column(a, r, C);
+        load_column<W>(a, r, C);
         bool close = false;
         live = false;
 #pragma unroll
-        for (int w = 0; w < kMatchW; ++w) {
+        for (int w = 0; w < W; ++w) {
             N[w] &= C[w];
             close |= (N[w] & a.close_first[w]) != 0;
             S[w] = N[w] & a.none[w];
@@ -85,15 +100,93 @@ __device__ void visit(const MatchArgs &a, uint64_t i, F emit) {
     }
 }
 
-__global__ void match_count_kernel(MatchArgs a) {
-    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= a.G) return;
-    uint64_t c = 0;
-    if (*a.status == RE_OK) {
-        const uint64_t end = min(64 * g + 64, a.n + 1);
-        for (uint64_t i = 64 * g; i < end; ++i) visit(a, i, [&](uint64_t) { ++c; });
+template <int W, typename F>
+__device__ __forceinline__ void warp_step(const MatchArgs &a, uint64_t base, const uint64_t (&c0)[W],
+                                          const uint64_t (&c1)[W], F emit) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t i = base + lane;
+    uint64_t S[W];
+    bool whole = false, live = false;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        whole |= (c0[w] & a.whole[w]) != 0;
+        S[w] = c0[w] & a.open[w];
+        live |= S[w] != 0;
     }
-    a.cnt[g] = c;
+    live = live && i <= a.n;
+    if (whole && i <= a.n) emit(i);
+    uint32_t d = 1;
+    for (; d <= 32 && __any_sync(0xFFFFFFFFu, live); ++d) {
+        const uint32_t src = lane + d;                        // column base + src: lane src of c0 or c1
+        uint64_t col[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const uint64_t x0 = __shfl_sync(0xFFFFFFFFu, c0[w], src & 31);
+            const uint64_t x1 = __shfl_sync(0xFFFFFFFFu, c1[w], src & 31);
+            col[w] = src < 32 ? x0 : x1;
+        }
+        if (live && i + d - 1 < a.n) {                         // step from column i + d - 1 to i + d
+            uint64_t N[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) N[w] = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                uint64_t m = S[w];
+                while (m) {
+                    const uint32_t q = 64 * w + (uint32_t)__ffsll((long long)m) - 1;
+                    m &= m - 1;
+#pragma unroll
+                    for (int w2 = 0; w2 < W; ++w2)
+                        if (w2 < (int)a.W) N[w2] |= __ldg(a.folseg + (size_t)q * a.W + w2);
+                }
+            }
+            bool close = false;
+            live = false;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                N[w] &= col[w];
+                close |= (N[w] & a.close_first[w]) != 0;
+                S[w] = N[w] & a.none[w];
+                live |= S[w] != 0;
+            }
+            if (close) emit(i + d);
+        } else {
+            live = false;
+        }
+    }
+    if (live) visit_from<W>(a, i, i + 32, S, emit);               // longer than the register window
+}
+
+// Columns base .. base + 63 into registers (zero past the last column).
+template <int W>
+__device__ __forceinline__ void load_window(const MatchArgs &a, uint64_t base, uint64_t (&c0)[W], uint64_t (&c1)[W]) {
+    const uint32_t lane = threadIdx.x & 31;
+    if (base + lane <= a.n) load_column<W>(a, base + lane, c0);
+    else for (int w = 0; w < W; ++w) c0[w] = 0;
+    if (base + 32 + lane <= a.n) load_column<W>(a, base + 32 + lane, c1);
+    else for (int w = 0; w < W; ++w) c1[w] = 0;
+}
+
+template <int W>
+__global__ void match_count_kernel(const __grid_constant__ MatchArgs a) {
+    const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wid >= a.G) return;                                   // whole warps: G counts warps
+    const uint32_t lane = threadIdx.x & 31;
+    uint64_t total = 0;
+    if (*a.status == RE_OK) {
+        for (uint32_t step = 0; step < kWarpCols / 32; ++step) {
+            const uint64_t base = wid * kWarpCols + 32 * step;
+            if (base > a.n) break;                            // warp-uniform
+            uint64_t c0[W], c1[W];
+            load_window<W>(a, base, c0, c1);
+            uint64_t c = 0;
+            warp_step<W>(a, base, c0, c1, [&](uint64_t) { ++c; });
+            uint64_t t;
+            warp_exclusive(c, t);
+            total += t;
+        }
+    }
+    if (lane == 0) a.cnt[wid] = total;
 }
 
 // Exclusive scan of kScanBlock values per block (in place); block totals to out.
@@ -149,39 +242,60 @@ __global__ void scan_totals_kernel(uint64_t *v, uint64_t n) {
     }
 }
 
-__global__ void match_write_kernel(MatchArgs a) {
-    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= a.G) return;
-    uint64_t off = a.cnt[g] + a.bsum[g / kScanBlock];
+template <int W>
+__global__ void match_write_kernel(const __grid_constant__ MatchArgs a) {
+    const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wid >= a.G) return;
+    const uint32_t lane = threadIdx.x & 31;
+    uint64_t off = a.cnt[wid] + a.bsum[wid / kScanBlock];
     if (*a.status == RE_OK) {
-        const uint64_t end = min(64 * g + 64, a.n + 1);
-        for (uint64_t i = 64 * g; i < end; ++i)
-            visit(a, i, [&](uint64_t j) {
-                if (off < a.cap) { a.pairs[2 * off] = i; a.pairs[2 * off + 1] = j; }
-                ++off;
-            });
+        for (uint32_t step = 0; step < kWarpCols / 32; ++step) {
+            const uint64_t base = wid * kWarpCols + 32 * step;
+            if (base > a.n) break;                            // warp-uniform
+            uint64_t c0[W], c1[W];
+            load_window<W>(a, base, c0, c1);
+            uint64_t c = 0;
+            warp_step<W>(a, base, c0, c1, [&](uint64_t) { ++c; });
+            uint64_t t;
+            uint64_t o = off + warp_exclusive(c, t);
+            if (__any_sync(0xFFFFFFFFu, c != 0)) {
+                const uint64_t i = base + lane;
+                warp_step<W>(a, base, c0, c1, [&](uint64_t j) {
+                    if (o < a.cap) { a.pairs[2 * o] = i; a.pairs[2 * o + 1] = j; }
+                    ++o;
+                });
+            }
+            off += t;
+        }
     }
-    if (g == a.G - 1) *a.count = off;                       // the last range ends the sequence
+    if (wid == a.G - 1 && lane == 0) *a.count = off;          // the last warp ends the sequence
 }
 
 }  // namespace
 
 size_t match_workspace_bytes(uint64_t n) {
-    const uint64_t G = n / 64 + 1;
+    const uint64_t G = n / kWarpCols + 1;
     const uint64_t nb = (G + kScanBlock - 1) / kScanBlock;
     return ((G * 8 + 255) & ~(size_t)255) + ((nb * 8 + 255) & ~(size_t)255);
 }
 
 void launch_matches(MatchArgs a, void *ws, cudaStream_t s) {
-    a.G = a.n / 64 + 1;
+    a.G = a.n / kWarpCols + 1;                                // warps, kWarpCols start columns each
     const uint64_t nb = (a.G + kScanBlock - 1) / kScanBlock;
     a.cnt = reinterpret_cast<uint64_t *>(ws);
     a.bsum = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(ws) + ((a.G * 8 + 255) & ~(size_t)255));
-    const uint32_t threads = 128, blocks = (uint32_t)((a.G + threads - 1) / threads);
-    match_count_kernel<<<blocks, threads, 0, s>>>(a);
-    scan_block_kernel<<<(uint32_t)nb, kScanBlock, 0, s>>>(a.cnt, a.G, a.bsum);
-    scan_totals_kernel<<<1, kScanBlock, 0, s>>>(a.bsum, nb);
-    match_write_kernel<<<blocks, threads, 0, s>>>(a);
+    const uint32_t threads = 128, blocks = (uint32_t)((a.G * 32 + threads - 1) / threads);
+    auto run = [&](auto wtag) {
+        constexpr int W = decltype(wtag)::value;
+        match_count_kernel<W><<<blocks, threads, 0, s>>>(a);
+        scan_block_kernel<<<(uint32_t)nb, kScanBlock, 0, s>>>(a.cnt, a.G, a.bsum);
+        scan_totals_kernel<<<1, kScanBlock, 0, s>>>(a.bsum, nb);
+        match_write_kernel<W><<<blocks, threads, 0, s>>>(a);
+    };
+    if (a.W <= 1) run(std::integral_constant<int, 1>{});
+    else if (a.W <= 2) run(std::integral_constant<int, 2>{});
+    else if (a.W <= 4) run(std::integral_constant<int, 4>{});
+    else run(std::integral_constant<int, 8>{});
 }
 
 }  // namespace slpf

@@ -218,7 +218,7 @@ __device__ void fixup_chunk(const Params &p, const Tabs &T, uint64_t i, bool &ba
 }
 
 template <int TM>
-__global__ void __launch_bounds__(kChunkThreads) fixup_kernel(Params p) {
+__global__ void __launch_bounds__(kChunkThreads) fixup_kernel(const __grid_constant__ Params p) {
     extern __shared__ __align__(16) uint8_t sm[];
     Tabs T;
     stage_tables<TM>(p.t, sm, T);
@@ -610,7 +610,7 @@ __global__ void __launch_bounds__(kBlockThreads, 3) merge_batch_kernel(const __g
     }
 }
 
-__global__ void empty_text_kernel(Params p) { empty_text(p); }
+__global__ void empty_text_kernel(const __grid_constant__ Params p) { empty_text(p); }
 
 template <typename K>
 int grid_for(K kernel, size_t smem, uint64_t items, int sm_count, uint32_t threads) {

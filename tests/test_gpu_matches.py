@@ -115,3 +115,18 @@ def test_dna_stop_codon_group_on_16mib(lib):
         want.extend(int(i) for i in stops if i >= first + 3)
     want = sorted((i, i + 3) for i in want)
     assert got == want and total > 100_000
+
+
+def test_wide_columns_log_re(lib):
+    """162 segments: three words per column (the kernels round up to four)."""
+    rx = lib(W.LOG_RE)
+    c = compile_re(W.LOG_RE)
+    assert rx.words == 3
+    host = W.log_text(20_000, seed=5)
+    cols = [serial.from_bits(row) for row in serial.parse(c, host.tobytes())]
+    ks = groups(c)
+    pick = [ks[0], ks[1], ks[len(ks) // 3], ks[len(ks) // 2], ks[-1]]
+    for k in pick:
+        want = M.matches_by_slpf(c, host.tobytes(), k, cols)
+        got, total, st = device_matches(rx, host, k)
+        assert st == 0 and total == len(want) and got == want, k
