@@ -316,3 +316,82 @@ def test_planted_mistakes_are_caught(golden, monkeypatch):
     monkeypatch.setattr(pe, "nfa_image", lambda c, S, b: frozenset(q for s in S for q in c.folseg[s]))
     with pytest.raises(Exception):
         assert e2_clean() == g["ex6_C"]
+
+
+def test_more_planted_mistakes_are_caught(golden, monkeypatch):
+    """Further plausible mistakes, each planted in the oracle on the CPU,
+    must make one of the pins fail: a dropped FolSeg arc, a wrong initial
+    set, an end-letter test that looks at the wrong byte, a wrong numbering
+    order, and a match rule that closes a group on its last parenthesis."""
+    import itertools
+    from oracle import matches as M
+    from oracle import re_front
+
+    def disagrees_with_trees(c, pattern_texts):
+        for text in pattern_texts:
+            want, _ = trees.slpf_by_trees(c, text)
+            if serial.parse_small(c, text) != want:
+                return True
+        return False
+
+    texts = [bytes(t) for n in range(0, 6) for t in itertools.product(b"ab", repeat=n)]
+    # 1) a FolSeg arc dropped
+    c = compile_re("(a|b|ab)*")
+    q = next(i for i, f in enumerate(c.folseg) if len(f) > 1)
+    c.folseg[q] = frozenset(sorted(c.folseg[q])[1:])
+    assert disagrees_with_trees(c, texts)
+    # 2) a segment wrongly taken as initial
+    c = compile_re("(a|b|ab)*")
+    extra = next(i for i in range(c.ell) if i not in c.initial and c.segments[i][-1][0] == "t")
+    c.initial = frozenset(c.initial | {extra})
+    assert disagrees_with_trees(c, texts)
+    # 3) the arc label tested against the wrong byte
+    c = compile_re("(a|b|ab)*")
+    orig = re_front.Compiled.matches
+    monkeypatch.setattr(re_front.Compiled, "matches", lambda self, q, b: orig(self, q, b ^ 3))
+    assert disagrees_with_trees(c, texts)
+    monkeypatch.setattr(re_front.Compiled, "matches", orig)
+    # 4) numbering in postorder instead of preorder: the e_1 numbering pin fails
+    g = golden["e1"]
+    orig_number = re_front.number
+
+    def postorder(root):
+        counter = [0]
+
+        def visit(nd):
+            for ch in nd.children:
+                visit(ch)
+            counter[0] += 1
+            nd.num = counter[0]
+        visit(root)
+        return counter[0]
+
+    monkeypatch.setattr(re_front, "number", postorder)
+    c = compile_re(g["pattern"])
+    assert [sym_name(s) for s in c.symbols] != g["numbered_symbols"]     # the e_1 pin fails
+    monkeypatch.setattr(re_front, "number", orig_number)
+    assert [sym_name(s) for s in compile_re(g["pattern"]).symbols] == g["numbered_symbols"]
+    # 5) a group closed on its last parenthesis instead of its first
+    c = compile_re("((ab)*c|a(bc)*)*")
+    orig_classes = M.segment_classes
+
+    def wrong_classes(cc, k):
+        opn, close_first, whole, none = orig_classes(cc, k)
+        close_last = frozenset(q for q in range(cc.ell)
+                               if M.k_parens(cc, q, k) and M.k_parens(cc, q, k)[-1] == ")")
+        return opn, close_last, whole, none
+
+    monkeypatch.setattr(M, "segment_classes", wrong_classes)
+    found = False
+    for n in range(1, 7):
+        for t in itertools.product(b"abc", repeat=n):
+            text = bytes(t)
+            for k in (1, 2, 3):
+                if M.matches_by_slpf(c, text, k) != M.matches_by_trees(c, text, k):
+                    found = True
+                    break
+            if found:
+                break
+        if found:
+            break
+    assert found
