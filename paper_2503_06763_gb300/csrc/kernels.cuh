@@ -21,7 +21,7 @@ namespace slpf {
 
 constexpr int kMaxW = 64;           // segments per column <= 4096
 constexpr uint32_t kBlockThreads = 256;     // build & merge
-constexpr uint32_t kChunkThreads = 128;     // reach and fix-up (one thread per chunk)
+constexpr uint32_t kChunkThreads = 128;     // batch reach, recognizer reach and fix-up blocks
 constexpr uint32_t kRecBounds = 32;   // boundaries recorded per chunk and direction before runs meet
 constexpr uint32_t kRecEntries = 96;  // (state, slot set) entries recorded per chunk and direction
 

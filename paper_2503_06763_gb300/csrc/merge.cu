@@ -5,11 +5,14 @@
 //   they met.  At every recorded boundary the exact state is the union, over
 //   the runs whose slot set the chunk's input J_{i-1} (or Ĵ_{i+1}) enters, of
 //   the run states: Eq. joiner applied at sub-chunk granularity.  Boundaries
-//   beyond the record are walked with the DFA from the last exact state.
+//   beyond the record are walked with the DFA from the last exact state
+//   (global tables: walks are rare, and no shared memory means more warps
+//   to hide the latency of the record loads).
 // build & merge: one thread per column group g (64 columns).  The forward
 //   builder (B from FC[g]) and the backward builder (B̂ from BC[g]) run at the
-//   same time from the two ends of the group, keep their first 32 states in
-//   shared memory, meet in the middle and then merge while they proceed to the
+//   same time from the two ends of the group, keep their first 32 states
+//   (in registers with two-byte tables, in shared memory otherwise), meet in
+//   the middle and then merge while they proceed to the
 //   opposite ends: each new state is intersected with the stored state of the
 //   other direction, C_r = B_r ∩ B̂_r (Eq. merger), and written in the
 //   requested encoding (DENSE bitset, or DICT index through the pair table

@@ -1,12 +1,14 @@
 // Reach phase, shared implementation included by reach_pair.cu, reach_smem.cu
 // and reach_global.cu (one translation unit per table mode).
 //
-// Reach phase (arXiv 2503.06763, Eq. reacher; Sect. 4.1 fuses the forward and
-// backward reacher of a chunk into one task, as here).
+// Reach phase (arXiv 2503.06763, Eq. reacher).
 //
-// One thread per chunk y_i runs, in the same loop, the forward ME-DFA from
-// every speculation slot of the chunk left to right and the reverse ME-DFA
-// from every backward slot right to left: two independent dependency chains.
+// One lane per chunk y_i and direction runs the forward ME-DFA from every
+// speculation slot of the chunk left to right, or the reverse ME-DFA from
+// every backward slot right to left.  A parse gives the two directions of a
+// 32-chunk tile to two warps (Sect. 4.1 fuses them into one task; on the GPU
+// separate warps double the chains in flight); batches and the recognizer
+// walk the needed directions in one warp.
 // Slots are the distinct start sets after the boundary byte (a run from a
 // singleton {q} reaches D_end(q) after one byte), restricted by the class of
 // the byte before the boundary (the last-character filter of Sect. 6).
@@ -16,10 +18,10 @@
 // Runs are kept distinct: at every 64-byte sub-chunk boundary dead runs are
 // dropped and runs in equal states are merged (equal states stay equal), each
 // run carrying the set of slots it stands for.  While several runs are live
-// the thread records, per boundary, the (state, slot set) of each run; the
+// the lane records, per boundary, the (state, slot set) of each run; the
 // fix-up later turns a record into the exact state by the union of Eq. joiner
 // over the slots its input enters.  Once one run is left its state is exact
-// for any input that enters a live slot, and the thread writes it as a
+// for any input that enters a live slot, and the lane writes it as a
 // checkpoint (FC / BC).  At the end it writes the end state of every slot
 // (R, R̂) and the first (forward) / last (backward) boundary where a single
 // run was left.  Active runs drop fast after a few bytes (Sect. 4.3), so
