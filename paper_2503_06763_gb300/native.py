@@ -223,6 +223,15 @@ class Regex:
                               ctypes.byref(slpf), workspace.data_ptr(), workspace.numel(), ctypes.byref(opts)))
         return out, status, kname
 
+    def parse_raw(self, text_ptr: int, n: int, out_ptr: int, out_cap: int, kind: str, cb: int, status_ptr: int,
+                  ws_ptr: int, ws_bytes: int, stream_ptr: int):
+        """re_parse on raw device pointers (no tensor views): for callers that
+        lay out their own buffers, such as the serving loop."""
+        slpf = Slpf(KINDS[kind], cb, 0, out_ptr, out_cap, status_ptr)
+        opts = ParseOpts(KINDS[kind], 0, 0, 0, None)
+        check(load().re_parse(self._h, text_ptr if n else None, n, ctypes.c_void_p(stream_ptr), ctypes.byref(slpf),
+                              ws_ptr, ws_bytes, ctypes.byref(opts)))
+
     def parse_static(self, text, kind: str = "auto", chunk_len: int = 0, stream=None, out=None, status=None):
         """Like ``parse`` but through re_parse_static: the library's fixed device
         scratch serves as workspace, so only the output tensors are allocated
@@ -389,6 +398,19 @@ class Batch:
                                     ctypes.c_void_p(s.cuda_stream)))
         self._keep = (list(texts), outs, status, workspace)     # bound buffers stay alive with the batch
         return outs, status, kinds
+
+    def parse_raw(self, text_ptrs, out_ptrs, out_caps, kinds, cbs, status_ptr: int, ws_ptr: int, ws_bytes: int,
+                  stream_ptr: int):
+        """re_parse_batch on raw device pointers: text j at text_ptrs[j], its
+        columns at out_ptrs[j] (out_caps[j] bytes, encoding kinds[j] / cbs[j]),
+        status words at status_ptr + 4 j.  The caller keeps the buffers alive."""
+        m = max(self.count, 1)
+        arr = (Slpf * m)()
+        ptrs = (ctypes.c_void_p * m)()
+        for j in range(self.count):
+            arr[j] = Slpf(KINDS[kinds[j]], cbs[j], 0, out_ptrs[j], out_caps[j], status_ptr + 4 * j)
+            ptrs[j] = text_ptrs[j] if self.lens[j] else None
+        check(load().re_parse_batch(self._b, ptrs, arr, ws_ptr, ws_bytes, ctypes.c_void_p(stream_ptr)))
 
     def run(self, stream=None):
         """Enqueue the kernels again over the buffers bound by ``parse``."""

@@ -80,21 +80,33 @@ class Server:
                 pin_in=torch.empty(arena_bytes // 4, dtype=torch.uint8).pin_memory(),
                 pin_out=torch.empty(arena_bytes // 2, dtype=torch.uint8).pin_memory()))
         self.stats = {"batches": 0, "requests": 0, "max_batch": 0, "max_inflight": 0}
+        self._prepare()
 
     # ------------------------------------------------------------------ sizing
-    def _layout(self, re_index: int, n: int):
-        rx = self.regexes[re_index]
-        kname, cb, nbytes = rx.layout(n, "auto")
-        return kname, cb, nbytes
+    def _prepare(self):
+        """Per RE: its column encoding (independent of the text length) and a
+        bound on a text's workspace for any chunk length of at least 256 (the
+        shortest the library picks): 8 bytes of checkpoints per 64 text bytes,
+        the slot ends and run records of every 256-byte chunk, and the
+        alignment of the workspace arrays."""
+        self._enc, self._ws_chunk = [], []
+        for rx in self.regexes:
+            kname, cb, _ = rx.layout(1, "auto")
+            info = rx.info
+            self._enc.append((kname, cb))
+            self._ws_chunk.append(4 * (info["fwd_slots_max"] + info["bwd_slots_max"]) + 64 + 2 * (32 * 4 + 96 * 8))
+
+    def ws_bound(self, re_index: int, n: int) -> int:
+        return 8192 + (n // 256 + 1) * self._ws_chunk[re_index] + (n // 64 + 1) * 8
 
     def footprint(self, req: Request) -> tuple[int, int, int]:
-        """(device bytes, pinned-in bytes, pinned-out bytes) a request needs,
-        with an upper bound on its workspace share (the single-text size)."""
+        """(device bytes, pinned-in bytes, pinned-out bytes) a request needs:
+        its text, its columns, a bound on its workspace and its share of the
+        batch descriptors (under 1 KiB a text)."""
         n = len(req.text)
-        _, cb, nbytes = self._layout(req.re_index, n)
-        ws = self.regexes[req.re_index].workspace_size(n)
-        # the batch descriptors (parameters and prefix sums) take under 1 KiB a text
-        return _align(n) + _align(nbytes) + _align(ws) + 1024, _align(n), _align(nbytes)
+        _, cb = self._enc[req.re_index]
+        cols = _align((n + 1) * cb)
+        return _align(n) + cols + _align(self.ws_bound(req.re_index, n)) + 1024, _align(n), cols
 
     def fits_alone(self, req: Request) -> bool:
         d, i, o = self.footprint(req)
@@ -105,62 +117,71 @@ class Server:
     def _launch(self, slot: _Slot, reqs: list):
         torch = self.torch
         lens = [len(r.text) for r in reqs]
-        b = Batch([self.regexes[r.re_index] for r in reqs], lens)
+        enc = [self._enc[r.re_index] for r in reqs]
         # arena: [texts][columns][status words][workspace]
         offs_t, o = [], 0
         for n in lens:
             offs_t.append(o)
             o += _align(n)
         text_end = o
-        offs_c, kinds, cbs = [], [], []
-        for r, n in zip(reqs, lens):
-            kname, cb, nbytes = self._layout(r.re_index, n)
+        offs_c = []
+        for n, (_, cb) in zip(lens, enc):
             offs_c.append(o)
-            kinds.append(kname)
-            cbs.append(cb)
-            o += _align(nbytes)
+            o += _align((n + 1) * cb)
         st_off = o
         o += _align(4 * len(reqs))
         out_end = o
         ws_off = o
-        if ws_off + b.workspace_size > self.arena_bytes or text_end > slot.pin_in.numel() \
+        single = len(reqs) == 1
+        if single:                                            # one text: plain re_parse, no batch plan
+            b = None
+            ws_bytes = self.regexes[reqs[0].re_index].workspace_size(lens[0])
+        else:
+            b = Batch([self.regexes[r.re_index] for r in reqs], lens)
+            ws_bytes = b.workspace_size
+        if ws_off + ws_bytes > self.arena_bytes or text_end > slot.pin_in.numel() \
                 or out_end - text_end > slot.pin_out.numel():
-            b.close()
+            if b is not None:
+                b.close()
             raise RuntimeError("slot arena too small for the admitted batch")
-        # texts into pinned staging, one copy to the device
-        pin_in = slot.pin_in.numpy()
+        pin_in = slot.pin_in.numpy()                         # texts into pinned staging
         for r, ot in zip(reqs, offs_t):
             pin_in[ot:ot + len(r.text)] = r.text
-        dt = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}
         A = slot.arena
-        texts = [A[ot:ot + n] for ot, n in zip(offs_t, lens)]
-        outs = [A[oc:oc + (n + 1) * cb].view(dt[cb]) for oc, n, cb in zip(offs_c, lens, cbs)]
-        status = A[st_off:st_off + 4 * len(reqs)].view(torch.int32)
-        ws = A[ws_off:ws_off + max(b.workspace_size, 256)]
+        base = A.data_ptr()
         with torch.cuda.stream(slot.stream):
             if text_end:
                 A[:text_end].copy_(slot.pin_in[:text_end], non_blocking=True)
-            b.parse(texts, outs=outs, status=status, workspace=ws, stream=slot.stream)
+            sp = slot.stream.cuda_stream
+            if single:
+                kname, cb = enc[0]
+                self.regexes[reqs[0].re_index].parse_raw(base + offs_t[0], lens[0], base + offs_c[0],
+                                                         (lens[0] + 1) * cb, kname, cb, base + st_off,
+                                                         base + ws_off, max(ws_bytes, 256), sp)
+            else:
+                b.parse_raw([base + ot for ot in offs_t], [base + oc for oc in offs_c],
+                            [(n + 1) * cb for n, (_, cb) in zip(lens, enc)], [k for k, _ in enc],
+                            [cb for _, cb in enc], base + st_off, base + ws_off, max(ws_bytes, 256), sp)
             slot.pin_out[:out_end - text_end].copy_(A[text_end:out_end], non_blocking=True)
             slot.event = torch.cuda.Event()
             slot.event.record(slot.stream)
         slot.reqs = reqs
         slot.batch = b
-        slot.views = [(oc - text_end, n, cb, k) for oc, n, cb, k in zip(offs_c, lens, cbs, kinds)] + \
-                     [st_off - text_end]
+        slot.views = [(oc - text_end, n, cb, k) for oc, n, (k, cb) in zip(offs_c, lens, enc)] + [st_off - text_end]
 
     def _retire(self, slot: _Slot, now: float, keep_cols: bool):
         out = slot.pin_out.numpy()
         st_rel = slot.views[-1]
-        status = out[st_rel:st_rel + 4 * len(slot.reqs)].view(np.int32)
+        status = out[st_rel:st_rel + 4 * len(slot.reqs)].view(np.int32).tolist()
         dt = {1: np.uint8, 2: np.uint16, 4: np.uint32, 8: np.uint64}
         for j, (r, (oc, n, cb, k)) in enumerate(zip(slot.reqs, slot.views[:-1])):
-            r.status = int(status[j])
+            r.status = status[j]
             r.kind = k
             r.done = now
             if keep_cols:
                 r.cols = out[oc:oc + (n + 1) * cb].view(dt[cb]).copy()
-        slot.batch.close()
+        if slot.batch is not None:
+            slot.batch.close()
         slot.batch, slot.reqs, slot.event, slot.views = None, [], None, []
 
     # ------------------------------------------------------------------ loop
@@ -172,6 +193,7 @@ class Server:
         for r in requests:
             if not self.fits_alone(r):
                 raise ValueError(f"request {r.rid} ({len(r.text)} bytes) exceeds a slot's arena")
+        fp = {id(r): self.footprint(r) for r in requests}
         waiting = deque()
         nxt = 0
         t0 = time.perf_counter()
@@ -194,7 +216,7 @@ class Server:
                     continue
                 take, dev_used, in_used, out_used = [], 1 << 20, 0, 4096
                 while waiting and len(take) < self.max_batch:
-                    d, i, o = self.footprint(waiting[0])
+                    d, i, o = fp[id(waiting[0])]
                     if take and (dev_used + d > self.arena_bytes or in_used + i > s.pin_in.numel()
                                  or out_used + o > s.pin_out.numel()):
                         break

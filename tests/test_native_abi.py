@@ -85,3 +85,19 @@ def test_ek_family_state_counts(native):
     for k in range(1, 8):
         r = native.Regex("(a|b)*a(a|b){%d}" % k, host_only=True)
         assert r.info["fwd_dfa_states"] == 2 ** (k + 1) + 1
+
+
+def test_serving_workspace_bound_covers_the_library(native):
+    """The serving loop admits requests with a workspace bound computed in
+    Python; it must cover the library's workspace for every chunk length the
+    library may pick (>= 256), for short and long texts."""
+    from paper_2503_06763_gb300 import serve
+    import workloads as W
+    pats = [W.DNA_RE, W.AB_RE, W.LOG_RE] + [W.random_re(4000 + i, 20, 300)[0] for i in range(4)]
+    srv = serve.Server.__new__(serve.Server)
+    srv.regexes = [native.Regex(p, host_only=True) for p in pats]
+    srv._prepare()
+    for ri, rx in enumerate(srv.regexes):
+        for n in (0, 1, 63, 64, 255, 256, 257, 4095, 65536, 1_000_003, 64 << 20):
+            for k in (256, 320, 4608):
+                assert rx.workspace_size(n, chunk_len=k) <= srv.ws_bound(ri, n), (pats[ri][:20], n, k)
