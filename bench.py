@@ -149,6 +149,20 @@ def cpu_baseline(text_host, pattern):
                       f"{dt:.1f} s, host {os.uname().machine} nproc={os.cpu_count()}"}
 
 
+def lsu_roofline(phase_ms: dict, n: int, device: int):
+    """Reach against the shared-memory pipe, its real bound: with at most 16
+    byte classes it does 3 shared-memory lookups per text byte (per direction
+    and byte pair: two class lookups and one two-byte table lookup).  Peak:
+    one 32-lane wavefront per SM and cycle at the maximum SM clock."""
+    import torch
+    props = torch.cuda.get_device_properties(device)
+    peak = props.multi_processor_count * 32 * 2.07e9 / 1e12
+    achieved = 3 * n / (phase_ms["reach"] / 1e3) / 1e12
+    return {"kernel": "reach", "bound": "lsu", "achieved": round(achieved, 3), "peak": round(peak, 3),
+            "unit": "T lookups/s", "frac": round(achieved / peak, 4),
+            "peak_source": "SM count x 32 lanes x 2070 MHz (one conflict-free wavefront per SM and cycle)"}
+
+
 def csrc_hash() -> str:
     """SHA-256 over every CUDA source of the library, in name order."""
     d = os.path.join(ROOT, "paper_2503_06763_gb300", "csrc")
@@ -277,7 +291,8 @@ def main():
                 "peak_source": src, "unit": "GB/s", "frac": round(achieved / hbm, 4),
                 "traffic": traffic_for(dominant, n),
                 "phase_ms": {k: round(v, 4) for k, v in phase_ms.items()},
-                "whole_step_frac": round((n + (n + 1) * cb) / (ms / 1e3) / 1e9 / hbm, 4)}
+                "whole_step_frac": round((n + (n + 1) * cb) / (ms / 1e3) / 1e9 / hbm, 4),
+                "lsu": lsu_roofline(phase_ms, n, local)}
 
     # recognizer mode (forward reach + join only, Sect. 4.2), same text
     rec_ws = torch.empty(rx.workspace_size(n, args.chunk_len, 1), dtype=torch.uint8, device=dev)
