@@ -48,7 +48,7 @@ def parse_args():
     ap.add_argument("--bytes", type=int, default=N_BYTES, help="text size (default 256 MiB)")
     ap.add_argument("--chunk-len", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "matches"],
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "matches", "latency"],
                     help="single: one 256 MiB text (default); batch: 4096 texts under 8 random REs; "
                          "serve: Poisson request stream")
     ap.add_argument("--texts", type=int, default=4096, help="batch mode: number of texts")
@@ -223,6 +223,8 @@ def main():
         return serve_mode(args, rank, world, local)
     if args.mode == "matches":
         return matches_mode(args, rank, world, local)
+    if args.mode == "latency":
+        return latency_mode(args, rank, world, local)
 
     import torch
     torch.cuda.set_device(local)
@@ -567,6 +569,54 @@ def matches_mode(args, rank, world, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": WORKLOAD, "group": "13 (stop codon closing an ORF)", "matches": total},
             "cpu_baseline": cpu}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def latency_mode(args, rank, world, local):
+    """One small text, (a|b|ab)* over 1 MiB of uniform a/b (seed 0): latency of
+    one parse with its 8 launches issued directly, and as a CUDA-graph
+    replay of the same re_parse call."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2503_06763_gb300 import Regex
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = 1 << 20
+    rx = Regex(W.AB_RE)
+    text = torch.from_numpy(W.ab_text(n, seed=0)).to(dev)
+    cols, st, kind = rx.parse(text)
+    ws = torch.empty(rx.workspace_size(n), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    reps = max(args.steps, 50)
+
+    def lat(fn):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        out = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+        a = np.array(out)
+        return {"p50_ms": round(float(np.percentile(a, 50)), 4), "p99_ms": round(float(np.percentile(a, 99)), 4),
+                "GBps_at_p50": round(n / (float(np.percentile(a, 50)) / 1e3) / 1e9, 2)}
+
+    direct = lat(lambda: rx.parse(text, out=cols, status=st, workspace=ws))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        rx.parse(text, out=cols, status=st, workspace=ws)
+    graph = lat(g.replay)
+    line = {"metric": "single-parse latency, 1 MiB (a|b|ab)* text (p50 ms)", "value": graph["p50_ms"], "unit": "ms",
+            "n_gpus": world, "steps": reps, "warmup": args.warmup, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "(a|b|ab)*, 1 MiB uniform a/b, seed 0", "encoding": kind},
+            "graph_replay": graph, "direct_launches": direct}
     if rank == 0:
         print(json.dumps(line))
 

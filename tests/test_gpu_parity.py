@@ -148,3 +148,34 @@ def test_recognizer_matches_oracle_acceptance(lib, chunk_len):
             torch.cuda.synchronize()
             want = serial.accepted(oracle_cols(pat, h.tobytes()))
             assert int(st.item()) == (0 if want else 1), (pat[:30], corrupt, len(h))
+
+
+def test_parse_captured_in_cuda_graph(lib):
+    """re_parse enqueues kernels only (after a first call has set up the
+    launch attributes), so it can be captured in a CUDA graph and replayed on
+    new text bytes; each replay gives the parse of the bytes present."""
+    rx = lib(W.DNA_RE)
+    n = 1 << 20
+    text = torch.from_numpy(W.dna_text(n, seed=51)).cuda()
+    cols, status, kind = rx.parse(text)
+    ws = torch.empty(rx.workspace_size(n), dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        rx.parse(text, out=cols, status=status, workspace=ws, stream=side)      # warm-up on the side stream
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        rx.parse(text, out=cols, status=status, workspace=ws)
+    for seed in (52, 53):
+        host = W.dna_text(n, seed=seed)
+        if seed == 53:
+            host[n // 2] = ord("N")                                             # rejected text
+        text.copy_(torch.from_numpy(host))
+        g.replay()
+        torch.cuda.synchronize()
+        want = oracle_cols(W.DNA_RE, host.tobytes())
+        assert int(status.item()) == (0 if serial.accepted(want) else 1)
+        assert np.array_equal(rx.decode(cols.cpu().numpy(), kind), want)
