@@ -472,13 +472,17 @@ __global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
     }
 }
 
-// Batch: warps take 32-chunk tiles of any text of the group from the work
-// list (an atomic counter); text bytes come in by plain loads.  Lanes past
-// their text's last chunk skip the tile and meet the others at the closing
-// __syncwarp, so no lane waits in a collective that the others do not run.
-template <int TM, int MS>
-__global__ void __launch_bounds__(kChunkThreads) reach_batch_kernel(const __grid_constant__ BatchGroup b) {
+// Batch: warps take work items from the group's list (an atomic counter).  An
+// item is a 32-chunk tile of any text of the group and, in SPLIT mode, one of
+// its two directions (the forward and backward walks of a tile go to two
+// warps, as in a single parse).  Text bytes come in by plain loads.  Lanes
+// past their text's last chunk skip the tile and meet the others at the
+// closing __syncwarp, so no lane waits in a collective the others do not run.
+template <int TM, int MS, bool SPLIT>
+__global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
+    reach_batch_kernel(const __grid_constant__ BatchGroup b) {
     extern __shared__ __align__(16) uint8_t sm[];
+    constexpr int TILES = SPLIT ? 1 : 2;
     Tabs T;
     uint8_t *rest = TM == TM_PAIR ? stage_reach_pair(b.t, sm, T) : stage_tables<TM>(b.t, sm, T);
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -486,17 +490,25 @@ __global__ void __launch_bounds__(kChunkThreads) reach_batch_kernel(const __grid
     {
         const uint32_t a = smem_u32(rest);
         uint8_t *aligned = rest + ((1024 - (a & 1023)) & 1023);
-        ring.tiles = aligned + warp * (kStages * 2 * kTileBytes);
+        ring.tiles = aligned + warp * (kStages * TILES * kTileBytes);
     }
+    const uint64_t items = SPLIT ? 2 * b.n_reach : b.n_reach;
     for (;;) {
-        uint32_t tile = 0;
-        if (lane == 0) tile = atomicAdd(b.queue + Q_REACH, 1u);
-        tile = __shfl_sync(0xFFFFFFFFu, tile, 0);
-        if (tile >= b.n_reach) break;
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(b.queue + Q_REACH, 1u);
+        item = __shfl_sync(0xFFFFFFFFu, item, 0);
+        if (item >= items) break;
+        const uint32_t tile = SPLIT ? item >> 1 : item;
         const uint32_t ti = text_of(b.rtile_base, b.nt, tile);
         const Params &p = b.texts[ti];
         const uint32_t i = (uint32_t)(tile - b.rtile_base[ti]) * 32 + lane;
-        if (i < p.c && !reach_chunk<TM, MS>(p, T, i, nullptr, ring, false)) atomicExch(&p.w.flags[FLAG_INTERNAL], 1);
+        if (i < p.c) {
+            bool ok;
+            if (!SPLIT) ok = reach_chunk<TM, MS, DIR_BOTH>(p, T, i, nullptr, ring, false);
+            else if (item & 1) ok = reach_chunk<TM, MS, DIR_B>(p, T, i, nullptr, ring, false);
+            else ok = reach_chunk<TM, MS, DIR_F>(p, T, i, nullptr, ring, false);
+            if (!ok) atomicExch(&p.w.flags[FLAG_INTERNAL], 1);
+        }
         __syncwarp();
     }
 }
@@ -506,19 +518,28 @@ inline size_t reach_smem(const DevTables &t, int tm, uint32_t threads = kChunkTh
     return tab + 1024 + (threads / 32) * (kStages * tiles * kTileBytes + kStages * 8);
 }
 
-template <int TM, int MS>
-void launch_batch_one(const BatchGroup &b, cudaStream_t s, int sm_count) {
-    const size_t smem = reach_smem(b.t, TM);
+template <int TM, int MS, bool SPLIT>
+void launch_batch_split(const BatchGroup &b, cudaStream_t s, int sm_count) {
+    const uint32_t threads = SPLIT ? kSplitThreads : kChunkThreads;
+    const size_t smem = reach_smem(b.t, TM, threads, SPLIT ? 1 : 2);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(reach_batch_kernel<TM, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(reach_batch_kernel<TM, MS, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
         attr = true;
     }
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_batch_kernel<TM, MS>, kChunkThreads, smem);
-    const uint64_t want = ((uint64_t)b.n_reach + kChunkThreads / 32 - 1) / (kChunkThreads / 32);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_batch_kernel<TM, MS, SPLIT>, threads, smem);
+    const uint64_t warps = (uint64_t)b.n_reach * (SPLIT ? 2 : 1);
+    const uint64_t want = (warps + threads / 32 - 1) / (threads / 32);
     const uint64_t blocks = std::min<uint64_t>(want, (uint64_t)std::max(per_sm, 1) * sm_count);
-    reach_batch_kernel<TM, MS><<<(uint32_t)std::max<uint64_t>(blocks, 1), kChunkThreads, smem, s>>>(b);
+    reach_batch_kernel<TM, MS, SPLIT><<<(uint32_t)std::max<uint64_t>(blocks, 1), threads, smem, s>>>(b);
+}
+
+template <int TM, int MS>
+void launch_batch_one(const BatchGroup &b, cudaStream_t s, int sm_count) {
+    if (b.recognize) launch_batch_split<TM, MS, false>(b, s, sm_count);
+    else launch_batch_split<TM, MS, true>(b, s, sm_count);
 }
 
 template <int TM>
