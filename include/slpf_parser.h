@@ -103,7 +103,8 @@ typedef struct {
     re_slpf_kind kind;        /* DENSE or DICT (never AUTO once laid out) */
     uint32_t col_bytes;       /* bytes per column */
     uint64_t n_cols;          /* number of columns, len + 1 */
-    void *d_cols;             /* device: n_cols * col_bytes bytes, written by re_parse */
+    void *d_cols;             /* n_cols * col_bytes bytes, written by re_parse: device memory, or
+                                 pinned host memory the device addresses (plain stores) */
     uint64_t cols_cap_bytes;  /* capacity of d_cols */
     int32_t *d_status;        /* device: one re_status word (RE_OK / RE_REJECTED / RE_E_INTERNAL) */
 } re_slpf;
@@ -280,7 +281,7 @@ re_status re_autotune(re_handle *h, const uint8_t *d_text, uint64_t len, re_slpf
  * results are valid once the stream has been synchronised.  Calls on
  * different streams with separate buffers overlap one text's copies with
  * another's kernels.  d_text: device, >= len bytes, 16-byte aligned;
- * host_cols: (len + 1) * slpf->col_bytes bytes, NULL in recognizer mode.    */
+ * host_cols: (len + 1) * slpf->col_bytes bytes, NULL in recognizer mode.   */
 re_status re_parse_host(re_handle *h, const uint8_t *text, uint64_t len, void *host_cols, int32_t *host_status,
                         uint8_t *d_text, re_slpf *slpf, void *d_workspace, uint64_t workspace_bytes,
                         re_stream stream, const re_parse_opts *opts);

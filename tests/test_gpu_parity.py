@@ -179,3 +179,35 @@ def test_parse_captured_in_cuda_graph(lib):
         want = oracle_cols(W.DNA_RE, host.tobytes())
         assert int(status.item()) == (0 if serial.accepted(want) else 1)
         assert np.array_equal(rx.decode(cols.cpu().numpy(), kind), want)
+
+
+def test_parse_host_and_host_columns(lib):
+    """re_parse_host with pinned and with pageable host buffers equals the
+    device parse; re_parse also writes its columns straight into pinned host
+    memory when given it (plain stores: no tensor stores into host memory)."""
+    rx = lib(W.DNA_RE)
+    n = 3_000_017
+    host = W.dna_text(n, seed=61)
+    want_cols, want_st, kind = rx.parse(torch.from_numpy(host).cuda())
+    torch.cuda.synchronize()
+    _, cb, _ = rx.layout(n, kind)
+    dt = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}[cb]
+    pin_in = torch.from_numpy(host).pin_memory()
+    d_text = torch.empty(n, dtype=torch.uint8, device="cuda")
+    d_cols = torch.zeros(n + 1, dtype=dt, device="cuda")
+    d_st = torch.empty(1, dtype=torch.int32, device="cuda")
+    ws = torch.empty(rx.workspace_size(n), dtype=torch.uint8, device="cuda")
+    for pinned in (True, False):
+        cols = torch.zeros(n + 1, dtype=dt)
+        st = torch.zeros(1, dtype=torch.int32)
+        if pinned:
+            cols, st = cols.pin_memory(), st.pin_memory()
+        rx.parse_host(pin_in, cols, st, d_text, d_cols, d_st, ws, kind=kind)
+        torch.cuda.synchronize()
+        assert int(st[0]) == int(want_st.item()) == 0
+        assert torch.equal(cols, want_cols.cpu()), pinned
+    direct = torch.zeros(n + 1, dtype=dt).pin_memory()
+    st2 = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rx.parse(torch.from_numpy(host).cuda(), out=direct, status=st2, workspace=ws)
+    torch.cuda.synchronize()
+    assert int(st2.item()) == 0 and torch.equal(direct, want_cols.cpu())
