@@ -184,6 +184,11 @@ bool in_device_memory(const void *ptr) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Shared memory the merge's encoder table takes when staged.
+size_t encoder_bytes(const DevTables &t, re_slpf_kind kind, uint32_t cb) {
+    return kind == RE_SLPF_DICT ? (size_t)t.nf * t.nb * cb : (size_t)(t.nf + t.nb) * 8;
+}
+
 uint32_t table_mode(const DevTables &t) {
     const bool fit16 = t.nf < 65536 && t.nb < 65536;
     if (t.f2 && t.b2 && tables_smem_bytes(t, TM_PAIR) <= kSmemPairMax) return TM_PAIR;
@@ -410,9 +415,10 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     // to pinned host memory (plain stores over the host link).
     p.out_tma = (!recognize && in_device_memory(slpf->d_cols) && output_tensor_map(out_map, slpf->d_cols, cb, p.Gfast))
                     ? 1u : 0u;
-    // Stage the dictionary pair table in shared memory when the merge's whole
-    // footprint (tables, stage, output tiles and the table) still fits.
-    if (kind == RE_SLPF_DICT && tab + merge_extra_smem(p) + (size_t)t.nf * t.nb * cb <= kSmemMergeMax) p.pt_in_smem = 1;
+    // Stage the encoder table (DICT pair table or DENSE state bitsets) in shared
+    // memory when the merge's whole footprint (tables, stage, output tiles and
+    // the table) still fits; otherwise it is read from global memory.
+    if (!recognize && tab + merge_extra_smem(p) + encoder_bytes(t, kind, cb) <= kSmemMergeMax) p.enc_in_smem = 1;
     alignas(64) CUtensorMap text_map;
     std::memset(&text_map, 0, sizeof(text_map));
     p.c_full = (uint32_t)(len / k);
@@ -608,7 +614,7 @@ struct re_batch {
     };
     struct Group {
         re_handle *h = nullptr;
-        uint32_t tmode = 0, ms = 0, pt_in_smem = 0, cb = 1;
+        uint32_t tmode = 0, ms = 0, enc_in_smem = 0, cb = 1;
         re_slpf_kind kind = RE_SLPF_DENSE;
         std::vector<uint32_t> members;  // caller indices, longest chunks first
         size_t params_off = 0, cbase_off = 0, rbase_off = 0, mbase_off = 0;
@@ -647,7 +653,7 @@ Params group_like(const re_batch::Group &g, bool recognize) {
     q.kind = g.kind;
     q.col_bytes = g.cb;
     q.recognize = recognize ? 1u : 0u;
-    q.pt_in_smem = g.pt_in_smem;
+    q.enc_in_smem = g.enc_in_smem;
     return q;
 }
 
@@ -751,9 +757,8 @@ re_status re_batch_plan(re_handle *const *hs, const uint64_t *lens, uint32_t cou
         g.mbase_off = off; off = align256(off + arr);
         Params q = group_like(g, b->recognize);
         const size_t tab = tables_smem_bytes(g.h->dev, g.tmode);
-        if (!b->recognize && g.kind == RE_SLPF_DICT &&
-            tab + merge_extra_smem(q) + (size_t)g.h->dev.nf * g.h->dev.nb * g.cb <= kSmemMergeMax)
-            g.pt_in_smem = 1;
+        if (!b->recognize && tab + merge_extra_smem(q) + encoder_bytes(g.h->dev, g.kind, g.cb) <= kSmemMergeMax)
+            g.enc_in_smem = 1;
     }
     b->queue_off = off;
     off = align256(off + b->groups.size() * kQueues * sizeof(uint32_t));

@@ -52,7 +52,7 @@ struct Params {
     int32_t *status;
     uint32_t recognize;             // forward reach + join only
     uint32_t tmode;                 // TM_GLOBAL / TM_SMEM / TM_PAIR (see Tabs)
-    uint32_t pt_in_smem;            // dictionary pair table staged in shared memory
+    uint32_t enc_in_smem;           // encoder table (DICT pair table, DENSE bitsets) in shared memory
     uint32_t out_tma;               // full column groups leave through TMA tensor stores
     uint32_t text_tma;              // reach reads full chunks through TMA tiles
     uint32_t c_full;                // chunks of exactly k bytes (rows of the text tensor map)

@@ -468,14 +468,14 @@ __device__ void group_tail(const Params &p, const Tabs &T, const Enc &e, uint64_
 // Shared-memory set-up of a merge block: staged tables, the per-thread state
 // stage (one-byte tables) and the encoder (pair table or segment bitsets).
 template <int TM, int E, typename St>
-__device__ void merge_setup(const DevTables &t, uint32_t pt_in_smem, uint8_t *base, Tabs &T, St *&stage, Enc &e) {
+__device__ void merge_setup(const DevTables &t, uint32_t enc_in_smem, uint8_t *base, Tabs &T, St *&stage, Enc &e) {
     uint8_t *rest = stage_tables<TM>(t, base, T);
     stage = reinterpret_cast<St *>(rest);                     // [2][32][kBlockThreads] (one-byte tables)
     if (TM != TM_PAIR) rest += (2 * 32 * kBlockThreads * sizeof(St) + 15) & ~(size_t)15;
     e = Enc{};
     e.nb = t.nb;
     if (E == ENC_X2 || E == ENC_X4) {
-        if (pt_in_smem) {
+        if (enc_in_smem) {
             const size_t cnt = (size_t)t.nf * t.nb;
             if (E == ENC_X2) {
                 uint16_t *pt = reinterpret_cast<uint16_t *>(rest);
@@ -489,12 +489,14 @@ __device__ void merge_setup(const DevTables &t, uint32_t pt_in_smem, uint8_t *ba
         } else {
             e.pt32 = t.pt;
         }
-    } else {
+    } else if (enc_in_smem) {                                 // DENSE: segment bitsets of the states
         uint64_t *fb = reinterpret_cast<uint64_t *>(rest);
         uint64_t *bb = fb + t.nf;
         for (uint32_t i = threadIdx.x; i < t.nf; i += blockDim.x) fb[i] = __ldg(t.fBits + i);
         for (uint32_t i = threadIdx.x; i < t.nb; i += blockDim.x) bb[i] = __ldg(t.bBits + i);
         e.fbits = fb; e.bbits = bb;
+    } else {
+        e.fbits = t.fBits; e.bbits = t.bBits;                 // too many states to stage
     }
     __syncthreads();
 }
@@ -550,7 +552,7 @@ __global__ void __launch_bounds__(kBlockThreads, TM == TM_PAIR ? 2 : 3)
     Tabs T;
     St *stage;
     Enc e;
-    merge_setup<TM, E, St>(p.t, p.pt_in_smem, base, T, stage, e);
+    merge_setup<TM, E, St>(p.t, p.enc_in_smem, base, T, stage, e);
     const bool ok = *p.status == RE_OK;
     bool bad = false;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -587,14 +589,14 @@ __global__ void __launch_bounds__(kBlockThreads, TM == TM_PAIR ? 2 : 3)
 // list; outputs leave through plain 16-byte stores.
 template <int TM, int E>
 __global__ void __launch_bounds__(kBlockThreads, 3) merge_batch_kernel(const __grid_constant__ BatchGroup b,
-                                                                       uint32_t pt_in_smem) {
+                                                                       uint32_t enc_in_smem) {
     using St = StOf<TM>;
     constexpr uint32_t ROWB = 64 * bytes_of(E);
     extern __shared__ __align__(16) uint8_t sm[];
     Tabs T;
     St *stage;
     Enc e;
-    merge_setup<TM, E, St>(b.t, pt_in_smem, sm, T, stage, e);
+    merge_setup<TM, E, St>(b.t, enc_in_smem, sm, T, stage, e);
     const uint32_t lane = threadIdx.x & 31;
     for (;;) {
         uint32_t tile = 0;
@@ -670,7 +672,7 @@ void merge_batch_one(const BatchGroup &b, const Params &like, cudaStream_t s, in
         attr = true;
     }
     const int blocks = grid_for(merge_batch_kernel<TM, E>, smem, (uint64_t)b.n_merge * 32, sm_count, kBlockThreads);
-    merge_batch_kernel<TM, E><<<blocks, kBlockThreads, smem, s>>>(b, q.pt_in_smem);
+    merge_batch_kernel<TM, E><<<blocks, kBlockThreads, smem, s>>>(b, q.enc_in_smem);
 }
 
 template <int TM>
@@ -719,7 +721,8 @@ size_t merge_extra_smem(const Params &p) {
     size_t a = 0;
     if (p.out_tma) a += 1024 + (size_t)(kBlockThreads / 32) * 32 * 64 * p.col_bytes;   // warp tiles + alignment
     if (p.tmode != TM_PAIR) a += (2 * 32 * kBlockThreads * (p.tmode == TM_GLOBAL ? 4 : 2) + 15) & ~(size_t)15;
-    if (p.kind == RE_SLPF_DICT) return a + (p.pt_in_smem ? (size_t)t.nf * t.nb * p.col_bytes : 0);
+    if (!p.enc_in_smem) return a;
+    if (p.kind == RE_SLPF_DICT) return a + (size_t)t.nf * t.nb * p.col_bytes;
     return a + (size_t)(t.nf + t.nb) * 8;
 }
 

@@ -211,3 +211,23 @@ def test_parse_host_and_host_columns(lib):
     rx.parse(torch.from_numpy(host).cuda(), out=direct, status=st2, workspace=ws)
     torch.cuda.synchronize()
     assert int(st2.item()) == 0 and torch.equal(direct, want_cols.cpu())
+
+
+@pytest.mark.parametrize("pattern,cb", [("(ab)*|b", 1), ("(a|b)*a(a|b){3}", 2), ("(a|b)*a(a|b){5}", 4),
+                                        ("(a|b)*a(a|b){13}", 8)])
+@pytest.mark.parametrize("kind", ["dense", "dict"])
+def test_every_column_width(lib, pattern, cb, kind):
+    """DENSE at 1, 2, 4 and 8 bytes per column and DICT at 2, on texts that
+    reach the tensor-store path (full 32-group tiles) and end in a ragged
+    tail, against the oracle."""
+    rx = lib(pattern)
+    got_kind, got_cb, _ = rx.layout(100, kind)
+    assert got_kind == kind and (got_cb == cb if kind == "dense" else got_cb == 2)
+    rng = np.random.Generator(np.random.PCG64(cb))
+    for n in (2048 + 37, 9000):
+        if pattern.startswith("(ab)*"):
+            host = np.frombuffer((b"ab" * (n // 2)), dtype=np.uint8).copy()
+        else:
+            host = rng.choice(np.frombuffer(b"ab", dtype=np.uint8), size=n)
+        check(rx, pattern, host, kind=kind, chunk_len=0)
+        check(rx, pattern, host, kind=kind, chunk_len=256)
