@@ -231,3 +231,15 @@ def test_every_column_width(lib, pattern, cb, kind):
             host = rng.choice(np.frombuffer(b"ab", dtype=np.uint8), size=n)
         check(rx, pattern, host, kind=kind, chunk_len=0)
         check(rx, pattern, host, kind=kind, chunk_len=256)
+
+
+@pytest.mark.parametrize("pattern", ["(a|b)*a(a|b){9}", "(a|b)*a(a|b){14}"])
+def test_large_automata(lib, pattern):
+    """REs with 2^10 .. 2^15 DFA states: one-byte tables in shared memory,
+    and (k = 14, about 200 KB of tables) tables read from global memory."""
+    rx = lib(pattern)
+    rng = np.random.Generator(np.random.PCG64(77))
+    for n in (3000, 20_001):
+        host = rng.choice(np.frombuffer(b"ab", dtype=np.uint8), size=n)
+        check(rx, pattern, host, kind="dict", chunk_len=0)
+        check(rx, pattern, host, kind="dense", chunk_len=256)
