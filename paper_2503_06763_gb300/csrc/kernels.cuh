@@ -304,13 +304,24 @@ __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bu
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // ---------------------------------------------------------------- launchers
+// Raise a kernel's dynamic shared-memory limit once per device (the setting
+// belongs to the device; *done holds one bit per device already set).
+template <typename K>
+inline void allow_smem(K kernel, uint64_t *done, int bytes = 200 * 1024) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t bit = dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (*done & bit)) return;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    *done |= bit;
+}
+
 size_t merge_extra_smem(const Params &p);
 bool launch_reach(const Params &p, const CUtensorMap &text_map, cudaStream_t s, uint32_t ms, int sm_count);
 void launch_join(const Params &p, cudaStream_t s);
 void launch_fixup(const Params &p, cudaStream_t s, int sm_count);
 void launch_merge(const Params &p, const CUtensorMap &out_map, cudaStream_t s, int sm_count);
 void launch_empty(const Params &p, cudaStream_t s);
-cudaError_t set_kernel_attributes();   // max dynamic shared memory, once per process
 
 // Match extraction (matches.cu).
 constexpr int kMatchW = 8;                    // segment words supported (ell <= 512)

@@ -628,11 +628,8 @@ int grid_for(K kernel, size_t smem, uint64_t items, int sm_count, uint32_t threa
 template <int TM, int E, bool TMA>
 void merge_one(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
     const size_t smem = tables_smem_bytes(p.t, TM) + merge_extra_smem(p);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(merge_kernel<TM, E, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    static uint64_t attr_done = 0;
+    allow_smem(merge_kernel<TM, E, TMA>, &attr_done);
     const int blocks = grid_for(merge_kernel<TM, E, TMA>, smem, p.Gc, sm_count, kBlockThreads);
     merge_kernel<TM, E, TMA><<<blocks, kBlockThreads, smem, s>>>(p, map);
 }
@@ -666,11 +663,8 @@ void merge_batch_one(const BatchGroup &b, const Params &like, cudaStream_t s, in
     Params q = like;
     q.out_tma = 0;
     const size_t smem = tables_smem_bytes(b.t, TM) + merge_extra_smem(q);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(merge_batch_kernel<TM, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    static uint64_t attr_done = 0;
+    allow_smem(merge_batch_kernel<TM, E>, &attr_done);
     const int blocks = grid_for(merge_batch_kernel<TM, E>, smem, (uint64_t)b.n_merge * 32, sm_count, kBlockThreads);
     merge_batch_kernel<TM, E><<<blocks, kBlockThreads, smem, s>>>(b, q.enc_in_smem);
 }
@@ -693,11 +687,8 @@ void merge_batch_enc(const BatchGroup &b, const Params &like, cudaStream_t s, in
 template <int TM>
 void fixup_batch_one(const BatchGroup &b, cudaStream_t s, int sm_count) {
     const size_t smem = tables_smem_bytes(b.t, TM);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(fixup_batch_kernel<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    static uint64_t attr_done = 0;
+    allow_smem(fixup_batch_kernel<TM>, &attr_done);
     fixup_batch_kernel<TM><<<grid_for(fixup_batch_kernel<TM>, smem, b.chunks * 32, sm_count, kChunkThreads),
                              kChunkThreads, smem, s>>>(b);
 }
@@ -705,11 +696,8 @@ void fixup_batch_one(const BatchGroup &b, cudaStream_t s, int sm_count) {
 template <int TM>
 void fixup_one(const Params &p, cudaStream_t s, int sm_count) {
     const size_t smem = tables_smem_bytes(p.t, TM);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(fixup_kernel<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    static uint64_t attr_done = 0;
+    allow_smem(fixup_kernel<TM>, &attr_done);
     fixup_kernel<TM><<<grid_for(fixup_kernel<TM>, smem, (uint64_t)p.c * 32, sm_count, kChunkThreads), kChunkThreads,
                        smem, s>>>(p);
 }

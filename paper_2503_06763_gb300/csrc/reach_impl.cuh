@@ -522,12 +522,8 @@ template <int TM, int MS, bool SPLIT>
 void launch_batch_split(const BatchGroup &b, cudaStream_t s, int sm_count) {
     const uint32_t threads = SPLIT ? kSplitThreads : kChunkThreads;
     const size_t smem = reach_smem(b.t, TM, threads, SPLIT ? 1 : 2);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(reach_batch_kernel<TM, MS, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
-        attr = true;
-    }
+    static uint64_t attr_done = 0;
+    allow_smem(reach_batch_kernel<TM, MS, SPLIT>, &attr_done);
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_batch_kernel<TM, MS, SPLIT>, threads, smem);
     const uint64_t warps = (uint64_t)b.n_reach * (SPLIT ? 2 : 1);
@@ -558,11 +554,8 @@ template <int TM, int MS, bool SPLIT>
 void launch_split(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
     const uint32_t threads = SPLIT ? kSplitThreads : kChunkThreads;
     const size_t smem = reach_smem(p.t, TM, threads, SPLIT ? 1 : 2);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(reach_kernel<TM, MS, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    static uint64_t attr_done = 0;
+    allow_smem(reach_kernel<TM, MS, SPLIT>, &attr_done);
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_kernel<TM, MS, SPLIT>, threads, smem);
     const uint64_t warps = ((uint64_t)p.c + 31) / 32 * (SPLIT ? 2 : 1);
