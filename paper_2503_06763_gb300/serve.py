@@ -26,6 +26,7 @@ from __future__ import annotations
 
 import time
 from collections import deque
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -65,7 +66,7 @@ class Server:
     """Continuous-batching request loop over resident compiled REs."""
 
     def __init__(self, patterns, slots: int = 4, arena_bytes: int = 2 << 30, max_batch: int = 4096,
-                 device=None):
+                 device=None, copy_threads: int = 8):
         import torch
         self.torch = torch
         self.dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
@@ -80,6 +81,9 @@ class Server:
                 pin_in=torch.empty(arena_bytes // 4, dtype=torch.uint8).pin_memory(),
                 pin_out=torch.empty(arena_bytes // 2, dtype=torch.uint8).pin_memory()))
         self.stats = {"batches": 0, "requests": 0, "max_batch": 0, "max_inflight": 0}
+        # staging copies of a batch's texts run on several host threads (numpy
+        # releases the interpreter lock while it copies)
+        self._copy_pool = ThreadPoolExecutor(max_workers=copy_threads) if copy_threads > 1 else None
         self._prepare()
 
     # ------------------------------------------------------------------ sizing
@@ -145,8 +149,21 @@ class Server:
                 b.close()
             raise RuntimeError("slot arena too small for the admitted batch")
         pin_in = slot.pin_in.numpy()                         # texts into pinned staging
-        for r, ot in zip(reqs, offs_t):
-            pin_in[ot:ot + len(r.text)] = r.text
+
+        def stage(lo, hi):
+            for r, ot in zip(reqs[lo:hi], offs_t[lo:hi]):
+                pin_in[ot:ot + len(r.text)] = r.text
+
+        if self._copy_pool is not None and text_end > (4 << 20):
+            parts = self._copy_pool._max_workers
+            cut = [0]                                         # equal bytes per thread
+            for j, ot in enumerate(offs_t):
+                if ot >= text_end * len(cut) / parts and len(cut) < parts:
+                    cut.append(j)
+            cut.append(len(reqs))
+            list(self._copy_pool.map(lambda ab: stage(*ab), zip(cut[:-1], cut[1:])))
+        else:
+            stage(0, len(reqs))
         A = slot.arena
         base = A.data_ptr()
         with torch.cuda.stream(slot.stream):
@@ -240,6 +257,8 @@ class Server:
 
     def close(self):
         self.torch.cuda.synchronize(self.dev)
+        if self._copy_pool is not None:
+            self._copy_pool.shutdown()
         for s in self.slots:
             if s.batch is not None:
                 s.batch.close()
