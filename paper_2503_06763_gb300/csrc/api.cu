@@ -37,14 +37,16 @@ constexpr size_t kSmemPairMax = 48 * 1024;      // both two-byte tables + class 
 constexpr size_t kSmemMergeMax = 190 * 1024;    // plus the dictionary pair table
 
 int sm_count_of(int device) {
-    static int cached[64] = {0};
+    static int cached[64] = {0};                        // read and written atomically: host threads share it
     if (device < 0 || device >= 64) return 152;
-    if (!cached[device]) {
+    int c = __atomic_load_n(&cached[device], __ATOMIC_RELAXED);
+    if (!c) {
         int v = 0;
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
-        cached[device] = v > 0 ? v : 152;
+        c = v > 0 ? v : 152;
+        __atomic_store_n(&cached[device], c, __ATOMIC_RELAXED);
     }
-    return cached[device];
+    return c;
 }
 
 // Chunk length k: one reach thread per chunk, about 2 resident warps per
@@ -76,16 +78,15 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
+    // A function-local static is initialised once, and other threads wait for it.
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
         void *ptr = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess && q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
-    }
+            return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+        return static_cast<PFN_cuTensorMapEncodeTiled_v12000>(nullptr);
+    }();
     return fn;
 }
 

@@ -305,15 +305,17 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 
 // ---------------------------------------------------------------- launchers
 // Raise a kernel's dynamic shared-memory limit once per device (the setting
-// belongs to the device; *done holds one bit per device already set).
+// belongs to the device; *done holds one bit per device already set).  Host
+// threads may race here: the bit is read and set atomically, and a thread
+// that finds it clear sets the attribute again, which is harmless.
 template <typename K>
 inline void allow_smem(K kernel, uint64_t *done, int bytes = 200 * 1024) {
     int dev = 0;
     cudaGetDevice(&dev);
     const uint64_t bit = dev < 64 ? 1ull << dev : 0ull;
-    if (bit && (*done & bit)) return;
+    if (bit && (__atomic_load_n(done, __ATOMIC_ACQUIRE) & bit)) return;
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    *done |= bit;
+    __atomic_fetch_or(done, bit, __ATOMIC_RELEASE);
 }
 
 size_t merge_extra_smem(const Params &p);
