@@ -193,7 +193,10 @@ class Regex:
 
         ``cols`` is a CUDA tensor of n+1 columns (uint8/int16/int32/int64 view of
         the DENSE bitsets or DICT indices), ``status`` a one-element int32 CUDA
-        tensor holding the re_status word.  Nothing is synchronised here."""
+        tensor holding the re_status word.  Nothing is synchronised here.
+        Buffers allocated here are allocated on the parse's stream, so torch's
+        caching allocator does not give them to other streams' work while the
+        parse still uses them."""
         import torch
         if not (isinstance(text, torch.Tensor) and text.is_cuda and text.dtype == torch.uint8):
             raise TypeError("text must be a CUDA uint8 tensor")
@@ -201,26 +204,27 @@ class Regex:
         n = text.numel()
         kname, cb, nbytes = self.layout(n, kind)
         dt = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}[cb]
-        if out is None and not recognize_only:  # the recognizer writes no columns
-            out = torch.empty(n + 1, dtype=dt, device=text.device)
-        if status is None:
-            status = torch.empty(1, dtype=torch.int32, device=text.device)
         flags = RE_PARSE_RECOGNIZE_ONLY if recognize_only else 0
         wsz = self.workspace_size(n, chunk_len, flags)
-        if workspace is None or workspace.numel() < wsz:
-            workspace = torch.empty(max(wsz, 256), dtype=torch.uint8, device=text.device)
         s = stream if stream is not None else torch.cuda.current_stream(text.device)
-        slpf = Slpf(KINDS[kname], cb, 0, out.data_ptr() if out is not None else None,
-                    out.numel() * out.element_size() if out is not None else 0, status.data_ptr())
-        opts = ParseOpts(KINDS[kname], chunk_len, flags, 0, None)
-        if events is not None:          # RE_PHASE_EVENTS torch.cuda.Event objects
-            for e in events:
-                if not e.cuda_event:        # torch creates the CUDA event on first record
-                    e.record(s)
-            arr = (ctypes.c_void_p * RE_PHASE_EVENTS)(*[ctypes.c_void_p(e.cuda_event) for e in events])
-            opts.n_events, opts.events = RE_PHASE_EVENTS, ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p))
-        check(load().re_parse(self._h, text.data_ptr() if n else None, n, ctypes.c_void_p(s.cuda_stream),
-                              ctypes.byref(slpf), workspace.data_ptr(), workspace.numel(), ctypes.byref(opts)))
+        with torch.cuda.stream(s):
+            if out is None and not recognize_only:  # the recognizer writes no columns
+                out = torch.empty(n + 1, dtype=dt, device=text.device)
+            if status is None:
+                status = torch.empty(1, dtype=torch.int32, device=text.device)
+            if workspace is None or workspace.numel() < wsz:
+                workspace = torch.empty(max(wsz, 256), dtype=torch.uint8, device=text.device)
+            slpf = Slpf(KINDS[kname], cb, 0, out.data_ptr() if out is not None else None,
+                        out.numel() * out.element_size() if out is not None else 0, status.data_ptr())
+            opts = ParseOpts(KINDS[kname], chunk_len, flags, 0, None)
+            if events is not None:          # RE_PHASE_EVENTS torch.cuda.Event objects
+                for e in events:
+                    if not e.cuda_event:        # torch creates the CUDA event on first record
+                        e.record(s)
+                arr = (ctypes.c_void_p * RE_PHASE_EVENTS)(*[ctypes.c_void_p(e.cuda_event) for e in events])
+                opts.n_events, opts.events = RE_PHASE_EVENTS, ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p))
+            check(load().re_parse(self._h, text.data_ptr() if n else None, n, ctypes.c_void_p(s.cuda_stream),
+                                  ctypes.byref(slpf), workspace.data_ptr(), workspace.numel(), ctypes.byref(opts)))
         return out, status, kname
 
     def parse_raw(self, text_ptr: int, n: int, out_ptr: int, out_cap: int, kind: str, cb: int, status_ptr: int,
@@ -243,11 +247,12 @@ class Regex:
         n = text.numel()
         kname, cb, _ = self.layout(n, kind)
         dt = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}[cb]
-        if out is None:
-            out = torch.empty(n + 1, dtype=dt, device=text.device)
-        if status is None:
-            status = torch.empty(1, dtype=torch.int32, device=text.device)
         s = stream if stream is not None else torch.cuda.current_stream(text.device)
+        with torch.cuda.stream(s):                  # outputs allocated on the parse's stream
+            if out is None:
+                out = torch.empty(n + 1, dtype=dt, device=text.device)
+            if status is None:
+                status = torch.empty(1, dtype=torch.int32, device=text.device)
         slpf = Slpf(KINDS[kname], cb, 0, out.data_ptr(), out.numel() * out.element_size(), status.data_ptr())
         opts = ParseOpts(KINDS[kname], chunk_len, 0, 0, None)
         check(load().re_parse_static(self._h, text.data_ptr() if n else None, n, ctypes.c_void_p(s.cuda_stream),
@@ -257,7 +262,8 @@ class Regex:
     def matches(self, cols, status, n: int, group: int, kind: str, cap=None, stream=None):
         """re_matches over the columns of a parse of an n-byte text: returns
         an int64 [m, 2] CUDA tensor of (i, j) spans of group ``group`` in
-        (i, j) order.  With cap=None a first call counts the matches."""
+        (i, j) order.  With cap=None a first call counts the matches.  The
+        counts are read on the call's stream, after its kernels."""
         import torch
         dev = cols.device
         s = stream if stream is not None else torch.cuda.current_stream(dev)
@@ -265,16 +271,17 @@ class Regex:
         slpf = Slpf(KINDS[kind], cb, n + 1, cols.data_ptr(), cols.numel() * cb, status.data_ptr())
         w = ctypes.c_uint64()
         check(load().re_match_workspace_size(self._h, n, ctypes.byref(w)))
-        ws = torch.empty(max(w.value, 256), dtype=torch.uint8, device=dev)
-        count = torch.zeros(1, dtype=torch.int64, device=dev)
-        if cap is None:
-            check(load().re_matches(self._h, ctypes.byref(slpf), n, group, None, 0, count.data_ptr(),
+        with torch.cuda.stream(s):
+            ws = torch.empty(max(w.value, 256), dtype=torch.uint8, device=dev)
+            count = torch.zeros(1, dtype=torch.int64, device=dev)
+            if cap is None:
+                check(load().re_matches(self._h, ctypes.byref(slpf), n, group, None, 0, count.data_ptr(),
+                                        ws.data_ptr(), ws.numel(), ctypes.c_void_p(s.cuda_stream)))
+                cap = int(count.item())
+            pairs = torch.empty((max(cap, 1), 2), dtype=torch.int64, device=dev)
+            check(load().re_matches(self._h, ctypes.byref(slpf), n, group, pairs.data_ptr(), cap, count.data_ptr(),
                                     ws.data_ptr(), ws.numel(), ctypes.c_void_p(s.cuda_stream)))
-            cap = int(count.item())
-        pairs = torch.empty((max(cap, 1), 2), dtype=torch.int64, device=dev)
-        check(load().re_matches(self._h, ctypes.byref(slpf), n, group, pairs.data_ptr(), cap, count.data_ptr(),
-                                ws.data_ptr(), ws.numel(), ctypes.c_void_p(s.cuda_stream)))
-        total = int(count.item())
+            total = int(count.item())
         return pairs[:min(total, cap)], total
 
     def autotune(self, text, kind: str = "auto", workspace=None, stream=None) -> int:
@@ -284,11 +291,13 @@ class Regex:
         n = text.numel()
         kname, cb, _ = self.layout(n, kind)
         dt = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}[cb]
-        out = torch.empty(n + 1, dtype=dt, device=text.device)
-        status = torch.empty(1, dtype=torch.int32, device=text.device)
-        if workspace is None:                   # room for every candidate (the shortest chunks need the most)
-            workspace = torch.empty(self.workspace_size(n, chunk_len=256), dtype=torch.uint8, device=text.device)
         s = stream if stream is not None else torch.cuda.current_stream(text.device)
+        with torch.cuda.stream(s):                  # scratch allocated on the stream the trials run on
+            out = torch.empty(n + 1, dtype=dt, device=text.device)
+            status = torch.empty(1, dtype=torch.int32, device=text.device)
+            if workspace is None:               # room for every candidate (the shortest chunks need the most)
+                workspace = torch.empty(self.workspace_size(n, chunk_len=256), dtype=torch.uint8,
+                                        device=text.device)
         slpf = Slpf(KINDS[kname], cb, 0, out.data_ptr(), out.numel() * out.element_size(), status.data_ptr())
         opts = ParseOpts(KINDS[kname], 0, 0, 0, None)
         k = ctypes.c_uint32()
@@ -377,15 +386,16 @@ class Batch:
                 kname, cb, _ = rx.layout(n, self.kind)
                 kinds.append(kname)
                 specs.append((KINDS[kname], cb))
-        if outs is None:
-            dts = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}
-            outs = [None if self.recognize_only else torch.empty(n + 1, dtype=dts[cb], device=dev)
-                    for n, (_, cb) in zip(self.lens, specs)]
-        if status is None:
-            status = torch.empty(max(self.count, 1), dtype=torch.int32, device=dev)
-        if workspace is None or workspace.numel() < self.workspace_size:
-            workspace = torch.empty(max(self.workspace_size, 256), dtype=torch.uint8, device=dev)
         s = stream if stream is not None else torch.cuda.current_stream(dev)
+        with torch.cuda.stream(s):                  # buffers allocated on the batch's stream
+            if outs is None:
+                dts = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}
+                outs = [None if self.recognize_only else torch.empty(n + 1, dtype=dts[cb], device=dev)
+                        for n, (_, cb) in zip(self.lens, specs)]
+            if status is None:
+                status = torch.empty(max(self.count, 1), dtype=torch.int32, device=dev)
+            if workspace is None or workspace.numel() < self.workspace_size:
+                workspace = torch.empty(max(self.workspace_size, 256), dtype=torch.uint8, device=dev)
         arr = (Slpf * max(self.count, 1))()
         ptrs = (ctypes.c_void_p * max(self.count, 1))()
         for j in range(self.count):
