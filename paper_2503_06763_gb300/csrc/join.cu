@@ -136,11 +136,15 @@ __device__ void chain_at(const Params &p, uint32_t i) {
 }
 
 __global__ void join_classify_kernel(const __grid_constant__ Params p) {
+    pdl_wait();
+    pdl_trigger();
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < p.c) classify_at(p, i);
 }
 
 __global__ void join_chain_kernel(const __grid_constant__ Params p) {
+    pdl_wait();
+    pdl_trigger();
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < p.c) chain_at(p, i);
 }
@@ -213,11 +217,17 @@ __device__ void status_of(const Params &p) {
 }
 
 __global__ void join_verify_kernel(const __grid_constant__ Params p) {
+    pdl_wait();
+    pdl_trigger();
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < p.c) verify_at(p, i);
 }
 
-__global__ void status_kernel(const __grid_constant__ Params p) { status_of(p); }
+__global__ void status_kernel(const __grid_constant__ Params p) {
+    pdl_wait();
+    pdl_trigger();
+    status_of(p);
+}
 
 __global__ void flags_init_kernel(const __grid_constant__ Params p) {
     if (threadIdx.x < FLAG_COUNT) p.w.flags[threadIdx.x] = threadIdx.x < 2 ? (int32_t)p.c : 0;
@@ -263,10 +273,10 @@ __global__ void batch_init_kernel(const Params *texts, uint32_t nt, uint32_t *qu
 
 void launch_join(const Params &p, cudaStream_t s) {
     const uint32_t blocks = (p.c + kBlockThreads - 1) / kBlockThreads;
-    join_classify_kernel<<<blocks, kBlockThreads, 0, s>>>(p);
-    join_chain_kernel<<<blocks, kBlockThreads, 0, s>>>(p);
-    join_verify_kernel<<<blocks, kBlockThreads, 0, s>>>(p);
-    status_kernel<<<1, 1, 0, s>>>(p);
+    launch_dependent(join_classify_kernel, blocks, kBlockThreads, 0, s, p);
+    launch_dependent(join_chain_kernel, blocks, kBlockThreads, 0, s, p);
+    launch_dependent(join_verify_kernel, blocks, kBlockThreads, 0, s, p);
+    launch_dependent(status_kernel, 1, 1, 0, s, p);
 }
 
 void launch_flags_init(const Params &p, cudaStream_t s) { flags_init_kernel<<<1, 32, 0, s>>>(p); }

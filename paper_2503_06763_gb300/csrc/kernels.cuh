@@ -15,13 +15,16 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "re_internal.h"
 
 namespace slpf {
 
 constexpr int kMaxW = 64;           // segments per column <= 4096
 constexpr uint32_t kBlockThreads = 256;     // build & merge
-constexpr uint32_t kChunkThreads = 128;     // batch reach, recognizer reach and fix-up blocks
+constexpr uint32_t kChunkThreads = 128;     // batch reach and recognizer reach blocks
+constexpr uint32_t kFixupThreads = 256;     // fix-up blocks: one thread per chunk and direction
 constexpr uint32_t kRecBounds = 32;   // boundaries recorded per chunk and direction before runs meet
 constexpr uint32_t kRecEntries = 96;  // (state, slot set) entries recorded per chunk and direction
 
@@ -302,6 +305,38 @@ constexpr uint32_t kWaitLimit = 1u << 22;   // try_wait rounds before a wait is 
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 // The bulk groups of this thread have completed.
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// ---------------------------------------------------------------- dependent launches
+// The kernels of one parse after the first are launched as programmatic
+// dependents of the kernel before them (sm_90 and later).  A dependent grid
+// may become resident while its predecessor drains and run its prologue
+// (staging immutable tables into shared memory); before it touches anything
+// an earlier kernel of the parse reads or writes it executes pdl_wait(),
+// which returns once the predecessor grid has completed and its memory is
+// visible.  Every block of such a kernel waits before it can exit, so a
+// completed grid implies that every grid before it has completed too.  In a
+// kernel launched the ordinary way the wait returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the dependent grid launch once every block of this grid has issued it
+// (or exited).  Issued after pdl_wait, so at most two grids overlap.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch kernel as a programmatic dependent of the previous work on stream s.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                    Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // ---------------------------------------------------------------- launchers
 // Raise a kernel's dynamic shared-memory limit once per device (the setting

@@ -5,9 +5,8 @@
 //   they met.  At every recorded boundary the exact state is the union, over
 //   the runs whose slot set the chunk's input J_{i-1} (or Ĵ_{i+1}) enters, of
 //   the run states: Eq. joiner applied at sub-chunk granularity.  Boundaries
-//   beyond the record are walked with the DFA from the last exact state
-//   (global tables: walks are rare, and no shared memory means more warps
-//   to hide the latency of the record loads).
+//   beyond the record are walked with the DFA from the last exact state,
+//   with the tables staged in shared memory.
 // build & merge: one thread per column group g (64 columns).  The forward
 //   builder (B from FC[g]) and the backward builder (B̂ from BC[g]) run at the
 //   same time from the two ends of the group, keep their first 32 states
@@ -146,72 +145,24 @@ __device__ __forceinline__ uint32_t walk_bwd(const Params &p, const Tabs &T, uin
     return st;
 }
 
-// One warp per chunk and direction pair: lanes 0-15 take the forward
-// direction, lanes 16-31 the backward one; lane r of a half turns records r
-// and r+16 into exact checkpoints; one lane per half walks any boundaries
-// past the record with the staged tables.  Called by the whole warp.
+// Boundaries of chunk i past its record (nrec records; `from` the state at
+// the last recorded boundary): walked with the DFA from the last exact state.
 template <int TM>
-__device__ void fixup_chunk(const Params &p, const Tabs &T, uint64_t i, bool &bad) {
-    const uint32_t lane = threadIdx.x & 31, half = lane >> 4, r = lane & 15;
-    const bool fwd = half == 0;
+__device__ void fixup_walk(const Params &p, const Tabs &T, uint64_t i, bool fwd, uint32_t nrec, uint32_t conv,
+                           uint32_t from) {
     const uint64_t base = i * p.k;
     const uint32_t len = chunk_len(p, (uint32_t)i);
     const uint32_t nsub = (len + 63) / 64;
     const uint64_t g0 = i * p.S;
-    uint32_t conv, nrec, H;
-    bool active;
     if (fwd) {
-        conv = p.w.fconv[i];
-        active = conv > 1;                                    // boundaries 1 .. conv-1
-        nrec = p.w.fnrec[i]; H = p.w.fhit[i];
-    } else {
-        conv = p.w.bconv[i];
-        active = !p.recognize && nsub >= 2 && conv + 1 <= nsub - 1;   // boundaries nsub-1 .. conv+1
-        nrec = p.w.bnrec[i]; H = p.w.bhit[i];
-    }
-    if (!active) nrec = 0;
-    const uint32_t *cnt_row = (fwd ? p.w.recFc : p.w.recBc) + i * kRecBounds;
-    const uint32_t c0 = r < nrec ? cnt_row[r] : 0u, c1 = r + 16 < nrec ? cnt_row[r + 16] : 0u;
-    uint32_t off0 = c0, tot = c0 + c1;                        // scans within the half
-#pragma unroll
-    for (int d = 1; d < 16; d <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, off0, d, 16);
-        if ((int)r >= d) off0 += v;
-    }
-    const uint32_t sum0 = __shfl_sync(0xFFFFFFFFu, off0, 15, 16);   // entries of records 0..15
-    uint32_t off1 = c1;
-#pragma unroll
-    for (int d = 1; d < 16; d <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, off1, d, 16);
-        if ((int)r >= d) off1 += v;
-    }
-    off0 -= c0;
-    off1 = sum0 + off1 - c1;
-    (void)tot;
-    const uint2 *ent = (fwd ? p.w.recFe : p.w.recBe) + i * kRecEntries;
-    uint32_t st0 = 0, st1 = 0;
-    if (r < nrec) {
-        st0 = record_union(p, fwd, ent + off0, c0, H, bad);
-        if (fwd) p.w.FC[g0 + r + 1] = st0;                    // record r: boundary r+1
-        else p.w.BC[g0 + (nsub - 1 - r) - 1] = st0;           // record r: boundary nsub-1-r
-    }
-    if (r + 16 < nrec) {
-        st1 = record_union(p, fwd, ent + off1, c1, H, bad);
-        if (fwd) p.w.FC[g0 + r + 17] = st1;
-        else p.w.BC[g0 + (nsub - 17 - r) - 1] = st1;
-    }
-    const uint32_t lastr = nrec > 0 ? nrec - 1 : 0;           // last record: lane lastr % 16
-    const uint32_t from = __shfl_sync(0xFFFFFFFFu, lastr >= 16 ? st1 : st0, (lastr & 15) + 16 * half, 32);
-    if (!active || r != 0) return;
-    if (fwd) {
-        if (nrec + 1 <= conv - 1) {                           // walk boundaries nrec+1 .. conv-1
+        if (nrec + 1 <= conv - 1) {                             // walk boundaries nrec+1 .. conv-1
             const uint32_t start = nrec == 0 ? p.w.FJ[i] : from;
             walk_fwd<TM>(p, T, base, 64 * nrec, 64 * (conv - 1), start,
                          [&](uint32_t b, uint32_t s2) { p.w.FC[g0 + b / 64] = s2; });
         }
     } else {
-        const uint32_t bb_first = nsub - 1 - nrec;            // first boundary not recorded
-        if (bb_first > conv) {                                // walk boundaries bb_first .. conv+1
+        const uint32_t bb_first = nsub - 1 - nrec;              // first boundary not recorded
+        if (bb_first > conv) {                                  // walk boundaries bb_first .. conv+1
             const uint32_t start = nrec == 0 ? p.w.BJ[i + 1] : from;
             const uint32_t t1 = nrec == 0 ? len : 64 * (bb_first + 1);
             walk_bwd<TM>(p, T, base, 64 * (conv + 1), t1, start,
@@ -220,34 +171,164 @@ __device__ void fixup_chunk(const Params &p, const Tabs &T, uint64_t i, bool &ba
     }
 }
 
-template <int TM>
-__global__ void __launch_bounds__(kChunkThreads) fixup_kernel(const __grid_constant__ Params p) {
-    extern __shared__ __align__(16) uint8_t sm[];
-    Tabs T;
-    stage_tables<TM>(p.t, sm, T);
-    if (*p.status != RE_OK) return;
-    bool bad = false;
-    const uint32_t wpb = blockDim.x / 32;
-    const uint64_t nw = (uint64_t)gridDim.x * wpb;
-    for (uint64_t i = (uint64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < p.c; i += nw) fixup_chunk<TM>(p, T, i, bad);
-    if (bad) atomicExch(p.status, RE_E_INTERNAL);
+// A fix-up block takes kFixItems (chunk, direction) items at a time and
+// spreads all their records over its threads, one record per thread: the
+// number of records per item varies widely (most chunks' runs meet after a
+// few boundaries, a run inside a long match may stay apart for the whole
+// record), so a thread per item would leave each warp waiting for its
+// longest record chain.
+constexpr uint32_t kFixItems = 32;
+
+struct FixShared {
+    uint32_t chunk[kFixItems], text[kFixItems], nrec[kFixItems], H[kFixItems], conv[kFixItems];
+    uint32_t walk[kFixItems];                 // 1: boundaries past the record remain (after record nrec-1)
+    uint32_t first[kFixItems + 1];            // flat index of each item's first record
+    uint32_t off[kFixItems][kRecBounds];      // entry offset of each record in its item's row
+    uint32_t cnt[kFixItems][kRecBounds];      // entries of each record
+    uint32_t ok;
+};
+
+// Item q of a text: forward items first.  Sets the item's slot in S
+// (warp 0, lane q % kFixItems); an inactive item gets no records and no walk.
+__device__ __forceinline__ void fix_item(const Params &p, FixShared &S, uint32_t slot, uint32_t ti, uint64_t i,
+                                         bool fwd, bool live) {
+    uint32_t conv = 0, nrec = 0, H = 0, walk = 0;
+    if (live) {
+        const uint32_t len = chunk_len(p, (uint32_t)i);
+        const uint32_t nsub = (len + 63) / 64;
+        bool active;
+        if (fwd) {
+            conv = p.w.fconv[i];
+            active = conv > 1;                                  // boundaries 1 .. conv-1
+            if (active) { nrec = p.w.fnrec[i]; H = p.w.fhit[i]; walk = nrec + 1 <= conv - 1; }
+        } else {
+            conv = p.w.bconv[i];
+            active = !p.recognize && nsub >= 2 && conv + 1 <= nsub - 1;   // boundaries nsub-1 .. conv+1
+            if (active) { nrec = p.w.bnrec[i]; H = p.w.bhit[i]; walk = nsub - 1 - nrec > conv; }
+        }
+    }
+    S.chunk[slot] = (uint32_t)i;
+    S.text[slot] = ti;
+    S.nrec[slot] = nrec;
+    S.H[slot] = H;
+    S.conv[slot] = conv;
+    S.walk[slot] = (fwd ? 2u : 0u) | walk;                   // bit 1: forward
 }
 
-// Batch: warps take the flat chunks of every text of the group in turn.
+// The records of the kFixItems items in S (filled by fix_item): counts and
+// offsets, then one record per thread, then the walks.  P(ti) gives the
+// Params of text ti; a record whose union is no DFA state marks its text's
+// status RE_E_INTERNAL.  Called by the whole block.
+template <int TM, typename PF>
+__device__ void fix_block(const Tabs &T, FixShared &S, PF P) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    if (warp == 0) {                                            // first[]: exclusive scan of nrec
+        const uint32_t v = S.nrec[lane];
+        uint32_t x = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+            if ((int)lane >= d) x += y;
+        }
+        S.first[lane] = x - v;
+        if (lane == 31) S.first[kFixItems] = x;
+    }
+    for (uint32_t q = warp; q < kFixItems; q += nwarps) {      // one warp per item: counts and offsets
+        const uint32_t nrec = S.nrec[q];
+        if (nrec == 0) continue;                                // warp-uniform
+        const Params &p = P(S.text[q]);
+        const bool fwd = S.walk[q] & 2u;
+        const uint32_t *cnt_row = (fwd ? p.w.recFc : p.w.recBc) + (uint64_t)S.chunk[q] * kRecBounds;
+        const uint32_t c = lane < nrec ? cnt_row[lane] : 0u;
+        uint32_t x = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+            if ((int)lane >= d) x += y;
+        }
+        S.off[q][lane] = x - c;
+        S.cnt[q][lane] = c;
+    }
+    __syncthreads();
+    const uint32_t total = S.first[kFixItems];
+    for (uint32_t f = threadIdx.x; f < total; f += blockDim.x) {
+        uint32_t lo = 0, hi = kFixItems;                        // item q: first[q] <= f < first[q+1]
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (S.first[mid] <= f) lo = mid; else hi = mid;
+        }
+        const uint32_t q = lo, r = f - S.first[q];
+        const Params &p = P(S.text[q]);
+        const bool fwd = S.walk[q] & 2u;
+        const uint64_t i = S.chunk[q];
+        const uint2 *ent = (fwd ? p.w.recFe : p.w.recBe) + i * kRecEntries + S.off[q][r];
+        bool bad = false;
+        const uint32_t st = record_union(p, fwd, ent, S.cnt[q][r], S.H[q], bad);
+        if (bad) atomicExch(p.status, RE_E_INTERNAL);
+        const uint64_t g0 = i * p.S;
+        if (fwd) {
+            p.w.FC[g0 + r + 1] = st;                            // record r: boundary r+1
+        } else {
+            const uint32_t nsub = (chunk_len(p, (uint32_t)i) + 63) / 64;
+            p.w.BC[g0 + (nsub - 1 - r) - 1] = st;               // record r: boundary nsub-1-r
+        }
+        if (r + 1 == S.nrec[q] && (S.walk[q] & 1u)) fixup_walk<TM>(p, T, i, fwd, S.nrec[q], S.conv[q], st);
+    }
+    if (threadIdx.x < kFixItems && S.nrec[threadIdx.x] == 0 && (S.walk[threadIdx.x] & 1u)) {   // walks with no record
+        const uint32_t q = threadIdx.x;
+        fixup_walk<TM>(P(S.text[q]), T, S.chunk[q], S.walk[q] & 2u, 0u, S.conv[q], 0u);
+    }
+    __syncthreads();                                            // S is refilled next
+}
+
+// Items 0 .. c-1 are the chunks' forward directions, c .. 2c-1 their
+// backward ones.
 template <int TM>
-__global__ void __launch_bounds__(kChunkThreads) fixup_batch_kernel(const __grid_constant__ BatchGroup b) {
+__global__ void __launch_bounds__(kFixupThreads, 4) fixup_kernel(const __grid_constant__ Params p) {
     extern __shared__ __align__(16) uint8_t sm[];
+    __shared__ FixShared S;
+    Tabs T;
+    stage_tables<TM>(p.t, sm, T);
+    pdl_wait();
+    pdl_trigger();
+    if (threadIdx.x == 0) S.ok = *p.status == RE_OK;
+    __syncthreads();
+    if (!S.ok) return;                                          // block-uniform
+    const uint64_t items = 2 * (uint64_t)p.c;
+    for (uint64_t q0 = (uint64_t)blockIdx.x * kFixItems; q0 < items; q0 += (uint64_t)gridDim.x * kFixItems) {
+        if (threadIdx.x < kFixItems) {
+            const uint64_t q = q0 + threadIdx.x;
+            const bool fwd = q < p.c;
+            fix_item(p, S, threadIdx.x, 0, fwd ? q : q - p.c, fwd, q < items);
+        }
+        __syncthreads();
+        fix_block<TM>(T, S, [&](uint32_t) -> const Params & { return p; });
+    }
+}
+
+// Batch: the same items over the flat chunks of every text of the group.
+template <int TM>
+__global__ void __launch_bounds__(kFixupThreads, 4) fixup_batch_kernel(const __grid_constant__ BatchGroup b) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    __shared__ FixShared S;
     Tabs T;
     stage_tables<TM>(b.t, sm, T);
-    const uint32_t wpb = blockDim.x / 32;
-    const uint64_t nw = (uint64_t)gridDim.x * wpb;
-    for (uint64_t j = (uint64_t)blockIdx.x * wpb + (threadIdx.x >> 5); j < b.chunks; j += nw) {
-        const uint32_t ti = text_of(b.chunk_base, b.nt, j);
-        const Params &p = b.texts[ti];
-        if (*p.status != RE_OK) continue;                         // warp-uniform: one text per warp
-        bool bad = false;
-        fixup_chunk<TM>(p, T, j - b.chunk_base[ti], bad);
-        if (bad) atomicExch(p.status, RE_E_INTERNAL);
+    const uint64_t items = 2 * b.chunks;
+    for (uint64_t q0 = (uint64_t)blockIdx.x * kFixItems; q0 < items; q0 += (uint64_t)gridDim.x * kFixItems) {
+        if (threadIdx.x < kFixItems) {
+            const uint64_t q = q0 + threadIdx.x;
+            const bool fwd = q < b.chunks;
+            const uint64_t f = fwd ? q : q - b.chunks;
+            uint32_t ti = 0;
+            bool live = false;
+            if (q < items) {
+                ti = text_of(b.chunk_base, b.nt, f);
+                live = *b.texts[ti].status == RE_OK;
+            }
+            fix_item(b.texts[ti], S, threadIdx.x, ti, live ? f - b.chunk_base[ti] : 0, fwd, live);
+        }
+        __syncthreads();
+        fix_block<TM>(T, S, [&](uint32_t ti) -> const Params & { return b.texts[ti]; });
     }
 }
 
@@ -553,6 +634,7 @@ __global__ void __launch_bounds__(kBlockThreads, TM == TM_PAIR ? 2 : 3)
     St *stage;
     Enc e;
     merge_setup<TM, E, St>(p.t, p.enc_in_smem, base, T, stage, e);
+    pdl_wait();
     const bool ok = *p.status == RE_OK;
     bool bad = false;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -631,7 +713,7 @@ void merge_one(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_c
     static uint64_t attr_done = 0;
     allow_smem(merge_kernel<TM, E, TMA>, &attr_done);
     const int blocks = grid_for(merge_kernel<TM, E, TMA>, smem, p.Gc, sm_count, kBlockThreads);
-    merge_kernel<TM, E, TMA><<<blocks, kBlockThreads, smem, s>>>(p, map);
+    launch_dependent(merge_kernel<TM, E, TMA>, blocks, kBlockThreads, smem, s, p, map);
 }
 
 template <int TM, int E>
@@ -689,8 +771,9 @@ void fixup_batch_one(const BatchGroup &b, cudaStream_t s, int sm_count) {
     const size_t smem = tables_smem_bytes(b.t, TM);
     static uint64_t attr_done = 0;
     allow_smem(fixup_batch_kernel<TM>, &attr_done);
-    fixup_batch_kernel<TM><<<grid_for(fixup_batch_kernel<TM>, smem, b.chunks * 32, sm_count, kChunkThreads),
-                             kChunkThreads, smem, s>>>(b);
+    fixup_batch_kernel<TM><<<grid_for(fixup_batch_kernel<TM>, smem, b.chunks * 2 * (kFixupThreads / kFixItems), sm_count,
+                                      kFixupThreads),
+                             kFixupThreads, smem, s>>>(b);
 }
 
 template <int TM>
@@ -698,8 +781,10 @@ void fixup_one(const Params &p, cudaStream_t s, int sm_count) {
     const size_t smem = tables_smem_bytes(p.t, TM);
     static uint64_t attr_done = 0;
     allow_smem(fixup_kernel<TM>, &attr_done);
-    fixup_kernel<TM><<<grid_for(fixup_kernel<TM>, smem, (uint64_t)p.c * 32, sm_count, kChunkThreads), kChunkThreads,
-                       smem, s>>>(p);
+    // a block per kFixItems items, at most one wave of resident blocks (they loop over the rest)
+    const int blocks = grid_for(fixup_kernel<TM>, smem, (uint64_t)p.c * 2 * (kFixupThreads / kFixItems), sm_count,
+                                kFixupThreads);
+    launch_dependent(fixup_kernel<TM>, blocks, kFixupThreads, smem, s, p);
 }
 
 }  // namespace
@@ -714,10 +799,14 @@ size_t merge_extra_smem(const Params &p) {
     return a + (size_t)(t.nf + t.nb) * 8;
 }
 
-// The fix-up reads its tables from global memory: walks past the records are
-// rare, and no staged tables means no shared memory, so more warps hide the
-// latency of the record loads.
-void launch_fixup(const Params &p, cudaStream_t s, int sm_count) { fixup_one<TM_GLOBAL>(p, s, sm_count); }
+// The fix-up walks with the parse's staged tables: its duration is that of
+// the longest walk past a chunk's record (a run that stays apart for more
+// boundaries than the record holds), a serial chain of dependent lookups.
+void launch_fixup(const Params &p, cudaStream_t s, int sm_count) {
+    if (p.tmode == TM_PAIR) fixup_one<TM_PAIR>(p, s, sm_count);
+    else if (p.tmode == TM_SMEM) fixup_one<TM_SMEM>(p, s, sm_count);
+    else fixup_one<TM_GLOBAL>(p, s, sm_count);
+}
 
 void launch_merge(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
     if (p.tmode == TM_PAIR) merge_enc<TM_PAIR>(p, map, s, sm_count);
@@ -728,9 +817,10 @@ void launch_merge(const Params &p, const CUtensorMap &map, cudaStream_t s, int s
 void launch_empty(const Params &p, cudaStream_t s) { empty_text_kernel<<<1, 1, 0, s>>>(p); }
 
 void launch_fixup_batch(const BatchGroup &b, uint32_t tmode, cudaStream_t s, int sm_count) {
-    (void)tmode;
     if (b.recognize || !b.chunks) return;
-    fixup_batch_one<TM_GLOBAL>(b, s, sm_count);
+    if (tmode == TM_PAIR) fixup_batch_one<TM_PAIR>(b, s, sm_count);
+    else if (tmode == TM_SMEM) fixup_batch_one<TM_SMEM>(b, s, sm_count);
+    else fixup_batch_one<TM_GLOBAL>(b, s, sm_count);
 }
 
 void launch_merge_batch(const BatchGroup &b, const Params &like, cudaStream_t s, int sm_count) {

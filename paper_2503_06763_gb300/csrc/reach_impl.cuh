@@ -448,6 +448,8 @@ __global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
         }
         __syncwarp();
     }
+    pdl_wait();                                               // the join flags are set by the kernel before
+    pdl_trigger();
     const uint64_t gw = (uint64_t)blockIdx.x * wpb + warp, nw = (uint64_t)gridDim.x * wpb;
     const uint64_t t0 = SPLIT ? gw >> 1 : gw, tstep = SPLIT ? nw >> 1 : nw;
     const bool backward_warp = SPLIT && (gw & 1);
@@ -561,7 +563,7 @@ void launch_split(const Params &p, const CUtensorMap &map, cudaStream_t s, int s
     const uint64_t warps = ((uint64_t)p.c + 31) / 32 * (SPLIT ? 2 : 1);
     const uint64_t want = (warps + threads / 32 - 1) / (threads / 32);
     const uint64_t blocks = std::min<uint64_t>(want, (uint64_t)std::max(per_sm, 1) * sm_count);
-    reach_kernel<TM, MS, SPLIT><<<(uint32_t)std::max<uint64_t>(blocks, 1), threads, smem, s>>>(p, map);
+    launch_dependent(reach_kernel<TM, MS, SPLIT>, (uint32_t)std::max<uint64_t>(blocks, 1), threads, smem, s, p, map);
 }
 
 template <int TM, int MS>
