@@ -188,40 +188,63 @@ struct FixShared {
     uint32_t ok;
 };
 
-// Item q of a text: forward items first.  Sets the item's slot in S
-// (warp 0, lane q % kFixItems); an inactive item gets no records and no walk.
-__device__ __forceinline__ void fix_item(const Params &p, FixShared &S, uint32_t slot, uint32_t ti, uint64_t i,
-                                         bool fwd, bool live) {
+// Item slot q of a block iteration: its text, chunk and direction; live =
+// an item of a text still being parsed.
+struct FixRef {
+    uint32_t ti;
+    uint64_t i;
+    bool fwd, live;
+};
+
+// Sets the item's entries in S (warp 0, lane = slot); an inactive item gets
+// no records and no walk.  Its three words are loaded together.
+__device__ __forceinline__ void fix_item(const Params &p, FixShared &S, uint32_t slot, const FixRef &r) {
     uint32_t conv = 0, nrec = 0, H = 0, walk = 0;
-    if (live) {
-        const uint32_t len = chunk_len(p, (uint32_t)i);
-        const uint32_t nsub = (len + 63) / 64;
-        bool active;
-        if (fwd) {
-            conv = p.w.fconv[i];
-            active = conv > 1;                                  // boundaries 1 .. conv-1
-            if (active) { nrec = p.w.fnrec[i]; H = p.w.fhit[i]; walk = nrec + 1 <= conv - 1; }
-        } else {
-            conv = p.w.bconv[i];
-            active = !p.recognize && nsub >= 2 && conv + 1 <= nsub - 1;   // boundaries nsub-1 .. conv+1
-            if (active) { nrec = p.w.bnrec[i]; H = p.w.bhit[i]; walk = nsub - 1 - nrec > conv; }
+    if (r.live) {
+        const uint64_t i = r.i;
+        const uint32_t c0 = r.fwd ? p.w.fconv[i] : p.w.bconv[i];
+        const uint32_t n0 = r.fwd ? p.w.fnrec[i] : p.w.bnrec[i];
+        const uint32_t h0 = r.fwd ? p.w.fhit[i] : p.w.bhit[i];
+        const uint32_t nsub = (chunk_len(p, (uint32_t)i) + 63) / 64;
+        if (r.fwd) {
+            if (c0 > 1) { conv = c0; nrec = n0; H = h0; walk = nrec + 1 <= conv - 1; }   // boundaries 1 .. conv-1
+        } else if (!p.recognize && nsub >= 2 && c0 + 1 <= nsub - 1) {                  // boundaries nsub-1 .. conv+1
+            conv = c0; nrec = n0; H = h0; walk = nsub - 1 - nrec > conv;
         }
     }
-    S.chunk[slot] = (uint32_t)i;
-    S.text[slot] = ti;
+    S.chunk[slot] = (uint32_t)r.i;
+    S.text[slot] = r.ti;
     S.nrec[slot] = nrec;
     S.H[slot] = H;
     S.conv[slot] = conv;
-    S.walk[slot] = (fwd ? 2u : 0u) | walk;                   // bit 1: forward
+    S.walk[slot] = (r.fwd ? 2u : 0u) | walk;                  // bit 1: forward
 }
 
-// The records of the kFixItems items in S (filled by fix_item): counts and
-// offsets, then one record per thread, then the walks.  P(ti) gives the
-// Params of text ti; a record whose union is no DFA state marks its text's
-// status RE_E_INTERNAL.  Called by the whole block.
-template <int TM, typename PF>
-__device__ void fix_block(const Tabs &T, FixShared &S, PF P) {
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+// One block iteration over kFixItems items: R(q) gives item slot q, P(ti)
+// the Params of text ti.  Item words and record counts are loaded in one
+// round (a count row depends only on the chunk), then scanned; then one
+// record per thread; then the walks.  A record whose union is no DFA state
+// marks its text's status RE_E_INTERNAL.  Called by the whole block.
+template <int TM, typename RF, typename PF>
+__device__ void fix_block(const Tabs &T, FixShared &S, RF R, PF P) {
+    constexpr uint32_t kWarps = kFixupThreads / 32, kPer = kFixItems / kWarps;
+    static_assert(kFixItems % kWarps == 0, "items per warp");
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        const FixRef r = R(lane);
+        fix_item(P(r.ti), S, lane, r);
+    }
+    uint32_t raw[kPer];                                        // count of record `lane` of this warp's items
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+        const FixRef r = R(warp + kWarps * k);
+        raw[k] = 0;
+        if (r.live) {
+            const Params &p = P(r.ti);
+            raw[k] = ((r.fwd ? p.w.recFc : p.w.recBc) + r.i * kRecBounds)[lane];
+        }
+    }
+    __syncthreads();
     if (warp == 0) {                                            // first[]: exclusive scan of nrec
         const uint32_t v = S.nrec[lane];
         uint32_t x = v;
@@ -233,13 +256,10 @@ __device__ void fix_block(const Tabs &T, FixShared &S, PF P) {
         S.first[lane] = x - v;
         if (lane == 31) S.first[kFixItems] = x;
     }
-    for (uint32_t q = warp; q < kFixItems; q += nwarps) {      // one warp per item: counts and offsets
-        const uint32_t nrec = S.nrec[q];
-        if (nrec == 0) continue;                                // warp-uniform
-        const Params &p = P(S.text[q]);
-        const bool fwd = S.walk[q] & 2u;
-        const uint32_t *cnt_row = (fwd ? p.w.recFc : p.w.recBc) + (uint64_t)S.chunk[q] * kRecBounds;
-        const uint32_t c = lane < nrec ? cnt_row[lane] : 0u;
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {                      // entry offsets of each item's records
+        const uint32_t q = warp + kWarps * k;
+        const uint32_t c = lane < S.nrec[q] ? raw[k] : 0u;
         uint32_t x = c;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -296,13 +316,12 @@ __global__ void __launch_bounds__(kFixupThreads, 4) fixup_kernel(const __grid_co
     if (!S.ok) return;                                          // block-uniform
     const uint64_t items = 2 * (uint64_t)p.c;
     for (uint64_t q0 = (uint64_t)blockIdx.x * kFixItems; q0 < items; q0 += (uint64_t)gridDim.x * kFixItems) {
-        if (threadIdx.x < kFixItems) {
-            const uint64_t q = q0 + threadIdx.x;
-            const bool fwd = q < p.c;
-            fix_item(p, S, threadIdx.x, 0, fwd ? q : q - p.c, fwd, q < items);
-        }
-        __syncthreads();
-        fix_block<TM>(T, S, [&](uint32_t) -> const Params & { return p; });
+        auto ref = [&](uint32_t q) -> FixRef {
+            const uint64_t j = q0 + q;
+            const bool fwd = j < p.c;
+            return FixRef{0u, fwd ? j : j - p.c, fwd, j < items};
+        };
+        fix_block<TM>(T, S, ref, [&](uint32_t) -> const Params & { return p; });
     }
 }
 
@@ -315,20 +334,16 @@ __global__ void __launch_bounds__(kFixupThreads, 4) fixup_batch_kernel(const __g
     stage_tables<TM>(b.t, sm, T);
     const uint64_t items = 2 * b.chunks;
     for (uint64_t q0 = (uint64_t)blockIdx.x * kFixItems; q0 < items; q0 += (uint64_t)gridDim.x * kFixItems) {
-        if (threadIdx.x < kFixItems) {
-            const uint64_t q = q0 + threadIdx.x;
-            const bool fwd = q < b.chunks;
-            const uint64_t f = fwd ? q : q - b.chunks;
-            uint32_t ti = 0;
-            bool live = false;
-            if (q < items) {
-                ti = text_of(b.chunk_base, b.nt, f);
-                live = *b.texts[ti].status == RE_OK;
-            }
-            fix_item(b.texts[ti], S, threadIdx.x, ti, live ? f - b.chunk_base[ti] : 0, fwd, live);
-        }
-        __syncthreads();
-        fix_block<TM>(T, S, [&](uint32_t ti) -> const Params & { return b.texts[ti]; });
+        auto ref = [&](uint32_t q) -> FixRef {
+            const uint64_t j = q0 + q;
+            if (j >= items) return FixRef{0u, 0u, true, false};
+            const bool fwd = j < b.chunks;
+            const uint64_t f = fwd ? j : j - b.chunks;
+            const uint32_t ti = text_of(b.chunk_base, b.nt, f);
+            const bool live = *b.texts[ti].status == RE_OK;
+            return FixRef{ti, live ? f - b.chunk_base[ti] : 0u, fwd, live};
+        };
+        fix_block<TM>(T, S, ref, [&](uint32_t ti) -> const Params & { return b.texts[ti]; });
     }
 }
 

@@ -38,11 +38,13 @@ namespace reach {
 // the byte offset of its row in one shared-memory array of two-byte
 // transition rows, forward rows first:
 //     forward state s  -> s * rowb,        backward state s -> (nf + s) * rowb,
-// rowb = ncls^2 * 4.  An entry of row s, column (c1, c2), is the offset of the
-// state after the byte pair, so one step is an add and a load:
-//     run = *(u32 *)(sm + kRows + run + cp4),  cp4 = 4 * (c1 * ncls + c2),
-// and cp4 comes from two byte-indexed class tables, H[b] = c(b) * ncls and
-// L[b] = 4 * c(b), as (H[b1] << 2) + L[b2].  The run's state id is needed only
+// rowb = ncls^2 * 2.  An entry of row s, column (c1, c2), is the offset (a
+// u16: pair-mode tables are at most 48 KB as u32, so offsets stay below 2^16)
+// of the state after the byte pair, so one step is an add and a load:
+//     run = *(u16 *)(sm + kRows + run + cp2),  cp2 = 2 * (c1 * ncls + c2),
+// and cp2 comes from two byte-indexed class tables, H[b] = c(b) * ncls and
+// L[b] = 2 * c(b), as (H[b1] << 1) + L[b2].  Two-byte entries halve the
+// rows' footprint in the banks, so fewer lanes of a warp meet in one bank.  The run's state id is needed only
 // at 64-byte boundaries (records, checkpoints, end states) and is the offset
 // divided by rowb (a multiply-high by a reciprocal: offsets are exact
 // multiples of rowb and small).  Blocks that start or end inside a chunk's
@@ -52,25 +54,26 @@ namespace reach {
 constexpr uint32_t kClsH = 0, kClsL = 256, kCls = 512, kRows = 1024;
 
 __host__ __device__ inline size_t reach_pair_smem(const DevTables &t) {
-    const size_t rows = (size_t)(t.nf + t.nb) * t.ncls * t.ncls * 4;
+    const size_t rows = (size_t)(t.nf + t.nb) * t.ncls * t.ncls * 2;
     return kRows + ((rows + 15) & ~(size_t)15) + (((size_t)t.nf * t.ncls * 2 + 15) & ~(size_t)15) +
            (((size_t)t.nb * t.ncls * 2 + 15) & ~(size_t)15);
 }
 
 // Stage the pair-mode layout (block-wide; ends with __syncthreads).
 __device__ inline uint8_t *stage_reach_pair(const DevTables &t, uint8_t *sm, Tabs &T) {
-    const uint32_t ncls = t.ncls, nc2 = ncls * ncls, rowb = nc2 * 4;
+    const uint32_t ncls = t.ncls, nc2 = ncls * ncls, rowb = nc2 * 2;
     for (uint32_t b = threadIdx.x; b < 256; b += blockDim.x) {
         const uint32_t c = __ldg(t.cls + b);
         sm[kClsH + b] = (uint8_t)(c * ncls);
-        sm[kClsL + b] = (uint8_t)(4 * c);
+        sm[kClsL + b] = (uint8_t)(2 * c);
         sm[kCls + b] = (uint8_t)c;
     }
-    uint32_t *rows = reinterpret_cast<uint32_t *>(sm + kRows);
+    uint16_t *rows = reinterpret_cast<uint16_t *>(sm + kRows);
     const size_t nfw = (size_t)t.nf * nc2, nbw = (size_t)t.nb * nc2;
-    for (size_t i = threadIdx.x; i < nfw; i += blockDim.x) rows[i] = (__ldg(t.f2 + i) >> 16) * rowb;
-    for (size_t i = threadIdx.x; i < nbw; i += blockDim.x) rows[nfw + i] = (t.nf + (__ldg(t.b2 + i) >> 16)) * rowb;
-    uint8_t *after = sm + kRows + (((nfw + nbw) * 4 + 15) & ~(size_t)15);
+    for (size_t i = threadIdx.x; i < nfw; i += blockDim.x) rows[i] = (uint16_t)((__ldg(t.f2 + i) >> 16) * rowb);
+    for (size_t i = threadIdx.x; i < nbw; i += blockDim.x)
+        rows[nfw + i] = (uint16_t)((t.nf + (__ldg(t.b2 + i) >> 16)) * rowb);
+    uint8_t *after = sm + kRows + (((nfw + nbw) * 2 + 15) & ~(size_t)15);
     uint16_t *f16 = reinterpret_cast<uint16_t *>(after);
     const size_t fsz = (size_t)t.nf * ncls, bsz = (size_t)t.nb * ncls;
     uint16_t *b16 = reinterpret_cast<uint16_t *>(after + ((fsz * 2 + 15) & ~(size_t)15));
@@ -108,9 +111,9 @@ template <int TM> __device__ __forceinline__ uint32_t dec_b(const Tabs &T, uint3
 // Byte k (0..3) of w, zero-extended (one byte permute).
 __device__ __forceinline__ uint32_t byte_k(uint32_t w, int k) { return __byte_perm(w, 0u, 0x4440u | (uint32_t)k); }
 
-// 4 * class pair of bytes (lo, hi) of w at positions k, k+1 in pair mode.
-__device__ __forceinline__ uint32_t cp4_of(const uint8_t *sm, uint32_t w, int k) {
-    return ((uint32_t)sm[kClsH + byte_k(w, k)] << 2) + sm[kClsL + byte_k(w, k + 1)];
+// 2 * class pair of bytes (lo, hi) of w at positions k, k+1 in pair mode.
+__device__ __forceinline__ uint32_t cp2_of(const uint8_t *sm, uint32_t w, int k) {
+    return ((uint32_t)sm[kClsH + byte_k(w, k)] << 1) + sm[kClsL + byte_k(w, k + 1)];
 }
 
 // One 64-byte block of both directions.  Runs j < W are stepped, W a
@@ -138,14 +141,14 @@ __device__ __forceinline__ void walk_block(const Params &p, const Tabs &T, const
 #pragma unroll
             for (int v = 0; v < 8; ++v) {
                 if (FW) {
-                    const uint32_t cpf = cp4_of(sm, fw[v >> 1], 2 * (v & 1));
+                    const uint32_t cpf = cp2_of(sm, fw[v >> 1], 2 * (v & 1));
 #pragma unroll
-                    for (int j = 0; j < W; ++j) sf[j] = *reinterpret_cast<const uint32_t *>(sm + kRows + sf[j] + cpf);
+                    for (int j = 0; j < W; ++j) sf[j] = *reinterpret_cast<const uint16_t *>(sm + kRows + sf[j] + cpf);
                 }
                 if (bwd) {                            // pair (14-2v, 15-2v), consumed right to left
-                    const uint32_t cpb = cp4_of(sm, bw[(7 - v) >> 1], 2 * ((7 - v) & 1));
+                    const uint32_t cpb = cp2_of(sm, bw[(7 - v) >> 1], 2 * ((7 - v) & 1));
 #pragma unroll
-                    for (int j = 0; j < W; ++j) sb[j] = *reinterpret_cast<const uint32_t *>(sm + kRows + sb[j] + cpb);
+                    for (int j = 0; j < W; ++j) sb[j] = *reinterpret_cast<const uint16_t *>(sm + kRows + sb[j] + cpb);
                 }
             }
         } else {
