@@ -14,7 +14,7 @@ Paper passages followed (arXiv 2503.06763):
   * Segments Q, initial I, final F: Fig. (segmentalgo), recursive MetaPrefix.
   * FolSeg: Eq. (folsegdef).
   * Character sets, wildcard, escapes, ε symbols, extra parentheses, bounded
-    repetition e{k}: App. A.
+    repetition e{h}, e{h,k}, e{h,}: App. A.
 
 Readings where the paper is silent (all listed in the design doc):
   * A parenthesised group creates a numbered node only through the operator it
@@ -23,7 +23,9 @@ Readings where the paper is silent (all listed in the design doc):
     parenthesis, App. A).
   * ``e?`` is ``(e|ε)``; an empty alternative or an empty group is ε.
   * ``e{k}`` is one numbered node whose k children are fresh copies of e
-    numbered progressively (App. A, "Bounded repetition"; Ex. 5).
+    numbered progressively (App. A, "Bounded repetition"; Ex. 5).  ``e{h,k}``
+    and ``e{h,}`` add the optional (resp. starred) further iterations, each
+    with its own copy; see ``expand_repetitions``.
   * ``.`` matches every byte but newline (App. A, "wildcard").
   * The initial symbol test of MetaPrefix (``s = 1(``) is read as "s is the
     first symbol of every LST", which is ``1(`` whenever the root is an
@@ -55,8 +57,9 @@ class Node:
     kind: str                      # 'term' | 'eps' | 'cat' | 'alt' | 'star' | 'plus' | 'rep'
     children: list = field(default_factory=list)
     chars: frozenset = frozenset()  # for 'term'
-    count: int = 0                  # for 'rep'
+    count: int = 0                  # for 'rep': the lower bound h of e{h}, e{h,k}, e{h,}
     num: int = 0                    # number assigned by numbering (Eq. numberedRE)
+    hi: int = 0                     # for 'rep': the upper bound (= count for e{h}; -1: none)
 
 
 def _escape_byte(s: bytes, i: int):
@@ -159,9 +162,14 @@ def parse(pattern) -> Node:
                 if j < 0:
                     raise OracleSyntaxError("unterminated {")
                 txt = s[pos + 1:j].decode("latin-1")
-                if not txt.isdigit() or int(txt) < 1:
-                    raise OracleSyntaxError("only e{k} with k >= 1 is supported")
-                node = Node("rep", [node], count=int(txt)); pos = j + 1
+                lo_txt, comma, hi_txt = txt.partition(",")
+                if not lo_txt.isdigit() or (hi_txt and not hi_txt.isdigit()):
+                    raise OracleSyntaxError("bounded repetition is e{h}, e{h,k} or e{h,}")
+                lo = int(lo_txt)
+                hi = lo if not comma else (int(hi_txt) if hi_txt else -1)
+                if (not comma and lo < 1) or (comma and hi_txt and not lo < hi):
+                    raise OracleSyntaxError("bounded repetition needs 1 <= h in e{h} and h < k in e{h,k}")
+                node = Node("rep", [node], count=lo, hi=hi); pos = j + 1
             else:
                 break
         return node
@@ -199,15 +207,32 @@ def parse(pattern) -> Node:
 
 
 def _copy(node: Node) -> Node:
-    return Node(node.kind, [_copy(ch) for ch in node.children], node.chars, node.count)
+    return Node(node.kind, [_copy(ch) for ch in node.children], node.chars, node.count, hi=node.hi)
 
 
 def expand_repetitions(node: Node) -> Node:
-    """e{k}: one node holding k fresh copies of e (App. A, bounded repetition)."""
+    """Bounded repetition (App. A): one node whose children are fresh copies
+    of e, so every iteration has its own numbered symbols.
+
+    * e{h}: the h copies.
+    * e{h,k}: the h copies, then copies h+1 .. k, each optional and present
+      only after the one before it: (e (e (... e?)?)?)?.  A tree with j
+      iterations therefore uses copies 1 .. j, in order.
+    * e{h,}: the h copies, then copy h+1 under a star.
+    """
     kids = [expand_repetitions(ch) for ch in node.children]
     if node.kind == "rep":
-        return Node("rep", [_copy(kids[0]) for _ in range(node.count)], count=node.count)
-    return Node(node.kind, kids, node.chars, node.count)
+        body, h, hi = kids[0], node.count, node.hi
+        reps = [_copy(body) for _ in range(h)]
+        if hi == -1:
+            reps.append(Node("star", [_copy(body)]))
+        elif hi > h:
+            tail = Node("alt", [_copy(body), Node("eps")])            # copy k
+            for _ in range(hi - h - 1):                               # copies k-1 .. h+1 around it
+                tail = Node("alt", [Node("cat", [_copy(body), tail]), Node("eps")])
+            reps.append(tail)
+        return Node("rep", reps, count=h, hi=hi)
+    return Node(node.kind, kids, node.chars, node.count, hi=node.hi)
 
 
 def derives_empty_text(node: Node) -> bool:

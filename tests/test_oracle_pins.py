@@ -175,7 +175,8 @@ def test_ek_dfa_state_count(golden, k):
 
 # --------------------------------------------------------------------------- brute force
 BRUTE_RES = ["(a|b|ab)*", "(ab|a)*", "(a|ab|aba)+", "(a|)b", "a(b|c)*d", "(a*b|ac)+", "((ab)*c|a(bc)*)*",
-             "(a|b)*a(a|b){2}", "a", "(ab){2}(a|b)?", "(a|b)(a|b)*", "[ab]([^b]|bb)*"]
+             "(a|b)*a(a|b){2}", "a", "(ab){2}(a|b)?", "(a|b)(a|b)*", "[ab]([^b]|bb)*",
+             "(a|bc){1,3}", "(ab|a){2,}", "a{0,2}b", "(a?){2,3}"]
 
 
 @pytest.mark.parametrize("pattern", BRUTE_RES)
@@ -284,12 +285,60 @@ def test_rejected_texts_give_empty_columns():
 
 
 def test_syntax_errors_and_infinite_ambiguity():
-    for bad in ["(a", "a)", "*a", "[ab", "a{0}", "\\"]:
+    for bad in ["(a", "a)", "*a", "[ab", "a{0}", "\\", "a{3,2}", "a{2,2}", "a{,2}", "a{}", "a{1,x}"]:
         with pytest.raises(OracleSyntaxError):
             compile_re(bad)
-    for amb in ["(a|)*", "(a*)*", "(a?b?)+", "()*"]:
+    for amb in ["(a|)*", "(a*)*", "(a?b?)+", "()*", "(a?){2,}"]:
         with pytest.raises(InfiniteAmbiguity):
             compile_re(amb)
+
+
+# --------------------------------------------------------------------------- bounded repetition
+BOUNDED = ["(a|bc){1,3}", "(ab|a){2,}", "a{0,2}b", "(a|b){2,3}c?", "(a|aa){2,3}", "(a?){2,3}", "(ab){0,}c"]
+
+
+@pytest.mark.parametrize("pattern", BOUNDED)
+def test_bounded_repetition_language(pattern):
+    """App. A, bounded repetition: e{h}, e{h,k}, e{h,} accept the same texts
+    as Python's re module (an independent definition), on every text over
+    {a, b, c} up to length 7."""
+    import re
+    c = compile_re(pattern)
+    rx = re.compile(pattern.encode())
+    for n in range(0, 8):
+        for tup in itertools.product(b"abc", repeat=n):
+            text = bytes(tup)
+            assert serial.accepted(serial.parse(c, text)) == (rx.fullmatch(text) is not None), (pattern, text)
+
+
+def test_bounded_repetition_tree_counts():
+    """(a|aa){h,k} on a^n: a tree is a sequence of j iterations, h <= j <= k,
+    each 'a' or 'aa', so there are sum_j C(j, n - j) trees (compositions of n
+    into j parts of size 1 or 2); e{h,} sums over every j >= h."""
+    from math import comb
+    for (h, k) in [(1, 1), (2, 3), (0, 2), (1, 4), (3, -1), (0, -1)]:
+        pat = "(a|aa){%d}" % h if k == h else ("(a|aa){%d,}" % h if k < 0 else "(a|aa){%d,%d}" % (h, k))
+        c = compile_re(pat)
+        for n in range(0, 8):
+            top = n if k < 0 else k
+            want = sum(comb(j, n - j) for j in range(h, top + 1) if 0 <= n - j <= j)
+            assert sum(1 for _ in trees.lsts(c, b"a" * n)) == want, (pat, n)
+
+
+def test_bounded_repetition_iteration_numbering():
+    """App. A: every iteration of a bounded repetition has its own numbered
+    symbols, and a tree with j iterations uses copies 1 .. j in order, so
+    the terminal numbers along a^2, a^3, a^4 under a{2,4} extend each other."""
+    c = compile_re("a{2,4}")
+    seen = []
+    for n in (2, 3, 4):
+        lsts = list(trees.lsts(c, b"a" * n))
+        assert len(lsts) == 1
+        nums = [s[1] for s in lsts[0] if s[0] == "t"]
+        assert len(nums) == n and nums == sorted(nums) and len(set(nums)) == n
+        seen.append(nums)
+    assert seen[1][:2] == seen[0] and seen[2][:3] == seen[1]
+    assert sum(1 for _ in trees.lsts(c, b"a" * 5)) == 0
 
 
 # --------------------------------------------------------------------------- mutation check
