@@ -124,7 +124,9 @@ typedef struct {
 } re_info;
 
 /* Compile a pattern (Sect. 2.1 syntax plus App. A character features:
- * '|' union, juxtaposition, postfix '*', '+', '?', 'e{k}', '(' ')' groups,
+ * '|' union, juxtaposition, postfix '*', '+', '?', bounded repetition
+ * 'e{h}' (1 <= h), 'e{h,k}' (h < k) and 'e{h,}' (bounds up to 4096; every
+ * iteration gets its own numbered copy of e), '(' ')' groups,
  * '[...]' / '[^...]' byte sets, '.', '\' escapes incl. \n \t \r \xHH; an empty
  * alternative is ε).  Builds segments (Fig. segmentalgo), FolSeg
  * (Eq. folsegdef), forward / reverse DFA and ME-DFA (Sect. 3.1) and uploads

@@ -40,9 +40,13 @@ struct Node {
     enum Kind { TERM, EPS, CAT, ALT, STAR, PLUS, REP } kind;
     std::vector<int> kids;
     uint64_t set[4] = {0, 0, 0, 0};   // byte set for TERM
-    uint32_t count = 0;               // REP
+    uint32_t count = 0;               // REP: lower bound h of e{h}, e{h,k}, e{h,}
+    uint32_t hi = 0;                  // REP: upper bound (= count for e{h}; kUnbounded for e{h,})
     uint32_t num = 0;
 };
+
+constexpr uint32_t kUnbounded = 0xFFFFFFFFu;
+constexpr uint64_t kMaxRepeat = 4096;
 
 struct SyntaxError {
     std::string msg;
@@ -155,15 +159,28 @@ class Parser {
             if (c == '*') { ++i_; nd = make(Node::STAR, {nd}); }
             else if (c == '+') { ++i_; nd = make(Node::PLUS, {nd}); }
             else if (c == '?') { ++i_; int e = make(Node::EPS); nd = make(Node::ALT, {nd, e}); }
-            else if (c == '{') {
+            else if (c == '{') {                   // e{h}, e{h,k}, e{h,} (App. A, bounded repetition)
                 size_t j = i_ + 1;
-                uint64_t v = 0;
-                while (j < n_ && s_[j] >= '0' && s_[j] <= '9' && v < 100000) v = v * 10 + (s_[j++] - '0');
-                if (j >= n_ || s_[j] != '}' || j == i_ + 1 || v < 1 || v > 4096)
-                    throw SyntaxError{"only e{k} with 1 <= k <= 4096 is supported"};
+                auto number = [&](uint64_t &v) {
+                    const size_t j0 = j;
+                    v = 0;
+                    while (j < n_ && s_[j] >= '0' && s_[j] <= '9' && v <= kMaxRepeat) v = v * 10 + (s_[j++] - '0');
+                    return j > j0;
+                };
+                uint64_t lo = 0, hi = 0;
+                bool ok = number(lo);
+                bool comma = false, has_hi = false;
+                if (ok && j < n_ && s_[j] == ',') { comma = true; ++j; has_hi = number(hi); }
+                ok = ok && j < n_ && s_[j] == '}' && lo <= kMaxRepeat && hi <= kMaxRepeat;
+                if (ok && !comma) ok = lo >= 1;
+                if (ok && has_hi) ok = lo < hi;
+                if (!ok)
+                    throw SyntaxError{"bounded repetition is e{h} (1 <= h), e{h,k} (h < k) or e{h,}, "
+                                      "with bounds up to 4096"};
                 i_ = j + 1;
                 nd = make(Node::REP, {nd});
-                nodes_[nd].count = (uint32_t)v;
+                nodes_[nd].count = (uint32_t)lo;
+                nodes_[nd].hi = !comma ? (uint32_t)lo : has_hi ? (uint32_t)hi : kUnbounded;
             } else break;
         }
         return nd;
@@ -183,7 +200,7 @@ class Parser {
     }
 };
 
-// Deep copy (for e{k} expansion).
+// Deep copy (for bounded-repetition expansion).
 int clone(std::vector<Node> &nodes, int id) {
     Node cp = nodes[id];
     const std::vector<int> src = nodes[id].kids;   // nodes grows below
@@ -194,14 +211,44 @@ int clone(std::vector<Node> &nodes, int id) {
     return (int)nodes.size() - 1;
 }
 
+// Bounded repetition (App. A): the node's children become fresh copies of
+// its body, so every iteration has its own numbered symbols.  e{h}: h copies;
+// e{h,k}: then copies h+1 .. k as nested optionals (e (e (... e?)?)?)?, so a
+// tree with j iterations uses copies 1 .. j in order; e{h,}: then copy h+1
+// under a star.
 void expand(std::vector<Node> &nodes, int id) {
     for (size_t i = 0; i < nodes[id].kids.size(); ++i) expand(nodes, nodes[id].kids[i]);
-    if (nodes[id].kind == Node::REP) {
-        int body = nodes[id].kids[0];
-        std::vector<int> copies{body};
-        for (uint32_t c = 1; c < nodes[id].count; ++c) copies.push_back(clone(nodes, body));
-        nodes[id].kids = copies;
+    if (nodes[id].kind != Node::REP) return;
+    const int body = nodes[id].kids[0];
+    const uint32_t h = nodes[id].count, hi = nodes[id].hi;
+    bool body_used = false;
+    auto fresh = [&]() {                            // the body itself first, then clones
+        if (!body_used) { body_used = true; return body; }
+        return clone(nodes, body);
+    };
+    auto add = [&](Node::Kind k, std::vector<int> kids) {
+        Node nd;
+        nd.kind = k;
+        nd.kids = std::move(kids);
+        nodes.push_back(nd);
+        return (int)nodes.size() - 1;
+    };
+    std::vector<int> reps;
+    for (uint32_t c = 0; c < h; ++c) reps.push_back(fresh());
+    if (hi == kUnbounded) {
+        const int copy = fresh();
+        reps.push_back(add(Node::STAR, {copy}));
+    } else if (hi > h) {
+        int copy = fresh();
+        int tail = add(Node::ALT, {copy, add(Node::EPS, {})});                 // copy k
+        for (uint32_t j = 0; j + 1 < hi - h; ++j) {                           // copies k-1 .. h+1 around it
+            copy = fresh();
+            const int cat = add(Node::CAT, {copy, tail});
+            tail = add(Node::ALT, {cat, add(Node::EPS, {})});
+        }
+        reps.push_back(tail);
     }
+    nodes[id].kids = reps;
 }
 
 bool empty_text(const std::vector<Node> &nodes, int id) {

@@ -75,7 +75,8 @@ def test_dna(lib, n, chunk_len):
 
 
 @pytest.mark.parametrize("pattern", ["(ab|a)*", "(a|ab|aba)+", "(a|b)*a(a|b){3}", "((ab)*c|a(bc)*)*",
-                                     "[ab]([^b]|bb)*", "(aa)*", "(a|b)*(aaa|bbb)(a|b)*"])
+                                     "[ab]([^b]|bb)*", "(aa)*", "(a|b)*(aaa|bbb)(a|b)*",
+                                     "((a|b){1,3}|c{1,2})*", "(a{0,2}b|a|c)*", "((a|b){2,}|a|b|c)*"])
 def test_fixed_res_random_texts(lib, pattern):
     rx = lib(pattern)
     rng = np.random.Generator(np.random.PCG64(len(pattern)))

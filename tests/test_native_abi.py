@@ -16,7 +16,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 PATTERNS = ["(a|b|ab)*", "(ab|a)*", "(a|ab|aba)+", "(a|)b", "(a|b)*a(a|b){3}", "a", "()",
             "([ACGT]|ATG([ACGT][ACGT][ACGT])*(TAA|TAG|TGA))*", "((ab)*c|a(bc)*)*", "[ab]([^b]|bb)*",
-            "(x(y|z)?w|[^a-c]+)*q", "a(b(c(d)))", "(a|(b|c)|d)*", "(\\.|[0-9]+\\.?)+", "((a|b)(a|b))*"]
+            "(x(y|z)?w|[^a-c]+)*q", "a(b(c(d)))", "(a|(b|c)|d)*", "(\\.|[0-9]+\\.?)+", "((a|b)(a|b))*",
+            "(a|bc){1,3}", "(ab|a){2,}", "a{0,2}b", "(a|b){2,3}c?", "(a?){2,3}", "(ab){0,}c", "((a|b){2}c){1,2}"]
 
 
 @pytest.fixture(scope="module")
@@ -72,7 +73,9 @@ def test_layout_and_errors(native):
     big = native.Regex("([ACGT]|ATG([ACGT][ACGT][ACGT])*(TAA|TAG|TGA))*", host_only=True)
     assert big.layout(10, "auto") == ("dict", 2, 22)
     assert big.layout(10, "dense") == ("dense", 8, 88)
-    for bad, code in (("(a", -2), ("a)", -2), ("(a|)*", -3), ("(a*)*", -3), ("a{0}", -2)):
+    for bad, code in (("(a", -2), ("a)", -2), ("(a|)*", -3), ("(a*)*", -3), ("a{0}", -2), ("a{3,2}", -2),
+                      ("a{2,2}", -2), ("a{,2}", -2), ("a{}", -2), ("a{1,x}", -2), ("a{4097}", -2),
+                      ("(a?){2,}", -3)):
         with pytest.raises(native.ReError) as e:
             native.Regex(bad, host_only=True)
         assert e.value.status == code
