@@ -48,7 +48,7 @@ def parse_args():
     ap.add_argument("--bytes", type=int, default=N_BYTES, help="text size (default 256 MiB)")
     ap.add_argument("--chunk-len", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "matches", "latency"],
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "matches", "latency", "ablation"],
                     help="single: one 256 MiB text (default); batch: 4096 texts under 8 random REs; "
                          "serve: Poisson request stream")
     ap.add_argument("--texts", type=int, default=4096, help="batch mode: number of texts")
@@ -225,6 +225,8 @@ def main():
         return matches_mode(args, rank, world, local)
     if args.mode == "latency":
         return latency_mode(args, rank, world, local)
+    if args.mode == "ablation":
+        return ablation_mode(args, rank, world, local)
 
     import torch
     torch.cuda.set_device(local)
@@ -271,7 +273,7 @@ def main():
         t_end = torch.cuda.Event(enable_timing=True)
         t_start.record(stream)
         for i in range(args.steps):
-            step(i)
+            step()
         t_end.record(stream)
         torch.cuda.synchronize()
         if dist:
@@ -281,7 +283,12 @@ def main():
     ms = ms_total / args.steps
     value = units / (ms / 1e3) / 1e9
 
-    # per-phase device times (averaged over the timed steps)
+    # per-phase device times: a second timed loop of the same K steps with an
+    # event on the launching stream between phases (kept out of the loop
+    # above: an event between two dependent launches serialises them)
+    for i in range(args.steps):
+        step(i)
+    torch.cuda.synchronize()
     phase_ms = {p: statistics.mean(ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(args.steps))
                 for j, p in enumerate(PHASES)}
     dominant = max(phase_ms, key=phase_ms.get)
@@ -293,6 +300,7 @@ def main():
                 "peak_source": src, "unit": "GB/s", "frac": round(achieved / hbm, 4),
                 "traffic": traffic_for(dominant, n),
                 "phase_ms": {k: round(v, 4) for k, v in phase_ms.items()},
+                "phase_timing": "second loop of the same K steps, CUDA events between phases",
                 "whole_step_frac": round((n + (n + 1) * cb) / (ms / 1e3) / 1e9 / hbm, 4),
                 "lsu": lsu_roofline(phase_ms, n, local)}
 
@@ -617,6 +625,78 @@ def latency_mode(args, rank, world, local):
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": "(a|b|ab)*, 1 MiB uniform a/b, seed 0", "encoding": kind},
             "graph_replay": graph, "direct_launches": direct}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def ablation_mode(args, rank, world, local):
+    """Speculation ablation (the ME-DFA of Sect. 3.1 against the DFA, as in
+    Sect. 5): the DNA workload and (a|b|ab)* over uniform a/b, each as large
+    as --bytes, parsed with the ME-DFA starts and with forward starts from
+    every DFA state (RE_COMPILE_DFA_STARTS).  Per variant: forward runs per
+    class pair, the autotuned chunk length, the full parse (GB/s, reach time)
+    and the recognizer (forward reach + join).  value = DNA full-parse time
+    with DFA starts / with ME-DFA starts."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2503_06763_gb300 import Regex
+    from paper_2503_06763_gb300.native import PHASES
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.bytes
+    stream = torch.cuda.current_stream(dev)
+    steps = max(args.steps, 5)
+    rows = []
+    for name, pattern, host in (("dna", W.DNA_RE, W.dna_text(n, seed=1)), ("ab", W.AB_RE, W.ab_text(n, seed=0))):
+        text = torch.from_numpy(host).to(dev)
+        for starts in ("me-dfa", "dfa"):
+            rx = Regex(pattern, dfa_starts=starts == "dfa")
+            k = rx.autotune(text)
+            kind, cb, _ = rx.layout(n, "auto")
+            dt = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}[cb]
+            out = torch.empty(n + 1, dtype=dt, device=dev)
+            status = torch.empty(1, dtype=torch.int32, device=dev)
+            ws = torch.empty(rx.workspace_size(n, chunk_len=256), dtype=torch.uint8, device=dev)
+
+            def run(recognize, events=None):
+                rx.parse(text, kind=kind, out=out, status=status, workspace=ws, recognize_only=recognize,
+                         events=events)
+
+            res = {"workload": name, "starts": starts, "fwd_runs_max": rx.info["fwd_slots_max"], "chunk_len": k}
+            for recognize in (False, True):
+                for _ in range(max(args.warmup, 3)):
+                    run(recognize)
+                torch.cuda.synchronize()
+                if int(status.item()) != 0:
+                    raise SystemExit(f"{name}/{starts}: parse status {int(status.item())}")
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(steps):
+                    run(recognize)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1) / steps
+                res["recognizer_GBps" if recognize else "parse_GBps"] = round(n / (ms / 1e3) / 1e9, 1)
+                if not recognize:
+                    res["parse_ms"] = round(ms, 4)
+                    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(PHASES) + 1)]
+                    run(False, ev)
+                    torch.cuda.synchronize()
+                    res["reach_ms"] = round(ev[0].elapsed_time(ev[1]), 4)
+                else:
+                    res["recognizer_ms"] = round(ms, 4)
+            rows.append(res)
+            del rx, out, ws
+            torch.cuda.empty_cache()
+    by = {(r["workload"], r["starts"]): r for r in rows}
+    ratio = by[("dna", "dfa")]["parse_ms"] / by[("dna", "me-dfa")]["parse_ms"]
+    line = {"metric": "speculation ablation: DNA full-parse time, all-DFA-state starts / ME-DFA starts",
+            "value": round(ratio, 3), "unit": "x", "n_gpus": world, "steps": steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"dna-motif and (a|b|ab)*, {n} bytes each, text resident",
+                       "variants": "ME-DFA starts with the last-class filter / forward starts from every DFA state"},
+            "rows": rows}
     if rank == 0:
         print(json.dumps(line))
 

@@ -67,7 +67,7 @@ typedef enum { RE_SLPF_AUTO = 0, RE_SLPF_DENSE = 1, RE_SLPF_DICT = 2 } re_slpf_k
 typedef struct {
     uint32_t max_states;      /* cap on forward + reverse automaton states; 0 = 1<<20 */
     uint32_t max_dict;        /* cap on dictionary pairs considered; 0 = 1<<24 */
-    uint32_t flags;           /* 0 or RE_COMPILE_HOST_ONLY */
+    uint32_t flags;           /* 0, RE_COMPILE_HOST_ONLY and/or RE_COMPILE_DFA_STARTS */
 } re_compile_opts;
 
 /* Build the host tables only (no device upload, no CUDA call): the handle
@@ -76,13 +76,25 @@ typedef struct {
  * without a GPU.                                                            */
 #define RE_COMPILE_HOST_ONLY 1u
 
+/* Ablation of the ME-DFA (Sect. 3.1; Sect. 5 compares it with the DFA): the
+ * forward speculative runs of a chunk start from every state of the classic
+ * forward DFA (those reachable from I), one run per distinct state after the
+ * chunk's first byte, with no last-character filter; the join then finds the
+ * run of the actual input state by an exact (class pair, state) lookup.
+ * Backward runs keep the ME-DFA starts.  Results are identical; only the
+ * speculation cost differs.  re_compile returns RE_E_TOO_MANY_STATES when a
+ * class pair would need more than 32 runs.                                  */
+#define RE_COMPILE_DFA_STARTS 2u
+
 typedef struct {
     re_slpf_kind kind;        /* requested encoding */
     uint32_t chunk_len;       /* text chunk length k in bytes (multiple of 64); 0 = automatic */
     uint32_t flags;           /* RE_PARSE_RECOGNIZE_ONLY or 0 */
     uint32_t n_events;        /* 0, or RE_PHASE_EVENTS */
     void **events;            /* n_events cudaEvent_t created by the caller; recorded on the
-                                 parse stream before the first phase and after each phase */
+                                 parse stream before the first phase and after each phase
+                                 (an event between phases keeps the next kernel from
+                                 starting while the previous one drains) */
 } re_parse_opts;
 
 /* Phase boundaries recorded into re_parse_opts.events: [0] start,

@@ -107,6 +107,10 @@ __device__ __forceinline__ bool any_and(const uint64_t *a, const uint64_t *b, ui
 
 // Slots of the class pair pr that input state S enters (bit j: slot j).
 __device__ __forceinline__ uint32_t slot_hits(const DevTables &t, bool fwd, uint32_t pr, uint32_t S) {
+    if (fwd && t.fSlotOf) {                      // starts from every DFA state: S enters its own slot only
+        const uint32_t j = S < t.nf ? __ldg(t.fSlotOf + (size_t)pr * t.nf + S) : 0xFFu;
+        return j == 0xFFu ? 0u : 1u << j;
+    }
     const uint32_t W = t.W;
     const uint32_t m = __ldg((fwd ? t.fSlotCount : t.bSlotCount) + pr);
     const uint32_t ms = fwd ? t.msf : t.msb;

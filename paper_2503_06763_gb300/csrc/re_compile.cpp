@@ -358,7 +358,10 @@ re_status compile_pattern(const char *pattern, size_t len, const re_compile_opts
                           Compiled &C, std::string &err) {
     uint32_t max_states = (opts && opts->max_states) ? opts->max_states : (1u << 20);
     uint64_t max_dict = (opts && opts->max_dict) ? opts->max_dict : (1ull << 24);
-    if (opts && (opts->flags & ~RE_COMPILE_HOST_ONLY)) { err = "unknown re_compile_opts.flags"; return RE_E_INVALID_ARG; }
+    if (opts && (opts->flags & ~(RE_COMPILE_HOST_ONLY | RE_COMPILE_DFA_STARTS))) {
+        err = "unknown re_compile_opts.flags";
+        return RE_E_INVALID_ARG;
+    }
 
     // ---- parse and number (Sects. 2.1, 2.2)
     std::vector<Node> nodes;
@@ -690,6 +693,32 @@ re_status compile_pattern(const char *pattern, size_t len, const re_compile_opts
             }
             msb = std::max<uint32_t>(msb, (uint32_t)L.size());
         }
+    if (opts && (opts->flags & RE_COMPILE_DFA_STARTS)) {
+        // Ablation: forward runs from every classic DFA state s (ids 1..nfd,
+        // reachable from I), one slot per distinct state after the first
+        // byte; an input state enters exactly the slot of its own successor.
+        const uint32_t nf = ftab.size();
+        C.fSlotOf.assign((size_t)ncls * ncls * nf, 0xFF);
+        msf = 1;
+        for (uint32_t cp = 0; cp < ncls; ++cp)
+            for (uint32_t cf = 0; cf < ncls; ++cf) {
+                const uint32_t pr = cp * ncls + cf;
+                auto &L = fsl[pr];
+                L.clear();
+                std::map<uint32_t, size_t> by_start;
+                for (uint32_t st = 1; st <= nfd; ++st) {
+                    const uint32_t nx = C.fT[(size_t)st * ncls + cf];
+                    if (nx == 0) continue;                 // the text cannot continue from st
+                    auto it = by_start.find(nx);
+                    if (it == by_start.end()) {
+                        it = by_start.emplace(nx, L.size()).first;
+                        L.push_back({nx, std::vector<uint64_t>(W, 0)});   // keys unused: exact lookup
+                    }
+                    if (it->second < 0xFF) C.fSlotOf[(size_t)pr * nf + st] = (uint8_t)it->second;
+                }
+                msf = std::max<uint32_t>(msf, (uint32_t)L.size());
+            }
+    }
     C.msf = msf; C.msb = msb;
     C.fSlotStart.assign((size_t)ncls * ncls * msf, 0);
     C.fSlotMask.assign((size_t)ncls * ncls * msf * W, 0);

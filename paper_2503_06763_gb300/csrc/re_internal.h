@@ -48,6 +48,8 @@ struct DevTables {
     const uint32_t *bSlotStart;  // [ncls][ncls][msb] start state after the chunk's last byte
     const uint64_t *bSlotMask;   // [ncls][ncls][msb][W] segments whose first symbol is a key
     const uint32_t *bSlotCount;  // [ncls][ncls]
+    const uint8_t *fSlotOf;      // RE_COMPILE_DFA_STARTS only: [ncls][ncls][nf] forward slot of an
+                                 // input state (0xFF: none); null for ME-DFA starts
     const uint32_t *pt;          // [nf][nb] dictionary index of B ∩ B̂ (DICT); pairs the
                                  // parse never produces hold 0xFFFFFFFF
     const uint32_t *f2, *b2;     // [n][ncls^2] two-byte tables (mid | end << 16), or null
@@ -74,6 +76,7 @@ struct Compiled {
     uint32_t fHashMask = 0, bHashMask = 0;
     std::vector<uint32_t> fSlotStart, fSlotCount, bSlotStart, bSlotCount;
     std::vector<uint64_t> fSlotMask, bSlotMask;
+    std::vector<uint8_t> fSlotOf;             // RE_COMPILE_DFA_STARTS: [ncls][ncls][nf] slot of a state
     std::vector<uint32_t> pt;                 // [nf][nb]
     std::vector<uint64_t> dict;               // [dict_size][W]
     uint32_t dict_size = 0;

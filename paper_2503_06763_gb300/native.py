@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "RE_OK", 1: "RE_REJECTED", -1: "RE_E_INVALID_ARG", -2: "RE_E_
 KINDS = {"auto": 0, "dense": 1, "dict": 2}
 KIND_NAMES = {0: "auto", 1: "dense", 2: "dict"}
 RE_COMPILE_HOST_ONLY = 1
+RE_COMPILE_DFA_STARTS = 2
 RE_PARSE_RECOGNIZE_ONLY = 1
 
 EXPORTS = ["re_compile", "re_free", "re_get_info", "re_segment_name", "re_dict_copy",
@@ -128,11 +129,15 @@ def check(status: int):
 class Regex:
     """A compiled RE (owns the library handle and its device tables)."""
 
-    def __init__(self, pattern, max_states: int = 0, max_dict: int = 0, host_only: bool = False):
+    def __init__(self, pattern, max_states: int = 0, max_dict: int = 0, host_only: bool = False,
+                 dfa_starts: bool = False):
+        """dfa_starts: forward speculation from every DFA state instead of the
+        ME-DFA starts (RE_COMPILE_DFA_STARTS, an ablation)."""
         lib = load()
         pat = pattern.encode("latin-1") if isinstance(pattern, str) else bytes(pattern)
         self.pattern = pat
-        opts = CompileOpts(max_states, max_dict, RE_COMPILE_HOST_ONLY if host_only else 0)
+        flags = (RE_COMPILE_HOST_ONLY if host_only else 0) | (RE_COMPILE_DFA_STARTS if dfa_starts else 0)
+        opts = CompileOpts(max_states, max_dict, flags)
         h = ctypes.c_void_p()
         check(lib.re_compile(pat, len(pat), ctypes.byref(opts), ctypes.byref(h)))
         self._h = h

@@ -244,3 +244,29 @@ def test_large_automata(lib, pattern):
         host = rng.choice(np.frombuffer(b"ab", dtype=np.uint8), size=n)
         check(rx, pattern, host, kind="dict", chunk_len=0)
         check(rx, pattern, host, kind="dense", chunk_len=256)
+
+
+DFA_START_RES = [W.DNA_RE, W.AB_RE, "(a|b)*a(a|b){3}", "((ab)*c|a(bc)*)*", "(a{0,2}b|a|c)*", "(a|ab|aba)+"]
+
+
+@pytest.mark.parametrize("pattern", DFA_START_RES)
+def test_dfa_starts_give_the_same_slpf(lib, pattern):
+    """Forward speculation from every DFA state (RE_COMPILE_DFA_STARTS, the
+    ablation of the ME-DFA of Sect. 3.1) changes only the speculation: the
+    columns and the recognizer's verdict equal the oracle's."""
+    import paper_2503_06763_gb300 as pkg
+    rx = pkg.Regex(pattern, dfa_starts=True)
+    rng = np.random.Generator(np.random.PCG64(31))
+    if pattern == W.DNA_RE:
+        texts = [W.dna_text(n, seed=5) for n in (1, 5000, 70_001)]
+    elif pattern == W.AB_RE:
+        texts = [W.ab_text(n, seed=6) for n in (1, 5000, 70_001)]
+    else:
+        texts = [rng.choice(np.frombuffer(b"aabbc", dtype=np.uint8), size=n) for n in (1, 777, 20_000)]
+    for host in texts:
+        for chunk_len in (64, 192, 0):
+            check(rx, pattern, host, chunk_len=chunk_len)
+            t = torch.from_numpy(np.array(host, dtype=np.uint8, copy=True)).cuda()
+            _, st, _ = rx.parse(t, chunk_len=chunk_len, recognize_only=True)
+            torch.cuda.synchronize()
+            assert int(st.item()) == (0 if serial.accepted(oracle_cols(pattern, host.tobytes())) else 1)

@@ -84,6 +84,46 @@ def test_layout_and_errors(native):
     assert e.value.status == -4
 
 
+def oracle_dfa_start_count(pattern):
+    """Most forward runs for one first byte when every classic DFA state is a
+    start: distinct non-empty successors of the states reachable from I,
+    computed with the oracle's NFA image (Sect. 3.1), one byte at a time."""
+    from oracle.serial import nfa_image
+    c = compile_re(pattern)
+    alphabet = sorted(set().union(*c.classes.values()))
+    start = frozenset(c.initial)
+    seen, todo = {start}, [start]
+    while todo:
+        s = todo.pop()
+        for b in alphabet:
+            t = nfa_image(c, s, b)
+            if t and t not in seen:
+                seen.add(t)
+                todo.append(t)
+    return max(len({nfa_image(c, s, b) for s in seen} - {frozenset()}) for b in alphabet)
+
+
+@pytest.mark.parametrize("pattern", ["([ACGT]|ATG([ACGT][ACGT][ACGT])*(TAA|TAG|TGA))*", "(a|b|ab)*",
+                                     "(a|b)*a(a|b){3}", "((ab)*c|a(bc)*)*", "(a{0,2}b|a|c)*", "(a|ab|aba)+"])
+def test_dfa_starts_slot_counts(native, pattern):
+    """RE_COMPILE_DFA_STARTS: the forward slots per class pair are the
+    distinct successors of all DFA states, as the oracle counts them."""
+    r = native.Regex(pattern, host_only=True, dfa_starts=True)
+    assert r.info["fwd_slots_max"] == oracle_dfa_start_count(pattern)
+    assert r.info["bwd_slots_max"] == native.Regex(pattern, host_only=True).info["bwd_slots_max"]
+
+
+def test_dfa_starts_refused_past_32_runs(native):
+    """The log RE needs more than 32 forward runs from all DFA states: the
+    compile is refused with RE_E_TOO_MANY_STATES (its ME-DFA starts fit)."""
+    import workloads as W
+    assert oracle_dfa_start_count(W.LOG_RE) > 32
+    assert native.Regex(W.LOG_RE, host_only=True).info["fwd_slots_max"] <= 32
+    with pytest.raises(native.ReError) as e:
+        native.Regex(W.LOG_RE, host_only=True, dfa_starts=True)
+    assert e.value.status == -4
+
+
 def test_ek_family_state_counts(native):
     for k in range(1, 8):
         r = native.Regex("(a|b)*a(a|b){%d}" % k, host_only=True)
