@@ -427,9 +427,9 @@ constexpr uint32_t kSplitThreads = 256;
 
 // One parse.  SPLIT: warp pairs take 32-chunk tiles, the even warp walking
 // the chunks forward and the odd one backward (each with a one-direction TMA
-// ring), which doubles the warps in flight for the same shared memory.
-// Otherwise (recognizer mode: forward only) every warp walks its tile in the
-// directions needed.
+// ring), which doubles the warps in flight for the same shared memory; in
+// recognizer mode every warp takes a tile of its own, forward.  Without SPLIT
+// every warp walks its tile in both directions (two tiles per ring stage).
 template <int TM, int MS, bool SPLIT>
 __global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
     reach_kernel(const __grid_constant__ Params p, const __grid_constant__ CUtensorMap map) {
@@ -454,8 +454,9 @@ __global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
     pdl_wait();                                               // the join flags are set by the kernel before
     pdl_trigger();
     const uint64_t gw = (uint64_t)blockIdx.x * wpb + warp, nw = (uint64_t)gridDim.x * wpb;
-    const uint64_t t0 = SPLIT ? gw >> 1 : gw, tstep = SPLIT ? nw >> 1 : nw;
-    const bool backward_warp = SPLIT && (gw & 1);
+    const bool pairs = SPLIT && !p.recognize;                // recognizer: every warp walks its own tile forward
+    const uint64_t t0 = pairs ? gw >> 1 : gw, tstep = pairs ? nw >> 1 : nw;
+    const bool backward_warp = pairs && (gw & 1);
     for (uint64_t t = t0; t * 32 < p.c; t += tstep) {
         const uint32_t i = (uint32_t)(t * 32) + lane;
         const bool tma = p.text_tma && t * 32 + 32 <= p.c_full;
@@ -563,16 +564,17 @@ void launch_split(const Params &p, const CUtensorMap &map, cudaStream_t s, int s
     allow_smem(reach_kernel<TM, MS, SPLIT>, &attr_done);
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_kernel<TM, MS, SPLIT>, threads, smem);
-    const uint64_t warps = ((uint64_t)p.c + 31) / 32 * (SPLIT ? 2 : 1);
+    const uint64_t warps = ((uint64_t)p.c + 31) / 32 * (SPLIT && !p.recognize ? 2 : 1);
     const uint64_t want = (warps + threads / 32 - 1) / (threads / 32);
     const uint64_t blocks = std::min<uint64_t>(want, (uint64_t)std::max(per_sm, 1) * sm_count);
     launch_dependent(reach_kernel<TM, MS, SPLIT>, (uint32_t)std::max<uint64_t>(blocks, 1), threads, smem, s, p, map);
 }
 
+// A parse: warp pairs per 32-chunk tile; the recognizer: one forward warp per
+// tile (the same kernel, so the same register budget and ring depth).
 template <int TM, int MS>
 void launch_one(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
-    if (p.recognize) launch_split<TM, MS, false>(p, map, s, sm_count);
-    else launch_split<TM, MS, true>(p, map, s, sm_count);
+    launch_split<TM, MS, true>(p, map, s, sm_count);
 }
 
 template <int TM>
