@@ -383,6 +383,46 @@ def main():
         dist.destroy_process_group()
 
 
+_ORACLE_RES = {}
+
+
+def _oracle_parse_job(job):
+    """One text through the serial oracle in a pool worker (REs compiled
+    once per worker).  Returns (bytes, parse seconds)."""
+    pattern, text = job
+    from oracle import serial
+    from oracle.re_front import compile_re
+    c = _ORACLE_RES.get(pattern)
+    if c is None:
+        c = _ORACLE_RES[pattern] = compile_re(pattern)
+    t0 = time.perf_counter()
+    serial.parse(c, text)
+    return len(text), time.perf_counter() - t0
+
+
+def batch_cpu_baseline(patterns, hosts, budget: int = 256 << 20):
+    """The oracle on all host cores: the batch's first texts (about `budget`
+    bytes) parsed one per task by a process pool started with spawn (safe
+    after CUDA is initialised)."""
+    import multiprocessing as mp
+    jobs, tot = [], 0
+    for pat, h in zip(patterns, hosts):
+        if tot >= budget:
+            break
+        jobs.append((pat, h.tobytes()))
+        tot += len(h)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        done = pool.map(_oracle_parse_job, jobs, chunksize=1)
+    wall = time.perf_counter() - t0
+    nbytes, parse_s = sum(d[0] for d in done), sum(d[1] for d in done)
+    return {"value": round(nbytes / wall / 1e9, 6), "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {len(jobs)} texts of the batch ({nbytes >> 20} MiB), one per task on a spawn pool of "
+                      f"{cores} processes, {wall:.1f} s wall including each worker's RE compiles; "
+                      f"parsing alone {nbytes / parse_s / 1e6:.1f} MB/s per core, host {os.uname().machine}"}
+
+
 def batch_res(seed0: int = 3000, count: int = 8, lo: int = 10, hi: int = 200):
     """count random REs (lo..hi positions, alphabet 4..64 each); an RE whose
     tables exceed the library's caps is replaced by the next seed."""
@@ -469,7 +509,10 @@ def batch_mode(args, rank, world, local):
         "roofline": {"bound": "hbm", "achieved": round((total + out_bytes) / (ms_batch / 1e3) / 1e9, 1),
                      "peak": hbm, "peak_source": src, "unit": "GB/s",
                      "frac": round((total + out_bytes) / (ms_batch / 1e3) / 1e9 / hbm, 4)},
+        "cpu_baseline": None,
     }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = batch_cpu_baseline([res[w][0] for w in which], hosts)
     if rank == 0:
         print(json.dumps(line))
 
