@@ -304,8 +304,14 @@ def main():
                 "whole_step_frac": round((n + (n + 1) * cb) / (ms / 1e3) / 1e9 / hbm, 4),
                 "lsu": lsu_roofline(phase_ms, n, local)}
 
-    # recognizer mode (forward reach + join only, Sect. 4.2), same text
-    rec_ws = torch.empty(rx.workspace_size(n, args.chunk_len, 1), dtype=torch.uint8, device=dev)
+    # recognizer mode (forward reach + join only, Sect. 4.2), same text, with
+    # its own autotuned chunk length (one forward warp per 32-chunk tile, so it
+    # prefers more, shorter chunks than the parse)
+    rec_k = args.chunk_len
+    if args.chunk_len == 0:
+        rec_k = rx.autotune(text, recognize_only=True)
+        torch.cuda.empty_cache()
+    rec_ws = torch.empty(rx.workspace_size(n, rec_k, 1), dtype=torch.uint8, device=dev)
     for _ in range(3):
         rx.parse(text, chunk_len=args.chunk_len, status=status, workspace=rec_ws, recognize_only=True)
     r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -315,7 +321,7 @@ def main():
     r1.record(stream)
     torch.cuda.synchronize()
     recognizer = {"value": round(n / (r0.elapsed_time(r1) / args.steps / 1e3) / 1e9, 3), "unit": "GB/s",
-                  "status": int(status.item())}
+                  "status": int(status.item()), "chunk_len": rec_k}
     del rec_ws
 
     # end to end through re_parse_host: pinned host text in, columns and status

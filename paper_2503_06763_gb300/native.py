@@ -289,9 +289,9 @@ class Regex:
             total = int(count.item())
         return pairs[:min(total, cap)], total
 
-    def autotune(self, text, kind: str = "auto", workspace=None, stream=None) -> int:
+    def autotune(self, text, kind: str = "auto", workspace=None, stream=None, recognize_only: bool = False) -> int:
         """re_autotune on a CUDA uint8 tensor: returns the chunk length chosen
-        (and kept for texts of this length bucket)."""
+        (and kept for texts of this length bucket, parse or recognizer mode)."""
         import torch
         n = text.numel()
         kname, cb, _ = self.layout(n, kind)
@@ -304,7 +304,7 @@ class Regex:
                 workspace = torch.empty(self.workspace_size(n, chunk_len=256), dtype=torch.uint8,
                                         device=text.device)
         slpf = Slpf(KINDS[kname], cb, 0, out.data_ptr(), out.numel() * out.element_size(), status.data_ptr())
-        opts = ParseOpts(KINDS[kname], 0, 0, 0, None)
+        opts = ParseOpts(KINDS[kname], 0, RE_PARSE_RECOGNIZE_ONLY if recognize_only else 0, 0, None)
         k = ctypes.c_uint32()
         check(load().re_autotune(self._h, text.data_ptr(), n, ctypes.byref(slpf), workspace.data_ptr(),
                                  workspace.numel(), ctypes.c_void_p(s.cuda_stream), ctypes.byref(opts),

@@ -43,3 +43,25 @@ def test_autotune_keeps_choice_and_result(lib):
     cols2, st2, _ = rx.parse(t, workspace=small)
     torch.cuda.synchronize()
     assert int(st2.item()) == 0 and torch.equal(cols2, cols)
+
+
+def test_recognizer_has_its_own_choice(lib):
+    """The recognizer's chunk length is tuned and kept apart from the parse's
+    (the key holds the mode), and recognizing with it gives the oracle's verdict."""
+    Regex = lib
+    n = 3 << 20
+    host = W.dna_text(n, seed=42)
+    t = torch.from_numpy(host).cuda()
+    rx = Regex(W.DNA_RE)
+    k_parse = rx.autotune(t)
+    k_rec = rx.autotune(t, recognize_only=True)
+    assert k_rec >= 256 and k_rec % 64 == 0
+    assert rx.workspace_size(n) == rx.workspace_size(n, chunk_len=k_parse)
+    assert rx.workspace_size(n, flags=1) == rx.workspace_size(n, chunk_len=k_rec, flags=1)
+    want = serial.accepted(serial.parse(compile_re(W.DNA_RE), host))
+    for h in (host, np.concatenate([host[:1000], np.frombuffer(b"X", dtype=np.uint8), host[1001:]])):
+        tt = torch.from_numpy(np.ascontiguousarray(h)).cuda()
+        _, st, _ = rx.parse(tt, recognize_only=True)
+        torch.cuda.synchronize()
+        expect = want if h is host else serial.accepted(serial.parse(compile_re(W.DNA_RE), h.tobytes()))
+        assert int(st.item()) == (0 if expect else 1)
