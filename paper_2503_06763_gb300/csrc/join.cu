@@ -207,7 +207,9 @@ __device__ void verify_at(const Params &p, uint32_t i) {
 __device__ void status_of(const Params &p) {
     const DevTables &t = p.t;
     int32_t st = RE_OK;
-    if (p.w.flags[FLAG_FFAIL] < (int32_t)p.c || (!p.recognize && p.w.flags[FLAG_BFAIL] < (int32_t)p.c)) {
+    // flags are updated by atomics of the verify blocks: read them from L2
+    const int32_t ffail = __ldcg(&p.w.flags[FLAG_FFAIL]), bfail = __ldcg(&p.w.flags[FLAG_BFAIL]);
+    if (ffail < (int32_t)p.c || (!p.recognize && bfail < (int32_t)p.c)) {
         st = RE_REJECTED;
     } else if (p.recognize) {
         const uint32_t jc = p.w.FJ[p.c];
@@ -216,21 +218,27 @@ __device__ void status_of(const Params &p) {
         const uint32_t b0 = p.w.BJ[0];
         if (!(b0 && any_and(t.fBits + (size_t)t.fI * t.W, t.bBits + (size_t)b0 * t.W, t.W))) st = RE_REJECTED;
     }
-    if (p.w.flags[FLAG_INTERNAL]) st = RE_E_INTERNAL;
+    if (__ldcg(&p.w.flags[FLAG_INTERNAL])) st = RE_E_INTERNAL;
     *p.status = st;
 }
 
+// Verify every chunk; the last block to finish then sets the status word,
+// once every block's writes are visible (each block fences its writes before
+// it takes a ticket; the last ticket holder fences again before reading).
 __global__ void join_verify_kernel(const __grid_constant__ Params p) {
     pdl_wait();
     pdl_trigger();
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < p.c) verify_at(p, i);
-}
-
-__global__ void status_kernel(const __grid_constant__ Params p) {
-    pdl_wait();
-    pdl_trigger();
-    status_of(p);
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&p.w.flags[FLAG_DONE], 1) == (int32_t)gridDim.x - 1;
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        status_of(p);
+    }
 }
 
 __global__ void flags_init_kernel(const __grid_constant__ Params p) {
@@ -280,7 +288,6 @@ void launch_join(const Params &p, cudaStream_t s) {
     launch_dependent(join_classify_kernel, blocks, kBlockThreads, 0, s, p);
     launch_dependent(join_chain_kernel, blocks, kBlockThreads, 0, s, p);
     launch_dependent(join_verify_kernel, blocks, kBlockThreads, 0, s, p);
-    launch_dependent(status_kernel, 1, 1, 0, s, p);
 }
 
 void launch_flags_init(const Params &p, cudaStream_t s) { flags_init_kernel<<<1, 32, 0, s>>>(p); }

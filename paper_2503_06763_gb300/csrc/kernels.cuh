@@ -28,7 +28,7 @@ constexpr uint32_t kFixupThreads = 256;     // fix-up blocks: one thread per chu
 constexpr uint32_t kRecBounds = 32;   // boundaries recorded per chunk and direction before runs meet
 constexpr uint32_t kRecEntries = 96;  // (state, slot set) entries recorded per chunk and direction
 
-enum Flag { FLAG_FFAIL = 0, FLAG_BFAIL = 1, FLAG_INTERNAL = 2, FLAG_COUNT = 4 };
+enum Flag { FLAG_FFAIL = 0, FLAG_BFAIL = 1, FLAG_INTERNAL = 2, FLAG_DONE = 3, FLAG_COUNT = 4 };
 
 struct Work {                       // device workspace, carved from the caller's buffer
     uint32_t *Rf, *Rb;              // [c][msf], [c][msb] end state of each speculation slot
