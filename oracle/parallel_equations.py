@@ -36,23 +36,12 @@ def run(c: Compiled, S, chunk: bytes, reverse: bool = False):
     return S
 
 
-def parse_parallel(c: Compiled, text: bytes, k: int):
-    """Clean SLPF by Eqs. reacher, joiner, builder, merger.  Returns
-    (columns, trace) where trace holds R, R̂, J, Ĵ, B, B̂ for inspection."""
-    y = split(text, k)
-    cnum = len(y)
-    ell = c.ell
-    # reach (FW and BW) from every ME-DFA initial state S_j = {j}
-    R = [None] + [[run(c, frozenset([j]), y[i - 1]) for j in range(ell)] for i in range(1, cnum + 1)]
+def backward_join(c: Compiled, y):
+    """Eq. reacher (backward) from every reverse ME-DFA singleton and
+    Eq. joiner: returns (R̂, Ĵ) with Ĵ_{c+1} = F."""
+    cnum, ell = len(y), c.ell
     Rh = [None] + [[run(c, frozenset([j]), y[i - 1], reverse=True) for j in range(ell)]
                    for i in range(1, cnum + 1)]
-    # join
-    J = [frozenset(c.initial)]
-    for i in range(1, cnum + 1):
-        acc = set()
-        for j in J[i - 1]:
-            acc |= R[i][j]
-        J.append(frozenset(acc))
     Jh = [None] * (cnum + 2)
     Jh[cnum + 1] = frozenset(c.final)
     for i in range(cnum, 0, -1):
@@ -60,7 +49,13 @@ def parse_parallel(c: Compiled, text: bytes, k: int):
         for j in Jh[i + 1]:
             acc |= Rh[i][j]
         Jh[i] = frozenset(acc)
-    # build (FW, BW) and merge
+    return Rh, Jh
+
+
+def build_merge_compose(c: Compiled, y, J, Jh):
+    """Eq. builder (forward from J_{i-1}, backward from Ĵ_{i+1}), Eq. merger
+    and compose: the clean columns C_0 .. C_n, and B, B̂."""
+    cnum = len(y)
     B, Bh, M = [None], [None], [None]
     for i in range(1, cnum + 1):
         yi = y[i - 1]
@@ -76,10 +71,47 @@ def parse_parallel(c: Compiled, text: bytes, k: int):
         B.append(b)
         Bh.append(bh)
         M.append([None] + [b[t] & bh[t] for t in range(1, kk + 1)])
-    # compose
     cols = [J[0] & Jh[1]] if cnum else [frozenset(c.initial) & frozenset(c.final)]
     for i in range(1, cnum + 1):
         cols.extend(M[i][1:])
+    return cols, B, Bh
+
+
+def parse_parallel(c: Compiled, text: bytes, k: int):
+    """Clean SLPF by Eqs. reacher, joiner, builder, merger.  Returns
+    (columns, trace) where trace holds R, R̂, J, Ĵ, B, B̂ for inspection."""
+    y = split(text, k)
+    cnum = len(y)
+    ell = c.ell
+    # reach (FW) from every ME-DFA initial state S_j = {j}, and join
+    R = [None] + [[run(c, frozenset([j]), y[i - 1]) for j in range(ell)] for i in range(1, cnum + 1)]
+    J = [frozenset(c.initial)]
+    for i in range(1, cnum + 1):
+        acc = set()
+        for j in J[i - 1]:
+            acc |= R[i][j]
+        J.append(frozenset(acc))
+    Rh, Jh = backward_join(c, y)
+    cols, B, Bh = build_merge_compose(c, y, J, Jh)
+    return cols, dict(R=R, Rh=Rh, J=J, Jh=Jh, B=B, Bh=Bh)
+
+
+def parse_parallel_dfa_starts(c: Compiled, text: bytes, k: int):
+    """The same equations with the forward reach started from every DFA
+    state instead of every ME-DFA singleton: the alternative the ME-DFA of
+    Sect. 3.1 improves on (Sect. 5 measures both).  R_{i,T} = delta*(T, y_i)
+    for every DFA state T; the join takes the run of the input state itself,
+    J_i = R_{i,J_{i-1}} (J_{i-1} is a DFA state, or the empty set when the
+    text cannot continue).  The backward side keeps the ME-DFA starts."""
+    y = split(text, k)
+    cnum = len(y)
+    starts = dfa_states(c)
+    R = [None] + [{T: run(c, T, y[i - 1]) for T in starts} for i in range(1, cnum + 1)]
+    J = [frozenset(c.initial)]
+    for i in range(1, cnum + 1):
+        J.append(R[i].get(J[i - 1], frozenset()))
+    Rh, Jh = backward_join(c, y)
+    cols, B, Bh = build_merge_compose(c, y, J, Jh)
     return cols, dict(R=R, Rh=Rh, J=J, Jh=Jh, B=B, Bh=Bh)
 
 
