@@ -165,6 +165,16 @@ def test_e4_epsilon_segment(golden):
     assert [sorted(c.names()[q] for q in s) for s in cols] == g["slpf"]
 
 
+def test_bounded_repetition_printed_example(golden):
+    """App. A's a^3: one numbered pair around three distinct terminal copies."""
+    from oracle.re_front import sym_name
+    g = golden["rep3"]
+    c = compile_re(g["pattern"])
+    assert sorted(n for n in c.names() if n.split()[-1].startswith("t")) == g["terminal_segments"]
+    lsts = list(trees.lsts(c, g["text"].encode()))
+    assert len(lsts) == 1 and [sym_name(s) for s in lsts[0]] == g["lst"]
+
+
 # --------------------------------------------------------------------------- e(k)
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
 def test_ek_dfa_state_count(golden, k):
