@@ -16,7 +16,7 @@ Paper passages followed (arXiv 2503.06763):
   * Character sets, wildcard, escapes, ε symbols, extra parentheses, bounded
     repetition e{h}, e{h,k}, e{h,}: App. A.
 
-Readings where the paper is silent (all listed in the design doc):
+Readings where the paper is silent or ambiguous:
   * A parenthesised group creates a numbered node only through the operator it
     encloses; ``(a)`` is just ``a`` and ``((ab))`` is one node; a group nested
     in an operand list of the same operator stays a separate node (extra
@@ -25,7 +25,10 @@ Readings where the paper is silent (all listed in the design doc):
   * ``e{k}`` is one numbered node whose k children are fresh copies of e
     numbered progressively (App. A, "Bounded repetition"; Ex. 5).  ``e{h,k}``
     and ``e{h,}`` add the optional (resp. starred) further iterations, each
-    with its own copy; see ``expand_repetitions``.
+    with its own copy; see ``expand_repetitions``.  With h = 0 there is no
+    mandatory copy and the optional (resp. starred) iterations are the node
+    itself, so ``e{0,1}`` is ``e?`` and ``e{0,}`` is ``e*``: App. A states the
+    identity e? = e{0,1}.
   * ``.`` matches every byte but newline (App. A, "wildcard").
   * The initial symbol test of MetaPrefix (``s = 1(``) is read as "s is the
     first symbol of every LST", which is ``1(`` whenever the root is an
@@ -219,6 +222,9 @@ def expand_repetitions(node: Node) -> Node:
       only after the one before it: (e (e (... e?)?)?)?.  A tree with j
       iterations therefore uses copies 1 .. j, in order.
     * e{h,}: the h copies, then copy h+1 under a star.
+    * h = 0: the node is the outermost optional (resp. the star) itself,
+      which makes e{0,1} the optional e? = (e|ε) and e{0,} the star e*
+      (App. A: e? = e{0,1}).
     """
     kids = [expand_repetitions(ch) for ch in node.children]
     if node.kind == "rep":
@@ -231,6 +237,8 @@ def expand_repetitions(node: Node) -> Node:
             for _ in range(hi - h - 1):                               # copies k-1 .. h+1 around it
                 tail = Node("alt", [Node("cat", [_copy(body), tail]), Node("eps")])
             reps.append(tail)
+        if h == 0:
+            return reps[0]
         return Node("rep", reps, count=h, hi=hi)
     return Node(node.kind, kids, node.chars, node.count, hi=node.hi)
 

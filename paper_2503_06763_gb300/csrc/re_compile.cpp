@@ -215,7 +215,9 @@ int clone(std::vector<Node> &nodes, int id) {
 // its body, so every iteration has its own numbered symbols.  e{h}: h copies;
 // e{h,k}: then copies h+1 .. k as nested optionals (e (e (... e?)?)?)?, so a
 // tree with j iterations uses copies 1 .. j in order; e{h,}: then copy h+1
-// under a star.
+// under a star.  With h = 0 the node is the outermost optional (or the star)
+// itself, so e{0,1} is the optional e? = (e|ε) and e{0,} the star e*, as App. A
+// states for the optional (e? = e{0,1}).
 void expand(std::vector<Node> &nodes, int id) {
     for (size_t i = 0; i < nodes[id].kids.size(); ++i) expand(nodes, nodes[id].kids[i]);
     if (nodes[id].kind != Node::REP) return;
@@ -247,6 +249,11 @@ void expand(std::vector<Node> &nodes, int id) {
             tail = add(Node::ALT, {cat, add(Node::EPS, {})});
         }
         reps.push_back(tail);
+    }
+    if (h == 0) {                                   // the optional / starred iterations are the node
+        const Node only = nodes[reps[0]];
+        nodes[id] = only;
+        return;
     }
     nodes[id].kids = reps;
 }
