@@ -421,7 +421,16 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     // Stage the encoder table (DICT pair table or DENSE state bitsets) in shared
     // memory when the merge's whole footprint (tables, stage, output tiles and
     // the table) still fits; otherwise it is read from global memory.
-    if (!recognize && tab + merge_extra_smem(p) + encoder_bytes(t, kind, cb) <= kSmemMergeMax) p.enc_in_smem = 1;
+    // One-byte tables: build & merge over the classic-DFA rows and pairs, the
+    // first half of each builder in registers, when that layout fits.
+    if (!recognize && p.tmode == TM_SMEM) {
+        Params q = p;
+        q.merge_reg = 1;
+        q.enc_in_smem = 1;
+        if (merge_smem_bytes(q) <= kSmemMergeMax) { p.merge_reg = 1; p.enc_in_smem = 1; }
+    }
+    if (!recognize && !p.merge_reg && tab + merge_extra_smem(p) + encoder_bytes(t, kind, cb) <= kSmemMergeMax)
+        p.enc_in_smem = 1;
     alignas(64) CUtensorMap text_map;
     std::memset(&text_map, 0, sizeof(text_map));
     p.c_full = (uint32_t)(len / k);

@@ -56,6 +56,9 @@ struct Params {
     uint32_t recognize;             // forward reach + join only
     uint32_t tmode;                 // TM_GLOBAL / TM_SMEM / TM_PAIR (see Tabs)
     uint32_t enc_in_smem;           // encoder table (DICT pair table, DENSE bitsets) in shared memory
+    uint32_t merge_reg;             // one-byte tables: build & merge stages the classic-DFA rows and the
+                                    // encoder over classic-DFA state pairs only, and keeps the first
+                                    // half of each builder's states in registers
     uint32_t out_tma;               // full column groups leave through TMA tensor stores
     uint32_t text_tma;              // reach reads full chunks through TMA tiles
     uint32_t c_full;                // chunks of exactly k bytes (rows of the text tensor map)
@@ -358,6 +361,17 @@ inline void allow_smem(K kernel, uint64_t *done, int bytes = 200 * 1024) {
 }
 
 size_t merge_extra_smem(const Params &p);
+size_t merge_smem_bytes(const Params &p);
+// The classic-DFA part of the tables: forward states 0 .. nfd (the DFA states
+// reachable from I get the first ids, and transitions from them stay among
+// them), reverse states 0 .. nbd.  Build & merge only meets these states: its
+// checkpoints are exact forward / backward states of the text.
+__host__ __device__ inline DevTables dfa_tables(const DevTables &t) {
+    DevTables c = t;
+    c.nf = t.nfd + 1;
+    c.nb = t.nbd + 1;
+    return c;
+}
 bool launch_reach(const Params &p, const CUtensorMap &text_map, cudaStream_t s, uint32_t ms, int sm_count);
 void launch_join(const Params &p, cudaStream_t s);
 void launch_fixup(const Params &p, cudaStream_t s, int sm_count);

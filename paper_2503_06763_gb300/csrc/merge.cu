@@ -541,15 +541,71 @@ __device__ __forceinline__ void group_full_pair(const Params &p, const Tabs &T, 
     }
 }
 
+// Full group with one-byte tables over the classic-DFA rows: as group_full,
+// but the first half of each direction stays in registers, two 16-bit states
+// per word (fully unrolled, so every index is static), instead of a staged
+// column per thread in shared memory.
+template <int E, bool TMA>
+__device__ __forceinline__ void group_full_reg(const Params &p, const Tabs &T, const Enc &e, uint64_t g, bool &bad,
+                                               const Sink<TMA, bytes_of(E)> &out) {
+    const uint64_t pos = g * 64;
+    uint32_t cw[16];                                           // byte classes, four per register
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p.x + pos) + q);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            cw[4 * q + j] = clsof<TM_SMEM>(T, w[j] & 0xFF) | (clsof<TM_SMEM>(T, (w[j] >> 8) & 0xFF) << 8) |
+                            (clsof<TM_SMEM>(T, (w[j] >> 16) & 0xFF) << 16) | (clsof<TM_SMEM>(T, w[j] >> 24) << 24);
+    }
+    auto cls_at = [&](int u) -> uint32_t { return (cw[u >> 2] >> (8 * (u & 3))) & 0xFFu; };
+    uint32_t f = p.w.FC[g];                                    // B_0
+    uint32_t b = p.w.BC[g];                                    // B̂_64
+    if (f == kUnknown || b == kUnknown || f > p.t.nfd || b > p.t.nbd) { bad = true; f = 0; b = 0; }
+    uint32_t rF[16], rB[16];                                   // B_0..B_31; B̂_32..B̂_63 (two per word)
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        if (i > 0) f = fnext<TM_SMEM>(T, f, cls_at(i - 1));   // B_i
+        if (i & 1) rF[i >> 1] |= f << 16; else rF[i >> 1] = f;
+        b = bnext<TM_SMEM>(T, b, cls_at(63 - i));             // B̂_{63-i}
+        const int j = 31 - i;                                  // B̂_{32+j}; j runs down, odd j first
+        if (j & 1) rB[j >> 1] = b << 16; else rB[j >> 1] |= b;
+    }
+    constexpr int CB = bytes_of(E);
+    constexpr int CPV = 16 / CB;                               // columns per 16-byte vector
+    uint32_t wf[4] = {0, 0, 0, 0}, wb[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int i = 32; i < 64; ++i) {
+        f = fnext<TM_SMEM>(T, f, cls_at(i - 1));              // B_i
+        b = bnext<TM_SMEM>(T, b, cls_at(63 - i));             // B̂_{63-i}
+        const int jb = i - 32, jf = 63 - i;
+        const uint32_t hb = (rB[jb >> 1] >> (16 * (jb & 1))) & 0xFFFFu;   // B̂_i
+        const uint32_t hf = (rF[jf >> 1] >> (16 * (jf & 1))) & 0xFFFFu;   // B_{63-i}
+        const uint64_t vf = enc_col<TM_SMEM, E>(e, f, hb, bad);           // column i
+        const uint64_t vb = enc_col<TM_SMEM, E>(e, hf, b, bad);           // column 63-i
+        put_col<CB>(wf, i % CPV, vf);
+        if (i % CPV == CPV - 1) {
+            out.put(i / CPV, make_uint4(wf[0], wf[1], wf[2], wf[3]));
+            wf[0] = wf[1] = wf[2] = wf[3] = 0;
+        }
+        put_col<CB>(wb, (63 - i) % CPV, vb);
+        if ((63 - i) % CPV == 0) {
+            out.put((63 - i) / CPV, make_uint4(wb[0], wb[1], wb[2], wb[3]));
+            wb[0] = wb[1] = wb[2] = wb[3] = 0;
+        }
+    }
+}
+
 // Last group (fewer than 64 columns or no byte after it): plain loops.
-template <int TM, int E>
+template <int TM, int E, bool REG = false>
 __device__ void group_tail(const Params &p, const Tabs &T, const Enc &e, uint64_t g, bool &bad) {
     const uint64_t pos = g * 64;
     const uint64_t nleft = p.n + 1 - pos;
     const uint32_t ncol = nleft < 64 ? (uint32_t)nleft : 64u;
     uint32_t F[64], B[64];
     uint32_t f = p.w.FC[g], b = p.w.BC[g];
-    if (f == kUnknown || b == kUnknown) { bad = true; f = 0; b = 0; }
+    if (f == kUnknown || b == kUnknown || (REG && (f > p.t.nfd || b > p.t.nbd))) { bad = true; f = 0; b = 0; }
     F[0] = f;
     for (uint32_t u = 1; u < ncol; ++u) F[u] = fnext<TM>(T, F[u - 1], clsof<TM>(T, __ldg(p.x + pos + u - 1)));
     if (pos + 64 <= p.n) b = bnext<TM>(T, b, clsof<TM>(T, __ldg(p.x + pos + 63)));
@@ -563,27 +619,36 @@ __device__ void group_tail(const Params &p, const Tabs &T, const Enc &e, uint64_
 
 // Shared-memory set-up of a merge block: staged tables, the per-thread state
 // stage (one-byte tables) and the encoder (pair table or segment bitsets).
-template <int TM, int E, typename St>
-__device__ void merge_setup(const DevTables &t, uint32_t enc_in_smem, uint8_t *base, Tabs &T, St *&stage, Enc &e) {
+// With REG (one-byte tables, merge_reg) only the classic-DFA rows are staged
+// and the encoder covers classic-DFA state pairs only (row stride nbd + 1);
+// there is no state stage.
+template <int TM, int E, bool REG, typename St>
+__device__ void merge_setup(const DevTables &t0, uint32_t enc_in_smem, uint8_t *base, Tabs &T, St *&stage, Enc &e) {
+    const DevTables t = REG ? dfa_tables(t0) : t0;
     uint8_t *rest = stage_tables<TM>(t, base, T);
     stage = reinterpret_cast<St *>(rest);                     // [2][32][kBlockThreads] (one-byte tables)
-    if (TM != TM_PAIR) rest += (2 * 32 * kBlockThreads * sizeof(St) + 15) & ~(size_t)15;
+    if (TM != TM_PAIR && !REG) rest += (2 * 32 * kBlockThreads * sizeof(St) + 15) & ~(size_t)15;
     e = Enc{};
     e.nb = t.nb;
     if (E == ENC_X2 || E == ENC_X4) {
         if (enc_in_smem) {
             const size_t cnt = (size_t)t.nf * t.nb;
+            const uint32_t nbs = t0.nb;                       // row stride of the device pair table
+            auto src = [&](size_t i) -> uint32_t {
+                return REG ? __ldg(t.pt + (i / t.nb) * nbs + i % t.nb) : __ldg(t.pt + i);
+            };
             if (E == ENC_X2) {
                 uint16_t *pt = reinterpret_cast<uint16_t *>(rest);
-                for (size_t i = threadIdx.x; i < cnt; i += blockDim.x) pt[i] = (uint16_t)__ldg(t.pt + i);
+                for (size_t i = threadIdx.x; i < cnt; i += blockDim.x) pt[i] = (uint16_t)src(i);
                 e.pt16 = pt;
             } else {
                 uint32_t *pt = reinterpret_cast<uint32_t *>(rest);
-                for (size_t i = threadIdx.x; i < cnt; i += blockDim.x) pt[i] = __ldg(t.pt + i);
+                for (size_t i = threadIdx.x; i < cnt; i += blockDim.x) pt[i] = src(i);
                 e.pt32 = pt;
             }
         } else {
             e.pt32 = t.pt;
+            e.nb = t0.nb;
         }
     } else if (enc_in_smem) {                                 // DENSE: segment bitsets of the states
         uint64_t *fb = reinterpret_cast<uint64_t *>(rest);
@@ -598,7 +663,7 @@ __device__ void merge_setup(const DevTables &t, uint32_t enc_in_smem, uint8_t *b
 }
 
 // Columns of group g of one text (this lane's group of its warp's tile).
-template <int TM, int E, bool TMA, typename St>
+template <int TM, int E, bool TMA, bool REG, typename St>
 __device__ __forceinline__ void merge_group(const Params &p, const Tabs &T, const Enc &e, St *stage, uint64_t g,
                                             bool ok, bool &bad, const Sink<TMA, bytes_of(E)> &out) {
     constexpr uint32_t ROWB = 64 * bytes_of(E);
@@ -616,11 +681,13 @@ __device__ __forceinline__ void merge_group(const Params &p, const Tabs &T, cons
     } else if (g < p.Gfast) {
         if constexpr (TM == TM_PAIR)
             group_full_pair<E, TMA>(p, T, e, g, bad, out);
+        else if constexpr (REG)
+            group_full_reg<E, TMA>(p, T, e, g, bad, out);
         else
             group_full<TM, E, TMA, St>(p, T, e, g, bad, stage + threadIdx.x, stage + 32 * kBlockThreads + threadIdx.x,
                                        out);
     } else {
-        group_tail<TM, E>(p, T, e, g, bad);
+        group_tail<TM, E, REG>(p, T, e, g, bad);
     }
 }
 
@@ -630,8 +697,8 @@ using StOf = typename std::conditional<TM != TM_GLOBAL, uint16_t, uint32_t>::typ
 // Persistent grid: each warp takes tiles of 32 consecutive column groups
 // (lane = group).  With TMA the warp's tile of outputs is written to shared
 // memory and stored with one tensor-store per tile.
-template <int TM, int E, bool TMA>
-__global__ void __launch_bounds__(kBlockThreads, TM == TM_PAIR ? 2 : 3)
+template <int TM, int E, bool TMA, bool REG = false>
+__global__ void __launch_bounds__(kBlockThreads, (TM == TM_PAIR || REG) ? 2 : 3)
     merge_kernel(const __grid_constant__ Params p, const __grid_constant__ CUtensorMap out_map) {
     using St = StOf<TM>;
     constexpr int CB = bytes_of(E);
@@ -648,7 +715,7 @@ __global__ void __launch_bounds__(kBlockThreads, TM == TM_PAIR ? 2 : 3)
     Tabs T;
     St *stage;
     Enc e;
-    merge_setup<TM, E, St>(p.t, p.enc_in_smem, base, T, stage, e);
+    merge_setup<TM, E, REG, St>(p.t, p.enc_in_smem, base, T, stage, e);
     pdl_wait();
     const bool ok = *p.status == RE_OK;
     bool bad = false;
@@ -668,7 +735,7 @@ __global__ void __launch_bounds__(kBlockThreads, TM == TM_PAIR ? 2 : 3)
         }
         Sink<TMA, CB> out{reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(p.out) + g * ROWB),
                           TMA ? tile + lane * ROWB : nullptr, lane};
-        merge_group<TM, E, TMA, St>(p, T, e, stage, g, ok, bad, out);
+        merge_group<TM, E, TMA, REG, St>(p, T, e, stage, g, ok, bad, out);
         if constexpr (TMA) {
             fence_async_smem();
             __syncwarp();
@@ -693,7 +760,7 @@ __global__ void __launch_bounds__(kBlockThreads, 3) merge_batch_kernel(const __g
     Tabs T;
     St *stage;
     Enc e;
-    merge_setup<TM, E, St>(b.t, enc_in_smem, sm, T, stage, e);
+    merge_setup<TM, E, false, St>(b.t, enc_in_smem, sm, T, stage, e);
     const uint32_t lane = threadIdx.x & 31;
     for (;;) {
         uint32_t tile = 0;
@@ -707,7 +774,7 @@ __global__ void __launch_bounds__(kBlockThreads, 3) merge_batch_kernel(const __g
         bool bad = false;
         Sink<false, bytes_of(E)> out{reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(p.out) + g * ROWB), nullptr,
                                      lane};
-        merge_group<TM, E, false, St>(p, T, e, stage, g, ok, bad, out);
+        merge_group<TM, E, false, false, St>(p, T, e, stage, g, ok, bad, out);
         if (bad) atomicExch(p.status, RE_E_INTERNAL);
     }
 }
@@ -722,13 +789,21 @@ int grid_for(K kernel, size_t smem, uint64_t items, int sm_count, uint32_t threa
     return (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)std::max(per_sm, 1) * sm_count));
 }
 
+template <int TM, int E, bool TMA, bool REG>
+void merge_launch(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
+    const size_t smem = merge_smem_bytes(p);
+    static uint64_t attr_done = 0;
+    allow_smem(merge_kernel<TM, E, TMA, REG>, &attr_done);
+    const int blocks = grid_for(merge_kernel<TM, E, TMA, REG>, smem, p.Gc, sm_count, kBlockThreads);
+    launch_dependent(merge_kernel<TM, E, TMA, REG>, blocks, kBlockThreads, smem, s, p, map);
+}
+
 template <int TM, int E, bool TMA>
 void merge_one(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
-    const size_t smem = tables_smem_bytes(p.t, TM) + merge_extra_smem(p);
-    static uint64_t attr_done = 0;
-    allow_smem(merge_kernel<TM, E, TMA>, &attr_done);
-    const int blocks = grid_for(merge_kernel<TM, E, TMA>, smem, p.Gc, sm_count, kBlockThreads);
-    launch_dependent(merge_kernel<TM, E, TMA>, blocks, kBlockThreads, smem, s, p, map);
+    if constexpr (TM == TM_SMEM) {
+        if (p.merge_reg) { merge_launch<TM, E, TMA, true>(p, map, s, sm_count); return; }
+    }
+    merge_launch<TM, E, TMA, false>(p, map, s, sm_count);
 }
 
 template <int TM, int E>
@@ -805,13 +880,20 @@ void fixup_one(const Params &p, cudaStream_t s, int sm_count) {
 }  // namespace
 
 size_t merge_extra_smem(const Params &p) {
-    const DevTables &t = p.t;
+    const DevTables t = p.merge_reg ? dfa_tables(p.t) : p.t;
     size_t a = 0;
     if (p.out_tma) a += 1024 + (size_t)(kBlockThreads / 32) * 32 * 64 * p.col_bytes;   // warp tiles + alignment
-    if (p.tmode != TM_PAIR) a += (2 * 32 * kBlockThreads * (p.tmode == TM_GLOBAL ? 4 : 2) + 15) & ~(size_t)15;
+    if (p.tmode != TM_PAIR && !p.merge_reg)
+        a += (2 * 32 * kBlockThreads * (p.tmode == TM_GLOBAL ? 4 : 2) + 15) & ~(size_t)15;
     if (!p.enc_in_smem) return a;
     if (p.kind == RE_SLPF_DICT) return a + (size_t)t.nf * t.nb * p.col_bytes;
     return a + (size_t)(t.nf + t.nb) * 8;
+}
+
+// Dynamic shared memory of one build & merge block: staged tables, then the
+// areas of merge_extra_smem.
+size_t merge_smem_bytes(const Params &p) {
+    return tables_smem_bytes(p.merge_reg ? dfa_tables(p.t) : p.t, p.tmode) + merge_extra_smem(p);
 }
 
 // The fix-up walks with the parse's staged tables: its duration is that of

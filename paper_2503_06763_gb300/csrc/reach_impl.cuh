@@ -251,6 +251,48 @@ __device__ __forceinline__ void compact(uint32_t (&s)[MS], uint32_t (&mk)[MS], u
     m = cnt;
 }
 
+// Wide lanes: a chunk whose speculation starts with more runs than the
+// register arrays hold keeps its runs in per-lane local arrays (they spill to
+// local memory, cached in L1) and walks them one byte at a time, merging runs
+// after every byte; once at most MS runs are left at a sub-chunk boundary they
+// move into the registers.  Runs drop fast after the first bytes of a chunk
+// (Sect. 4.3), so the register arrays, and the kernel's register budget, can be
+// sized for the common case instead of for the largest slot count.
+constexpr int kWide = 32;                    // local run capacity (= slot capacity)
+
+// Drop dead runs and merge equal ones (slot sets joined), in place.
+__device__ __forceinline__ void compact_local(uint32_t *s, uint32_t *mk, uint32_t &m) {
+    uint32_t cnt = 0;
+    for (uint32_t j = 0; j < m; ++j) {
+        const uint32_t v = s[j];
+        if (v == 0) continue;
+        uint32_t k = 0;
+        while (k < cnt && s[k] != v) ++k;
+        if (k < cnt) { mk[k] |= mk[j]; continue; }
+        s[cnt] = v;
+        mk[cnt] = mk[j];
+        ++cnt;
+    }
+    m = cnt;
+}
+
+// Walk bytes [lo, hi) of this lane's 64-byte tile row (forward: ascending;
+// backward: descending from hi - 1) for the m runs of the local arrays (state
+// ids), with the one-byte tables; runs are merged after every byte.
+template <int TM, bool FWD>
+__device__ __forceinline__ void walk_local(const Tabs &T, const uint8_t *row, uint32_t *s, uint32_t *mk, uint32_t &m,
+                                          int lo, int hi) {
+    constexpr int T1 = TM == TM_PAIR ? TM_SMEM : TM;     // pair layouts stage the one-byte tables too
+    const uint32_t swz = ((threadIdx.x & 31) >> 1) & 3;
+    for (int u = 0; u < hi - lo; ++u) {
+        const int t = FWD ? lo + u : hi - 1 - u;
+        const uint32_t b = row[((((uint32_t)t >> 4) ^ swz) << 4) | ((uint32_t)t & 15)];
+        const uint32_t c = clsof<T1>(T, b);
+        for (uint32_t j = 0; j < m; ++j) s[j] = FWD ? fnext<T1>(T, s[j], c) : bnext<T1>(T, s[j], c);
+        compact_local(s, mk, m);
+    }
+}
+
 // Record the runs at one boundary (while more than one run is live).
 template <int TM, int MS, bool FWD>
 __device__ __forceinline__ void record(const Params &p, const Tabs &T, uint32_t *cnt_row, uint2 *ent_row,
@@ -261,6 +303,19 @@ __device__ __forceinline__ void record(const Params &p, const Tabs &T, uint32_t 
 #pragma unroll
     for (int j = 0; j < MS; ++j)
         if (j < (int)m) ent_row[used + j] = make_uint2(FWD ? dec_f<TM>(T, s[j]) : dec_b<TM>(T, s[j]), mk[j]);
+    used += m;
+    cnt_row[slot] = m;
+    nrec = slot + 1;
+}
+
+// record() for the runs of a wide lane (state ids in local arrays).
+template <bool FWD>
+__device__ __forceinline__ void record_local(uint32_t *cnt_row, uint2 *ent_row, uint32_t &used, uint32_t &nrec,
+                                             bool &open, uint32_t slot, const uint32_t *s, const uint32_t *mk,
+                                             uint32_t m) {
+    if (!open) return;
+    if (slot >= kRecBounds || used + m > kRecEntries) { open = false; return; }
+    for (uint32_t j = 0; j < m; ++j) ent_row[used + j] = make_uint2(s[j], mk[j]);
     used += m;
     cnt_row[slot] = m;
     nrec = slot + 1;
@@ -285,9 +340,10 @@ __device__ __forceinline__ unsigned block_lanes(const Params &p, uint32_t i, uin
     return mask;
 }
 
-template <int TM, int MS, int DIR = DIR_BOTH>
+template <int TM, int MS, int DIR = DIR_BOTH, bool WIDE = false>
 __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CUtensorMap *map, Ring &ring,
                             bool tma) {
+    static_assert(!WIDE || DIR != DIR_BOTH, "wide lanes walk one direction");
     constexpr bool FW = DIR != DIR_B;
     const DevTables &t = p.t;
     const uint64_t base = (uint64_t)i * p.k;
@@ -300,12 +356,21 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
     for (int j = 0; j < MS; ++j) { sf[j] = dead_f; sb[j] = dead_b; kf[j] = 0u; kb[j] = 0u; }
     uint32_t mf = 0, mb = 0;
     int tstart = 0, tlast = -1;
+    // wide lanes: the runs of the one direction this warp walks, as state ids
+    uint32_t xs[WIDE ? kWide : 1], xk[WIDE ? kWide : 1], mx = 0;
+    bool big = false;
     if (!FW) {
     } else if (i == 0) {
         mf = 1; sf[0] = enc_f<TM>(T, t.fI); kf[0] = 1; tstart = 0;      // J_0 = I
     } else {
         const uint32_t pr = clsof<TM>(T, __ldg(p.x + base - 1)) * t.ncls + clsof<TM>(T, __ldg(p.x + base));
         mf = __ldg(t.fSlotCount + pr);
+        if (WIDE && mf > (uint32_t)MS) {
+            big = true;
+            mx = mf;
+            mf = 0;
+            for (uint32_t j = 0; j < mx; ++j) { xs[j] = __ldg(t.fSlotStart + pr * t.msf + j); xk[j] = 1u << j; }
+        }
 #pragma unroll
         for (int j = 0; j < MS; ++j)
             if (j < (int)mf) { sf[j] = enc_f<TM>(T, __ldg(t.fSlotStart + pr * t.msf + j)); kf[j] = 1u << j; }
@@ -318,13 +383,19 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
             const uint32_t pr = clsof<TM>(T, __ldg(p.x + base + len - 1)) * t.ncls +
                                 clsof<TM>(T, __ldg(p.x + base + len));
             mb = __ldg(t.bSlotCount + pr);
+            if (WIDE && mb > (uint32_t)MS) {
+                big = true;
+                mx = mb;
+                mb = 0;
+                for (uint32_t j = 0; j < mx; ++j) { xs[j] = __ldg(t.bSlotStart + pr * t.msb + j); xk[j] = 1u << j; }
+            }
 #pragma unroll
             for (int j = 0; j < MS; ++j)
                 if (j < (int)mb) { sb[j] = enc_b<TM>(T, __ldg(t.bSlotStart + pr * t.msb + j)); kb[j] = 1u << j; }
             tlast = (int)len - 2;                          // slot states precede the last byte
         }
     }
-    bool fconv = mf <= 1, bconv = mb <= 1;
+    bool fconv = mf <= 1 && !(FW && big), bconv = mb <= 1 && !(!FW && big);
     uint32_t fconv_sub = fconv ? 1 : nsub, bconv_sub = bconv ? nsub - 1 : 0;
     uint32_t *fcnt = p.w.recFc + (size_t)i * kRecBounds, *bcnt = p.w.recBc + (size_t)i * kRecBounds;
     uint2 *fent = p.w.recFe + (size_t)i * kRecEntries, *bent = p.w.recBe + (size_t)i * kRecEntries;
@@ -339,7 +410,18 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
         const uint32_t fb = blk, bb = nsub - 1 - blk;
         const int stage = (int)(blk % kStages);
         if (FW && fb >= 1) {                                // boundary before forward block fb
-            if (!fconv) {
+            if (WIDE && big) {
+                compact_local(xs, xk, mx);
+                if (mx > 1) record_local<true>(fcnt, fent, fused, fnrec, fopen, fb - 1, xs, xk, mx);
+                if (mx <= (uint32_t)MS) {                     // into the registers
+                    big = false;
+                    mf = mx;
+#pragma unroll
+                    for (int j = 0; j < MS; ++j)
+                        if (j < (int)mx) { sf[j] = enc_f<TM>(T, xs[j]); kf[j] = xk[j]; }
+                    if (mf <= 1) { fconv = true; fconv_sub = fb; }
+                }
+            } else if (!fconv) {
                 compact<MS>(sf, kf, mf, dead_f);
                 if (mf <= 1) { fconv = true; fconv_sub = fb; }
                 else record<TM, MS, true>(p, T, fcnt, fent, fused, fnrec, fopen, fb - 1, sf, kf, mf);
@@ -377,6 +459,10 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
         else if (MS > 2 && wm <= 2) walk_block<TM, MS, false, (MS > 2 ? 2 : MS), FW>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
         else if (MS > 4 && wm <= 4) walk_block<TM, MS, false, (MS > 4 ? 4 : MS), FW>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
         else walk_block<TM, MS, false, MS, FW>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
+        if (WIDE && big) {                                    // this lane's runs past the register arrays
+            if (FW) walk_local<TM, true>(T, frow, xs, xk, mx, f_lo, f_hi);
+            else walk_local<TM, false>(T, brow, xs, xk, mx, 0, b_hi + 1);
+        }
         if (tma) {
             __syncwarp();                                     // every lane has read this stage
             if (lane == 0 && blk + kStages < nsub)
@@ -385,7 +471,18 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
             __syncwarp(act);                                  // stage read before the next fill
         }
         if (bwd && bb >= 1) {                               // boundary at the start of backward block bb
-            if (!bconv) {
+            if (WIDE && big) {
+                compact_local(xs, xk, mx);
+                if (mx > 1) record_local<false>(bcnt, bent, bused, bnrec, bopen, nsub - 1 - bb, xs, xk, mx);
+                if (mx <= (uint32_t)MS) {                     // into the registers
+                    big = false;
+                    mb = mx;
+#pragma unroll
+                    for (int j = 0; j < MS; ++j)
+                        if (j < (int)mx) { sb[j] = enc_b<TM>(T, xs[j]); kb[j] = xk[j]; }
+                    if (mb <= 1) { bconv = true; bconv_sub = bb; }
+                }
+            } else if (!bconv) {
                 compact<MS>(sb, kb, mb, dead_b);
                 if (mb <= 1) { bconv = true; bconv_sub = bb; }
                 else record<TM, MS, false>(p, T, bcnt, bent, bused, bnrec, bopen, nsub - 1 - bb, sb, kb, mb);
@@ -394,13 +491,19 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
         }
     }
     // end state of every slot: the state of the run standing for it (0 if none)
+    if (WIDE && big) compact_local(xs, xk, mx);         // runs still past the registers at the end
     if (FW) {
         const uint32_t msf = t.msf;
         for (uint32_t j = 0; j < msf; ++j) {
             uint32_t v = 0;
+            if (WIDE && big) {
+                for (uint32_t r = 0; r < mx; ++r)
+                    if ((xk[r] >> j) & 1) v = xs[r];
+            } else {
 #pragma unroll
-            for (int r = 0; r < MS; ++r)
-                if (r < (int)mf && ((kf[r] >> j) & 1)) v = dec_f<TM>(T, sf[r]);
+                for (int r = 0; r < MS; ++r)
+                    if (r < (int)mf && ((kf[r] >> j) & 1)) v = dec_f<TM>(T, sf[r]);
+            }
             p.w.Rf[(size_t)i * msf + j] = v;
         }
         p.w.fconv[i] = fconv_sub;
@@ -410,9 +513,14 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
         const uint32_t msb = t.msb;
         for (uint32_t j = 0; j < msb; ++j) {
             uint32_t v = 0;
+            if (WIDE && big) {
+                for (uint32_t r = 0; r < mx; ++r)
+                    if ((xk[r] >> j) & 1) v = xs[r];
+            } else {
 #pragma unroll
-            for (int r = 0; r < MS; ++r)
-                if (r < (int)mb && ((kb[r] >> j) & 1)) v = dec_b<TM>(T, sb[r]);
+                for (int r = 0; r < MS; ++r)
+                    if (r < (int)mb && ((kb[r] >> j) & 1)) v = dec_b<TM>(T, sb[r]);
+            }
             p.w.Rb[(size_t)i * msb + j] = v;
         }
         p.w.bconv[i] = bconv_sub;
@@ -430,7 +538,7 @@ constexpr uint32_t kSplitThreads = 256;
 // ring), which doubles the warps in flight for the same shared memory; in
 // recognizer mode every warp takes a tile of its own, forward.  Without SPLIT
 // every warp walks its tile in both directions (two tiles per ring stage).
-template <int TM, int MS, bool SPLIT>
+template <int TM, int MS, bool SPLIT, bool WIDE = false>
 __global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
     reach_kernel(const __grid_constant__ Params p, const __grid_constant__ CUtensorMap map) {
     extern __shared__ __align__(16) uint8_t sm[];
@@ -462,9 +570,9 @@ __global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
         const bool tma = p.text_tma && t * 32 + 32 <= p.c_full;
         if (i >= p.c) continue;                               // lanes past the text (plain path only)
         bool ok;
-        if (!SPLIT) ok = reach_chunk<TM, MS, DIR_BOTH>(p, T, i, &map, ring, tma);
-        else if (backward_warp) ok = reach_chunk<TM, MS, DIR_B>(p, T, i, &map, ring, tma);
-        else ok = reach_chunk<TM, MS, DIR_F>(p, T, i, &map, ring, tma);
+        if constexpr (!SPLIT) ok = reach_chunk<TM, MS, DIR_BOTH>(p, T, i, &map, ring, tma);
+        else if (backward_warp) ok = reach_chunk<TM, MS, DIR_B, WIDE>(p, T, i, &map, ring, tma);
+        else ok = reach_chunk<TM, MS, DIR_F, WIDE>(p, T, i, &map, ring, tma);
         if (!ok) {
             atomicExch(p.status, RE_E_INTERNAL);
             atomicExch(&p.w.flags[FLAG_INTERNAL], 1);
@@ -484,7 +592,7 @@ __global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
 // warps, as in a single parse).  Text bytes come in by plain loads.  Lanes
 // past their text's last chunk skip the tile and meet the others at the
 // closing __syncwarp, so no lane waits in a collective the others do not run.
-template <int TM, int MS, bool SPLIT>
+template <int TM, int MS, bool SPLIT, bool WIDE = false>
 __global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
     reach_batch_kernel(const __grid_constant__ BatchGroup b) {
     extern __shared__ __align__(16) uint8_t sm[];
@@ -510,9 +618,9 @@ __global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
         const uint32_t i = (uint32_t)(tile - b.rtile_base[ti]) * 32 + lane;
         if (i < p.c) {
             bool ok;
-            if (!SPLIT) ok = reach_chunk<TM, MS, DIR_BOTH>(p, T, i, nullptr, ring, false);
-            else if (item & 1) ok = reach_chunk<TM, MS, DIR_B>(p, T, i, nullptr, ring, false);
-            else ok = reach_chunk<TM, MS, DIR_F>(p, T, i, nullptr, ring, false);
+            if constexpr (!SPLIT) ok = reach_chunk<TM, MS, DIR_BOTH>(p, T, i, nullptr, ring, false);
+            else if (item & 1) ok = reach_chunk<TM, MS, DIR_B, WIDE>(p, T, i, nullptr, ring, false);
+            else ok = reach_chunk<TM, MS, DIR_F, WIDE>(p, T, i, nullptr, ring, false);
             if (!ok) atomicExch(&p.w.flags[FLAG_INTERNAL], 1);
         }
         __syncwarp();
@@ -524,18 +632,18 @@ inline size_t reach_smem(const DevTables &t, int tm, uint32_t threads = kChunkTh
     return tab + 1024 + (threads / 32) * (kStages * tiles * kTileBytes + kStages * 8);
 }
 
-template <int TM, int MS, bool SPLIT>
+template <int TM, int MS, bool SPLIT, bool WIDE = false>
 void launch_batch_split(const BatchGroup &b, cudaStream_t s, int sm_count) {
     const uint32_t threads = SPLIT ? kSplitThreads : kChunkThreads;
     const size_t smem = reach_smem(b.t, TM, threads, SPLIT ? 1 : 2);
     static uint64_t attr_done = 0;
-    allow_smem(reach_batch_kernel<TM, MS, SPLIT>, &attr_done);
+    allow_smem(reach_batch_kernel<TM, MS, SPLIT, WIDE>, &attr_done);
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_batch_kernel<TM, MS, SPLIT>, threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_batch_kernel<TM, MS, SPLIT, WIDE>, threads, smem);
     const uint64_t warps = (uint64_t)b.n_reach * (SPLIT ? 2 : 1);
     const uint64_t want = (warps + threads / 32 - 1) / (threads / 32);
     const uint64_t blocks = std::min<uint64_t>(want, (uint64_t)std::max(per_sm, 1) * sm_count);
-    reach_batch_kernel<TM, MS, SPLIT><<<(uint32_t)std::max<uint64_t>(blocks, 1), threads, smem, s>>>(b);
+    reach_batch_kernel<TM, MS, SPLIT, WIDE><<<(uint32_t)std::max<uint64_t>(blocks, 1), threads, smem, s>>>(b);
 }
 
 template <int TM, int MS>
@@ -544,47 +652,48 @@ void launch_batch_one(const BatchGroup &b, cudaStream_t s, int sm_count) {
     else launch_batch_split<TM, MS, true>(b, s, sm_count);
 }
 
+// More than 8 slots: a parse batch uses wide lanes (4 runs in registers, the
+// rest in local memory until they merge); the recognizer batch, which walks
+// one chunk in both directions per lane, keeps every run in registers.
 template <int TM>
 bool launch_ms_batch(const BatchGroup &b, cudaStream_t s, uint32_t ms, int sm_count) {
     constexpr bool FULL = TM != TM_GLOBAL;
     if (FULL && ms <= 2) launch_batch_one<TM, 2>(b, s, sm_count);
     else if (FULL && ms <= 4) launch_batch_one<TM, 4>(b, s, sm_count);
     else if (ms <= 8) launch_batch_one<TM, 8>(b, s, sm_count);
-    else if (FULL && ms <= 16) launch_batch_one<TM, 16>(b, s, sm_count);
-    else if (ms <= 32) launch_batch_one<TM, 32>(b, s, sm_count);
-    else return false;
+    else if (ms > 32) return false;
+    else if (!b.recognize) launch_batch_split<TM, 4, true, true>(b, s, sm_count);
+    else if (FULL && ms <= 16) launch_batch_split<TM, 16, false>(b, s, sm_count);
+    else launch_batch_split<TM, 32, false>(b, s, sm_count);
     return true;
 }
 
-template <int TM, int MS, bool SPLIT>
+template <int TM, int MS, bool SPLIT, bool WIDE = false>
 void launch_split(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
     const uint32_t threads = SPLIT ? kSplitThreads : kChunkThreads;
     const size_t smem = reach_smem(p.t, TM, threads, SPLIT ? 1 : 2);
     static uint64_t attr_done = 0;
-    allow_smem(reach_kernel<TM, MS, SPLIT>, &attr_done);
+    allow_smem(reach_kernel<TM, MS, SPLIT, WIDE>, &attr_done);
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_kernel<TM, MS, SPLIT>, threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_kernel<TM, MS, SPLIT, WIDE>, threads, smem);
     const uint64_t warps = ((uint64_t)p.c + 31) / 32 * (SPLIT && !p.recognize ? 2 : 1);
     const uint64_t want = (warps + threads / 32 - 1) / (threads / 32);
     const uint64_t blocks = std::min<uint64_t>(want, (uint64_t)std::max(per_sm, 1) * sm_count);
-    launch_dependent(reach_kernel<TM, MS, SPLIT>, (uint32_t)std::max<uint64_t>(blocks, 1), threads, smem, s, p, map);
+    launch_dependent(reach_kernel<TM, MS, SPLIT, WIDE>, (uint32_t)std::max<uint64_t>(blocks, 1), threads, smem, s, p,
+                     map);
 }
 
 // A parse: warp pairs per 32-chunk tile; the recognizer: one forward warp per
-// tile (the same kernel, so the same register budget and ring depth).
-template <int TM, int MS>
-void launch_one(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
-    launch_split<TM, MS, true>(p, map, s, sm_count);
-}
-
+// tile (the same kernel, so the same register budget and ring depth).  More
+// than 8 slots: wide lanes (4 runs in registers, the rest in local memory
+// until they merge, which they do within the first bytes of most chunks).
 template <int TM>
 bool launch_ms(const Params &p, const CUtensorMap &map, cudaStream_t s, uint32_t ms, int sm_count) {
     constexpr bool FULL = TM != TM_GLOBAL;          // fewer instantiations for the rare global mode
-    if (FULL && ms <= 2) launch_one<TM, 2>(p, map, s, sm_count);
-    else if (FULL && ms <= 4) launch_one<TM, 4>(p, map, s, sm_count);
-    else if (ms <= 8) launch_one<TM, 8>(p, map, s, sm_count);
-    else if (FULL && ms <= 16) launch_one<TM, 16>(p, map, s, sm_count);
-    else if (ms <= 32) launch_one<TM, 32>(p, map, s, sm_count);
+    if (FULL && ms <= 2) launch_split<TM, 2, true>(p, map, s, sm_count);
+    else if (FULL && ms <= 4) launch_split<TM, 4, true>(p, map, s, sm_count);
+    else if (ms <= 8) launch_split<TM, 8, true>(p, map, s, sm_count);
+    else if (ms <= 32) launch_split<TM, 4, true, true>(p, map, s, sm_count);
     else return false;
     return true;
 }
