@@ -1,16 +1,20 @@
-"""Benchmark: SLPF parse throughput (text GB/s) on a DNA-like motif workload.
+"""Benchmark: SLPF parse throughput (text GB/s) of one text per GPU.
 
 One step = one full parse of a device-resident text: forward / backward
 speculative reach, join, checkpoint fix-up and build & merge with compose
 (every kernel of the path), the clean SLPF written to HBM.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload log|dna|ab] [--mode ...]
 
-Workload: RE ([ACGT]|ATG([ACGT][ACGT][ACGT])*(TAA|TAG|TGA))* over a 256 MiB
-text of i.i.d. uniform bases with ORF motifs planted at 1 per 10 kB (seed 1
-on rank 0).  The text is larger than L2, so every step streams it from HBM.
-N > 1 (torchrun): every rank parses its own text of the same size (weak
-scaling, no collective on the data path); time is the max over ranks.
+Default workload (the headline): web-server-like log records, 1 GiB of text
+(seed 2 on rank 0) under the RE ((good|[^\n]*)\n)* with 124 numbered
+positions and 162 segments, 2 % of the lines malformed; DICT columns.  The
+DNA-like motif text (256 MiB, seed 1) is measured after it in the same run
+and reported under the "dna" key.  Both texts are larger than L2, so every
+step streams them from HBM.  N > 1 (torchrun): every rank parses its own
+text of the same size (weak scaling, no collective on the data path); time
+is the max over ranks.
 
 Printed: one JSON line (rank 0) with the contract keys plus ``roofline``
 (the dominant kernel timed live with the library's per-phase CUDA events),
@@ -33,9 +37,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "SLPF parse GB/s of text on 1 GB300, % of HBM roofline; p50/p99 latency served"
-WORKLOAD = "dna-motif: RE ([ACGT]|ATG([ACGT][ACGT][ACGT])*(TAA|TAG|TGA))*, 256 MiB uniform ACGT, ORFs 30-900 codons at 1 per 10 kB, seed 1"
-N_BYTES = 256 << 20
-CPU_SAMPLE = 256 << 20
+# name -> (description, RE attribute of workloads, text maker, default bytes, seed, oracle sample bytes)
+WORKLOADS = {
+    "log": ("log-records: RE ((IPv4 - - [timestamp] \"METHOD /path HTTP/1.x\" status size|[^\\n]*)\\n)*, "
+            "124 positions, 162 segments; 1 GiB of web-server-like lines (paths Zipf over 1e5 tokens, "
+            "status 200 w.p. 0.9, 2% malformed), seed 2", "LOG_RE", "log_text", 1 << 30, 2, 16 << 20),
+    "dna": ("dna-motif: RE ([ACGT]|ATG([ACGT][ACGT][ACGT])*(TAA|TAG|TGA))*, 256 MiB uniform ACGT, "
+            "ORFs 30-900 codons at 1 per 10 kB, seed 1", "DNA_RE", "dna_text", 256 << 20, 1, 256 << 20),
+    "ab": ("ab: RE (a|b|ab)*, i.i.d. uniform {a,b}, seed 0", "AB_RE", "ab_text", 1 << 20, 0, 64 << 20),
+}
+WORKLOAD = WORKLOADS["log"][0]
 FALLBACK_HBM = 6800.0
 
 
@@ -45,7 +56,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--bytes", type=int, default=N_BYTES, help="text size (default 256 MiB)")
+    ap.add_argument("--workload", default="log", choices=sorted(WORKLOADS),
+                    help="single mode: log (1 GiB, the headline), dna (256 MiB) or ab")
+    ap.add_argument("--bytes", type=int, default=0, help="text size (default: the workload's)")
+    ap.add_argument("--no-extra", action="store_true", help="single mode: skip the DNA line after the log one")
     ap.add_argument("--chunk-len", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "matches", "latency", "ablation"],
@@ -134,13 +148,13 @@ class ClockSampler:
                 "samples": len(loaded), "power_w_max": max((num(r[3]) or 0) for r in loaded)}
 
 
-def cpu_baseline(text_host, pattern):
+def cpu_baseline(text_host, pattern, sample_bytes):
     """The CPU oracle as it stands (serial two-way NFA parser, one core) on a
     bounded prefix of the same text."""
     from oracle import serial
     from oracle.re_front import compile_re
     c = compile_re(pattern)
-    sample = text_host[:CPU_SAMPLE].tobytes()
+    sample = text_host[:sample_bytes].tobytes()
     t0 = time.perf_counter()
     serial.parse(c, sample)
     dt = time.perf_counter() - t0
@@ -149,16 +163,19 @@ def cpu_baseline(text_host, pattern):
                       f"{dt:.1f} s, host {os.uname().machine} nproc={os.cpu_count()}"}
 
 
-def lsu_roofline(phase_ms: dict, n: int, device: int):
-    """Reach against the shared-memory pipe, its real bound: with at most 16
+def lsu_roofline(phase_ms: dict, n: int, device: int, ncls: int):
+    """Reach against the shared-memory pipe, its real bound.  With at most 16
     byte classes it does 3 shared-memory lookups per text byte (per direction
-    and byte pair: two class lookups and one two-byte table lookup).  Peak:
-    one 32-lane wavefront per SM and cycle at the maximum SM clock."""
+    and byte pair: two class lookups and one two-byte table lookup); with more
+    classes 4 (per direction and byte: one class and one transition lookup).
+    Peak: one 32-lane wavefront per SM and cycle at the maximum SM clock."""
     import torch
     props = torch.cuda.get_device_properties(device)
     peak = props.multi_processor_count * 32 * 2.07e9 / 1e12
-    achieved = 3 * n / (phase_ms["reach"] / 1e3) / 1e12
-    return {"kernel": "reach", "bound": "lsu", "achieved": round(achieved, 3), "peak": round(peak, 3),
+    per_byte = 3 if ncls <= 16 else 4
+    achieved = per_byte * n / (phase_ms["reach"] / 1e3) / 1e12
+    return {"kernel": "reach", "bound": "lsu", "lookups_per_byte": per_byte, "achieved": round(achieved, 3),
+            "peak": round(peak, 3),
             "unit": "T lookups/s", "frac": round(achieved / peak, 4),
             "peak_source": "SM count x 32 lanes x 2070 MHz (one conflict-free wavefront per SM and cycle)"}
 
@@ -174,16 +191,16 @@ def csrc_hash() -> str:
     return h.hexdigest()
 
 
-def traffic_for(kernel: str, n: int):
+def traffic_for(workload: str, kernel: str, n: int):
     """ncu DRAM bytes of the dominant kernel, scaled per text byte, if the
-    committed capture matches the current kernel source."""
+    committed capture of this workload matches the current kernel source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         if d.get("csrc_sha256") != csrc_hash():
             return None
-        per = d.get("dram_bytes_per_text_byte", {}).get(kernel)
+        per = d.get("dram_bytes_per_text_byte", {}).get(workload, {}).get(kernel)
         return None if per is None else per * n
     except Exception:
         return None
@@ -207,40 +224,20 @@ def rank_seed(base: int, rank: int) -> int:
     return base + 1000 * rank
 
 
-def main():
-    args = parse_args()
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    import numpy as np
-    import workloads as W
-
-    if args.impl == "reference":
-        return reference_arm(args, rank, world)
-    if args.mode == "batch":
-        return batch_mode(args, rank, world, local)
-    if args.mode == "serve":
-        return serve_mode(args, rank, world, local)
-    if args.mode == "matches":
-        return matches_mode(args, rank, world, local)
-    if args.mode == "latency":
-        return latency_mode(args, rank, world, local)
-    if args.mode == "ablation":
-        return ablation_mode(args, rank, world, local)
-
+def measure_single(args, name, n, rank, world, local, dist, full=True):
+    """One workload on one text per rank: the timed headline loop, per-phase
+    times, and (full) the recognizer, end-to-end and CPU-oracle legs.
+    Returns the fields of the JSON line."""
     import torch
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-
+    import workloads as W
     from paper_2503_06763_gb300 import Regex
     from paper_2503_06763_gb300.native import PHASES
 
-    n = args.bytes
-    host = W.dna_text(n, seed=rank_seed(1, rank))
-    rx = Regex(W.DNA_RE)
+    desc, re_attr, maker, _, seed, cpu_bytes = WORKLOADS[name]
+    pattern = getattr(W, re_attr)
+    host = getattr(W, maker)(n, seed=rank_seed(seed, rank))
+    n = int(host.size)
+    rx = Regex(pattern)
     dev = torch.device("cuda", local)
     text = torch.from_numpy(host).to(dev)
     tuned = None
@@ -264,7 +261,7 @@ def main():
     torch.cuda.synchronize()
     st = int(status.item())
     if st != 0:
-        raise SystemExit(f"parse status {st}")
+        raise SystemExit(f"{name}: parse status {st}")
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -298,11 +295,23 @@ def main():
     achieved = alg[dominant] / (phase_ms[dominant] / 1e3) / 1e9 if alg[dominant] else 0.0
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1), "peak": hbm,
                 "peak_source": src, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                "traffic": traffic_for(dominant, n),
+                "traffic": traffic_for(name, dominant, n),
                 "phase_ms": {k: round(v, 4) for k, v in phase_ms.items()},
                 "phase_timing": "second loop of the same K steps, CUDA events between phases",
+                "algorithmic_bytes": {k: v for k, v in alg.items() if v},
                 "whole_step_frac": round((n + (n + 1) * cb) / (ms / 1e3) / 1e9 / hbm, 4),
-                "lsu": lsu_roofline(phase_ms, n, local)}
+                "lsu": lsu_roofline(phase_ms, n, local, rx.info["n_classes"])}
+    res = {"value": round(value, 3), "ms_per_step": round(ms, 4), "roofline": roofline, "clocks": clocks,
+           "config": {"workload": desc, "text_bytes_per_gpu": n, "encoding": f"{kind}-{8 * cb}bit",
+                      "chunk_len": args.chunk_len or tuned,
+                      "chunk_len_from": "fixed" if args.chunk_len else "re_autotune", "segments": rx.ell,
+                      "byte_classes": rx.info["n_classes"],
+                      "l2": f"text {n >> 20} MiB > 129 MB L2 (no flush needed)",
+                      "parallelism": f"independent texts per GPU x{world}"}}
+    if not full:
+        del text, out, ws
+        torch.cuda.empty_cache()
+        return res
 
     # recognizer mode (forward reach + join only, Sect. 4.2), same text, with
     # its own autotuned chunk length (one forward warp per 32-chunk tile, so it
@@ -320,8 +329,8 @@ def main():
         rx.parse(text, chunk_len=args.chunk_len, status=status, workspace=rec_ws, recognize_only=True)
     r1.record(stream)
     torch.cuda.synchronize()
-    recognizer = {"value": round(n / (r0.elapsed_time(r1) / args.steps / 1e3) / 1e9, 3), "unit": "GB/s",
-                  "status": int(status.item()), "chunk_len": rec_k}
+    res["recognizer"] = {"value": round(n / (r0.elapsed_time(r1) / args.steps / 1e3) / 1e9, 3), "unit": "GB/s",
+                         "status": int(status.item()), "chunk_len": rec_k}
     del rec_ws
 
     # end to end through re_parse_host: pinned host text in, columns and status
@@ -343,10 +352,10 @@ def main():
         rx.parse_host(pin_in, b["out"], b["st"], b["d_text"], b["d_out"], b["d_st"], b["ws"], stream=b["s"],
                       kind=kind, chunk_len=args.chunk_len)
 
-    for k in range(8):                          # warm-up: first use of the pinned buffers and copy paths
+    for k in range(4):                          # warm-up: first use of the pinned buffers and copy paths
         e2e_step(k)
     torch.cuda.synchronize()
-    e_steps = max(4, min(args.steps, 12))
+    e_steps = max(4, min(args.steps, 8))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for b in sets:
@@ -362,28 +371,65 @@ def main():
     e_ms = e0.elapsed_time(e1) / e_steps
     if not all(int(b["st"][0]) == st for b in sets) or not torch.equal(sets[0]["out"], out.cpu()):
         raise SystemExit("end-to-end columns differ from the device-resident parse")
-    e2e = {"value": round(n * world / (e_ms / 1e3) / 1e9, 3), "unit": "GB/s",
-           "h2d_bytes_per_step": n, "d2h_bytes_per_step": (n + 1) * cb + 4,
-           "api": "re_parse_host, 2 streams alternating"}
+    res["e2e"] = {"value": round(n * world / (e_ms / 1e3) / 1e9, 3), "unit": "GB/s",
+                  "h2d_bytes_per_step": n, "d2h_bytes_per_step": (n + 1) * cb + 4,
+                  "api": "re_parse_host, 2 streams alternating"}
+    del sets, pin_in, text, out, ws
+    torch.cuda.empty_cache()
+    res["cpu_baseline"] = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        res["cpu_baseline"] = cpu_baseline(host, pattern, cpu_bytes)
+    return res
 
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    if args.mode == "batch":
+        return batch_mode(args, rank, world, local)
+    if args.mode == "serve":
+        return serve_mode(args, rank, world, local)
+    if args.mode == "matches":
+        return matches_mode(args, rank, world, local)
+    if args.mode == "latency":
+        return latency_mode(args, rank, world, local)
+    if args.mode == "ablation":
+        return ablation_mode(args, rank, world, local)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    name = args.workload
+    n = args.bytes or WORKLOADS[name][3]
+    r = measure_single(args, name, n, rank, world, local, dist, full=True)
+    extra = None
+    if name == "log" and not args.no_extra:     # the DNA motif text, same protocol, headline loop only
+        d = measure_single(args, "dna", WORKLOADS["dna"][3], rank, world, local, dist, full=False)
+        extra = {"workload": d["config"]["workload"], "value": d["value"], "unit": "GB/s",
+                 "ms_per_step": d["ms_per_step"], "chunk_len": d["config"]["chunk_len"],
+                 "phase_ms": d["roofline"]["phase_ms"], "whole_step_frac": d["roofline"]["whole_step_frac"],
+                 "dominant": {k: d["roofline"][k] for k in ("kernel", "achieved", "frac")}}
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    cpu = None
-    if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(host, W.DNA_RE)
     line = {
-        "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "text_bytes_per_gpu": n, "encoding": f"{kind}-{8 * cb}bit",
-                   "chunk_len": args.chunk_len or tuned, "chunk_len_from": "fixed" if args.chunk_len else "re_autotune", "segments": rx.ell,
-                   "l2": "text 256 MiB > 129 MB L2 (no flush needed)",
-                   "parallelism": f"independent texts per GPU x{world}"},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "recognizer": recognizer,
-        "gpu_launches": 7 * args.steps, "clocks": clocks,
+        "metric": METRIC, "value": r["value"], "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic", "config": r["config"],
+        "roofline": r["roofline"], "cpu_baseline": r.get("cpu_baseline"), "e2e": r.get("e2e"),
+        "recognizer": r.get("recognizer"), "gpu_launches": 7 * args.steps, "clocks": r["clocks"],
     }
+    if extra:
+        line["dna"] = extra
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
@@ -590,7 +636,7 @@ def matches_mode(args, rank, world, local):
     from paper_2503_06763_gb300 import Regex
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    n = args.bytes
+    n = args.bytes or (256 << 20)
     host = W.dna_text(n, seed=rank_seed(1, rank))
     rx = Regex(W.DNA_RE)
     text = torch.from_numpy(host).to(dev)
@@ -693,7 +739,7 @@ def ablation_mode(args, rank, world, local):
     from paper_2503_06763_gb300.native import PHASES
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    n = args.bytes
+    n = args.bytes or (256 << 20)
     stream = torch.cuda.current_stream(dev)
     steps = max(args.steps, 5)
     rows = []
@@ -758,8 +804,10 @@ def reference_arm(args, rank, world):
     import workloads as W
     from oracle import serial
     from oracle.re_front import compile_re
-    host = W.dna_text(min(args.bytes, 64 << 20), seed=1)
-    c = compile_re(W.DNA_RE)
+    name = args.workload
+    desc, re_attr, maker, _, seed, _ = WORKLOADS[name]
+    host = getattr(W, maker)(4 << 20, seed=seed)
+    c = compile_re(getattr(W, re_attr))
     sample = host[:1 << 20].tobytes()
     for _ in range(args.warmup):
         serial.parse(c, sample)
@@ -771,7 +819,7 @@ def reference_arm(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "text_bytes_per_step": len(sample)},
+            "config": {"workload": desc, "text_bytes_per_step": len(sample)},
             "cpu_baseline": {"value": round(v, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
                              "sample": "first 1 MiB of the workload text per step, serial oracle"},
             "e2e": {"value": round(v, 6), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

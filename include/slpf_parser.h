@@ -243,6 +243,12 @@ void re_batch_free(re_batch *b);
  *   - RE_E_CUDA when the scratch address cannot be resolved.
  * The first call on each device resolves that address (cudaGetSymbolAddress)
  * with the device current; make that first call before any stream capture.
+ * The address is kept for the life of the process and belongs to the device's
+ * primary context (the one the CUDA runtime uses): it is not valid in another
+ * context, nor after cudaDeviceReset.  A text that fits only with the
+ * built-in chunk-length rule, not with a length re_autotune chose, is parsed
+ * with the rule's length (as re_parse does when its workspace is too small
+ * for the tuned layout).
  * Every call on a device shares the one scratch: calls whose work can overlap
  * on the device (different streams with no ordering between them, or several
  * host threads) race and corrupt each other's results.  Successive calls on

@@ -9,7 +9,9 @@ reverse NFA has N̂_a = N_a^T and I, F switched (Eq. reverseNFAdef).
 
 ``parse_small`` runs Fig. serialparser with Python sets, one column at a time.
 ``parse`` runs the same products in ``serial_parser.c`` over bitsets.  Both
-return the clean SLPF columns C_r ∩ Ĉ_r, r = 0..n.
+return the clean SLPF columns C_r ∩ Ĉ_r, r = 0..n.  ``parse_ids`` returns
+the same columns interned (an id per position and a table of distinct
+columns), for texts too long to hold W words per position.
 """
 from __future__ import annotations
 
@@ -48,6 +50,11 @@ def _load():
             lib.oracle_serial_parse.argtypes = [
                 ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                 ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+            lib.oracle_serial_parse_ids.restype = ctypes.c_int
+            lib.oracle_serial_parse_ids.argtypes = [
+                ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                ctypes.c_void_p]
             _lib = lib
     return _lib
 
@@ -134,6 +141,31 @@ def parse(c: Compiled, text) -> np.ndarray:
     if rc != 0:
         raise RuntimeError("oracle_serial_parse failed")
     return out
+
+
+def parse_ids(c: Compiled, text, cap: int = 1 << 20):
+    """The clean SLPF of ``parse`` with every column interned, for long texts:
+    returns (ids, cols) with ids a uint32 array of n+1 indices into cols, a
+    [D, W] uint64 array of the distinct clean columns.  Column r of the SLPF
+    is cols[ids[r]].  The forward and backward columns are interned as well,
+    and each product of a stored column with a byte is computed once (the same
+    loops as ``parse``), so a GiB of text needs 4 bytes per position."""
+    lib = _load()
+    x = np.frombuffer(bytes(text), dtype=np.uint8) if not isinstance(text, np.ndarray) else text
+    x = np.ascontiguousarray(x, dtype=np.uint8)
+    n = int(x.shape[0])
+    W = words(c.ell)
+    ncol = nfa_columns(c)
+    I = to_bits(c, c.initial)
+    F = to_bits(c, c.final)
+    ids = np.empty(n + 1, dtype=np.uint32)
+    cols = np.zeros((cap, W), dtype=np.uint64)
+    nc = ctypes.c_int64(0)
+    rc = lib.oracle_serial_parse_ids(c.ell, W, ncol.ctypes.data, I.ctypes.data, F.ctypes.data, x.ctypes.data,
+                                     n, ids.ctypes.data, cols.ctypes.data, cap, ctypes.byref(nc))
+    if rc != 0:
+        raise RuntimeError(f"oracle_serial_parse_ids failed ({rc})")
+    return ids, cols[:nc.value].copy()
 
 
 def accepted(columns: np.ndarray) -> bool:

@@ -365,6 +365,22 @@ re_status re_workspace_size(const re_handle *h, uint64_t len, const re_parse_opt
     return RE_OK;
 }
 
+}  // extern "C"
+
+namespace slpf {
+// Workspace for the built-in chunk-length rule, ignoring any autotuned length:
+// what re_parse falls back to when the workspace it is given cannot hold the
+// tuned layout.
+re_status workspace_rule_bytes(const re_handle *h, uint64_t len, const re_parse_opts *opts, uint64_t *bytes) {
+    const uint32_t k = choose_chunk(len, sm_count_of(h->device), opts);
+    if (k % kSub || k == 0) { set_error("chunk_len must be a positive multiple of 64"); return RE_E_INVALID_ARG; }
+    *bytes = layout_for(h, len, k).total;
+    return RE_OK;
+}
+}  // namespace slpf
+
+extern "C" {
+
 re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream stream, re_slpf *slpf,
                    void *d_workspace, uint64_t workspace_bytes, const re_parse_opts *opts) {
     if (!h || !slpf || !slpf->d_status || (len && !d_text)) { set_error("null argument"); return RE_E_INVALID_ARG; }

@@ -167,15 +167,19 @@ __device__ inline void empty_text(const Params &p) {
 //   TM_SMEM:   one-byte tables staged in shared memory as u16;
 //   TM_PAIR:   two-byte tables in shared memory, one 32-bit entry per
 //              (state, class pair): low half the state after the first byte
-//              consumed, high half after both (used when ncls^2 is small).
+//              consumed, high half after both (used when ncls^2 is small);
+//   TM_SMEM8:  one-byte tables in shared memory as u8 (at most 256 states per
+//              direction; the reach's choice for larger class alphabets, a
+//              quarter of the u32 footprint, so more blocks fit an SM).
 // Row s, column = byte class (or class pair c1*ncls + c2 for the left and
 // right byte of the pair).  A forward pair consumes c1 then c2, a backward
 // pair c2 then c1.
-enum { TM_GLOBAL = 0, TM_SMEM = 1, TM_PAIR = 2 };
+enum { TM_GLOBAL = 0, TM_SMEM = 1, TM_PAIR = 2, TM_SMEM8 = 3 };
 
 struct Tabs {
     const uint8_t *cls;
     const uint16_t *f16, *b16;
+    const uint8_t *f8, *b8;
     const uint32_t *f32, *b32;
     const uint32_t *f2, *b2;
     uint32_t ncls, nc2;
@@ -185,12 +189,14 @@ struct Tabs {
 template <int TM>
 __device__ __forceinline__ uint32_t fnext(const Tabs &T, uint32_t s, uint32_t c) {
     if (TM == TM_SMEM) return T.f16[s * T.ncls + c];
+    if (TM == TM_SMEM8) return T.f8[s * T.ncls + c];
     if (TM == TM_PAIR) return T.f2[s * T.nc2 + c * T.ncls] & 0xFFFFu;
     return __ldg(T.f32 + (size_t)s * T.ncls + c);
 }
 template <int TM>
 __device__ __forceinline__ uint32_t bnext(const Tabs &T, uint32_t s, uint32_t c) {
     if (TM == TM_SMEM) return T.b16[s * T.ncls + c];
+    if (TM == TM_SMEM8) return T.b8[s * T.ncls + c];
     if (TM == TM_PAIR) return T.b2[s * T.nc2 + c] & 0xFFFFu;
     return __ldg(T.b32 + (size_t)s * T.ncls + c);
 }
@@ -207,9 +213,10 @@ __device__ __forceinline__ uint32_t clsof(const Tabs &T, uint32_t b) {
 __host__ __device__ inline size_t tables_smem_bytes(const DevTables &t, int tm) {
     if (tm == TM_GLOBAL) return 0;
     size_t a = 256;
-    if (tm == TM_SMEM) {
-        a += ((size_t)t.nf * t.ncls * 2 + 15) & ~(size_t)15;
-        a += ((size_t)t.nb * t.ncls * 2 + 15) & ~(size_t)15;
+    if (tm == TM_SMEM || tm == TM_SMEM8) {
+        const size_t eb = tm == TM_SMEM ? 2 : 1;
+        a += ((size_t)t.nf * t.ncls * eb + 15) & ~(size_t)15;
+        a += ((size_t)t.nb * t.ncls * eb + 15) & ~(size_t)15;
     } else {
         a += (size_t)(t.nf + t.nb) * t.ncls * t.ncls * 4;
         a = (a + 15) & ~(size_t)15;                  // keep the next area 16-byte aligned
@@ -226,6 +233,7 @@ __device__ uint8_t *stage_tables(const DevTables &t, uint8_t *sm, Tabs &T) {
     T.f32 = t.fT;
     T.b32 = t.bT;
     T.f16 = T.b16 = nullptr;
+    T.f8 = T.b8 = nullptr;
     T.f2 = T.b2 = nullptr;
     if (TM == TM_GLOBAL) {
         T.cls = t.cls;
@@ -245,6 +253,18 @@ __device__ uint8_t *stage_tables(const DevTables &t, uint8_t *sm, Tabs &T) {
         T.b16 = b16;
         __syncthreads();
         return reinterpret_cast<uint8_t *>(b16) + ((bsz * 2 + 15) & ~(size_t)15);
+    }
+    if (TM == TM_SMEM8) {
+        uint8_t *f8 = sm + 256;
+        const size_t fsz = (size_t)t.nf * t.ncls;
+        uint8_t *b8 = f8 + ((fsz + 15) & ~(size_t)15);
+        const size_t bsz = (size_t)t.nb * t.ncls;
+        for (size_t i = threadIdx.x; i < fsz; i += blockDim.x) f8[i] = (uint8_t)__ldg(t.fT + i);
+        for (size_t i = threadIdx.x; i < bsz; i += blockDim.x) b8[i] = (uint8_t)__ldg(t.bT + i);
+        T.f8 = f8;
+        T.b8 = b8;
+        __syncthreads();
+        return b8 + ((bsz + 15) & ~(size_t)15);
     }
     const uint32_t nc2 = t.ncls * t.ncls;
     uint32_t *f2 = reinterpret_cast<uint32_t *>(sm + 256);

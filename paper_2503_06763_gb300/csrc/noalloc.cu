@@ -27,8 +27,15 @@ extern "C" re_status re_parse_static(re_handle *h, const uint8_t *d_text, uint64
                                      re_slpf *slpf, const re_parse_opts *opts) {
     if (!h) { slpf::set_error("null handle"); return RE_E_INVALID_ARG; }
     uint64_t need = 0;
-    const re_status ws = re_workspace_size(h, len, opts, &need);
+    re_status ws = re_workspace_size(h, len, opts, &need);
     if (ws != RE_OK) return ws;
+    if (need > RE_STATIC_SCRATCH_BYTES) {
+        // an autotuned chunk length can need more than the built-in rule;
+        // re_parse then falls back to the rule's length, as with any workspace
+        // too small for the tuned layout
+        ws = slpf::workspace_rule_bytes(h, len, opts, &need);
+        if (ws != RE_OK) return ws;
+    }
     if (need > RE_STATIC_SCRATCH_BYTES) {
         slpf::set_error("the text needs " + std::to_string(need) + " bytes of workspace, more than "
                         "RE_STATIC_SCRATCH_BYTES; use re_parse with a caller workspace");

@@ -91,6 +91,7 @@ re_status compile_pattern(const char *pattern, size_t len, const re_compile_opts
                           Compiled &out, std::string &err);
 
 void set_error(const std::string &msg);
+re_status workspace_rule_bytes(const re_handle *h, uint64_t len, const re_parse_opts *opts, uint64_t *bytes);
 
 }  // namespace slpf
 

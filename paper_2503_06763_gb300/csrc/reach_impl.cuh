@@ -82,6 +82,7 @@ __device__ inline uint8_t *stage_reach_pair(const DevTables &t, uint8_t *sm, Tab
     T.cls = sm + kCls;
     T.f16 = f16;
     T.b16 = b16;
+    T.f8 = T.b8 = nullptr;
     T.f32 = t.fT;
     T.b32 = t.bT;
     T.f2 = T.b2 = nullptr;

@@ -241,7 +241,8 @@ class Regex:
         check(load().re_parse(self._h, text_ptr if n else None, n, ctypes.c_void_p(stream_ptr), ctypes.byref(slpf),
                               ws_ptr, ws_bytes, ctypes.byref(opts)))
 
-    def parse_static(self, text, kind: str = "auto", chunk_len: int = 0, stream=None, out=None, status=None):
+    def parse_static(self, text, kind: str = "auto", chunk_len: int = 0, stream=None, out=None, status=None,
+                     recognize_only: bool = False):
         """Like ``parse`` but through re_parse_static: the library's fixed device
         scratch serves as workspace, so only the output tensors are allocated
         here (pass ``out`` and ``status`` to allocate nothing)."""
@@ -254,12 +255,13 @@ class Regex:
         dt = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}[cb]
         s = stream if stream is not None else torch.cuda.current_stream(text.device)
         with torch.cuda.stream(s):                  # outputs allocated on the parse's stream
-            if out is None:
+            if out is None and not recognize_only:  # the recognizer writes no columns
                 out = torch.empty(n + 1, dtype=dt, device=text.device)
             if status is None:
                 status = torch.empty(1, dtype=torch.int32, device=text.device)
-        slpf = Slpf(KINDS[kname], cb, 0, out.data_ptr(), out.numel() * out.element_size(), status.data_ptr())
-        opts = ParseOpts(KINDS[kname], chunk_len, 0, 0, None)
+        slpf = Slpf(KINDS[kname], cb, 0, out.data_ptr() if out is not None else None,
+                    out.numel() * out.element_size() if out is not None else 0, status.data_ptr())
+        opts = ParseOpts(KINDS[kname], chunk_len, RE_PARSE_RECOGNIZE_ONLY if recognize_only else 0, 0, None)
         check(load().re_parse_static(self._h, text.data_ptr() if n else None, n, ctypes.c_void_p(s.cuda_stream),
                                      ctypes.byref(slpf), ctypes.byref(opts)))
         return out, status, kname

@@ -51,6 +51,7 @@ def check(rx, pattern, host, kind="auto", chunk_len=0):
     assert got.shape == want.shape
     bad = np.nonzero(np.any(got != want, axis=1))[0]
     assert bad.size == 0, f"{bad.size} columns differ, first at r={bad[:5].tolist()}"
+    return st
 
 
 SIZES = [0, 1, 2, 63, 64, 65, 127, 1000, 4097, 20000]
@@ -74,16 +75,74 @@ def test_dna(lib, n, chunk_len):
         check(rx, W.DNA_RE, x, kind="dense", chunk_len=chunk_len)
 
 
-@pytest.mark.parametrize("pattern", ["(ab|a)*", "(a|ab|aba)+", "(a|b)*a(a|b){3}", "((ab)*c|a(bc)*)*",
-                                     "[ab]([^b]|bb)*", "(aa)*", "(a|b)*(aaa|bbb)(a|b)*",
-                                     "((a|b){1,3}|c{1,2})*", "(a{0,2}b|a|c)*", "((a|b){2,}|a|b|c)*"])
-def test_fixed_res_random_texts(lib, pattern):
+def _ab(rng, lo, hi):
+    return "".join(rng.choice(["a", "b"]) for _ in range(int(rng.integers(lo, hi + 1))))
+
+
+# Texts in each RE's language, built from its own structure: a prefix, then
+# pieces of the top-level iteration until about n bytes, then a suffix.
+FIXED_RES = {
+    "(ab|a)*": (lambda r: "", lambda r: str(r.choice(["ab", "a"])), lambda r: ""),
+    "(a|ab|aba)+": (lambda r: "aba", lambda r: str(r.choice(["a", "ab", "aba"])), lambda r: ""),
+    "(a|b)*a(a|b){3}": (lambda r: "", lambda r: str(r.choice(["a", "b"])), lambda r: "a" + _ab(r, 3, 3)),
+    "((ab)*c|a(bc)*)*": (lambda r: "", lambda r: ("ab" * int(r.integers(0, 4)) + "c") if r.random() < 0.5
+                         else ("a" + "bc" * int(r.integers(0, 4))), lambda r: ""),
+    "[ab]([^b]|bb)*": (lambda r: str(r.choice(["a", "b"])), lambda r: str(r.choice(["a", "c", "bb"])),
+                       lambda r: ""),
+    "(aa)*": (lambda r: "", lambda r: "aa", lambda r: ""),
+    "(a|b)*(aaa|bbb)(a|b)*": (lambda r: "", lambda r: str(r.choice(["a", "b"])),
+                              lambda r: str(r.choice(["aaa", "bbb"])) + _ab(r, 0, 5)),
+    "((a|b){1,3}|c{1,2})*": (lambda r: "", lambda r: _ab(r, 1, 3) if r.random() < 0.7
+                             else "c" * int(r.integers(1, 3)), lambda r: ""),
+    "(a{0,2}b|a|c)*": (lambda r: "", lambda r: str(r.choice(["a" * int(r.integers(0, 3)) + "b", "a", "c"])),
+                       lambda r: ""),
+    "((a|b){2,}|a|b|c)*": (lambda r: "", lambda r: _ab(r, 2, 6) if r.random() < 0.5
+                           else str(r.choice(["a", "b", "c"])), lambda r: ""),
+}
+
+
+def _valid_text(pattern, n, rng):
+    pre, piece, post = FIXED_RES[pattern]
+    parts, total = [pre(rng)], 0
+    total = len(parts[0])
+    while total < n:
+        p = piece(rng)
+        parts.append(p)
+        total += len(p)
+    parts.append(post(rng))
+    return np.frombuffer("".join(parts).encode(), dtype=np.uint8).copy()
+
+
+@pytest.mark.parametrize("pattern", list(FIXED_RES))
+def test_fixed_res_valid_and_corrupted_texts(lib, pattern):
+    """Each RE on texts drawn from its own structure (accepted: the columns
+    carry the parse), and on corrupted copies of them (one byte replaced by a
+    byte the RE has no position for: rejected, every column empty)."""
+    import re
     rx = lib(pattern)
     rng = np.random.Generator(np.random.PCG64(len(pattern)))
+    accepted = rejected = 0
     for n in (0, 1, 100, 777, 5000):
+        x = _valid_text(pattern, n, rng)
+        if n <= 100:                              # independent language check (backtracking: short texts)
+            assert re.fullmatch(pattern.encode(), x.tobytes()), (pattern, n)
+        bad = None
+        for _ in range(20):                       # a one-byte change that leaves the language
+            if not len(x):
+                break
+            y = x.copy()
+            at = int(rng.integers(0, len(y)))
+            y[at] = ord("c") if at == 0 else ord("d")
+            if not serial.accepted(oracle_cols(pattern, y.tobytes())):
+                bad = y
+                break
         for chunk_len in (64, 128, 0):
-            x = rng.choice(np.frombuffer(b"aabbc", dtype=np.uint8), size=n)
-            check(rx, pattern, x, chunk_len=chunk_len)
+            assert check(rx, pattern, x, chunk_len=chunk_len) == 0
+            accepted += 1
+            if bad is not None:
+                assert check(rx, pattern, bad, chunk_len=chunk_len) == 1
+                rejected += 1
+    assert accepted == 15 and rejected >= 9
 
 
 def test_unconverged_parity_chunks(lib):
