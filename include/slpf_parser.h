@@ -58,8 +58,9 @@ typedef enum {
  *           ell <= 64.  Segment ids are the canonical order reported by
  *           re_segment_name.
  *   DICT  : column r is an index into the handle's column dictionary
- *           (re_dict_copy); index 0 is the empty column.  col_bytes = 2 when
- *           the dictionary has fewer than 65536 entries, else 4.
+ *           (re_dict_copy); index 0 is the empty column.  col_bytes = 1 when
+ *           the dictionary has fewer than 255 entries, 2 when it has fewer
+ *           than 65535, else 4.
  *   AUTO  : DENSE when ell <= 16, else DICT when the handle has a
  *           dictionary, else DENSE when ell <= 64.                            */
 typedef enum { RE_SLPF_AUTO = 0, RE_SLPF_DENSE = 1, RE_SLPF_DICT = 2 } re_slpf_kind;

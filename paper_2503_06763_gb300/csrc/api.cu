@@ -168,7 +168,7 @@ re_status resolve_kind(const re_handle *h, re_slpf_kind kind, re_slpf_kind &out,
         cb = C.ell <= 8 ? 1 : C.ell <= 16 ? 2 : C.ell <= 32 ? 4 : 8;
     } else if (kind == RE_SLPF_DICT) {
         if (!C.has_dict) { set_error("this RE has no column dictionary (too many state pairs)"); return RE_E_CAPACITY; }
-        cb = C.dict_size < 65535 ? 2 : 4;
+        cb = C.dict_size < 255 ? 1 : C.dict_size < 65535 ? 2 : 4;
     } else {
         set_error("unknown SLPF kind");
         return RE_E_INVALID_ARG;

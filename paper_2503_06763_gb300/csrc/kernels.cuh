@@ -149,7 +149,8 @@ __device__ inline void empty_text(const Params &p) {
     if (!p.out) return;
     if (p.kind == RE_SLPF_DICT) {
         const uint32_t d = meet ? t.pt[(size_t)t.fI * t.nb + t.bF] : 0u;
-        if (p.col_bytes == 2) reinterpret_cast<uint16_t *>(p.out)[0] = (uint16_t)d;
+        if (p.col_bytes == 1) reinterpret_cast<uint8_t *>(p.out)[0] = (uint8_t)d;
+        else if (p.col_bytes == 2) reinterpret_cast<uint16_t *>(p.out)[0] = (uint16_t)d;
         else reinterpret_cast<uint32_t *>(p.out)[0] = d;
     } else {
         switch (p.col_bytes) {

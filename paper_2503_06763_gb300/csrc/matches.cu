@@ -27,8 +27,9 @@ namespace {
 template <int W>
 __device__ __forceinline__ void load_column(const MatchArgs &a, uint64_t r, uint64_t (&v)[W]) {
     if (a.kind == RE_SLPF_DICT) {
-        const uint32_t id = a.col_bytes == 2 ? __ldg(reinterpret_cast<const uint16_t *>(a.cols) + r)
-                                             : __ldg(reinterpret_cast<const uint32_t *>(a.cols) + r);
+        const uint32_t id = a.col_bytes == 1   ? __ldg(reinterpret_cast<const uint8_t *>(a.cols) + r)
+                            : a.col_bytes == 2 ? __ldg(reinterpret_cast<const uint16_t *>(a.cols) + r)
+                                               : __ldg(reinterpret_cast<const uint32_t *>(a.cols) + r);
 #pragma unroll
         for (int w = 0; w < W; ++w)                          // W rounds a.W up: the rows have stride a.W
             v[w] = (w < (int)a.W && id) ? __ldg(a.dict + (size_t)(id - 1) * a.W + w) : 0ull;

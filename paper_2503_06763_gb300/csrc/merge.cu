@@ -348,10 +348,12 @@ __global__ void __launch_bounds__(kFixupThreads, 4) fixup_batch_kernel(const __g
 }
 
 // ------------------------------------------------------------------ encodings
-enum { ENC_D1 = 1, ENC_D2 = 2, ENC_D4 = 4, ENC_D8 = 8, ENC_X2 = 0x12, ENC_X4 = 0x14 };
+enum { ENC_D1 = 1, ENC_D2 = 2, ENC_D4 = 4, ENC_D8 = 8, ENC_X1 = 0x11, ENC_X2 = 0x12, ENC_X4 = 0x14 };
+constexpr bool is_dict(int E) { return E == ENC_X1 || E == ENC_X2 || E == ENC_X4; }
 
 struct Enc {
     const uint64_t *fbits, *bbits;   // DENSE: segment set of each state (W == 1)
+    const uint8_t *pt8;              // DICT, fewer than 255 columns: pair table in shared memory (u8)
     const uint16_t *pt16;            // DICT: pair table in shared memory (u16)
     const uint32_t *pt32;            // DICT: pair table (u32; shared or global)
     uint32_t nb;
@@ -359,8 +361,9 @@ struct Enc {
 
 template <int E>
 __device__ __forceinline__ uint32_t enc_lo(const Enc &e, uint32_t f, uint32_t b, bool &bad) {
-    if (E == ENC_X2 || E == ENC_X4) {
+    if (is_dict(E)) {
         const uint32_t at = f * e.nb + b;                 // the pair table spans every state pair
+        if (E == ENC_X1 && e.pt8) return e.pt8[at];
         return e.pt16 ? (uint32_t)e.pt16[at] : e.pt32[at];
     }
     return (uint32_t)(e.fbits[f] & e.bbits[b]);
@@ -369,13 +372,13 @@ __device__ __forceinline__ uint64_t enc_d8(const Enc &e, uint32_t f, uint32_t b)
 
 template <int E>
 __device__ __forceinline__ void store_col(void *out, uint64_t r, uint64_t v) {
-    if (E == ENC_D1) reinterpret_cast<uint8_t *>(out)[r] = (uint8_t)v;
+    if (E == ENC_D1 || E == ENC_X1) reinterpret_cast<uint8_t *>(out)[r] = (uint8_t)v;
     else if (E == ENC_D2 || E == ENC_X2) reinterpret_cast<uint16_t *>(out)[r] = (uint16_t)v;
     else if (E == ENC_D4 || E == ENC_X4) reinterpret_cast<uint32_t *>(out)[r] = (uint32_t)v;
     else reinterpret_cast<uint64_t *>(out)[r] = v;
 }
 
-constexpr int bytes_of(int E) { return (E == ENC_X2) ? 2 : (E == ENC_X4) ? 4 : E; }
+constexpr int bytes_of(int E) { return (E == ENC_X1) ? 1 : (E == ENC_X2) ? 2 : (E == ENC_X4) ? 4 : E; }
 
 // Put one column value into a 16-byte vector being assembled (slot k).
 template <int CB>
@@ -630,14 +633,18 @@ __device__ void merge_setup(const DevTables &t0, uint32_t enc_in_smem, uint8_t *
     if (TM != TM_PAIR && !REG) rest += (2 * 32 * kBlockThreads * sizeof(St) + 15) & ~(size_t)15;
     e = Enc{};
     e.nb = t.nb;
-    if (E == ENC_X2 || E == ENC_X4) {
+    if (is_dict(E)) {
         if (enc_in_smem) {
             const size_t cnt = (size_t)t.nf * t.nb;
             const uint32_t nbs = t0.nb;                       // row stride of the device pair table
             auto src = [&](size_t i) -> uint32_t {
                 return REG ? __ldg(t.pt + (i / t.nb) * nbs + i % t.nb) : __ldg(t.pt + i);
             };
-            if (E == ENC_X2) {
+            if (E == ENC_X1) {                                // indices below 255 (0xFF: never produced)
+                uint8_t *pt = rest;
+                for (size_t i = threadIdx.x; i < cnt; i += blockDim.x) pt[i] = (uint8_t)src(i);
+                e.pt8 = pt;
+            } else if (E == ENC_X2) {
                 uint16_t *pt = reinterpret_cast<uint16_t *>(rest);
                 for (size_t i = threadIdx.x; i < cnt; i += blockDim.x) pt[i] = (uint16_t)src(i);
                 e.pt16 = pt;
@@ -818,7 +825,8 @@ void merge_tma(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_c
 template <int TM>
 void merge_enc(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
     if (p.kind == RE_SLPF_DICT) {
-        if (p.col_bytes == 2) merge_tma<TM, ENC_X2>(p, map, s, sm_count);
+        if (p.col_bytes == 1) merge_tma<TM, ENC_X1>(p, map, s, sm_count);
+        else if (p.col_bytes == 2) merge_tma<TM, ENC_X2>(p, map, s, sm_count);
         else merge_tma<TM, ENC_X4>(p, map, s, sm_count);
     } else {
         switch (p.col_bytes) {
@@ -844,7 +852,8 @@ void merge_batch_one(const BatchGroup &b, const Params &like, cudaStream_t s, in
 template <int TM>
 void merge_batch_enc(const BatchGroup &b, const Params &like, cudaStream_t s, int sm_count) {
     if (like.kind == RE_SLPF_DICT) {
-        if (like.col_bytes == 2) merge_batch_one<TM, ENC_X2>(b, like, s, sm_count);
+        if (like.col_bytes == 1) merge_batch_one<TM, ENC_X1>(b, like, s, sm_count);
+        else if (like.col_bytes == 2) merge_batch_one<TM, ENC_X2>(b, like, s, sm_count);
         else merge_batch_one<TM, ENC_X4>(b, like, s, sm_count);
     } else {
         switch (like.col_bytes) {

@@ -338,7 +338,7 @@ class Regex:
         if kind == "dense":
             v = cols.view({1: np.uint8, 2: np.uint16, 4: np.uint32, 8: np.uint64}[cols.dtype.itemsize])
             return v.astype(np.uint64).reshape(-1, 1)
-        idx = cols.view(np.uint16 if cols.dtype.itemsize == 2 else np.uint32).astype(np.int64)
+        idx = cols.view({1: np.uint8, 2: np.uint16, 4: np.uint32}[cols.dtype.itemsize]).astype(np.int64)
         d = self.dictionary()
         table = np.concatenate([np.zeros((1, self.words), dtype=np.uint64), d], axis=0)
         return table[idx]

@@ -82,7 +82,7 @@ def assert_interned_equal(rx, cols, kind, ids, table):
     if missing.size:                                      # an oracle column the GPU encoding cannot express
         used = np.isin(ids, missing)
         assert not used.any(), f"oracle column absent from the GPU encoding at r={np.nonzero(used)[0][:5].tolist()}"
-    got = cols.view(np.uint16 if cols.dtype.itemsize == 2 else np.uint32)
+    got = cols.view({1: np.uint8, 2: np.uint16, 4: np.uint32}[cols.dtype.itemsize])
     step = 1 << 26
     for a in range(0, len(got), step):
         exp = want_id[ids[a:a + step]]

@@ -71,7 +71,9 @@ def test_layout_and_errors(native):
     assert r.layout(100, "auto") == ("dense", 2, 202)
     assert r.layout(100, "dict")[0] == "dict"
     big = native.Regex("([ACGT]|ATG([ACGT][ACGT][ACGT])*(TAA|TAG|TGA))*", host_only=True)
-    assert big.layout(10, "auto") == ("dict", 2, 22)
+    assert big.layout(10, "auto") == ("dict", 2, 22)          # 351 dictionary entries: two bytes
+    small = native.Regex("(a|b)*a(a|b){3}", host_only=True)     # fewer than 255 entries: one byte
+    assert small.info["dict_size"] < 255 and small.layout(10, "dict") == ("dict", 1, 11)
     assert big.layout(10, "dense") == ("dense", 8, 88)
     for bad, code in (("(a", -2), ("a)", -2), ("(a|)*", -3), ("(a*)*", -3), ("a{0}", -2), ("a{3,2}", -2),
                       ("a{2,2}", -2), ("a{,2}", -2), ("a{}", -2), ("a{1,x}", -2), ("a{4097}", -2),
