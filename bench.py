@@ -62,7 +62,8 @@ def parse_args():
     ap.add_argument("--no-extra", action="store_true", help="single mode: skip the DNA line after the log one")
     ap.add_argument("--chunk-len", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "matches", "latency", "ablation"],
+    ap.add_argument("--mode", default="single",
+                    choices=["single", "batch", "serve", "matches", "latency", "ablation", "join"],
                     help="single: one 256 MiB text (default); batch: 4096 texts under 8 random REs; "
                          "serve: Poisson request stream")
     ap.add_argument("--texts", type=int, default=4096, help="batch mode: number of texts")
@@ -400,6 +401,8 @@ def main():
         return latency_mode(args, rank, world, local)
     if args.mode == "ablation":
         return ablation_mode(args, rank, world, local)
+    if args.mode == "join":
+        return join_mode(args, rank, world, local)
 
     import torch
     torch.cuda.set_device(local)
@@ -794,6 +797,53 @@ def ablation_mode(args, rank, world, local):
             "rows": rows}
     if rank == 0:
         print(json.dumps(line))
+
+
+def join_mode(args, rank, world, local):
+    """The join phase (Eq. joiner) on 256 MiB texts: the DNA and log
+    workloads, whose speculative runs meet inside nearly every chunk, and
+    (aa)* on a^n, whose even and odd runs never meet, so every chunk's map
+    depends on its input and the join resolves a chain through all of them.
+    Per-phase times from CUDA events between phases, autotuned chunk length."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2503_06763_gb300 import Regex
+    from paper_2503_06763_gb300.native import PHASES
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.bytes or (256 << 20)
+    steps = max(args.steps, 5)
+    rows = {}
+    cases = (("dna", W.DNA_RE, W.dna_text(n, seed=1)), ("log", W.LOG_RE, W.log_text(n, seed=2)),
+             ("aa_star_on_a^n", "(aa)*", np.full(n, ord("a"), dtype=np.uint8)))
+    for name, pattern, host in cases:
+        rx = Regex(pattern)
+        text = torch.from_numpy(host).to(dev)
+        k = rx.autotune(text)
+        torch.cuda.empty_cache()
+        kind, cb, _ = rx.layout(n, "auto")
+        dt = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}[cb]
+        out = torch.empty(n + 1, dtype=dt, device=dev)
+        st = torch.empty(1, dtype=torch.int32, device=dev)
+        ws = torch.empty(rx.workspace_size(n), dtype=torch.uint8, device=dev)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(PHASES) + 1)] for _ in range(steps)]
+        for _ in range(max(args.warmup, 3)):
+            rx.parse(text, kind=kind, out=out, status=st, workspace=ws)
+        for i in range(steps):
+            rx.parse(text, kind=kind, out=out, status=st, workspace=ws, events=ev[i])
+        torch.cuda.synchronize()
+        ph = {p: round(statistics.median(ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(steps)), 4)
+              for j, p in enumerate(PHASES)}
+        rows[name] = {"status": int(st.item()), "chunk_len": k, "chunks": (n + k - 1) // k, "phase_ms": ph,
+                      "parse_GBps": round(n / (sum(ph.values()) / 1e3) / 1e9, 1)}
+        del text, out, ws
+        torch.cuda.empty_cache()
+    if rank == 0:
+        print(json.dumps({"metric": "join phase ms (Eq. joiner, scan over chunk maps)", "unit": "ms",
+                          "text_bytes": n, "rows": rows,
+                          "join_ratio_to_dna": {k: round(v["phase_ms"]["join"] / rows["dna"]["phase_ms"]["join"], 2)
+                                                for k, v in rows.items()}}))
 
 
 def reference_arm(args, rank, world):

@@ -48,6 +48,7 @@ typedef enum {
     RE_E_TOO_MANY_STATES = -4,     /* automaton exceeds re_compile_opts.max_states */
     RE_E_NOMEM = -5,               /* host or device allocation failed (re_compile only) */
     RE_E_CUDA = -6,                /* CUDA runtime error; see re_last_error() */
+    RE_E_TIMEOUT = -7,             /* status word only: a bounded device wait ran out (the join's grid barrier) */
     RE_E_CAPACITY = -8,            /* an output / workspace buffer is smaller than required */
     RE_E_INTERNAL = -9             /* status word only: a device consistency check failed */
 } re_status;
@@ -109,6 +110,13 @@ typedef struct {
  * only, write the accept / reject status and no columns.                    */
 #define RE_PARSE_RECOGNIZE_ONLY 1u
 
+/* For tests of the join's bounded waits only: one block of the join scan
+ * leaves before its first grid barrier, so the others' waits run out (about a
+ * second) and the status word becomes RE_E_TIMEOUT.  The device stays usable;
+ * the columns of such a parse are unspecified.  No effect when the join runs
+ * as chains (automata with more than 255 classic-DFA states).               */
+#define RE_PARSE_TEST_STALL_JOIN 0x80000000u
+
 /* Output descriptor.  Filled by the caller: kind, col_bytes, d_cols,
  * cols_cap_bytes and d_status; re_slpf_layout gives the sizes.  n_cols is
  * written by re_parse (len + 1).                                            */
@@ -119,7 +127,8 @@ typedef struct {
     void *d_cols;             /* n_cols * col_bytes bytes, written by re_parse: device memory, or
                                  pinned host memory the device addresses (plain stores) */
     uint64_t cols_cap_bytes;  /* capacity of d_cols */
-    int32_t *d_status;        /* device: one re_status word (RE_OK / RE_REJECTED / RE_E_INTERNAL) */
+    int32_t *d_status;        /* device: one re_status word (RE_OK / RE_REJECTED / RE_E_INTERNAL /
+                                 RE_E_TIMEOUT) */
 } re_slpf;
 
 typedef struct {

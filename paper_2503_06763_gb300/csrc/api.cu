@@ -120,7 +120,7 @@ bool output_tensor_map(CUtensorMap &map, void *d_cols, uint32_t cb, uint64_t row
     return r == CUDA_SUCCESS;
 }
 
-constexpr int kArrays = 19;
+constexpr int kArrays = 24;
 
 struct Layout {
     uint32_t k, c, S;
@@ -128,6 +128,9 @@ struct Layout {
     size_t off[kArrays];
     size_t total;
 };
+
+// The join runs as a scan when both classic DFAs fit byte state ids.
+bool scan_join(const re_handle *h) { return h->host.nfd + 1 <= kScanStates && h->host.nbd + 1 <= kScanStates; }
 
 Layout layout_for(const re_handle *h, uint64_t n, uint32_t k) {
     Layout L{};
@@ -145,7 +148,11 @@ Layout layout_for(const re_handle *h, uint64_t n, uint32_t k) {
         c * 4, c * 4,                                     // fhit, bhit
         c * kRecBounds * 4, c * kRecBounds * 4,           // recFc, recBc
         c * kRecEntries * 8, c * kRecEntries * 8,         // recFe, recBe
-        FLAG_COUNT * 4};
+        FLAG_COUNT * 4,
+        scan_join(h) ? 2 * c * (h->host.nfd + 1) : 0,      // fTab
+        scan_join(h) ? 2 * c * (h->host.nbd + 1) : 0,      // bTab
+        scan_join(h) ? 2 * c * 4 : 0, scan_join(h) ? 2 * c * 4 : 0,   // fLink, bLink
+        kScanWords * 4};
     size_t o = 0;
     for (int j = 0; j < kArrays; ++j) {
         L.off[j] = o;
@@ -209,6 +216,9 @@ void carve(Params &p, const Layout &L, uint8_t *w) {
     p.w.recFc = (uint32_t *)(w + L.off[14]); p.w.recBc = (uint32_t *)(w + L.off[15]);
     p.w.recFe = (uint2 *)(w + L.off[16]); p.w.recBe = (uint2 *)(w + L.off[17]);
     p.w.flags = (int32_t *)(w + L.off[18]);
+    p.w.fTab = w + L.off[19]; p.w.bTab = w + L.off[20];
+    p.w.fLink = (uint32_t *)(w + L.off[21]); p.w.bLink = (uint32_t *)(w + L.off[22]);
+    p.w.scan = (uint32_t *)(w + L.off[23]);
 }
 
 // Check one output descriptor against the resolved encoding.
@@ -386,7 +396,10 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     if (!h || !slpf || !slpf->d_status || (len && !d_text)) { set_error("null argument"); return RE_E_INVALID_ARG; }
     if (h->host_only) { set_error("handle was compiled with RE_COMPILE_HOST_ONLY"); return RE_E_INVALID_ARG; }
     if (len && ((uintptr_t)d_text & 15)) { set_error("d_text must be 16-byte aligned"); return RE_E_INVALID_ARG; }
-    if (opts && (opts->flags & ~RE_PARSE_RECOGNIZE_ONLY)) { set_error("unknown parse flags"); return RE_E_INVALID_ARG; }
+    if (opts && (opts->flags & ~(RE_PARSE_RECOGNIZE_ONLY | RE_PARSE_TEST_STALL_JOIN))) {
+        set_error("unknown parse flags");
+        return RE_E_INVALID_ARG;
+    }
     if (opts && opts->n_events && (opts->n_events != RE_PHASE_EVENTS || !opts->events)) {
         set_error("n_events must be 0 or RE_PHASE_EVENTS");
         return RE_E_INVALID_ARG;
@@ -424,6 +437,8 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     p.out = recognize ? nullptr : slpf->d_cols;
     p.col_bytes = cb; p.kind = kind; p.status = slpf->d_status;
     p.recognize = recognize ? 1u : 0u;
+    p.scan = scan_join(h) ? 1u : 0u;
+    p.scan_stall = (opts && (opts->flags & RE_PARSE_TEST_STALL_JOIN)) ? 1u : 0u;
     const DevTables &t = h->dev;
     p.tmode = table_mode(t);
     const size_t tab = tables_smem_bytes(t, p.tmode);
@@ -467,7 +482,7 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
         return RE_E_INTERNAL;
     }
     CUDA_TRY(mark(1), "event");
-    launch_join(p, s);
+    if (!launch_join(p, s, sms)) return cuda_fail(cudaGetLastError(), "join launch");
     CUDA_TRY(mark(2), "event");
     if (!recognize) {
         launch_fixup(p, s, sms);

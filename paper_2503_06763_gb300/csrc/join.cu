@@ -11,6 +11,8 @@
 // neighbour.  A verify pass checks each guessed output against its actual
 // input; the first chunk where the text cannot continue makes the whole text
 // rejected (no accepting run: every clean column is empty).
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace slpf {
@@ -98,6 +100,7 @@ __device__ void classify(const Params &p, bool fwd, uint32_t i) {
         p.w.bkind[i] = gen ? 1u : 0u;
         if (!gen) p.w.BJ[i] = rep;
     }
+    if (gen && p.scan) atomicAdd(p.w.scan + kScanGeneral, 1u);   // the scan has work
 }
 
 __device__ void classify_at(const Params &p, uint32_t i) {
@@ -219,6 +222,7 @@ __device__ void status_of(const Params &p) {
         if (!(b0 && any_and(t.fBits + (size_t)t.fI * t.W, t.bBits + (size_t)b0 * t.W, t.W))) st = RE_REJECTED;
     }
     if (__ldcg(&p.w.flags[FLAG_INTERNAL])) st = RE_E_INTERNAL;
+    if (__ldcg(&p.w.flags[FLAG_TIMEOUT])) st = RE_E_TIMEOUT;
     *p.status = st;
 }
 
@@ -243,6 +247,127 @@ __global__ void join_verify_kernel(const __grid_constant__ Params p) {
 
 __global__ void flags_init_kernel(const __grid_constant__ Params p) {
     if (threadIdx.x < FLAG_COUNT) p.w.flags[threadIdx.x] = threadIdx.x < 2 ? (int32_t)p.c : 0;
+    if (p.scan)
+        for (uint32_t q = threadIdx.x; q < kScanWords; q += blockDim.x) p.w.scan[q] = 0;
+}
+
+// ------------------------------------------------------------------ scan join
+// Eq. (joiner) as a scan.  Chunk i maps its input state J_i to J_{i+1}; a
+// chunk whose live slots all end in one state maps every input that can
+// continue to that state (classify resolves it at once).  Every other chunk
+// gets its map over the classic-DFA states (a byte table; the union of the
+// slot end states the input enters, as eval_chunk computes it), and the
+// chunks are resolved by pointer jumping: chunk i holds the map of the
+// chunk range (l_i, i] and the link l_i; in each round, if chunk l_i is
+// resolved, J_{i+1} = map(J_{l_i + 1}), else the range doubles: map becomes
+// map_i o map_{l_i} and l_i becomes l_{l_i}.  A chain of L chunks resolves in
+// ceil(log2 L) + 1 rounds instead of L dependent steps.  Backward (Ĵ) the same
+// with the chunks taken right to left.  The rounds are separated by a grid
+// barrier of this cooperative launch; each barrier wait is bounded, and a
+// wait that runs out sets the status RE_E_TIMEOUT.
+constexpr uint32_t kResolved = 0xFFFFFFFFu;
+static_assert(kScanGeneral < kScanWords, "scan words");
+
+// All blocks of the grid meet here; false when this block's wait ran out.
+__device__ bool grid_barrier(uint32_t *w) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile uint32_t *gen = w + 1;
+        const uint32_t g = *gen;
+        __threadfence();
+        if (atomicAdd(w, 1u) == gridDim.x - 1) {
+            w[0] = 0;                                   // every other block waits on gen: reset first
+            __threadfence();
+            atomicAdd(w + 1, 1u);
+        } else {
+            uint32_t it = 0;
+            while (*gen == g)
+                if (++it > kWaitLimit) { ok = 0; break; }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// One direction of one chunk in a round.  LANES = 32: a warp, whose lanes
+// share the table work; LANES = 1: one thread (small automata, where the
+// latency of the link reads, not the table, sets the time of a round).
+template <bool FWD, uint32_t LANES>
+__device__ uint32_t scan_step(const Params &p, uint32_t i, uint32_t cur) {
+    const uint32_t lane = LANES == 1 ? 0u : (threadIdx.x & 31), c = p.c, ns = (FWD ? p.t.nfd : p.t.nbd) + 1;
+    uint32_t *link = FWD ? p.w.fLink : p.w.bLink;
+    uint8_t *tab = FWD ? p.w.fTab : p.w.bTab;
+    uint32_t *J = FWD ? p.w.FJ : p.w.BJ;
+    const uint32_t nxt = cur ^ 1u;
+    const uint32_t l = __ldcg(link + (size_t)cur * c + i);
+    if (l == kResolved) {
+        if (lane == 0) link[(size_t)nxt * c + i] = kResolved;
+        return 0;
+    }
+    const uint8_t *Ti = tab + ((size_t)cur * c + i) * ns;
+    const uint32_t ll = __ldcg(link + (size_t)cur * c + l);
+    if (ll == kResolved) {                             // the range's input is known
+        if (lane == 0) {
+            const uint32_t v = __ldcg(J + (FWD ? l + 1 : l));   // output of chunk l
+            J[FWD ? i + 1 : i] = v < ns ? (uint32_t)__ldcg(Ti + v) : 0u;   // v >= ns: no DFA state, rejected
+            link[(size_t)nxt * c + i] = kResolved;
+        }
+        return 0;
+    }
+    const uint8_t *Tl = tab + ((size_t)cur * c + l) * ns;
+    uint8_t *Tn = tab + ((size_t)nxt * c + i) * ns;
+    for (uint32_t S = lane; S < ns; S += LANES) Tn[S] = __ldcg(Ti + __ldcg(Tl + S));
+    if (lane == 0) link[(size_t)nxt * c + i] = ll;
+    return 1;
+}
+
+template <uint32_t LANES>
+__device__ void join_scan(const Params &p) {
+    const uint32_t lane = LANES == 1 ? 0u : (threadIdx.x & 31), upb = blockDim.x / LANES;
+    const uint64_t gw = (uint64_t)blockIdx.x * upb + threadIdx.x / LANES, nw = (uint64_t)gridDim.x * upb;
+    const bool bwd = !p.recognize;
+    // maps of the chunks whose output depends on their input
+    bool bad = false;
+    for (uint64_t i = gw; i < p.c; i += nw) {
+        if (p.w.fkind[i]) {                           // i >= 1: chunk 0 always has one output
+            uint8_t *T = p.w.fTab + i * (p.t.nfd + 1);
+            for (uint32_t S = lane; S <= p.t.nfd; S += LANES)
+                T[S] = (uint8_t)eval_chunk(p, true, (uint32_t)i, S, bad);
+        }
+        if (lane == 0) p.w.fLink[i] = p.w.fkind[i] ? (uint32_t)i - 1 : kResolved;
+        if (!bwd) continue;
+        if (p.w.bkind[i]) {                           // i <= c-2
+            uint8_t *T = p.w.bTab + i * (p.t.nbd + 1);
+            for (uint32_t S = lane; S <= p.t.nbd; S += LANES)
+                T[S] = (uint8_t)eval_chunk(p, false, (uint32_t)i, S, bad);
+        }
+        if (lane == 0) p.w.bLink[i] = p.w.bkind[i] ? (uint32_t)i + 1 : kResolved;
+    }
+    if (bad) atomicExch(&p.w.flags[FLAG_INTERNAL], 1);
+    if (p.scan_stall && blockIdx.x == 0) return;      // test hook: the other blocks' waits run out
+    if (!grid_barrier(p.w.scan)) { atomicExch(&p.w.flags[FLAG_TIMEOUT], 1); return; }
+    for (uint32_t r = 0; r < kScanRounds; ++r) {
+        uint32_t open = 0;
+        for (uint64_t i = gw; i < p.c; i += nw) {
+            open += scan_step<true, LANES>(p, (uint32_t)i, r & 1);
+            if (bwd) open += scan_step<false, LANES>(p, (uint32_t)i, r & 1);
+        }
+        if (LANES == 1) open = __reduce_add_sync(0xFFFFFFFFu, open);
+        if ((threadIdx.x & 31) == 0 && open) atomicAdd(p.w.scan + 2 + r, open);
+        if (!grid_barrier(p.w.scan)) { atomicExch(&p.w.flags[FLAG_TIMEOUT], 1); return; }
+        if (__ldcg(p.w.scan + 2 + r) == 0) break;     // every chunk resolved (same value in every block)
+    }
+}
+
+__global__ void __launch_bounds__(kBlockThreads) join_scan_kernel(const __grid_constant__ Params p) {
+    // every chunk has one output for every input (the common case): classify
+    // has resolved them all
+    if (__ldcg(p.w.scan + kScanGeneral) == 0 && !p.scan_stall) return;
+    if (p.t.nfd < 16 && p.t.nbd < 16) join_scan<1>(p);   // tables of at most 16 entries: a thread per chunk
+    else join_scan<32>(p);
 }
 
 // ------------------------------------------------------------------ batch
@@ -283,11 +408,33 @@ __global__ void batch_init_kernel(const Params *texts, uint32_t nt, uint32_t *qu
 
 }  // namespace
 
-void launch_join(const Params &p, cudaStream_t s) {
+// Classify, then the scan (a cooperative launch: its blocks meet at grid
+// barriers, so they must all be resident) or the chains, then verify.
+bool launch_join(const Params &p, cudaStream_t s, int sm_count) {
     const uint32_t blocks = (p.c + kBlockThreads - 1) / kBlockThreads;
     launch_dependent(join_classify_kernel, blocks, kBlockThreads, 0, s, p);
-    launch_dependent(join_chain_kernel, blocks, kBlockThreads, 0, s, p);
+    if (p.scan) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, join_scan_kernel, kBlockThreads, 0);
+        const uint64_t units = p.c;                      // a warp (or a thread) per chunk and round
+        const uint64_t want = (units + kBlockThreads / 32 - 1) / (kBlockThreads / 32);
+        const uint32_t grid = (uint32_t)std::max<uint64_t>(
+            1, std::min<uint64_t>(want, (uint64_t)std::max(per_sm, 1) * sm_count));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = kBlockThreads;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, join_scan_kernel, p) != cudaSuccess) return false;
+    } else {
+        launch_dependent(join_chain_kernel, blocks, kBlockThreads, 0, s, p);
+    }
     launch_dependent(join_verify_kernel, blocks, kBlockThreads, 0, s, p);
+    return true;
 }
 
 void launch_flags_init(const Params &p, cudaStream_t s) { flags_init_kernel<<<1, 32, 0, s>>>(p); }

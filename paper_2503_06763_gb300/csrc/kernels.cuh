@@ -28,7 +28,15 @@ constexpr uint32_t kFixupThreads = 256;     // fix-up blocks: one thread per chu
 constexpr uint32_t kRecBounds = 32;   // boundaries recorded per chunk and direction before runs meet
 constexpr uint32_t kRecEntries = 96;  // (state, slot set) entries recorded per chunk and direction
 
-enum Flag { FLAG_FFAIL = 0, FLAG_BFAIL = 1, FLAG_INTERNAL = 2, FLAG_DONE = 3, FLAG_COUNT = 4 };
+enum Flag { FLAG_FFAIL = 0, FLAG_BFAIL = 1, FLAG_INTERNAL = 2, FLAG_DONE = 3, FLAG_TIMEOUT = 4, FLAG_COUNT = 5 };
+
+// Join as a scan over chunk maps (join.cu): used when both classic DFAs have
+// at most kScanStates states (ids fit a byte), so a chunk's map over them is
+// a byte table.
+constexpr uint32_t kScanStates = 256;
+constexpr uint32_t kScanRounds = 40;        // pointer-jumping rounds (chains up to 2^40 chunks)
+constexpr uint32_t kScanWords = 64;         // barrier words + per-round counters
+constexpr uint32_t kScanGeneral = 2 + kScanRounds;   // scan word: chunks whose output depends on their input
 
 struct Work {                       // device workspace, carved from the caller's buffer
     uint32_t *Rf, *Rb;              // [c][msf], [c][msb] end state of each speculation slot
@@ -41,6 +49,9 @@ struct Work {                       // device workspace, carved from the caller'
     uint32_t *recFc, *recBc;        // [c][kRecBounds] runs recorded at each boundary
     uint2 *recFe, *recBe;           // [c][kRecEntries] (state, slot set) of those runs
     int32_t *flags;                 // [FLAG_COUNT]
+    uint8_t *fTab, *bTab;           // [2][c][nfd+1], [2][c][nbd+1]: maps of chunk ranges (scan join)
+    uint32_t *fLink, *bLink;        // [2][c]: chunk whose output feeds the range's map (scan join)
+    uint32_t *scan;                 // [kScanWords]: grid barrier and per-round counters (scan join)
 };
 
 struct Params {
@@ -54,6 +65,8 @@ struct Params {
     uint32_t col_bytes, kind;       // output encoding (re_slpf_kind)
     int32_t *status;
     uint32_t recognize;             // forward reach + join only
+    uint32_t scan;                  // join by the pointer-jumping scan (else chains, one thread each)
+    uint32_t scan_stall;            // test hook: one block of the scan never reaches its first barrier
     uint32_t tmode;                 // TM_GLOBAL / TM_SMEM / TM_PAIR (see Tabs)
     uint32_t enc_in_smem;           // encoder table (DICT pair table, DENSE bitsets) in shared memory
     uint32_t merge_reg;             // one-byte tables: build & merge stages the classic-DFA rows and the
@@ -394,7 +407,7 @@ __host__ __device__ inline DevTables dfa_tables(const DevTables &t) {
     return c;
 }
 bool launch_reach(const Params &p, const CUtensorMap &text_map, cudaStream_t s, uint32_t ms, int sm_count);
-void launch_join(const Params &p, cudaStream_t s);
+bool launch_join(const Params &p, cudaStream_t s, int sm_count);
 void launch_fixup(const Params &p, cudaStream_t s, int sm_count);
 void launch_merge(const Params &p, const CUtensorMap &out_map, cudaStream_t s, int sm_count);
 void launch_empty(const Params &p, cudaStream_t s);

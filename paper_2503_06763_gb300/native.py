@@ -16,12 +16,13 @@ LIB_PATH = os.path.join(HERE, "libslpf.so")
 RE_OK, RE_REJECTED = 0, 1
 STATUS_NAMES = {0: "RE_OK", 1: "RE_REJECTED", -1: "RE_E_INVALID_ARG", -2: "RE_E_SYNTAX",
                 -3: "RE_E_INFINITE_AMBIGUITY", -4: "RE_E_TOO_MANY_STATES", -5: "RE_E_NOMEM",
-                -6: "RE_E_CUDA", -8: "RE_E_CAPACITY", -9: "RE_E_INTERNAL"}
+                -6: "RE_E_CUDA", -7: "RE_E_TIMEOUT", -8: "RE_E_CAPACITY", -9: "RE_E_INTERNAL"}
 KINDS = {"auto": 0, "dense": 1, "dict": 2}
 KIND_NAMES = {0: "auto", 1: "dense", 2: "dict"}
 RE_COMPILE_HOST_ONLY = 1
 RE_COMPILE_DFA_STARTS = 2
 RE_PARSE_RECOGNIZE_ONLY = 1
+RE_PARSE_TEST_STALL_JOIN = 0x80000000     # tests of the join's bounded waits only
 
 EXPORTS = ["re_compile", "re_free", "re_get_info", "re_segment_name", "re_dict_copy",
            "re_slpf_layout", "re_workspace_size", "re_parse", "re_batch_plan", "re_batch_workspace_size",
@@ -193,7 +194,7 @@ class Regex:
         return b.value
 
     def parse(self, text, kind: str = "auto", chunk_len: int = 0, stream=None, out=None, status=None,
-              workspace=None, recognize_only: bool = False, events=None):
+              workspace=None, recognize_only: bool = False, events=None, extra_flags: int = 0):
         """Enqueue the parse of a CUDA uint8 tensor; returns (cols, status, kind).
 
         ``cols`` is a CUDA tensor of n+1 columns (uint8/int16/int32/int64 view of
@@ -209,8 +210,8 @@ class Regex:
         n = text.numel()
         kname, cb, nbytes = self.layout(n, kind)
         dt = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}[cb]
-        flags = RE_PARSE_RECOGNIZE_ONLY if recognize_only else 0
-        wsz = self.workspace_size(n, chunk_len, flags)
+        flags = (RE_PARSE_RECOGNIZE_ONLY if recognize_only else 0) | extra_flags
+        wsz = self.workspace_size(n, chunk_len, flags & RE_PARSE_RECOGNIZE_ONLY)
         s = stream if stream is not None else torch.cuda.current_stream(text.device)
         with torch.cuda.stream(s):
             if out is None and not recognize_only:  # the recognizer writes no columns

@@ -91,17 +91,19 @@ class Server:
         """Per RE: its column encoding (independent of the text length) and a
         bound on a text's workspace for any chunk length of at least 256 (the
         shortest the library picks): 8 bytes of checkpoints per 64 text bytes,
-        the slot ends and run records of every 256-byte chunk, and the
-        alignment of the workspace arrays."""
+        the slot ends, run records and join-scan maps of every 256-byte chunk, and
+        the alignment of the workspace arrays."""
         self._enc, self._ws_chunk = [], []
         for rx in self.regexes:
             kname, cb, _ = rx.layout(1, "auto")
             info = rx.info
             self._enc.append((kname, cb))
-            self._ws_chunk.append(4 * (info["fwd_slots_max"] + info["bwd_slots_max"]) + 64 + 2 * (32 * 4 + 96 * 8))
+            scan = 2 * (info["fwd_dfa_states"] + 1) + 2 * (info["bwd_dfa_states"] + 1) + 16   # join scan maps
+            self._ws_chunk.append(4 * (info["fwd_slots_max"] + info["bwd_slots_max"]) + 64 + 2 * (32 * 4 + 96 * 8)
+                                  + scan)
 
     def ws_bound(self, re_index: int, n: int) -> int:
-        return 8192 + (n // 256 + 1) * self._ws_chunk[re_index] + (n // 64 + 1) * 8
+        return 12288 + (n // 256 + 1) * self._ws_chunk[re_index] + (n // 64 + 1) * 8
 
     def footprint(self, req: Request) -> tuple[int, int, int]:
         """(device bytes, pinned-in bytes, pinned-out bytes) a request needs:
