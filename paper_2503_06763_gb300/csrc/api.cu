@@ -120,7 +120,7 @@ bool output_tensor_map(CUtensorMap &map, void *d_cols, uint32_t cb, uint64_t row
     return r == CUDA_SUCCESS;
 }
 
-constexpr int kArrays = 24;
+constexpr int kArrays = 26;
 
 struct Layout {
     uint32_t k, c, S;
@@ -132,7 +132,19 @@ struct Layout {
 // The join runs as a scan when both classic DFAs fit byte state ids.
 bool scan_join(const re_handle *h) { return h->host.nfd + 1 <= kScanStates && h->host.nbd + 1 <= kScanStates; }
 
-Layout layout_for(const re_handle *h, uint64_t n, uint32_t k) {
+uint32_t table_mode(const DevTables &t);
+
+// Per-position states (mat): one-byte tables staged as u8 for the reach (at
+// most 256 states per direction), so every classic-DFA state fits a byte.
+bool mat_capable(const re_handle *h) {
+    const Compiled &C = h->host;
+    return !h->host_only && table_mode(h->dev) == TM_SMEM && C.nf <= 256 && C.nb <= 256;
+}
+bool mat_for(const re_handle *h, const re_parse_opts *opts) {
+    return mat_capable(h) && !(opts && (opts->flags & RE_PARSE_RECOGNIZE_ONLY));
+}
+
+Layout layout_for(const re_handle *h, uint64_t n, uint32_t k, bool mat) {
     Layout L{};
     L.k = k;
     L.c = (uint32_t)((n + k - 1) / k);
@@ -152,7 +164,8 @@ Layout layout_for(const re_handle *h, uint64_t n, uint32_t k) {
         scan_join(h) ? 2 * c * (h->host.nfd + 1) : 0,      // fTab
         scan_join(h) ? 2 * c * (h->host.nbd + 1) : 0,      // bTab
         scan_join(h) ? 2 * c * 4 : 0, scan_join(h) ? 2 * c * 4 : 0,   // fLink, bLink
-        kScanWords * 4};
+        kScanWords * 4,
+        mat ? (size_t)n + 1 + 128 : 0, mat ? (size_t)n + 1 + 128 : 0};   // FS, BS (one byte per column)
     size_t o = 0;
     for (int j = 0; j < kArrays; ++j) {
         L.off[j] = o;
@@ -219,6 +232,7 @@ void carve(Params &p, const Layout &L, uint8_t *w) {
     p.w.fTab = w + L.off[19]; p.w.bTab = w + L.off[20];
     p.w.fLink = (uint32_t *)(w + L.off[21]); p.w.bLink = (uint32_t *)(w + L.off[22]);
     p.w.scan = (uint32_t *)(w + L.off[23]);
+    p.w.FS = w + L.off[24]; p.w.BS = w + L.off[25];
 }
 
 // Check one output descriptor against the resolved encoding.
@@ -371,7 +385,7 @@ re_status re_workspace_size(const re_handle *h, uint64_t len, const re_parse_opt
     const uint32_t kt = tuned_chunk(const_cast<re_handle *>(h), len, opts);
     const uint32_t k = kt ? kt : choose_chunk(len, sm_count_of(h->device), opts);
     if (k % kSub || k == 0) { set_error("chunk_len must be a positive multiple of 64"); return RE_E_INVALID_ARG; }
-    *bytes = layout_for(h, len, k).total;
+    *bytes = layout_for(h, len, k, mat_for(h, opts)).total;
     return RE_OK;
 }
 
@@ -384,7 +398,7 @@ namespace slpf {
 re_status workspace_rule_bytes(const re_handle *h, uint64_t len, const re_parse_opts *opts, uint64_t *bytes) {
     const uint32_t k = choose_chunk(len, sm_count_of(h->device), opts);
     if (k % kSub || k == 0) { set_error("chunk_len must be a positive multiple of 64"); return RE_E_INVALID_ARG; }
-    *bytes = layout_for(h, len, k).total;
+    *bytes = layout_for(h, len, k, mat_for(h, opts)).total;
     return RE_OK;
 }
 }  // namespace slpf
@@ -420,11 +434,12 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     const int sms = sm_count_of(h->device);
     uint32_t k = choose_chunk(len, sms, opts);
     if (const uint32_t kt = tuned_chunk(h, len, opts)) {      // tuned length, if the workspace holds it
-        if (!len || layout_for(h, len, kt).total <= workspace_bytes) k = kt;
+        if (!len || layout_for(h, len, kt, mat_for(h, opts)).total <= workspace_bytes) k = kt;
     }
     if (k % kSub || k == 0) { set_error("chunk_len must be a positive multiple of 64"); return RE_E_INVALID_ARG; }
     if (len / k >= 0xFFFFFFF0ull) { set_error("text too long for this chunk length"); return RE_E_INVALID_ARG; }
-    const Layout L = layout_for(h, len, k);
+    const bool mat_ws = mat_for(h, opts);                     // the workspace holds FS and BS
+    const Layout L = layout_for(h, len, k, mat_ws);
     if (len && (!d_workspace || workspace_bytes < L.total || ((uintptr_t)d_workspace & 255))) {
         set_error("workspace missing, too small or not 256-byte aligned");
         return RE_E_CAPACITY;
@@ -466,6 +481,18 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     std::memset(&text_map, 0, sizeof(text_map));
     p.c_full = (uint32_t)(len / k);
     p.text_tma = text_tensor_map(text_map, d_text, k, p.c_full) ? 1u : 0u;
+    // Per-position states: the reach writes them, the fix-up fills the heads,
+    // build & merge gathers (when the gather's encoder fits shared memory).
+    alignas(64) StateMaps smaps;
+    std::memset(&smaps, 0, sizeof(smaps));
+    if (mat_ws && len && mat_gather_smem(p) <= kSmemMergeMax) {
+        p.mat = 1;
+        uint8_t *w = (uint8_t *)d_workspace;
+        const bool maps = p.text_tma && text_tensor_map(smaps.f, w + L.off[24], k, p.c_full) &&
+                          text_tensor_map(smaps.b, w + L.off[25], k, p.c_full);
+        if (!maps) p.text_tma = 0;                            // state rows and text tiles use the same path
+        p.state_tma = p.text_tma;
+    }
     auto mark = [&](int j) -> cudaError_t { return ev ? cudaEventRecord(ev[j], s) : cudaSuccess; };
     if (len == 0) {
         CUDA_TRY(mark(0), "event");
@@ -477,7 +504,7 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     carve(p, L, (uint8_t *)d_workspace);
     CUDA_TRY(mark(0), "event");
     launch_flags_init(p, s);
-    if (!launch_reach(p, text_map, s, std::max(t.msf, recognize ? 1u : t.msb), sms)) {
+    if (!launch_reach(p, text_map, smaps, s, std::max(t.msf, recognize ? 1u : t.msb), sms)) {
         set_error("too many speculative starts");
         return RE_E_INTERNAL;
     }
@@ -512,7 +539,7 @@ extern "C" re_status re_autotune(re_handle *h, const uint8_t *d_text, uint64_t l
         uint64_t k = (uint64_t)k0 * num / 4;
         k = std::max<uint64_t>(256, (k + kSub - 1) / kSub * kSub);
         if (k > (1u << 20) || std::find(cand.begin(), cand.end(), (uint32_t)k) != cand.end()) continue;
-        if (layout_for(h, len, (uint32_t)k).total > workspace_bytes) continue;
+        if (layout_for(h, len, (uint32_t)k, mat_for(h, opts)).total > workspace_bytes) continue;
         cand.push_back((uint32_t)k);
     }
     if (cand.empty()) { set_error("workspace too small for any candidate chunk length"); return RE_E_CAPACITY; }
@@ -782,7 +809,7 @@ re_status re_batch_plan(re_handle *const *hs, const uint64_t *lens, uint32_t cou
         re_batch::Text &t = b->texts[j];
         t.k = batch_chunk(t.len, gbytes[t.group], b->sms, opts);
         if (t.len / t.k >= 0xFFFFFFF0ull) { set_error("text too long for this chunk length"); return RE_E_INVALID_ARG; }
-        if (t.len) t.L = layout_for(b->groups[t.group].h, t.len, t.k);
+        if (t.len) t.L = layout_for(b->groups[t.group].h, t.len, t.k, false);
     }
     uint32_t slot = 0;                                       // every text's Params, group after group
     for (auto &g : b->groups) {

@@ -49,6 +49,7 @@ struct Work {                       // device workspace, carved from the caller'
     uint32_t *recFc, *recBc;        // [c][kRecBounds] runs recorded at each boundary
     uint2 *recFe, *recBe;           // [c][kRecEntries] (state, slot set) of those runs
     int32_t *flags;                 // [FLAG_COUNT]
+    uint8_t *FS, *BS;               // [n+1+pad] per-position forward / backward states (mat), one byte each
     uint8_t *fTab, *bTab;           // [2][c][nfd+1], [2][c][nbd+1]: maps of chunk ranges (scan join)
     uint32_t *fLink, *bLink;        // [2][c]: chunk whose output feeds the range's map (scan join)
     uint32_t *scan;                 // [kScanWords]: grid barrier and per-round counters (scan join)
@@ -67,6 +68,9 @@ struct Params {
     uint32_t recognize;             // forward reach + join only
     uint32_t scan;                  // join by the pointer-jumping scan (else chains, one thread each)
     uint32_t scan_stall;            // test hook: one block of the scan never reaches its first barrier
+    uint32_t mat;                   // reach writes every position's state once its runs have met; the
+                                    // fix-up fills the positions before; build & merge is a gather
+    uint32_t state_tma;             // reach stores its state rows through TMA (mat)
     uint32_t tmode;                 // TM_GLOBAL / TM_SMEM / TM_PAIR (see Tabs)
     uint32_t enc_in_smem;           // encoder table (DICT pair table, DENSE bitsets) in shared memory
     uint32_t merge_reg;             // one-byte tables: build & merge stages the classic-DFA rows and the
@@ -76,6 +80,12 @@ struct Params {
     uint32_t text_tma;              // reach reads full chunks through TMA tiles
     uint32_t c_full;                // chunks of exactly k bytes (rows of the text tensor map)
     uint64_t Gfast;                 // groups g with 64g + 64 <= n (computed on the fast path)
+};
+
+// TMA maps of the per-position state arrays FS and BS (mat): rows of k
+// positions (one chunk), boxes of 32 rows x 64 positions, SWIZZLE_64B.
+struct StateMaps {
+    CUtensorMap f, b;
 };
 
 // Texts of one batch that share one compiled RE (re_parse_batch).  Every
@@ -344,6 +354,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t ph) {
 constexpr uint32_t kWaitLimit = 1u << 22;   // try_wait rounds before a wait is declared lost
 // The bulk groups of this thread have finished reading shared memory.
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// At most one bulk group of this thread still reads shared memory.
+__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 // The bulk groups of this thread have completed.
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
@@ -396,6 +408,7 @@ inline void allow_smem(K kernel, uint64_t *done, int bytes = 200 * 1024) {
 
 size_t merge_extra_smem(const Params &p);
 size_t merge_smem_bytes(const Params &p);
+size_t mat_gather_smem(const Params &p);
 // The classic-DFA part of the tables: forward states 0 .. nfd (the DFA states
 // reachable from I get the first ids, and transitions from them stay among
 // them), reverse states 0 .. nbd.  Build & merge only meets these states: its
@@ -406,7 +419,8 @@ __host__ __device__ inline DevTables dfa_tables(const DevTables &t) {
     c.nb = t.nbd + 1;
     return c;
 }
-bool launch_reach(const Params &p, const CUtensorMap &text_map, cudaStream_t s, uint32_t ms, int sm_count);
+bool launch_reach(const Params &p, const CUtensorMap &text_map, const StateMaps &smaps, cudaStream_t s, uint32_t ms,
+                  int sm_count);
 bool launch_join(const Params &p, cudaStream_t s, int sm_count);
 void launch_fixup(const Params &p, cudaStream_t s, int sm_count);
 void launch_merge(const Params &p, const CUtensorMap &out_map, cudaStream_t s, int sm_count);

@@ -786,6 +786,164 @@ __global__ void __launch_bounds__(kBlockThreads, 3) merge_batch_kernel(const __g
     }
 }
 
+// ------------------------------------------------------------------ per-position states (mat)
+// Fix-up: the positions the reach could not give.  Forward, columns 0 ..
+// 64 fv - 1 of chunk i (fv: the first block the reach walked with one run),
+// walked from the exact J_i; backward, columns len - 1 .. 64 bv, walked from
+// the exact Ĵ_{i+1} (bv: the blocks below it were walked with one run).
+// Eq. (builder) from the join's exact boundary states, one thread per chunk
+// and direction, with the classic-DFA rows of the one-byte tables.
+template <int TM>
+__global__ void __launch_bounds__(kFixupThreads) fixup_mat_kernel(const __grid_constant__ Params p) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    __shared__ int ok;
+    Tabs T;
+    stage_tables<TM>(dfa_tables(p.t), sm, T);
+    pdl_wait();
+    pdl_trigger();
+    if (threadIdx.x == 0) ok = *p.status == RE_OK;
+    __syncthreads();
+    if (!ok) return;                                            // rejected: build & merge writes zeros
+    const uint64_t items = 2 * (uint64_t)p.c;
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < items;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        const bool fwd = j < p.c;
+        const uint32_t i = (uint32_t)(fwd ? j : j - p.c);
+        const uint64_t base = (uint64_t)i * p.k;
+        const uint32_t len = chunk_len(p, i);
+        const uint32_t nfs = p.t.nfd + 1, nbs = p.t.nbd + 1;  // the staged rows
+        // states go out 16 at a time (16-byte stores; base is a multiple of 64)
+        if (fwd) {
+            const uint32_t fv = p.w.fconv[i];
+            const uint32_t end = max(1u, min(64u * fv, len));  // columns [0, end)
+            uint32_t st = p.w.FJ[i];
+            if (st >= nfs) st = 0;                              // never for an accepted text
+            for (uint32_t g = 0; g < end; g += 16) {
+                uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {                  // column g + u: the state before byte g + u
+                    w[u >> 2] |= (st & 0xFFu) << (8 * (u & 3));
+                    if (g + u + 1 < end) st = fnext<TM>(T, st, clsof<TM>(T, __ldg(p.x + base + g + u)));
+                }
+                if (g + 16 <= end) {
+                    *reinterpret_cast<uint4 *>(p.w.FS + base + g) = make_uint4(w[0], w[1], w[2], w[3]);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 16; ++u)
+                        if (g + u < end) p.w.FS[base + g + u] = (uint8_t)(w[u >> 2] >> (8 * (u & 3)));
+                }
+            }
+            if (i == p.c - 1) p.w.FS[p.n] = (uint8_t)p.w.FJ[p.c];
+        } else {
+            const uint32_t lo = 64u * p.w.bconv[i];            // columns [lo, len)
+            uint32_t st = p.w.BJ[i + 1];                        // column len
+            if (st >= nbs) st = 0;
+            const uint32_t top = (len + 15) & ~15u;             // 16-column groups, from the top
+            for (uint32_t g = top; g > lo; g -= 16) {
+                const uint32_t g0 = g - 16;                     // columns g0 .. g0 + 15
+                uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+                for (int u = 15; u >= 0; --u) {                 // column g0 + u: after consuming byte g0 + u
+                    if (g0 + u < len) st = bnext<TM>(T, st, clsof<TM>(T, __ldg(p.x + base + g0 + u)));
+                    w[u >> 2] |= (st & 0xFFu) << (8 * (u & 3));
+                }
+                if (g0 + 16 <= len && g0 >= lo) {
+                    *reinterpret_cast<uint4 *>(p.w.BS + base + g0) = make_uint4(w[0], w[1], w[2], w[3]);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 16; ++u)
+                        if (g0 + u < len && g0 + u >= lo) p.w.BS[base + g0 + u] = (uint8_t)(w[u >> 2] >> (8 * (u & 3)));
+                }
+            }
+            if (i == p.c - 1) p.w.BS[p.n] = (uint8_t)p.w.BJ[p.c];
+        }
+    }
+}
+
+// Build & merge from the stored states: C_r = B_r ∩ B̂_r (Eq. merger) for
+// every column, encoded (DENSE bitset, or DICT index through the pair table
+// over classic-DFA state pairs).  A thread takes 16 consecutive columns: two
+// 16-byte state loads, 16 encoder lookups in shared memory, one vector store.
+template <int E>
+__global__ void __launch_bounds__(kBlockThreads) merge_gather_kernel(const __grid_constant__ Params p) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    constexpr int CB = bytes_of(E);
+    const uint32_t nfs = p.t.nfd + 1, nbs = p.t.nbd + 1;
+    Enc e{};
+    e.nb = nbs;
+    if constexpr (is_dict(E)) {
+        const size_t cnt = (size_t)nfs * nbs;
+        for (size_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+            const uint32_t v = __ldg(p.t.pt + (q / nbs) * p.t.nb + q % nbs);
+            if (E == ENC_X1) sm[q] = (uint8_t)v;
+            else if (E == ENC_X2) reinterpret_cast<uint16_t *>(sm)[q] = (uint16_t)v;
+            else reinterpret_cast<uint32_t *>(sm)[q] = v;
+        }
+        if (E == ENC_X1) e.pt8 = sm;
+        else if (E == ENC_X2) e.pt16 = reinterpret_cast<uint16_t *>(sm);
+        else e.pt32 = reinterpret_cast<uint32_t *>(sm);
+    } else {
+        uint64_t *fb = reinterpret_cast<uint64_t *>(sm), *bb = fb + nfs;
+        for (uint32_t q = threadIdx.x; q < nfs; q += blockDim.x) fb[q] = __ldg(p.t.fBits + q);
+        for (uint32_t q = threadIdx.x; q < nbs; q += blockDim.x) bb[q] = __ldg(p.t.bBits + q);
+        e.fbits = fb;
+        e.bbits = bb;
+    }
+    __syncthreads();
+    pdl_wait();
+    const bool ok = *p.status == RE_OK;
+    bool bad = false;
+    const uint64_t ncol = p.n + 1, full = ncol / 16;
+    // full units of 16 columns: every index static, so the values stay in registers
+    for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < full;
+         u += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t r0 = 16 * u;
+        uint32_t fw[4] = {0, 0, 0, 0}, bw[4] = {0, 0, 0, 0};
+        if (ok) {
+            const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(p.w.FS + r0));
+            const uint4 b = __ldcs(reinterpret_cast<const uint4 *>(p.w.BS + r0));
+            fw[0] = a.x; fw[1] = a.y; fw[2] = a.z; fw[3] = a.w;
+            bw[0] = b.x; bw[1] = b.y; bw[2] = b.z; bw[3] = b.w;
+        }
+        uint32_t ow[CB * 4];                                    // 16 columns of CB bytes
+#pragma unroll
+        for (int k = 0; k < CB * 4; ++k) ow[k] = 0;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const uint32_t f = (fw[k >> 2] >> (8 * (k & 3))) & 0xFFu, b = (bw[k >> 2] >> (8 * (k & 3))) & 0xFFu;
+            uint64_t v = 0;
+            if (ok) {
+                if (f >= nfs || b >= nbs) bad = true;
+                else v = enc_col<TM_SMEM, E>(e, f, b, bad);
+            }
+            if constexpr (CB == 8) {
+                ow[2 * k] = (uint32_t)v;
+                ow[2 * k + 1] = (uint32_t)(v >> 32);
+            } else if constexpr (CB == 4) {
+                ow[k] = (uint32_t)v;
+            } else {
+                constexpr uint32_t m = (1u << (8 * CB)) - 1;
+                ow[(k * CB) >> 2] |= ((uint32_t)v & m) << (8 * ((k * CB) & 3));
+            }
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(p.out) + r0 * CB);
+#pragma unroll
+        for (int q = 0; q < CB; ++q) __stcs(dst + q, make_uint4(ow[4 * q], ow[4 * q + 1], ow[4 * q + 2], ow[4 * q + 3]));
+    }
+    // the last columns (fewer than 16), one at a time
+    if (blockIdx.x == 0 && threadIdx.x < ncol - 16 * full) {
+        const uint64_t r = 16 * full + threadIdx.x;
+        uint64_t v = 0;
+        if (ok) {
+            const uint32_t f = p.w.FS[r], b = p.w.BS[r];
+            if (f >= nfs || b >= nbs) bad = true;
+            else v = enc_col<TM_SMEM, E>(e, f, b, bad);
+        }
+        store_col<E>(p.out, r, v);
+    }
+    if (bad) atomicExch(p.status, RE_E_INTERNAL);
+}
+
 __global__ void empty_text_kernel(const __grid_constant__ Params p) { empty_text(p); }
 
 template <typename K>
@@ -886,7 +1044,49 @@ void fixup_one(const Params &p, cudaStream_t s, int sm_count) {
     launch_dependent(fixup_kernel<TM>, blocks, kFixupThreads, smem, s, p);
 }
 
+// Shared memory of the gather's encoder (pair table or bitsets over the
+// classic-DFA states).
+size_t gather_smem(const Params &p) {
+    const size_t nfs = p.t.nfd + 1, nbs = p.t.nbd + 1;
+    return p.kind == RE_SLPF_DICT ? nfs * nbs * p.col_bytes : (nfs + nbs) * 8;
+}
+
+template <int TM>
+void fixup_mat_one(const Params &p, cudaStream_t s, int sm_count) {
+    const size_t smem = tables_smem_bytes(dfa_tables(p.t), TM);
+    static uint64_t attr_done = 0;
+    allow_smem(fixup_mat_kernel<TM>, &attr_done);
+    const int blocks = grid_for(fixup_mat_kernel<TM>, smem, 2 * (uint64_t)p.c, sm_count, kFixupThreads);
+    launch_dependent(fixup_mat_kernel<TM>, blocks, kFixupThreads, smem, s, p);
+}
+
+template <int E>
+void gather_one(const Params &p, cudaStream_t s, int sm_count) {
+    const size_t smem = gather_smem(p);
+    static uint64_t attr_done = 0;
+    allow_smem(merge_gather_kernel<E>, &attr_done);
+    const int blocks = grid_for(merge_gather_kernel<E>, smem, (p.n + 16) / 16, sm_count, kBlockThreads);
+    launch_dependent(merge_gather_kernel<E>, blocks, kBlockThreads, smem, s, p);
+}
+
+void launch_gather(const Params &p, cudaStream_t s, int sm_count) {
+    if (p.kind == RE_SLPF_DICT) {
+        if (p.col_bytes == 1) gather_one<ENC_X1>(p, s, sm_count);
+        else if (p.col_bytes == 2) gather_one<ENC_X2>(p, s, sm_count);
+        else gather_one<ENC_X4>(p, s, sm_count);
+    } else {
+        switch (p.col_bytes) {
+            case 1: gather_one<ENC_D1>(p, s, sm_count); break;
+            case 2: gather_one<ENC_D2>(p, s, sm_count); break;
+            case 4: gather_one<ENC_D4>(p, s, sm_count); break;
+            default: gather_one<ENC_D8>(p, s, sm_count); break;
+        }
+    }
+}
+
 }  // namespace
+
+size_t mat_gather_smem(const Params &p) { return gather_smem(p); }
 
 size_t merge_extra_smem(const Params &p) {
     const DevTables t = p.merge_reg ? dfa_tables(p.t) : p.t;
@@ -909,12 +1109,14 @@ size_t merge_smem_bytes(const Params &p) {
 // the longest walk past a chunk's record (a run that stays apart for more
 // boundaries than the record holds), a serial chain of dependent lookups.
 void launch_fixup(const Params &p, cudaStream_t s, int sm_count) {
+    if (p.mat) { fixup_mat_one<TM_SMEM8>(p, s, sm_count); return; }
     if (p.tmode == TM_PAIR) fixup_one<TM_PAIR>(p, s, sm_count);
     else if (p.tmode == TM_SMEM) fixup_one<TM_SMEM>(p, s, sm_count);
     else fixup_one<TM_GLOBAL>(p, s, sm_count);
 }
 
 void launch_merge(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
+    if (p.mat) { launch_gather(p, s, sm_count); return; }
     if (p.tmode == TM_PAIR) merge_enc<TM_PAIR>(p, map, s, sm_count);
     else if (p.tmode == TM_SMEM) merge_enc<TM_SMEM>(p, map, s, sm_count);
     else merge_enc<TM_GLOBAL>(p, map, s, sm_count);

@@ -125,10 +125,17 @@ __device__ __forceinline__ uint32_t cp2_of(const uint8_t *sm, uint32_t w, int k)
 // (64-byte rows, SWIZZLE_64B layout: 16-byte chunk q of row r sits at chunk
 // q ^ ((r >> 1) & 3)), filled by TMA or, for warps TMA cannot serve, by the
 // lanes themselves.
-template <int TM, int MS, bool EDGE, int W, bool FW = true>
+// With OUT (one-byte modes, a lane walking one direction) the lane also
+// writes the state of run 0 at every column of the block into its row of the
+// warp's state tile (same row layout as the text tile): forward, column t is
+// the state before byte t; backward, the state after consuming byte t (right
+// to left).  Columns the lane does not consume keep the state it has there.
+template <int TM, int MS, bool EDGE, int W, bool FW = true, bool OUT = false>
 __device__ __forceinline__ void walk_block(const Params &p, const Tabs &T, const uint8_t *frow, const uint8_t *brow,
                                            uint32_t (&sf)[MS], uint32_t (&sb)[MS], uint32_t wmf, uint32_t wmb,
-                                           bool bwd, int f_lo, int f_hi, int b_lo, int b_hi) {
+                                           bool bwd, int f_lo, int f_hi, int b_lo, int b_hi,
+                                           uint8_t *orow = nullptr) {
+    static_assert(!OUT || TM != TM_PAIR, "state rows need one-byte steps");
     const uint32_t swz = ((threadIdx.x & 31) >> 1) & 3;
 #pragma unroll 1
     for (int q = 0; q < 4; ++q) {
@@ -153,9 +160,11 @@ __device__ __forceinline__ void walk_block(const Params &p, const Tabs &T, const
                 }
             }
         } else {
+            uint32_t ow[4] = {0, 0, 0, 0};                      // OUT: 16 states of this q (forward) or 3-q
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
                 const int tf = 16 * q + u, tb = 63 - tf;
+                if (OUT && FW) ow[u >> 2] |= (sf[0] & 0xFFu) << (8 * (u & 3));
                 if (FW && (!EDGE || (tf >= f_lo && tf < f_hi))) {
                     const uint32_t c = clsof<TM>(T, byte_of(fx, u));
 #pragma unroll
@@ -166,7 +175,11 @@ __device__ __forceinline__ void walk_block(const Params &p, const Tabs &T, const
 #pragma unroll
                     for (int j = 0; j < W; ++j) sb[j] = bnext<TM>(T, sb[j], c);
                 }
+                if (OUT && !FW) ow[(15 - u) >> 2] |= (sb[0] & 0xFFu) << (8 * ((15 - u) & 3));
             }
+            if (OUT)
+                *reinterpret_cast<uint4 *>(orow + ((((uint32_t)(FW ? q : 3 - q)) ^ swz) << 4)) =
+                    make_uint4(ow[0], ow[1], ow[2], ow[3]);
         }
     }
 }
@@ -341,10 +354,17 @@ __device__ __forceinline__ unsigned block_lanes(const Params &p, uint32_t i, uin
     return mask;
 }
 
-template <int TM, int MS, int DIR = DIR_BOTH, bool WIDE = false>
+// MAT: the lane also writes the state of every column of its chunk into FS
+// (forward) or BS (backward), block by block, through the warp's two state
+// tiles (TMA tensor stores, or plain stores where TMA does not serve); rows
+// of blocks walked with more than one live run are written too and are
+// overwritten by the fix-up, which gets here the first (forward) / last
+// (backward) block the lane walked with one run.  No records or checkpoints.
+template <int TM, int MS, int DIR = DIR_BOTH, bool WIDE = false, bool MAT = false>
 __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CUtensorMap *map, Ring &ring,
-                            bool tma) {
+                            bool tma, const CUtensorMap *smap = nullptr, uint8_t *otile = nullptr) {
     static_assert(!WIDE || DIR != DIR_BOTH, "wide lanes walk one direction");
+    static_assert(!MAT || (DIR != DIR_BOTH && TM != TM_PAIR), "state rows: one direction, one-byte steps");
     constexpr bool FW = DIR != DIR_B;
     const DevTables &t = p.t;
     const uint64_t base = (uint64_t)i * p.k;
@@ -397,7 +417,9 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
         }
     }
     bool fconv = mf <= 1 && !(FW && big), bconv = mb <= 1 && !(!FW && big);
+    const bool single0 = FW ? fconv : bconv;                  // one run from the chunk's edge on
     uint32_t fconv_sub = fconv ? 1 : nsub, bconv_sub = bconv ? nsub - 1 : 0;
+    uint32_t obuf = 0;                                        // MAT: state tile being filled (0 / 1)
     uint32_t *fcnt = p.w.recFc + (size_t)i * kRecBounds, *bcnt = p.w.recBc + (size_t)i * kRecBounds;
     uint2 *fent = p.w.recFe + (size_t)i * kRecEntries, *bent = p.w.recBe + (size_t)i * kRecEntries;
     uint32_t fused = 0, bused = 0, fnrec = 0, bnrec = 0;
@@ -413,7 +435,7 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
         if (FW && fb >= 1) {                                // boundary before forward block fb
             if (WIDE && big) {
                 compact_local(xs, xk, mx);
-                if (mx > 1) record_local<true>(fcnt, fent, fused, fnrec, fopen, fb - 1, xs, xk, mx);
+                if (!MAT && mx > 1) record_local<true>(fcnt, fent, fused, fnrec, fopen, fb - 1, xs, xk, mx);
                 if (mx <= (uint32_t)MS) {                     // into the registers
                     big = false;
                     mf = mx;
@@ -425,9 +447,9 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
             } else if (!fconv) {
                 compact<MS>(sf, kf, mf, dead_f);
                 if (mf <= 1) { fconv = true; fconv_sub = fb; }
-                else record<TM, MS, true>(p, T, fcnt, fent, fused, fnrec, fopen, fb - 1, sf, kf, mf);
+                else if (!MAT) record<TM, MS, true>(p, T, fcnt, fent, fused, fnrec, fopen, fb - 1, sf, kf, mf);
             }
-            p.w.FC[(uint64_t)i * p.S + fb] = fconv ? dec_f<TM>(T, sf[0]) : kUnknown;
+            if (!MAT) p.w.FC[(uint64_t)i * p.S + fb] = fconv ? dec_f<TM>(T, sf[0]) : kUnknown;
         }
         const uint64_t fpos = base + 64ull * fb, bpos = base + 64ull * bb;
         const int f_lo = fb == 0 ? tstart : 0;
@@ -445,6 +467,11 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
         const uint8_t *frow = tile_f<DIR>(ring, stage) + lane * 64;
         const uint8_t *brow = tile_b<DIR>(ring, stage) + lane * 64;
         const uint32_t wm = max(wmf, wmb);
+        uint8_t *orow = MAT ? otile + obuf * kTileBytes + lane * 64 : nullptr;
+        if (MAT && tma) {                                     // the store two blocks back has read this tile
+            if (lane == 0) bulk_wait_read_1();
+            __syncwarp();
+        }
         if (edge) {
             if constexpr (TM == TM_PAIR) {              // one byte at a time on state ids
 #pragma unroll
@@ -453,13 +480,40 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
 #pragma unroll
                 for (int j = 0; j < MS; ++j) { sf[j] = enc_f<TM>(T, sf[j]); sb[j] = enc_b<TM>(T, sb[j]); }
             } else {
-                walk_block<TM, MS, true, MS, FW>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, f_lo, f_hi, 0, b_hi);
+                walk_block<TM, MS, true, MS, FW, MAT>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, f_lo, f_hi, 0, b_hi, orow);
             }
         }
-        else if (wm <= 1) walk_block<TM, MS, false, 1, FW>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
-        else if (MS > 2 && wm <= 2) walk_block<TM, MS, false, (MS > 2 ? 2 : MS), FW>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
-        else if (MS > 4 && wm <= 4) walk_block<TM, MS, false, (MS > 4 ? 4 : MS), FW>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
-        else walk_block<TM, MS, false, MS, FW>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63);
+        else if (wm <= 1) walk_block<TM, MS, false, 1, FW, MAT>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63, orow);
+        else if (MS > 2 && wm <= 2) walk_block<TM, MS, false, (MS > 2 ? 2 : MS), FW, MAT>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63, orow);
+        else if (MS > 4 && wm <= 4) walk_block<TM, MS, false, (MS > 4 ? 4 : MS), FW, MAT>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63, orow);
+        else walk_block<TM, MS, false, MS, FW, MAT>(p, T, frow, brow, sf, sb, wmf, wmb, bwd, 0, 64, 0, 63, orow);
+        if (MAT) {                                            // this block's state row
+            const uint32_t ob = FW ? fb : bb;
+            uint8_t *dst = (FW ? p.w.FS : p.w.BS) + base + 64ull * ob;
+            if (tma) {
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    tma_store_2d(smap, smem_u32(otile + obuf * kTileBytes), 64 * ob, (int32_t)i0);
+                    bulk_commit();
+                }
+            } else {                                          // plain stores, clipped to the chunk
+                const uint32_t swz = (lane >> 1) & 3;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t col = 64 * ob + 16 * q;
+                    if (col >= len) break;
+                    const uint4 v = *reinterpret_cast<const uint4 *>(orow + (((uint32_t)q ^ swz) << 4));
+                    if (col + 16 <= len) {
+                        *reinterpret_cast<uint4 *>(dst + 16 * q) = v;
+                    } else {
+                        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+                        for (uint32_t u = 0; u < len - col; ++u) dst[16 * q + u] = (uint8_t)(w[u >> 2] >> (8 * (u & 3)));
+                    }
+                }
+            }
+            obuf ^= 1u;
+        }
         if (WIDE && big) {                                    // this lane's runs past the register arrays
             if (FW) walk_local<TM, true>(T, frow, xs, xk, mx, f_lo, f_hi);
             else walk_local<TM, false>(T, brow, xs, xk, mx, 0, b_hi + 1);
@@ -474,7 +528,7 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
         if (bwd && bb >= 1) {                               // boundary at the start of backward block bb
             if (WIDE && big) {
                 compact_local(xs, xk, mx);
-                if (mx > 1) record_local<false>(bcnt, bent, bused, bnrec, bopen, nsub - 1 - bb, xs, xk, mx);
+                if (!MAT && mx > 1) record_local<false>(bcnt, bent, bused, bnrec, bopen, nsub - 1 - bb, xs, xk, mx);
                 if (mx <= (uint32_t)MS) {                     // into the registers
                     big = false;
                     mb = mx;
@@ -486,9 +540,9 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
             } else if (!bconv) {
                 compact<MS>(sb, kb, mb, dead_b);
                 if (mb <= 1) { bconv = true; bconv_sub = bb; }
-                else record<TM, MS, false>(p, T, bcnt, bent, bused, bnrec, bopen, nsub - 1 - bb, sb, kb, mb);
+                else if (!MAT) record<TM, MS, false>(p, T, bcnt, bent, bused, bnrec, bopen, nsub - 1 - bb, sb, kb, mb);
             }
-            p.w.BC[(uint64_t)i * p.S + bb - 1] = bconv ? dec_b<TM>(T, sb[0]) : kUnknown;
+            if (!MAT) p.w.BC[(uint64_t)i * p.S + bb - 1] = bconv ? dec_b<TM>(T, sb[0]) : kUnknown;
         }
     }
     // end state of every slot: the state of the run standing for it (0 if none)
@@ -507,7 +561,8 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
             }
             p.w.Rf[(size_t)i * msf + j] = v;
         }
-        p.w.fconv[i] = fconv_sub;
+        // MAT: the first block walked with one run (every block from there on is exact)
+        p.w.fconv[i] = MAT ? (single0 ? 0u : fconv_sub) : fconv_sub;
         p.w.fnrec[i] = fnrec;
     }
     if (bwd) {
@@ -524,7 +579,8 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
             }
             p.w.Rb[(size_t)i * msb + j] = v;
         }
-        p.w.bconv[i] = bconv_sub;
+        // MAT: blocks below this one were walked with one run (exact)
+        p.w.bconv[i] = MAT ? (single0 ? nsub : (bconv ? bconv_sub : 0u)) : bconv_sub;
         p.w.bnrec[i] = bnrec;
     }
     return true;
@@ -539,14 +595,16 @@ constexpr uint32_t kSplitThreads = 256;
 // ring), which doubles the warps in flight for the same shared memory; in
 // recognizer mode every warp takes a tile of its own, forward.  Without SPLIT
 // every warp walks its tile in both directions (two tiles per ring stage).
-template <int TM, int MS, bool SPLIT, bool WIDE = false>
+template <int TM, int MS, bool SPLIT, bool WIDE = false, bool MAT = false>
 __global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
-    reach_kernel(const __grid_constant__ Params p, const __grid_constant__ CUtensorMap map) {
+    reach_kernel(const __grid_constant__ Params p, const __grid_constant__ CUtensorMap map,
+                 const __grid_constant__ StateMaps smaps) {
     extern __shared__ __align__(16) uint8_t sm[];
     constexpr int TILES = SPLIT ? 1 : 2;                      // tiles per ring stage
     Tabs T;
     uint8_t *rest = TM == TM_PAIR ? stage_reach_pair(p.t, sm, T) : stage_tables<TM>(p.t, sm, T);
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x / 32;
+    uint8_t *otile = nullptr;
     Ring ring{};
     {
         const uint32_t a = smem_u32(rest);
@@ -554,6 +612,11 @@ __global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
         ring.tiles = aligned + warp * (kStages * TILES * kTileBytes);
         ring.bars = smem_u32(aligned + wpb * (kStages * TILES * kTileBytes)) + warp * kStages * 8;
         ring.phase = 0;
+        if (MAT) {                                            // two state tiles per warp, 1024-byte aligned
+            uint8_t *after = aligned + wpb * (kStages * TILES * kTileBytes + kStages * 8);
+            after += (1024 - (smem_u32(after) & 1023)) & 1023;
+            otile = after + warp * 2 * kTileBytes;
+        }
         if (p.text_tma && lane == 0) {
             for (int st = 0; st < kStages; ++st) mbar_init(ring.bars + 8 * st, 1);
             mbar_init_fence();
@@ -572,8 +635,8 @@ __global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
         if (i >= p.c) continue;                               // lanes past the text (plain path only)
         bool ok;
         if constexpr (!SPLIT) ok = reach_chunk<TM, MS, DIR_BOTH>(p, T, i, &map, ring, tma);
-        else if (backward_warp) ok = reach_chunk<TM, MS, DIR_B, WIDE>(p, T, i, &map, ring, tma);
-        else ok = reach_chunk<TM, MS, DIR_F, WIDE>(p, T, i, &map, ring, tma);
+        else if (backward_warp) ok = reach_chunk<TM, MS, DIR_B, WIDE, MAT>(p, T, i, &map, ring, tma, &smaps.b, otile);
+        else ok = reach_chunk<TM, MS, DIR_F, WIDE, MAT>(p, T, i, &map, ring, tma, &smaps.f, otile);
         if (!ok) {
             atomicExch(p.status, RE_E_INTERNAL);
             atomicExch(&p.w.flags[FLAG_INTERNAL], 1);
@@ -582,9 +645,11 @@ __global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
                 for (uint32_t it = 0; it < kWaitLimit && !done; ++it)
                     done = mbar_try_wait(ring.bars + 8 * st, (ring.phase >> st) & 1u);
             }
+            if (MAT && lane == 0) bulk_wait_all();
             return;
         }
     }
+    if (MAT && lane == 0) bulk_wait_all();                    // state rows written before the grid ends
 }
 
 // Batch: warps take work items from the group's list (an atomic counter).  An
@@ -628,9 +693,11 @@ __global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
     }
 }
 
-inline size_t reach_smem(const DevTables &t, int tm, uint32_t threads = kChunkThreads, int tiles = 2) {
+inline size_t reach_smem(const DevTables &t, int tm, uint32_t threads = kChunkThreads, int tiles = 2,
+                         bool mat = false) {
     const size_t tab = tm == TM_PAIR ? reach_pair_smem(t) : tables_smem_bytes(t, tm);
-    return tab + 1024 + (threads / 32) * (kStages * tiles * kTileBytes + kStages * 8);
+    const size_t out = mat ? 1024 + (threads / 32) * 2 * kTileBytes : 0;   // two state tiles per warp
+    return tab + 1024 + (threads / 32) * (kStages * tiles * kTileBytes + kStages * 8) + out;
 }
 
 template <int TM, int MS, bool SPLIT, bool WIDE = false>
@@ -669,19 +736,19 @@ bool launch_ms_batch(const BatchGroup &b, cudaStream_t s, uint32_t ms, int sm_co
     return true;
 }
 
-template <int TM, int MS, bool SPLIT, bool WIDE = false>
-void launch_split(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
+template <int TM, int MS, bool SPLIT, bool WIDE = false, bool MAT = false>
+void launch_split(const Params &p, const CUtensorMap &map, const StateMaps &smaps, cudaStream_t s, int sm_count) {
     const uint32_t threads = SPLIT ? kSplitThreads : kChunkThreads;
-    const size_t smem = reach_smem(p.t, TM, threads, SPLIT ? 1 : 2);
+    const size_t smem = reach_smem(p.t, TM, threads, SPLIT ? 1 : 2, MAT);
     static uint64_t attr_done = 0;
-    allow_smem(reach_kernel<TM, MS, SPLIT, WIDE>, &attr_done);
+    allow_smem(reach_kernel<TM, MS, SPLIT, WIDE, MAT>, &attr_done);
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_kernel<TM, MS, SPLIT, WIDE>, threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_kernel<TM, MS, SPLIT, WIDE, MAT>, threads, smem);
     const uint64_t warps = ((uint64_t)p.c + 31) / 32 * (SPLIT && !p.recognize ? 2 : 1);
     const uint64_t want = (warps + threads / 32 - 1) / (threads / 32);
     const uint64_t blocks = std::min<uint64_t>(want, (uint64_t)std::max(per_sm, 1) * sm_count);
-    launch_dependent(reach_kernel<TM, MS, SPLIT, WIDE>, (uint32_t)std::max<uint64_t>(blocks, 1), threads, smem, s, p,
-                     map);
+    launch_dependent(reach_kernel<TM, MS, SPLIT, WIDE, MAT>, (uint32_t)std::max<uint64_t>(blocks, 1), threads, smem,
+                     s, p, map, smaps);
 }
 
 // A parse: warp pairs per 32-chunk tile; the recognizer: one forward warp per
@@ -689,12 +756,23 @@ void launch_split(const Params &p, const CUtensorMap &map, cudaStream_t s, int s
 // than 8 slots: wide lanes (4 runs in registers, the rest in local memory
 // until they merge, which they do within the first bytes of most chunks).
 template <int TM>
-bool launch_ms(const Params &p, const CUtensorMap &map, cudaStream_t s, uint32_t ms, int sm_count) {
+bool launch_ms(const Params &p, const CUtensorMap &map, const StateMaps &smaps, cudaStream_t s, uint32_t ms,
+               int sm_count) {
     constexpr bool FULL = TM != TM_GLOBAL;          // fewer instantiations for the rare global mode
-    if (FULL && ms <= 2) launch_split<TM, 2, true>(p, map, s, sm_count);
-    else if (FULL && ms <= 4) launch_split<TM, 4, true>(p, map, s, sm_count);
-    else if (ms <= 8) launch_split<TM, 8, true>(p, map, s, sm_count);
-    else if (ms <= 32) launch_split<TM, 4, true, true>(p, map, s, sm_count);
+    if constexpr (TM == TM_SMEM8) {                 // per-position states (mat) only here
+        if (p.mat) {
+            if (ms <= 2) launch_split<TM, 2, true, false, true>(p, map, smaps, s, sm_count);
+            else if (ms <= 4) launch_split<TM, 4, true, false, true>(p, map, smaps, s, sm_count);
+            else if (ms <= 8) launch_split<TM, 8, true, false, true>(p, map, smaps, s, sm_count);
+            else if (ms <= 32) launch_split<TM, 4, true, true, true>(p, map, smaps, s, sm_count);
+            else return false;
+            return true;
+        }
+    }
+    if (FULL && ms <= 2) launch_split<TM, 2, true>(p, map, smaps, s, sm_count);
+    else if (FULL && ms <= 4) launch_split<TM, 4, true>(p, map, smaps, s, sm_count);
+    else if (ms <= 8) launch_split<TM, 8, true>(p, map, smaps, s, sm_count);
+    else if (ms <= 32) launch_split<TM, 4, true, true>(p, map, smaps, s, sm_count);
     else return false;
     return true;
 }

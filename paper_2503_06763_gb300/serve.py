@@ -103,7 +103,9 @@ class Server:
                                   + scan)
 
     def ws_bound(self, re_index: int, n: int) -> int:
-        return 12288 + (n // 256 + 1) * self._ws_chunk[re_index] + (n // 64 + 1) * 8
+        # + per-position forward and backward states (one byte each, when the
+        # library stores them)
+        return 12288 + (n // 256 + 1) * self._ws_chunk[re_index] + (n // 64 + 1) * 8 + 2 * (n + 1 + 128) + 512
 
     def footprint(self, req: Request) -> tuple[int, int, int]:
         """(device bytes, pinned-in bytes, pinned-out bytes) a request needs:
