@@ -296,6 +296,7 @@ re_status re_compile(const char *pattern, size_t len, const re_compile_opts *opt
     const size_t i_f2 = add(C.f2.data(), C.f2.size() * 4), i_b2 = add(C.b2.data(), C.b2.size() * 4);
     const size_t i_fs = add(C.folseg.data(), C.folseg.size() * 8), i_dc = add(C.dict.data(), C.dict.size() * 8);
     const size_t i_fso = add(C.fSlotOf.data(), C.fSlotOf.size());
+    const size_t i_fby = add(C.fbyte.data(), C.fbyte.size()), i_bby = add(C.bbyte.data(), C.bbyte.size());
     DevTables &t = h->dev;
     t.fHashMask = C.fHashMask; t.bHashMask = C.bHashMask;
     t.ncls = C.ncls; t.W = C.W; t.ell = C.ell;
@@ -326,6 +327,8 @@ re_status re_compile(const char *pattern, size_t len, const re_compile_opts *opt
     t.f2 = C.f2.empty() ? nullptr : (const uint32_t *)(b + pc[i_f2].off);
     t.b2 = C.b2.empty() ? nullptr : (const uint32_t *)(b + pc[i_b2].off);
     t.folseg = (const uint64_t *)(b + pc[i_fs].off);
+    t.fbyte = C.fbyte.empty() ? nullptr : b + pc[i_fby].off;
+    t.bbyte = C.bbyte.empty() ? nullptr : b + pc[i_bby].off;
     t.dict = C.dict.empty() ? nullptr : (const uint64_t *)(b + pc[i_dc].off);
     *out = h;
     return RE_OK;

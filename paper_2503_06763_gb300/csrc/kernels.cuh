@@ -194,11 +194,16 @@ __device__ inline void empty_text(const Params &p) {
 //              consumed, high half after both (used when ncls^2 is small);
 //   TM_SMEM8:  one-byte tables in shared memory as u8 (at most 256 states per
 //              direction; the reach's choice for larger class alphabets, a
-//              quarter of the u32 footprint, so more blocks fit an SM).
+//              quarter of the u32 footprint, so more blocks fit an SM);
+//   TM_BYTE8:  tables indexed by the text byte itself (not its class), u8,
+//              rows of kByteRow bytes (256 entries and 4 of padding, which
+//              puts equal bytes of different states in different banks); a
+//              reach block stages one direction's table (about 65 KB).
 // Row s, column = byte class (or class pair c1*ncls + c2 for the left and
 // right byte of the pair).  A forward pair consumes c1 then c2, a backward
 // pair c2 then c1.
-enum { TM_GLOBAL = 0, TM_SMEM = 1, TM_PAIR = 2, TM_SMEM8 = 3 };
+enum { TM_GLOBAL = 0, TM_SMEM = 1, TM_PAIR = 2, TM_SMEM8 = 3, TM_BYTE8 = 4 };
+constexpr uint32_t kByteRow = 260;
 
 struct Tabs {
     const uint8_t *cls;
@@ -214,6 +219,7 @@ template <int TM>
 __device__ __forceinline__ uint32_t fnext(const Tabs &T, uint32_t s, uint32_t c) {
     if (TM == TM_SMEM) return T.f16[s * T.ncls + c];
     if (TM == TM_SMEM8) return T.f8[s * T.ncls + c];
+    if (TM == TM_BYTE8) return T.f8[s * kByteRow + c];          // c is the byte itself
     if (TM == TM_PAIR) return T.f2[s * T.nc2 + c * T.ncls] & 0xFFFFu;
     return __ldg(T.f32 + (size_t)s * T.ncls + c);
 }
@@ -221,6 +227,7 @@ template <int TM>
 __device__ __forceinline__ uint32_t bnext(const Tabs &T, uint32_t s, uint32_t c) {
     if (TM == TM_SMEM) return T.b16[s * T.ncls + c];
     if (TM == TM_SMEM8) return T.b8[s * T.ncls + c];
+    if (TM == TM_BYTE8) return T.b8[s * kByteRow + c];
     if (TM == TM_PAIR) return T.b2[s * T.nc2 + c] & 0xFFFFu;
     return __ldg(T.b32 + (size_t)s * T.ncls + c);
 }
@@ -229,8 +236,46 @@ __device__ __forceinline__ uint32_t bpair(const Tabs &T, uint32_t s, uint32_t cp
 
 template <int TM>
 __device__ __forceinline__ uint32_t clsof(const Tabs &T, uint32_t b) {
+    if (TM == TM_BYTE8) return b;                               // the tables are indexed by the byte
     if (TM != TM_GLOBAL) return T.cls[b];
     return __ldg(T.cls + b);
+}
+// The byte class itself (slot selection), in every table mode.
+template <int TM>
+__device__ __forceinline__ uint32_t class_of(const Tabs &T, const DevTables &t, uint32_t b) {
+    if (TM == TM_BYTE8) return __ldg(t.cls + b);
+    return clsof<TM>(T, b);
+}
+
+// Stage the byte-indexed tables of the directions asked for (block-wide;
+// ends with __syncthreads).  Returns the end of the used area.
+__device__ inline uint8_t *stage_byte8(const DevTables &t, uint8_t *sm, Tabs &T, bool fwd, bool bwd) {
+    T.ncls = t.ncls;
+    T.nc2 = t.ncls * t.ncls;
+    T.cls = t.cls;
+    T.f32 = t.fT;
+    T.b32 = t.bT;
+    T.f16 = T.b16 = nullptr;
+    T.f2 = T.b2 = nullptr;
+    T.f8 = T.b8 = nullptr;
+    uint8_t *at = sm;
+    for (int d = 0; d < 2; ++d) {
+        if (!(d == 0 ? fwd : bwd)) continue;
+        const uint8_t *src = d == 0 ? t.fbyte : t.bbyte;
+        const uint32_t n = d == 0 ? t.nf : t.nb;
+        uint32_t *dst = reinterpret_cast<uint32_t *>(at);
+        // row s: 64 words of entries, then one word of padding
+        for (uint32_t q = threadIdx.x; q < n * 64; q += blockDim.x)
+            dst[(q >> 6) * (kByteRow / 4) + (q & 63)] = __ldg(reinterpret_cast<const uint32_t *>(src) + q);
+        (d == 0 ? T.f8 : T.b8) = at;
+        at += (((size_t)n * kByteRow) + 15) & ~(size_t)15;
+    }
+    __syncthreads();
+    return at;
+}
+__host__ __device__ inline size_t byte8_smem_bytes(const DevTables &t, bool fwd, bool bwd) {
+    return (fwd ? (((size_t)t.nf * kByteRow) + 15) & ~(size_t)15 : 0) +
+           (bwd ? (((size_t)t.nb * kByteRow) + 15) & ~(size_t)15 : 0);
 }
 
 // Bytes of shared memory used by stage_tables.

@@ -894,27 +894,20 @@ __global__ void __launch_bounds__(kBlockThreads) merge_gather_kernel(const __gri
     const bool ok = *p.status == RE_OK;
     bool bad = false;
     const uint64_t ncol = p.n + 1, full = ncol / 16;
-    // full units of 16 columns: every index static, so the values stay in registers
-    for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < full;
-         u += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t r0 = 16 * u;
-        uint32_t fw[4] = {0, 0, 0, 0}, bw[4] = {0, 0, 0, 0};
-        if (ok) {
-            const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(p.w.FS + r0));
-            const uint4 b = __ldcs(reinterpret_cast<const uint4 *>(p.w.BS + r0));
-            fw[0] = a.x; fw[1] = a.y; fw[2] = a.z; fw[3] = a.w;
-            bw[0] = b.x; bw[1] = b.y; bw[2] = b.z; bw[3] = b.w;
-        }
+    // two units of 16 columns per thread and step (their four 16-byte loads
+    // in flight together); every index static, so the values stay in registers
+    auto unit = [&](uint64_t r0, const uint4 &a, const uint4 &b) {
+        const uint32_t fw[4] = {a.x, a.y, a.z, a.w}, bw[4] = {b.x, b.y, b.z, b.w};
         uint32_t ow[CB * 4];                                    // 16 columns of CB bytes
 #pragma unroll
         for (int k = 0; k < CB * 4; ++k) ow[k] = 0;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-            const uint32_t f = (fw[k >> 2] >> (8 * (k & 3))) & 0xFFu, b = (bw[k >> 2] >> (8 * (k & 3))) & 0xFFu;
+            const uint32_t f = (fw[k >> 2] >> (8 * (k & 3))) & 0xFFu, g = (bw[k >> 2] >> (8 * (k & 3))) & 0xFFu;
             uint64_t v = 0;
             if (ok) {
-                if (f >= nfs || b >= nbs) bad = true;
-                else v = enc_col<TM_SMEM, E>(e, f, b, bad);
+                if (f >= nfs || g >= nbs) bad = true;
+                else v = enc_col<TM_SMEM, E>(e, f, g, bad);
             }
             if constexpr (CB == 8) {
                 ow[2 * k] = (uint32_t)v;
@@ -929,6 +922,32 @@ __global__ void __launch_bounds__(kBlockThreads) merge_gather_kernel(const __gri
         uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(p.out) + r0 * CB);
 #pragma unroll
         for (int q = 0; q < CB; ++q) __stcs(dst + q, make_uint4(ow[4 * q], ow[4 * q + 1], ow[4 * q + 2], ow[4 * q + 3]));
+    };
+    const uint64_t pairs = full / 2;
+    const uint4 zero = make_uint4(0, 0, 0, 0);
+    for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < pairs;
+         u += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t r0 = 32 * u;
+        uint4 a0 = zero, a1 = zero, b0 = zero, b1 = zero;
+        if (ok) {
+            a0 = __ldcs(reinterpret_cast<const uint4 *>(p.w.FS + r0));
+            a1 = __ldcs(reinterpret_cast<const uint4 *>(p.w.FS + r0 + 16));
+            b0 = __ldcs(reinterpret_cast<const uint4 *>(p.w.BS + r0));
+            b1 = __ldcs(reinterpret_cast<const uint4 *>(p.w.BS + r0 + 16));
+        }
+        unit(r0, a0, b0);
+        unit(r0 + 16, a1, b1);
+    }
+    if (full & 1) {                                             // an odd last full unit
+        const uint64_t r0 = 16 * (full - 1);
+        if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+            uint4 a = zero, b = zero;
+            if (ok) {
+                a = __ldcs(reinterpret_cast<const uint4 *>(p.w.FS + r0));
+                b = __ldcs(reinterpret_cast<const uint4 *>(p.w.BS + r0));
+            }
+            unit(r0, a, b);
+        }
     }
     // the last columns (fewer than 16), one at a time
     if (blockIdx.x == 0 && threadIdx.x < ncol - 16 * full) {

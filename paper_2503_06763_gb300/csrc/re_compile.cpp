@@ -821,6 +821,17 @@ re_status compile_pattern(const char *pattern, size_t len, const re_compile_opts
                     C.b2[(size_t)st * nc2 + c1 * ncls + c2] = mid | (C.bT[(size_t)mid * ncls + c1] << 16);
                 }
     }
+    // ---- byte-indexed one-byte tables (states fit a byte): the reach looks a
+    // transition up by the text byte itself, with no class lookup first.
+    C.fbyte.clear(); C.bbyte.clear();
+    if (C.nf <= 256 && C.nb <= 256) {
+        C.fbyte.resize((size_t)C.nf * 256);
+        C.bbyte.resize((size_t)C.nb * 256);
+        for (uint32_t st = 0; st < C.nf; ++st)
+            for (uint32_t b = 0; b < 256; ++b) C.fbyte[(size_t)st * 256 + b] = (uint8_t)C.fT[(size_t)st * ncls + C.cls[b]];
+        for (uint32_t st = 0; st < C.nb; ++st)
+            for (uint32_t b = 0; b < 256; ++b) C.bbyte[(size_t)st * 256 + b] = (uint8_t)C.bT[(size_t)st * ncls + C.cls[b]];
+    }
     C.fHash = build_device_hash(C.fBits, C.nf, W, C.fHashMask);
     C.bHash = build_device_hash(C.bBits, C.nb, W, C.bHashMask);
     return RE_OK;

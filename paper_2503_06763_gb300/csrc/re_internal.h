@@ -53,6 +53,7 @@ struct DevTables {
     const uint32_t *pt;          // [nf][nb] dictionary index of B ∩ B̂ (DICT); pairs the
                                  // parse never produces hold 0xFFFFFFFF
     const uint32_t *f2, *b2;     // [n][ncls^2] two-byte tables (mid | end << 16), or null
+    const uint8_t *fbyte, *bbyte;  // [n][256] next state by byte (not class), u8; null unless n <= 256
     uint32_t fHashMask, bHashMask;
     uint32_t ncls, W, ell;
     uint32_t nf, nb, nfd, nbd;   // states incl. empty row 0; nfd/nbd = classic DFA states
@@ -71,6 +72,7 @@ struct Compiled {
     uint32_t nf = 0, nb = 0, nfd = 0, nbd = 0, msf = 0, msb = 0;
     std::vector<uint32_t> fT, bT;             // [n][ncls]
     std::vector<uint32_t> f2, b2;             // [n][ncls^2] two-byte tables (empty when too large)
+    std::vector<uint8_t> fbyte, bbyte;        // [n][256] next state by byte (empty unless n <= 256)
     std::vector<uint64_t> fBits, bBits;       // [n][W]
     std::vector<uint32_t> fHash, bHash;
     uint32_t fHashMask = 0, bHashMask = 0;

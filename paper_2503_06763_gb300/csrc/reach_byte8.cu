@@ -1,0 +1,10 @@
+// Reach kernels for the byte-indexed table mode (see reach_impl.cuh).
+#include "reach_impl.cuh"
+
+namespace slpf {
+bool launch_reach_byte8(const Params &p, const CUtensorMap &map, const StateMaps &smaps, cudaStream_t s, uint32_t ms,
+                        int sm_count) {
+    if (p.mat) return reach::launch_dir_ms<true>(p, map, smaps, s, ms, sm_count);
+    return reach::launch_dir_ms<false>(p, map, smaps, s, ms, sm_count);
+}
+}  // namespace slpf

@@ -189,9 +189,10 @@ __device__ __forceinline__ void walk_block(const Params &p, const Tabs &T, const
 constexpr int kStages = 3;
 constexpr uint32_t kTileBytes = 32 * 64;
 struct Ring {
-    uint8_t *tiles;       // [kStages][2][kTileBytes], 1024-byte aligned
-    uint32_t bars;        // shared address of kStages mbarriers
+    uint8_t *tiles;       // [nst][2][kTileBytes], 1024-byte aligned
+    uint32_t bars;        // shared address of nst mbarriers
     uint32_t phase;       // bit s: parity of the next completion of stage s
+    uint32_t nst = kStages;   // stages (kStages; 2 in the one-direction-per-block kernel)
 };
 
 // Directions a warp walks: both (one lane per chunk), or one of them (the
@@ -384,7 +385,7 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
     } else if (i == 0) {
         mf = 1; sf[0] = enc_f<TM>(T, t.fI); kf[0] = 1; tstart = 0;      // J_0 = I
     } else {
-        const uint32_t pr = clsof<TM>(T, __ldg(p.x + base - 1)) * t.ncls + clsof<TM>(T, __ldg(p.x + base));
+        const uint32_t pr = class_of<TM>(T, t, __ldg(p.x + base - 1)) * t.ncls + class_of<TM>(T, t, __ldg(p.x + base));
         mf = __ldg(t.fSlotCount + pr);
         if (WIDE && mf > (uint32_t)MS) {
             big = true;
@@ -401,8 +402,8 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
         if (i == p.c - 1) {
             mb = 1; sb[0] = enc_b<TM>(T, t.bF); kb[0] = 1; tlast = (int)len - 1;   // Ĵ_{c+1} = F
         } else {
-            const uint32_t pr = clsof<TM>(T, __ldg(p.x + base + len - 1)) * t.ncls +
-                                clsof<TM>(T, __ldg(p.x + base + len));
+            const uint32_t pr = class_of<TM>(T, t, __ldg(p.x + base + len - 1)) * t.ncls +
+                                class_of<TM>(T, t, __ldg(p.x + base + len));
             mb = __ldg(t.bSlotCount + pr);
             if (WIDE && mb > (uint32_t)MS) {
                 big = true;
@@ -427,11 +428,11 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
 
     const uint32_t lane = threadIdx.x & 31, i0 = i - lane;
     if (tma && lane == 0)                                     // prologue: first stages in flight
-        for (uint32_t b = 0; b < (uint32_t)kStages && b < nsub; ++b)
+        for (uint32_t b = 0; b < ring.nst && b < nsub; ++b)
             ring_issue<DIR>(p, map, ring, b, i0, b, nsub - 1 - b, FW, bwd);
     for (uint32_t blk = 0; blk < nsub; ++blk) {
         const uint32_t fb = blk, bb = nsub - 1 - blk;
-        const int stage = (int)(blk % kStages);
+        const int stage = (int)(blk % ring.nst);
         if (FW && fb >= 1) {                                // boundary before forward block fb
             if (WIDE && big) {
                 compact_local(xs, xk, mx);
@@ -520,8 +521,8 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
         }
         if (tma) {
             __syncwarp();                                     // every lane has read this stage
-            if (lane == 0 && blk + kStages < nsub)
-                ring_issue<DIR>(p, map, ring, stage, i0, blk + kStages, nsub - 1 - (blk + kStages), FW, bwd);
+            if (lane == 0 && blk + ring.nst < nsub)
+                ring_issue<DIR>(p, map, ring, stage, i0, blk + ring.nst, nsub - 1 - (blk + ring.nst), FW, bwd);
         } else {
             __syncwarp(act);                                  // stage read before the next fill
         }
@@ -650,6 +651,102 @@ __global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
         }
     }
     if (MAT && lane == 0) bulk_wait_all();                    // state rows written before the grid ends
+}
+
+// One parse with byte-indexed tables (TM_BYTE8): every warp of a block walks
+// the same direction, so a block stages one direction's table (about 65 KB
+// for 251 states) instead of both.  Even blocks walk 32-chunk tiles forward,
+// odd blocks backward (every block forward in recognizer mode); 16 warps per
+// block, 2-stage TMA rings, and (MAT) two state tiles per warp.
+constexpr uint32_t kDirThreads = 512;
+constexpr uint32_t kDirStages = 2;
+
+template <int MS, bool WIDE, bool MAT>
+__global__ void __launch_bounds__(kDirThreads, 1)
+    reach_dir_kernel(const __grid_constant__ Params p, const __grid_constant__ CUtensorMap map,
+                     const __grid_constant__ StateMaps smaps) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    const bool pairs = !p.recognize;
+    const bool backward_block = pairs && (blockIdx.x & 1);
+    Tabs T;
+    uint8_t *rest = stage_byte8(p.t, sm, T, !backward_block, backward_block);
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x / 32;
+    uint8_t *otile = nullptr;
+    Ring ring{};
+    ring.nst = kDirStages;
+    {
+        const uint32_t a = smem_u32(rest);
+        uint8_t *aligned = rest + ((1024 - (a & 1023)) & 1023);
+        ring.tiles = aligned + warp * (kDirStages * kTileBytes);
+        ring.bars = smem_u32(aligned + wpb * (kDirStages * kTileBytes)) + warp * kDirStages * 8;
+        ring.phase = 0;
+        if (MAT) {
+            uint8_t *after = aligned + wpb * (kDirStages * kTileBytes + kDirStages * 8);
+            after += (1024 - (smem_u32(after) & 1023)) & 1023;
+            otile = after + warp * 2 * kTileBytes;
+        }
+        if (p.text_tma && lane == 0) {
+            for (uint32_t st = 0; st < kDirStages; ++st) mbar_init(ring.bars + 8 * st, 1);
+            mbar_init_fence();
+        }
+        __syncwarp();
+    }
+    pdl_wait();
+    pdl_trigger();
+    const uint64_t gblk = pairs ? blockIdx.x >> 1 : blockIdx.x, nblk = pairs ? gridDim.x >> 1 : gridDim.x;
+    for (uint64_t t = gblk * wpb + warp; t * 32 < p.c; t += nblk * wpb) {
+        const uint32_t i = (uint32_t)(t * 32) + lane;
+        const bool tma = p.text_tma && t * 32 + 32 <= p.c_full;
+        if (i >= p.c) continue;                               // lanes past the text (plain path only)
+        const bool ok = backward_block
+                            ? reach_chunk<TM_BYTE8, MS, DIR_B, WIDE, MAT>(p, T, i, &map, ring, tma, &smaps.b, otile)
+                            : reach_chunk<TM_BYTE8, MS, DIR_F, WIDE, MAT>(p, T, i, &map, ring, tma, &smaps.f, otile);
+        if (!ok) {
+            atomicExch(p.status, RE_E_INTERNAL);
+            atomicExch(&p.w.flags[FLAG_INTERNAL], 1);
+            for (uint32_t st = 0; st < kDirStages; ++st) {   // drain: bounded wait on every stage
+                bool done = false;
+                for (uint32_t it = 0; it < kWaitLimit && !done; ++it)
+                    done = mbar_try_wait(ring.bars + 8 * st, (ring.phase >> st) & 1u);
+            }
+            if (MAT && lane == 0) bulk_wait_all();
+            return;
+        }
+    }
+    if (MAT && lane == 0) bulk_wait_all();
+}
+
+inline size_t reach_dir_smem(const DevTables &t, bool mat) {
+    const size_t tab = std::max(byte8_smem_bytes(t, true, false), byte8_smem_bytes(t, false, true));
+    const size_t wpb = kDirThreads / 32;
+    return tab + 1024 + wpb * (kDirStages * kTileBytes + kDirStages * 8) + (mat ? 1024 + wpb * 2 * kTileBytes : 0);
+}
+
+template <int MS, bool WIDE, bool MAT>
+void launch_dir(const Params &p, const CUtensorMap &map, const StateMaps &smaps, cudaStream_t s, int sm_count) {
+    const size_t smem = reach_dir_smem(p.t, MAT);
+    static uint64_t attr_done = 0;
+    allow_smem(reach_dir_kernel<MS, WIDE, MAT>, &attr_done, 227 * 1024);
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_dir_kernel<MS, WIDE, MAT>, kDirThreads, smem);
+    const uint64_t tiles = ((uint64_t)p.c + 31) / 32, wpb = kDirThreads / 32;
+    const uint64_t per_dir = (tiles + wpb - 1) / wpb;          // blocks one direction would want
+    const uint64_t dirs = p.recognize ? 1 : 2;
+    uint64_t blocks = std::min<uint64_t>(per_dir * dirs, (uint64_t)std::max(per_sm, 1) * sm_count);
+    if (dirs == 2) blocks = std::max<uint64_t>(2, blocks & ~1ull);   // pairs of blocks: one per direction
+    launch_dependent(reach_dir_kernel<MS, WIDE, MAT>, (uint32_t)std::max<uint64_t>(blocks, 1), kDirThreads, smem, s,
+                     p, map, smaps);
+}
+
+template <bool MAT>
+bool launch_dir_ms(const Params &p, const CUtensorMap &map, const StateMaps &smaps, cudaStream_t s, uint32_t ms,
+                   int sm_count) {
+    if (ms <= 2) launch_dir<2, false, MAT>(p, map, smaps, s, sm_count);
+    else if (ms <= 4) launch_dir<4, false, MAT>(p, map, smaps, s, sm_count);
+    else if (ms <= 8) launch_dir<8, false, MAT>(p, map, smaps, s, sm_count);
+    else if (ms <= 32) launch_dir<4, true, MAT>(p, map, smaps, s, sm_count);
+    else return false;
+    return true;
 }
 
 // Batch: warps take work items from the group's list (an atomic counter).  An
