@@ -110,6 +110,22 @@ typedef struct {
  * only, write the accept / reject status and no columns.                    */
 #define RE_PARSE_RECOGNIZE_ONLY 1u
 
+/* Reach kernel shape (the reach of Sect. 3.2; every shape computes the same
+ * end states and the same SLPF).  re_autotune chooses one per handle and
+ * length bucket together with the chunk length; RE_PARSE_REACH(v) in
+ * re_parse_opts.flags forces one (tests, measurements):
+ *   1: tables indexed by the byte itself, one direction per 16-warp block,
+ *      2-stage TMA ring (automata of at most 256 states per direction);
+ *   2: a warp per direction of each 32-chunk tile (two lanes per chunk),
+ *      tables by byte class, 3-stage TMA ring;
+ *   3: as 2 with a 2-stage ring;
+ *   4: one lane per chunk walking both directions, 3-stage ring.
+ * 0 (the default) is the tuned shape, else 1 where it applies, else 2.
+ * Shapes 1 (and 2, 3 when the class alphabet is above 16) let the reach
+ * store every position's state, so build & merge is a gather.              */
+#define RE_PARSE_REACH(v) ((uint32_t)(v) << 8)
+#define RE_PARSE_REACH_MASK 0x700u
+
 /* For tests of the join's bounded waits only: one block of the join scan
  * leaves before its first grid barrier, so the others' waits run out (about a
  * second) and the status word becomes RE_E_TIMEOUT.  The device stays usable;
@@ -290,17 +306,24 @@ re_status re_matches(re_handle *h, const re_slpf *slpf, uint64_t len, uint32_t g
                      uint64_t cap_pairs, uint64_t *d_count, void *d_workspace, uint64_t workspace_bytes,
                      re_stream stream);
 
-/* Chunk-length autotuner (no counterpart in the paper, which fixes c to the
- * thread count).  Parses d_text[0..len) with candidate chunk lengths around
- * the built-in rule's choice (1/2x to 2x, multiples of 64, those whose
- * workspace fits workspace_bytes), one warm-up and two timed runs each on
- * stream, and keeps the fastest for this handle, the length bucket
- * floor(log2(len)) and recognizer mode: later re_parse / re_workspace_size
- * calls with chunk_len 0 use it (re_parse falls back to the rule's length if
- * the workspace given is too small for it).  Blocks until the timing runs
- * finish; *slpf is overwritten.  *chunk_len receives the choice.            */
+/* Autotuner (no counterpart in the paper, which fixes c to the thread
+ * count).  Parses d_text[0..len) with every reach shape the automaton can
+ * run (RE_PARSE_REACH: lanes per chunk, table kind, TMA staging depth) and
+ * candidate chunk lengths around the built-in rule's choice (1/2x to 2x,
+ * multiples of 64, those whose workspace fits workspace_bytes), one warm-up
+ * and two timed runs each on stream, and keeps the fastest (shape, length)
+ * for this handle (so for its |Q|), the length bucket floor(log2(len)) and
+ * recognizer mode: later re_parse / re_workspace_size calls with chunk_len 0
+ * and no shape flag use it (re_parse falls back to the rule's length if the
+ * workspace given is too small for it).  Blocks until the timing runs
+ * finish; *slpf is overwritten.  *chunk_len receives the chosen length.    */
 re_status re_autotune(re_handle *h, const uint8_t *d_text, uint64_t len, re_slpf *slpf, void *d_workspace,
                       uint64_t workspace_bytes, re_stream stream, const re_parse_opts *opts, uint32_t *chunk_len);
+
+/* What re_autotune kept for texts of len bytes (flags: 0 or
+ * RE_PARSE_RECOGNIZE_ONLY): the chunk length and the reach shape
+ * (RE_PARSE_REACH numbering); both 0 when nothing was tuned.               */
+re_status re_tuned(const re_handle *h, uint64_t len, uint32_t flags, uint32_t *chunk_len, uint32_t *shape);
 
 /* re_parse for a text in host memory: enqueue on stream the copy of
  * text[0..len) into d_text, the parse (as re_parse, into the device buffers

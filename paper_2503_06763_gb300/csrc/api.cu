@@ -71,7 +71,22 @@ uint32_t tuned_chunk(re_handle *h, uint64_t n, const re_parse_opts *opts) {
     const int rec = (opts && (opts->flags & RE_PARSE_RECOGNIZE_ONLY)) ? 1 : 0;
     std::lock_guard<std::mutex> g(h->tune_lock);
     auto it = h->tuned.find({length_bucket(n), rec});
-    return it == h->tuned.end() ? 0u : it->second;
+    return it == h->tuned.end() ? 0u : it->second.first;
+}
+
+// The reach shape re_autotune chose with that chunk length, or 0.
+uint32_t tuned_shape(re_handle *h, uint64_t n, const re_parse_opts *opts) {
+    const int rec = (opts && (opts->flags & RE_PARSE_RECOGNIZE_ONLY)) ? 1 : 0;
+    std::lock_guard<std::mutex> g(h->tune_lock);
+    auto it = h->tuned.find({length_bucket(n), rec});
+    return it == h->tuned.end() ? 0u : it->second.second;
+}
+
+// Reach shapes this handle can run (bit v: shape v of RE_PARSE_REACH).
+uint32_t shapes_of(const re_handle *h) {
+    uint32_t m = (1u << 2) | (1u << 3) | (1u << 4);
+    if (h->dev.fbyte && h->dev.bbyte) m |= 1u << 1;
+    return m;
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -134,11 +149,16 @@ bool scan_join(const re_handle *h) { return h->host.nfd + 1 <= kScanStates && h-
 
 uint32_t table_mode(const DevTables &t);
 
-// Per-position states (mat): one-byte tables staged as u8 for the reach (at
-// most 256 states per direction), so every classic-DFA state fits a byte.
+// Per-position states (mat): automata of at most 256 states per direction
+// (the byte tables exist, and every classic-DFA state fits a byte).
 bool mat_capable(const re_handle *h) {
     const Compiled &C = h->host;
-    return !h->host_only && table_mode(h->dev) == TM_SMEM && C.nf <= 256 && C.nb <= 256;
+    return !h->host_only && !C.fbyte.empty() && C.nf <= 256 && C.nb <= 256;
+}
+// Shapes whose reach kernels store the states: byte tables, or warp pairs
+// with u8 class tables (not the pair layout of small class alphabets).
+bool shape_stores_states(const re_handle *h, uint32_t v) {
+    return v == 1 || ((v == 2 || v == 3) && table_mode(h->dev) == TM_SMEM);
 }
 bool mat_for(const re_handle *h, const re_parse_opts *opts) {
     return mat_capable(h) && !(opts && (opts->flags & RE_PARSE_RECOGNIZE_ONLY));
@@ -413,8 +433,13 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     if (!h || !slpf || !slpf->d_status || (len && !d_text)) { set_error("null argument"); return RE_E_INVALID_ARG; }
     if (h->host_only) { set_error("handle was compiled with RE_COMPILE_HOST_ONLY"); return RE_E_INVALID_ARG; }
     if (len && ((uintptr_t)d_text & 15)) { set_error("d_text must be 16-byte aligned"); return RE_E_INVALID_ARG; }
-    if (opts && (opts->flags & ~(RE_PARSE_RECOGNIZE_ONLY | RE_PARSE_TEST_STALL_JOIN))) {
+    if (opts && (opts->flags & ~(RE_PARSE_RECOGNIZE_ONLY | RE_PARSE_TEST_STALL_JOIN | RE_PARSE_REACH_MASK))) {
         set_error("unknown parse flags");
+        return RE_E_INVALID_ARG;
+    }
+    uint32_t shape = opts ? (opts->flags & RE_PARSE_REACH_MASK) >> 8 : 0u;
+    if (shape > 4 || (shape && !(shapes_of(h) >> shape & 1))) {
+        set_error("reach shape not available for this automaton");
         return RE_E_INVALID_ARG;
     }
     if (opts && opts->n_events && (opts->n_events != RE_PHASE_EVENTS || !opts->events)) {
@@ -459,6 +484,11 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     p.scan_stall = (opts && (opts->flags & RE_PARSE_TEST_STALL_JOIN)) ? 1u : 0u;
     const DevTables &t = h->dev;
     p.tmode = table_mode(t);
+    if (!shape) shape = tuned_shape(h, len, opts);            // chosen with the tuned chunk length
+    if (!shape || !(shapes_of(h) >> shape & 1))
+        shape = (shapes_of(h) >> 1 & 1) && p.tmode == TM_SMEM ? 1u : 2u;
+    p.rvar = shape;
+    p.rstages = shape == 3 ? 2u : 3u;
     const size_t tab = tables_smem_bytes(t, p.tmode);
     p.Gfast = len / kSub;
     alignas(64) CUtensorMap out_map;
@@ -488,7 +518,7 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     // build & merge gathers (when the gather's encoder fits shared memory).
     alignas(64) StateMaps smaps;
     std::memset(&smaps, 0, sizeof(smaps));
-    if (mat_ws && len && mat_gather_smem(p) <= kSmemMergeMax) {
+    if (mat_ws && len && shape_stores_states(h, shape) && mat_gather_smem(p) <= kSmemMergeMax) {
         p.mat = 1;
         uint8_t *w = (uint8_t *)d_workspace;
         const bool maps = p.text_tma && text_tensor_map(smaps.f, w + L.off[24], k, p.c_full) &&
@@ -536,6 +566,7 @@ extern "C" re_status re_autotune(re_handle *h, const uint8_t *d_text, uint64_t l
     if (!h || !chunk_len || !len) { set_error("null argument or empty text"); return RE_E_INVALID_ARG; }
     if (opts && opts->chunk_len) { set_error("autotune chooses chunk_len: pass 0"); return RE_E_INVALID_ARG; }
     if (opts && opts->n_events) { set_error("autotune records its own events"); return RE_E_INVALID_ARG; }
+    if (opts && (opts->flags & RE_PARSE_REACH_MASK)) { set_error("autotune chooses the reach shape"); return RE_E_INVALID_ARG; }
     const uint32_t k0 = choose_chunk(len, sm_count_of(h->device), nullptr);
     std::vector<uint32_t> cand;
     for (uint32_t num : {2u, 3u, 4u, 5u, 6u, 8u}) {            // k0 * num / 4, multiples of 64, >= 256
@@ -545,31 +576,38 @@ extern "C" re_status re_autotune(re_handle *h, const uint8_t *d_text, uint64_t l
         if (layout_for(h, len, (uint32_t)k, mat_for(h, opts)).total > workspace_bytes) continue;
         cand.push_back((uint32_t)k);
     }
+    std::vector<uint32_t> shapes;                              // every reach shape this automaton can run
+    for (uint32_t v = 1; v <= 4; ++v)
+        if (shapes_of(h) >> v & 1) shapes.push_back(v);
     if (cand.empty()) { set_error("workspace too small for any candidate chunk length"); return RE_E_CAPACITY; }
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0), "event");
     CUDA_TRY(cudaEventCreate(&e1), "event");
-    uint32_t best = cand[0];
+    uint32_t best = cand[0], best_shape = shapes[0];
     float best_ms = 1e30f;
     re_status st = RE_OK;
-    for (uint32_t k : cand) {
-        re_parse_opts o = opts ? *opts : re_parse_opts{};
-        o.chunk_len = k;
-        o.n_events = 0;
-        o.events = nullptr;
-        float ms = 0.f;
-        for (int rep = 0; rep < 3 && st == RE_OK; ++rep) {   // one warm-up, two timed
-            cudaEventRecord(e0, s);
-            st = re_parse(h, d_text, len, stream, slpf, d_workspace, workspace_bytes, &o);
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) { st = cuda_fail(cudaGetLastError(), "autotune"); break; }
-            float t = 0.f;
-            cudaEventElapsedTime(&t, e0, e1);
-            if (rep) ms += t;
+    for (uint32_t v : shapes) {
+        for (uint32_t k : cand) {
+            re_parse_opts o = opts ? *opts : re_parse_opts{};
+            o.chunk_len = k;
+            o.flags = (o.flags & ~RE_PARSE_REACH_MASK) | RE_PARSE_REACH(v);
+            o.n_events = 0;
+            o.events = nullptr;
+            float ms = 0.f;
+            for (int rep = 0; rep < 3 && st == RE_OK; ++rep) {   // one warm-up, two timed
+                cudaEventRecord(e0, s);
+                st = re_parse(h, d_text, len, stream, slpf, d_workspace, workspace_bytes, &o);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) { st = cuda_fail(cudaGetLastError(), "autotune"); break; }
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep) ms += t;
+            }
+            if (st != RE_OK) break;
+            if (ms < best_ms) { best_ms = ms; best = k; best_shape = v; }
         }
         if (st != RE_OK) break;
-        if (ms < best_ms) { best_ms = ms; best = k; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -577,9 +615,19 @@ extern "C" re_status re_autotune(re_handle *h, const uint8_t *d_text, uint64_t l
     const int rec = (opts && (opts->flags & RE_PARSE_RECOGNIZE_ONLY)) ? 1 : 0;
     {
         std::lock_guard<std::mutex> g(h->tune_lock);
-        h->tuned[{length_bucket(len), rec}] = best;
+        h->tuned[{length_bucket(len), rec}] = {best, best_shape};
     }
     *chunk_len = best;
+    return RE_OK;
+}
+
+extern "C" re_status re_tuned(const re_handle *h, uint64_t len, uint32_t flags, uint32_t *chunk_len,
+                              uint32_t *shape) {
+    if (!h || !chunk_len || !shape) { set_error("null argument"); return RE_E_INVALID_ARG; }
+    re_parse_opts o{};
+    o.flags = flags & RE_PARSE_RECOGNIZE_ONLY;
+    *chunk_len = tuned_chunk(const_cast<re_handle *>(h), len, &o);
+    *shape = tuned_shape(const_cast<re_handle *>(h), len, &o);
     return RE_OK;
 }
 

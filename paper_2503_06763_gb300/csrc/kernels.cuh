@@ -71,6 +71,9 @@ struct Params {
     uint32_t mat;                   // reach writes every position's state once its runs have met; the
                                     // fix-up fills the positions before; build & merge is a gather
     uint32_t state_tma;             // reach stores its state rows through TMA (mat)
+    uint32_t rvar;                  // reach shape (RE_PARSE_REACH): 1 byte tables, one direction per
+                                    // block; 2 / 3 warp pairs, 3 / 2 stages; 4 one lane per chunk
+    uint32_t rstages;               // TMA ring stages of the warp-pair and one-lane shapes
     uint32_t tmode;                 // TM_GLOBAL / TM_SMEM / TM_PAIR (see Tabs)
     uint32_t enc_in_smem;           // encoder table (DICT pair table, DENSE bitsets) in shared memory
     uint32_t merge_reg;             // one-byte tables: build & merge stages the classic-DFA rows and the

@@ -104,7 +104,8 @@ struct re_handle {
     size_t d_bytes = 0;
     int device = 0;
     bool host_only = false;
-    // chunk lengths chosen by re_autotune: key = (floor(log2(len)), recognizer)
+    // choices of re_autotune: key = (floor(log2(len)), recognizer), value =
+    // (chunk length, reach shape)
     std::mutex tune_lock;
-    std::map<std::pair<int, int>, uint32_t> tuned;
+    std::map<std::pair<int, int>, std::pair<uint32_t, uint32_t>> tuned;
 };

@@ -31,9 +31,9 @@ bool launch_reach_byte8(const Params &p, const CUtensorMap &map, const StateMaps
 
 bool launch_reach(const Params &p, const CUtensorMap &map, const StateMaps &smaps, cudaStream_t s, uint32_t ms,
                   int sm_count) {
+    // shape 1, byte-indexed tables: no class lookup per byte; a block per direction
+    if (p.rvar == 1 && p.t.fbyte && p.t.bbyte) return launch_reach_byte8(p, map, smaps, s, ms, sm_count);
     if (p.tmode == TM_PAIR) return launch_reach_pair(p, map, smaps, s, ms, sm_count);
-    // byte-indexed tables: no class lookup per byte; a block per direction
-    if (p.tmode == TM_SMEM && p.t.fbyte && p.t.bbyte) return launch_reach_byte8(p, map, smaps, s, ms, sm_count);
     if (p.tmode == TM_SMEM && byte_states(p.t)) return launch_reach_smem8(p, map, smaps, s, ms, sm_count);
     if (p.tmode == TM_SMEM) return launch_reach_smem(p, map, smaps, s, ms, sm_count);
     return launch_reach_global(p, map, smaps, s, ms, sm_count);

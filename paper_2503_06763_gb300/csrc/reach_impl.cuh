@@ -607,19 +607,21 @@ __global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x / 32;
     uint8_t *otile = nullptr;
     Ring ring{};
+    const uint32_t nst = p.rstages ? p.rstages : (uint32_t)kStages;   // ring stages (2 or 3)
     {
         const uint32_t a = smem_u32(rest);
         uint8_t *aligned = rest + ((1024 - (a & 1023)) & 1023);
-        ring.tiles = aligned + warp * (kStages * TILES * kTileBytes);
-        ring.bars = smem_u32(aligned + wpb * (kStages * TILES * kTileBytes)) + warp * kStages * 8;
+        ring.nst = nst;
+        ring.tiles = aligned + warp * (nst * TILES * kTileBytes);
+        ring.bars = smem_u32(aligned + wpb * (nst * TILES * kTileBytes)) + warp * nst * 8;
         ring.phase = 0;
         if (MAT) {                                            // two state tiles per warp, 1024-byte aligned
-            uint8_t *after = aligned + wpb * (kStages * TILES * kTileBytes + kStages * 8);
+            uint8_t *after = aligned + wpb * (nst * TILES * kTileBytes + nst * 8);
             after += (1024 - (smem_u32(after) & 1023)) & 1023;
             otile = after + warp * 2 * kTileBytes;
         }
         if (p.text_tma && lane == 0) {
-            for (int st = 0; st < kStages; ++st) mbar_init(ring.bars + 8 * st, 1);
+            for (uint32_t st = 0; st < nst; ++st) mbar_init(ring.bars + 8 * st, 1);
             mbar_init_fence();
         }
         __syncwarp();
@@ -641,7 +643,7 @@ __global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
         if (!ok) {
             atomicExch(p.status, RE_E_INTERNAL);
             atomicExch(&p.w.flags[FLAG_INTERNAL], 1);
-            for (int st = 0; st < kStages; ++st) {            // drain: bounded wait on every stage
+            for (uint32_t st = 0; st < nst; ++st) {           // drain: bounded wait on every stage
                 bool done = false;
                 for (uint32_t it = 0; it < kWaitLimit && !done; ++it)
                     done = mbar_try_wait(ring.bars + 8 * st, (ring.phase >> st) & 1u);
@@ -791,10 +793,10 @@ __global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
 }
 
 inline size_t reach_smem(const DevTables &t, int tm, uint32_t threads = kChunkThreads, int tiles = 2,
-                         bool mat = false) {
+                         bool mat = false, uint32_t stages = kStages) {
     const size_t tab = tm == TM_PAIR ? reach_pair_smem(t) : tables_smem_bytes(t, tm);
     const size_t out = mat ? 1024 + (threads / 32) * 2 * kTileBytes : 0;   // two state tiles per warp
-    return tab + 1024 + (threads / 32) * (kStages * tiles * kTileBytes + kStages * 8) + out;
+    return tab + 1024 + (threads / 32) * (stages * tiles * kTileBytes + stages * 8) + out;
 }
 
 template <int TM, int MS, bool SPLIT, bool WIDE = false>
@@ -836,7 +838,7 @@ bool launch_ms_batch(const BatchGroup &b, cudaStream_t s, uint32_t ms, int sm_co
 template <int TM, int MS, bool SPLIT, bool WIDE = false, bool MAT = false>
 void launch_split(const Params &p, const CUtensorMap &map, const StateMaps &smaps, cudaStream_t s, int sm_count) {
     const uint32_t threads = SPLIT ? kSplitThreads : kChunkThreads;
-    const size_t smem = reach_smem(p.t, TM, threads, SPLIT ? 1 : 2, MAT);
+    const size_t smem = reach_smem(p.t, TM, threads, SPLIT ? 1 : 2, MAT, p.rstages ? p.rstages : kStages);
     static uint64_t attr_done = 0;
     allow_smem(reach_kernel<TM, MS, SPLIT, WIDE, MAT>, &attr_done);
     int per_sm = 1;
@@ -856,6 +858,15 @@ template <int TM>
 bool launch_ms(const Params &p, const CUtensorMap &map, const StateMaps &smaps, cudaStream_t s, uint32_t ms,
                int sm_count) {
     constexpr bool FULL = TM != TM_GLOBAL;          // fewer instantiations for the rare global mode
+    if (p.rvar == 4) {                              // one lane per chunk, both directions: every run in registers
+        if (FULL && ms <= 2) launch_split<TM, 2, false>(p, map, smaps, s, sm_count);
+        else if (FULL && ms <= 4) launch_split<TM, 4, false>(p, map, smaps, s, sm_count);
+        else if (ms <= 8) launch_split<TM, 8, false>(p, map, smaps, s, sm_count);
+        else if (FULL && ms <= 16) launch_split<TM, 16, false>(p, map, smaps, s, sm_count);
+        else if (ms <= 32) launch_split<TM, 32, false>(p, map, smaps, s, sm_count);
+        else return false;
+        return true;
+    }
     if constexpr (TM == TM_SMEM8) {                 // per-position states (mat) only here
         if (p.mat) {
             if (ms <= 2) launch_split<TM, 2, true, false, true>(p, map, smaps, s, sm_count);

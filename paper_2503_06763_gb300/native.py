@@ -23,11 +23,18 @@ RE_COMPILE_HOST_ONLY = 1
 RE_COMPILE_DFA_STARTS = 2
 RE_PARSE_RECOGNIZE_ONLY = 1
 RE_PARSE_TEST_STALL_JOIN = 0x80000000     # tests of the join's bounded waits only
+REACH_SHAPES = {1: "byte tables, one direction per block, 2 stages", 2: "warp pairs, class tables, 3 stages",
+                3: "warp pairs, class tables, 2 stages", 4: "one lane per chunk, both directions, 3 stages"}
+
+
+def reach_flag(shape: int) -> int:
+    """RE_PARSE_REACH(shape): force a reach kernel shape (0: automatic)."""
+    return (shape & 7) << 8
 
 EXPORTS = ["re_compile", "re_free", "re_get_info", "re_segment_name", "re_dict_copy",
            "re_slpf_layout", "re_workspace_size", "re_parse", "re_batch_plan", "re_batch_workspace_size",
            "re_batch_chunk_len", "re_parse_batch", "re_batch_run", "re_batch_free", "re_match_workspace_size",
-           "re_matches", "re_autotune", "re_parse_host",
+           "re_matches", "re_autotune", "re_tuned", "re_parse_host",
            "re_parse_static",
            "re_last_error"]
 RE_STATIC_SCRATCH_BYTES = 64 << 20
@@ -112,6 +119,8 @@ def load():
     lib.re_autotune.argtypes = [vp, vp, u64, ctypes.POINTER(Slpf), vp, u64, vp, ctypes.POINTER(ParseOpts),
                                 ctypes.POINTER(u32)]
     lib.re_autotune.restype = i32
+    lib.re_tuned.argtypes = [vp, u64, u32, ctypes.POINTER(u32), ctypes.POINTER(u32)]
+    lib.re_tuned.restype = i32
     lib.re_parse_host.argtypes = [vp, vp, u64, vp, vp, vp, ctypes.POINTER(Slpf), vp, u64, vp, ctypes.POINTER(ParseOpts)]
     lib.re_parse_host.restype = i32
     lib.re_parse_static.argtypes = [vp, vp, u64, vp, ctypes.POINTER(Slpf), ctypes.POINTER(ParseOpts)]
@@ -194,7 +203,8 @@ class Regex:
         return b.value
 
     def parse(self, text, kind: str = "auto", chunk_len: int = 0, stream=None, out=None, status=None,
-              workspace=None, recognize_only: bool = False, events=None, extra_flags: int = 0):
+              workspace=None, recognize_only: bool = False, events=None, extra_flags: int = 0,
+              reach_shape: int = 0):
         """Enqueue the parse of a CUDA uint8 tensor; returns (cols, status, kind).
 
         ``cols`` is a CUDA tensor of n+1 columns (uint8/int16/int32/int64 view of
@@ -210,7 +220,7 @@ class Regex:
         n = text.numel()
         kname, cb, nbytes = self.layout(n, kind)
         dt = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}[cb]
-        flags = (RE_PARSE_RECOGNIZE_ONLY if recognize_only else 0) | extra_flags
+        flags = (RE_PARSE_RECOGNIZE_ONLY if recognize_only else 0) | extra_flags | reach_flag(reach_shape)
         wsz = self.workspace_size(n, chunk_len, flags & RE_PARSE_RECOGNIZE_ONLY)
         s = stream if stream is not None else torch.cuda.current_stream(text.device)
         with torch.cuda.stream(s):
@@ -313,6 +323,13 @@ class Regex:
                                  workspace.numel(), ctypes.c_void_p(s.cuda_stream), ctypes.byref(opts),
                                  ctypes.byref(k)))
         return k.value
+
+    def tuned(self, n: int, recognize_only: bool = False):
+        """(chunk length, reach shape) re_autotune kept for n-byte texts, or (0, 0)."""
+        k, v = ctypes.c_uint32(), ctypes.c_uint32()
+        check(load().re_tuned(self._h, n, RE_PARSE_RECOGNIZE_ONLY if recognize_only else 0, ctypes.byref(k),
+                              ctypes.byref(v)))
+        return k.value, v.value
 
     def parse_host(self, text, cols, status, d_text, d_cols, d_status, workspace, stream=None, kind: str = "auto",
                    chunk_len: int = 0):

@@ -65,3 +65,21 @@ def test_recognizer_has_its_own_choice(lib):
         torch.cuda.synchronize()
         expect = want if h is host else serial.accepted(serial.parse(compile_re(W.DNA_RE), h.tobytes()))
         assert int(st.item()) == (0 if expect else 1)
+
+
+def test_autotune_chooses_a_reach_shape(lib):
+    """The tuner searches reach shapes too; the (length, shape) it keeps is
+    reported by re_tuned and the parse with it matches the oracle."""
+    Regex = lib
+    host = W.log_text(2 << 20, seed=43)
+    t = torch.from_numpy(host).cuda()
+    rx = Regex(W.LOG_RE)
+    assert rx.tuned(len(host)) == (0, 0)
+    k = rx.autotune(t)
+    kt, shape = rx.tuned(len(host))
+    assert kt == k and shape in (1, 2, 3, 4)
+    ids, table = serial.parse_ids(compile_re(W.LOG_RE), host)
+    cols, st, kind = rx.parse(t)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    assert np.array_equal(rx.decode(cols.cpu().numpy(), kind), table[ids])

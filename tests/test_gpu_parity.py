@@ -330,3 +330,33 @@ def test_dfa_starts_give_the_same_slpf(lib, pattern):
             _, st, _ = rx.parse(t, chunk_len=chunk_len, recognize_only=True)
             torch.cuda.synchronize()
             assert int(st.item()) == (0 if serial.accepted(oracle_cols(pattern, host.tobytes())) else 1)
+
+
+# ---------------------------------------------------------------- reach shapes
+SHAPE_CASES = [("dna", W.DNA_RE, lambda: W.dna_text(200_003, seed=5, mean_gap=700)),
+               ("ab", W.AB_RE, lambda: W.ab_text(100_001, seed=6)),
+               ("log", W.LOG_RE, lambda: W.log_text(150_000, seed=7)),
+               ("aa", "(aa)*", lambda: np.full(70_000, ord("a"), dtype=np.uint8))]
+
+
+@pytest.mark.parametrize("shape", [1, 2, 3, 4])
+@pytest.mark.parametrize("case", range(len(SHAPE_CASES)))
+def test_every_reach_shape(lib, shape, case):
+    """Every reach kernel shape (RE_PARSE_REACH: byte tables with a block per
+    direction, warp pairs with 3 or 2 ring stages, one lane per chunk) gives
+    the oracle's columns, with automatic and short chunks, and the oracle's
+    verdict in recognizer mode."""
+    name, pattern, make = SHAPE_CASES[case]
+    rx = lib(pattern)
+    host = make()
+    want = oracle_cols(pattern, host.tobytes())
+    for chunk_len in (0, 128):
+        t = torch.from_numpy(host).cuda()
+        cols, st, kind = rx.parse(t, chunk_len=chunk_len, reach_shape=shape)
+        _, rst, _ = rx.parse(t, chunk_len=chunk_len, reach_shape=shape, recognize_only=True)
+        torch.cuda.synchronize()
+        acc = serial.accepted(want)
+        assert int(st.item()) == int(rst.item()) == (0 if acc else 1), (name, shape, chunk_len)
+        got = rx.decode(cols.cpu().numpy(), kind)
+        bad = np.nonzero(np.any(got != want, axis=1))[0]
+        assert bad.size == 0, (name, shape, chunk_len, bad[:5].tolist())
