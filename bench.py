@@ -63,7 +63,7 @@ def parse_args():
     ap.add_argument("--chunk-len", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="single",
-                    choices=["single", "batch", "serve", "matches", "latency", "ablation", "join"],
+                    choices=["single", "batch", "serve", "matches", "latency", "ablation", "join", "shard"],
                     help="single: one 256 MiB text (default); batch: 4096 texts under 8 random REs; "
                          "serve: Poisson request stream")
     ap.add_argument("--texts", type=int, default=4096, help="batch mode: number of texts")
@@ -403,6 +403,8 @@ def main():
         return ablation_mode(args, rank, world, local)
     if args.mode == "join":
         return join_mode(args, rank, world, local)
+    if args.mode == "shard":
+        return shard_mode(args, rank, world, local)
 
     import torch
     torch.cuda.set_device(local)
@@ -844,6 +846,60 @@ def join_mode(args, rank, world, local):
                           "text_bytes": n, "rows": rows,
                           "join_ratio_to_dna": {k: round(v["phase_ms"]["join"] / rows["dna"]["phase_ms"]["join"], 2)
                                                 for k, v in rows.items()}}))
+
+
+def shard_mode(args, rank, world, local):
+    """One text split across the N ranks (Sect. 3.2): every rank holds the
+    whole log text (seed 2, default 1 GiB), computes the maps of its slice,
+    the maps are all-gathered (the one exchange step, a few hundred bytes per
+    rank), every rank composes them into its entry states and parses its
+    slice.  A step is all of that; time is the max over ranks and the value
+    the text's bytes over it (strong scaling: the work is one text)."""
+    import torch
+    import workloads as W
+    from paper_2503_06763_gb300 import Regex, shard
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    n = args.bytes or (1 << 30)
+    host = W.log_text(n, seed=2)
+    n = int(host.size)
+    rx = Regex(W.LOG_RE)
+    text = torch.from_numpy(host).to(dev)
+    a, b = shard.slice_bounds(n, world)[rank]
+    piece = text[a:b]
+
+    def step():
+        return shard.parse_sharded(rx, piece, a > 0, b < n)
+
+    for _ in range(max(args.warmup, 3)):
+        cols, st, acc = step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cols, st, acc = step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_local = (time.perf_counter() - t0) * 1e3
+    ms_total, _ = aggregate(ms_local, b - a, dist, dev)
+    ms = ms_total / args.steps
+    if rank == 0:
+        print(json.dumps({"metric": "sharded SLPF parse GB/s of one text (slice maps, all-gather, slice parse)",
+                          "value": round(n / (ms / 1e3) / 1e9, 3), "unit": "GB/s", "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+                          "higher_is_better": True, "scaling": "strong", "status": int(st.item()),
+                          "accepted": bool(acc),
+                          "config": {"workload": WORKLOADS["log"][0], "text_bytes": n,
+                                     "slices": world, "timing": "host clock around the steps (maps leave the "
+                                     "device for the exchange every step)"}}))
+    if dist:
+        dist.destroy_process_group()
 
 
 def reference_arm(args, rank, world):

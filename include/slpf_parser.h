@@ -339,6 +339,46 @@ re_status re_parse_host(re_handle *h, const uint8_t *text, uint64_t len, void *h
                         uint8_t *d_text, re_slpf *slpf, void *d_workspace, uint64_t workspace_bytes,
                         re_stream stream, const re_parse_opts *opts);
 
+/* ---------------------------------------------------------------- sharded parse
+ * One text split into contiguous slices x[a_r, b_r), r = 0 .. N-1, parsed
+ * slice by slice, on different GPUs or one (Sect. 3.2: chunks depend on one
+ * another only through the join, Eq. joiner).  Needs both classic DFAs below
+ * 256 states (re_shard_map_size says whether).
+ *  1. re_shard_map on every slice: reach, and the slice's chunk maps
+ *     composed into its maps (bytes, on the device): fwd[S] is the forward
+ *     state at b_r when it is S at a_r, bwd[S] the backward state at a_r
+ *     when it is S at b_r (classic-DFA state ids, 0 the empty set).  The
+ *     maps are exact for every state a text can bring to the slice's edges
+ *     (the states after the byte before it, resp. after it).  With
+ *     RE_SHARD_PREV the slice's first chunk speculates from the byte before
+ *     it (d_text[-1] must be readable); without it the slice is the first
+ *     and starts from I.  With RE_SHARD_NEXT the last chunk speculates from
+ *     the byte after it (d_text[len]); without it the slice is the last and
+ *     ends in F.  d_status receives RE_OK, RE_E_INTERNAL or RE_E_TIMEOUT.
+ *  2. re_shard_entry (host) composes the maps of every slice, in order, into
+ *     each slice's entry states (forward at a_r, backward at b_r) and the
+ *     text's verdict; for a rejected text every forward entry state is 0.
+ *  3. re_parse_slice on every slice with its entry states: the slice's
+ *     len + 1 columns are columns a_r .. b_r of the whole text's SLPF, as
+ *     re_parse lays them out (column b_r is also column 0 of slice r+1).
+ * The maps are what the slices exchange: fwd_entries + bwd_entries bytes
+ * each (an all-gather).  d_maps: device, fwd then bwd.  Workspace: as
+ * re_parse (re_workspace_size of the slice's length).                      */
+#define RE_SHARD_PREV 1u
+#define RE_SHARD_NEXT 2u
+re_status re_shard_map_size(const re_handle *h, uint32_t *fwd_entries, uint32_t *bwd_entries);
+re_status re_shard_map(re_handle *h, const uint8_t *d_text, uint64_t len, uint32_t flags, re_stream stream,
+                       void *d_workspace, uint64_t workspace_bytes, uint8_t *d_maps, int32_t *d_status);
+re_status re_shard_entry(const re_handle *h, const uint8_t *maps, uint32_t count, uint32_t *entry,
+                         uint32_t *entry_bwd, int32_t *accepted);
+re_status re_parse_slice(re_handle *h, const uint8_t *d_text, uint64_t len, uint32_t entry, uint32_t entry_bwd,
+                         re_stream stream, re_slpf *slpf, void *d_workspace, uint64_t workspace_bytes,
+                         const re_parse_opts *opts);
+
+/* Segment set of a state (host): bit q of words [0, W) is segment q.
+ * forward: 1 for the forward automaton, 0 for the reverse one.             */
+re_status re_state_bits(const re_handle *h, int32_t forward, uint32_t id, uint64_t *bits, uint32_t cap_words);
+
 /* Thread-local description of the last error returned on this thread.     */
 const char *re_last_error(void);
 

@@ -428,8 +428,34 @@ re_status workspace_rule_bytes(const re_handle *h, uint64_t len, const re_parse_
 
 extern "C" {
 
+}  // extern "C"
+
+namespace slpf {
+// A slice of a sharded text: its entry states (forward at its start,
+// backward at its end; I and F for a whole text), and in map mode the
+// device buffer of its maps and its SHARD_* flags.
+struct SliceArgs {
+    uint32_t fin = 1, bin = 1;
+    uint32_t shard = 0;
+    uint8_t *maps = nullptr;
+};
+re_status parse_impl(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream stream, re_slpf *slpf,
+                     void *d_workspace, uint64_t workspace_bytes, const re_parse_opts *opts, const SliceArgs &sa);
+}  // namespace slpf
+
+extern "C" {
+
 re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream stream, re_slpf *slpf,
                    void *d_workspace, uint64_t workspace_bytes, const re_parse_opts *opts) {
+    return parse_impl(h, d_text, len, stream, slpf, d_workspace, workspace_bytes, opts, SliceArgs{});
+}
+
+}  // extern "C"
+
+re_status slpf::parse_impl(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream stream, re_slpf *slpf,
+                           void *d_workspace, uint64_t workspace_bytes, const re_parse_opts *opts,
+                           const SliceArgs &sa) {
+    const bool map_mode = sa.maps != nullptr;
     if (!h || !slpf || !slpf->d_status || (len && !d_text)) { set_error("null argument"); return RE_E_INVALID_ARG; }
     if (h->host_only) { set_error("handle was compiled with RE_COMPILE_HOST_ONLY"); return RE_E_INVALID_ARG; }
     if (len && ((uintptr_t)d_text & 15)) { set_error("d_text must be 16-byte aligned"); return RE_E_INVALID_ARG; }
@@ -446,11 +472,15 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
         set_error("n_events must be 0 or RE_PHASE_EVENTS");
         return RE_E_INVALID_ARG;
     }
-    const bool recognize = opts && (opts->flags & RE_PARSE_RECOGNIZE_ONLY);
+    const bool recognize = (opts && (opts->flags & RE_PARSE_RECOGNIZE_ONLY)) || map_mode;
     cudaEvent_t *ev = (opts && opts->n_events) ? (cudaEvent_t *)opts->events : nullptr;
     re_slpf_kind kind = RE_SLPF_DENSE;
     uint32_t cb = 1;
-    if (!recognize || slpf->d_cols) {
+    if (map_mode && (!scan_join(h) || !len)) {
+        set_error("slice maps need both classic DFAs below 256 states and a non-empty slice");
+        return RE_E_INVALID_ARG;
+    }
+    if (!map_mode && (!recognize || slpf->d_cols)) {
         const re_status st = resolve_kind(h, slpf->kind, kind, cb);
         if (st != RE_OK) return st;
         const re_status so = check_output(slpf, len, cb);
@@ -466,7 +496,7 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     }
     if (k % kSub || k == 0) { set_error("chunk_len must be a positive multiple of 64"); return RE_E_INVALID_ARG; }
     if (len / k >= 0xFFFFFFF0ull) { set_error("text too long for this chunk length"); return RE_E_INVALID_ARG; }
-    const bool mat_ws = mat_for(h, opts);                     // the workspace holds FS and BS
+    const bool mat_ws = !map_mode && mat_for(h, opts);        // the workspace holds FS and BS
     const Layout L = layout_for(h, len, k, mat_ws);
     if (len && (!d_workspace || workspace_bytes < L.total || ((uintptr_t)d_workspace & 255))) {
         set_error("workspace missing, too small or not 256-byte aligned");
@@ -476,10 +506,13 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     cudaStream_t s = (cudaStream_t)stream;
     Params p{};
     p.t = h->dev;
+    p.t.fI = sa.fin;                                          // a slice starts and ends in its entry states
+    p.t.bF = sa.bin;
+    p.shard = sa.shard;
     p.x = d_text; p.n = len; p.k = k; p.c = L.c; p.S = L.S; p.Gc = L.Gc;
     p.out = recognize ? nullptr : slpf->d_cols;
     p.col_bytes = cb; p.kind = kind; p.status = slpf->d_status;
-    p.recognize = recognize ? 1u : 0u;
+    p.recognize = (recognize && !map_mode) ? 1u : 0u;          // map mode walks both directions
     p.scan = scan_join(h) ? 1u : 0u;
     p.scan_stall = (opts && (opts->flags & RE_PARSE_TEST_STALL_JOIN)) ? 1u : 0u;
     const DevTables &t = h->dev;
@@ -537,11 +570,17 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     carve(p, L, (uint8_t *)d_workspace);
     CUDA_TRY(mark(0), "event");
     launch_flags_init(p, s);
-    if (!launch_reach(p, text_map, smaps, s, std::max(t.msf, recognize ? 1u : t.msb), sms)) {
+    if (!launch_reach(p, text_map, smaps, s, std::max(t.msf, p.recognize ? 1u : t.msb), sms)) {
         set_error("too many speculative starts");
         return RE_E_INTERNAL;
     }
     CUDA_TRY(mark(1), "event");
+    if (map_mode) {                                           // the slice's maps, no columns
+        if (!launch_shard_map(p, sa.maps, s, sms)) return cuda_fail(cudaGetLastError(), "slice map launch");
+        for (int j = 2; j < (int)RE_PHASE_EVENTS; ++j) CUDA_TRY(mark(j), "event");
+        CUDA_TRY(cudaGetLastError(), "launch");
+        return RE_OK;
+    }
     if (!launch_join(p, s, sms)) return cuda_fail(cudaGetLastError(), "join launch");
     CUDA_TRY(mark(2), "event");
     if (!recognize) {
@@ -555,8 +594,6 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
     CUDA_TRY(cudaGetLastError(), "launch");
     return RE_OK;
 }
-
-}  // extern "C"
 
 // Time candidate chunk lengths around the rule's choice on the caller's text
 // and keep the fastest for this handle and length bucket.
@@ -999,3 +1036,82 @@ void re_batch_free(re_batch *b) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ sharded parse
+extern "C" re_status re_shard_map(re_handle *h, const uint8_t *d_text, uint64_t len, uint32_t flags,
+                                  re_stream stream, void *d_workspace, uint64_t workspace_bytes, uint8_t *d_maps,
+                                  int32_t *d_status) {
+    if (!h || !d_maps || !d_status) { set_error("null argument"); return RE_E_INVALID_ARG; }
+    if (flags & ~(RE_SHARD_PREV | RE_SHARD_NEXT)) { set_error("unknown shard flags"); return RE_E_INVALID_ARG; }
+    re_slpf slot{};
+    slot.d_status = d_status;
+    SliceArgs sa;
+    sa.shard = (flags & RE_SHARD_PREV ? SHARD_PREV : 0u) | (flags & RE_SHARD_NEXT ? SHARD_NEXT : 0u);
+    sa.maps = d_maps;
+    return parse_impl(h, d_text, len, stream, &slot, d_workspace, workspace_bytes, nullptr, sa);
+}
+
+extern "C" re_status re_shard_map_size(const re_handle *h, uint32_t *fwd_entries, uint32_t *bwd_entries) {
+    if (!h || !fwd_entries || !bwd_entries) { set_error("null argument"); return RE_E_INVALID_ARG; }
+    if (!scan_join(h)) { set_error("slice maps need both classic DFAs below 256 states"); return RE_E_CAPACITY; }
+    *fwd_entries = h->host.nfd + 1;
+    *bwd_entries = h->host.nbd + 1;
+    return RE_OK;
+}
+
+extern "C" re_status re_shard_entry(const re_handle *h, const uint8_t *maps, uint32_t count, uint32_t *entry,
+                                    uint32_t *entry_bwd, int32_t *accepted) {
+    if (!h || (count && (!maps || !entry || !entry_bwd)) || !accepted) { set_error("null argument"); return RE_E_INVALID_ARG; }
+    if (!scan_join(h)) { set_error("slice maps need both classic DFAs below 256 states"); return RE_E_CAPACITY; }
+    const Compiled &C = h->host;
+    const uint32_t nsf = C.nfd + 1, nsb = C.nbd + 1, per = nsf + nsb;
+    if (!count) { *accepted = 0; return RE_OK; }
+    // forward: E_0 = I; E_{r+1} = fwd_r(E_r); the text ends in fwd_{N-1}(E_{N-1})
+    uint32_t e = 1;
+    bool alive = true;
+    for (uint32_t r = 0; r < count; ++r) {
+        entry[r] = e;
+        e = e < nsf ? maps[(size_t)r * per + e] : 0u;
+        alive = alive && e != 0;
+    }
+    // backward: Ê_{N-1} = F; Ê_{r-1} = bwd_r(Ê_r)
+    uint32_t b = 1;
+    for (uint32_t r = count; r-- > 0;) {
+        entry_bwd[r] = b;
+        b = b < nsb ? maps[(size_t)r * per + nsf + b] : 0u;
+    }
+    // accepted iff the forward states survive the whole text and the last one meets F
+    bool acc = alive;
+    if (acc) {
+        acc = false;
+        for (uint32_t w = 0; w < C.W; ++w)
+            acc = acc || (C.fBits[(size_t)e * C.W + w] & C.bBits[(size_t)1 * C.W + w]) != 0;
+    }
+    *accepted = acc ? 1 : 0;
+    if (!acc)                                                 // every column of a rejected text is empty
+        for (uint32_t r = 0; r < count; ++r) entry[r] = 0;
+    return RE_OK;
+}
+
+extern "C" re_status re_parse_slice(re_handle *h, const uint8_t *d_text, uint64_t len, uint32_t entry,
+                                    uint32_t entry_bwd, re_stream stream, re_slpf *slpf, void *d_workspace,
+                                    uint64_t workspace_bytes, const re_parse_opts *opts) {
+    if (!h) { set_error("null handle"); return RE_E_INVALID_ARG; }
+    if (!len) { set_error("a slice is not empty"); return RE_E_INVALID_ARG; }
+    if (entry > h->host.nfd || entry_bwd > h->host.nbd) { set_error("entry state out of range"); return RE_E_INVALID_ARG; }
+    if (opts && (opts->flags & RE_PARSE_RECOGNIZE_ONLY)) { set_error("slices are parsed, not recognized"); return RE_E_INVALID_ARG; }
+    SliceArgs sa;
+    sa.fin = entry;
+    sa.bin = entry_bwd;
+    return parse_impl(h, d_text, len, stream, slpf, d_workspace, workspace_bytes, opts, sa);
+}
+
+extern "C" re_status re_state_bits(const re_handle *h, int32_t forward, uint32_t id, uint64_t *bits, uint32_t cap_words) {
+    if (!h || !bits) { set_error("null argument"); return RE_E_INVALID_ARG; }
+    const Compiled &C = h->host;
+    if (cap_words < C.W) { set_error("buffer too small"); return RE_E_CAPACITY; }
+    if (id >= (forward ? C.nf : C.nb)) { set_error("state id out of range"); return RE_E_INVALID_ARG; }
+    const std::vector<uint64_t> &src = forward ? C.fBits : C.bBits;
+    std::memcpy(bits, src.data() + (size_t)id * C.W, C.W * 8);
+    return RE_OK;
+}

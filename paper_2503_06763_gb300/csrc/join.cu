@@ -104,7 +104,7 @@ __device__ void classify(const Params &p, bool fwd, uint32_t i) {
 }
 
 __device__ void classify_at(const Params &p, uint32_t i) {
-    if (i == 0) {
+    if (i == 0 && !(p.shard & SHARD_PREV)) {
         p.w.FJ[0] = p.t.fI;
         p.w.FJ[1] = p.w.Rf[0];
         p.w.fkind[0] = 0;
@@ -112,7 +112,7 @@ __device__ void classify_at(const Params &p, uint32_t i) {
         classify(p, true, i);
     }
     if (p.recognize) return;
-    if (i == p.c - 1) {
+    if (i == p.c - 1 && !(p.shard & SHARD_NEXT)) {
         p.w.BJ[p.c] = p.t.bF;
         p.w.BJ[i] = p.w.Rb[(size_t)i * p.t.msb];
         p.w.bkind[i] = 0;
@@ -154,6 +154,71 @@ __global__ void join_chain_kernel(const __grid_constant__ Params p) {
     pdl_trigger();
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < p.c) chain_at(p, i);
+}
+
+__device__ bool grid_barrier(uint32_t *w);
+
+// ------------------------------------------------------------------ slice maps
+// A slice of a longer text (sharded parse): its forward map sends the
+// forward state S at the slice's start to the state at its end, the
+// composition of its chunk maps (Eq. joiner) in order; its backward map sends
+// the backward state at the slice's end to the state at its start.  Every
+// chunk's map over the classic-DFA states is a byte table (eval_chunk; the
+// first chunk of the text's first slice starts from I, so its map is
+// constant, and the last chunk of the last slice from F), and the tables are
+// composed by a tree reduction: in round r, the table of chunk i (i a
+// multiple of 2^{r+1}) absorbs that of chunk i + 2^r.  Cooperative launch,
+// the rounds separated by the bounded grid barrier.
+template <uint32_t LANES>
+__device__ void shard_map(const Params &p, uint8_t *maps) {
+    const uint32_t lane = LANES == 1 ? 0u : (threadIdx.x & 31), upb = blockDim.x / LANES;
+    const uint64_t gw = (uint64_t)blockIdx.x * upb + threadIdx.x / LANES, nw = (uint64_t)gridDim.x * upb;
+    const uint32_t nsf = p.t.nfd + 1, nsb = p.t.nbd + 1, c = p.c;
+    bool bad = false;
+    for (uint64_t i = gw; i < c; i += nw) {
+        uint8_t *T = p.w.fTab + i * nsf;
+        const bool first = i == 0 && !(p.shard & SHARD_PREV);           // runs from I: one output
+        for (uint32_t S = lane; S < nsf; S += LANES)
+            T[S] = (uint8_t)(first ? (S ? p.w.Rf[0] : 0u) : eval_chunk(p, true, (uint32_t)i, S, bad));
+        uint8_t *B = p.w.bTab + i * nsb;
+        const bool last = i == c - 1 && !(p.shard & SHARD_NEXT);         // runs from F: one output
+        for (uint32_t S = lane; S < nsb; S += LANES)
+            B[S] = (uint8_t)(last ? (S ? p.w.Rb[(size_t)i * p.t.msb] : 0u) : eval_chunk(p, false, (uint32_t)i, S, bad));
+    }
+    if (bad) atomicExch(&p.w.flags[FLAG_INTERNAL], 1);
+    for (uint32_t r = 0; (1ull << r) < c; ++r) {
+        if (!grid_barrier(p.w.scan)) { atomicExch(&p.w.flags[FLAG_TIMEOUT], 1); return; }
+        const uint64_t step = 1ull << r, pairs = (c + 2 * step - 1) / (2 * step);
+        for (uint64_t q = gw; q < pairs; q += nw) {
+            const uint64_t i = q * 2 * step, j = i + step;
+            if (j >= c) continue;
+            uint8_t *Ti = p.w.fTab + i * nsf;                          // [i, j) then [j, j + step)
+            const uint8_t *Tj = p.w.fTab + j * nsf;
+            for (uint32_t S = lane; S < nsf; S += LANES) Ti[S] = __ldcg(Tj + __ldcg(Ti + S));
+            uint8_t *Bi = p.w.bTab + i * nsb;                          // the later range first
+            const uint8_t *Bj = p.w.bTab + j * nsb;
+            uint8_t v[kScanStates / (LANES == 1 ? 1 : 32)];
+            uint32_t nv = 0;
+            for (uint32_t S = lane; S < nsb; S += LANES) v[nv++] = __ldcg(Bi + __ldcg(Bj + S));
+            if (LANES == 32) __syncwarp();
+            nv = 0;
+            for (uint32_t S = lane; S < nsb; S += LANES) Bi[S] = v[nv++];
+        }
+    }
+    if (!grid_barrier(p.w.scan)) { atomicExch(&p.w.flags[FLAG_TIMEOUT], 1); return; }
+    if (blockIdx.x == 0) {                                            // the slice's maps
+        for (uint32_t S = threadIdx.x; S < nsf; S += blockDim.x) maps[S] = __ldcg(p.w.fTab + S);
+        for (uint32_t S = threadIdx.x; S < nsb; S += blockDim.x) maps[nsf + S] = __ldcg(p.w.bTab + S);
+        if (threadIdx.x == 0) {
+            const int32_t fl = __ldcg(&p.w.flags[FLAG_INTERNAL]), to = __ldcg(&p.w.flags[FLAG_TIMEOUT]);
+            *p.status = to ? RE_E_TIMEOUT : fl ? RE_E_INTERNAL : RE_OK;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlockThreads) join_map_kernel(const __grid_constant__ Params p, uint8_t *maps) {
+    if (p.t.nfd < 16 && p.t.nbd < 16) shard_map<1>(p, maps);
+    else shard_map<32>(p, maps);
 }
 
 // Live slots of chunk i (their end state is not the empty set).
@@ -442,6 +507,26 @@ void launch_flags_init(const Params &p, cudaStream_t s) { flags_init_kernel<<<1,
 void launch_batch_init(const Params *texts, uint32_t nt, uint32_t *queues, uint32_t nq, cudaStream_t s) {
     const uint32_t n = nt > nq ? nt : nq;
     batch_init_kernel<<<(n + kBlockThreads - 1) / kBlockThreads, kBlockThreads, 0, s>>>(texts, nt, queues, nq);
+}
+
+// A slice's maps: classify (for the chunks' live slots), then the reduction.
+bool launch_shard_map(const Params &p, uint8_t *d_maps, cudaStream_t s, int sm_count) {
+    const uint32_t blocks = (p.c + kBlockThreads - 1) / kBlockThreads;
+    launch_dependent(join_classify_kernel, blocks, kBlockThreads, 0, s, p);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, join_map_kernel, kBlockThreads, 0);
+    const uint64_t want = ((uint64_t)p.c + kBlockThreads / 32 - 1) / (kBlockThreads / 32);
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)std::max(per_sm, 1) * sm_count));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = kBlockThreads;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, join_map_kernel, p, d_maps) == cudaSuccess;
 }
 
 void launch_join_batch(const BatchGroup &b, cudaStream_t s) {

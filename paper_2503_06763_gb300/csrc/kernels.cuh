@@ -30,6 +30,8 @@ constexpr uint32_t kRecEntries = 96;  // (state, slot set) entries recorded per 
 
 enum Flag { FLAG_FFAIL = 0, FLAG_BFAIL = 1, FLAG_INTERNAL = 2, FLAG_DONE = 3, FLAG_TIMEOUT = 4, FLAG_COUNT = 5 };
 
+enum { SHARD_PREV = 1, SHARD_NEXT = 2 };
+
 // Join as a scan over chunk maps (join.cu): used when both classic DFAs have
 // at most kScanStates states (ids fit a byte), so a chunk's map over them is
 // a byte table.
@@ -74,6 +76,9 @@ struct Params {
     uint32_t rvar;                  // reach shape (RE_PARSE_REACH): 1 byte tables, one direction per
                                     // block; 2 / 3 warp pairs, 3 / 2 stages; 4 one lane per chunk
     uint32_t rstages;               // TMA ring stages of the warp-pair and one-lane shapes
+    uint32_t shard;                 // a slice of a longer text: SHARD_PREV, its first chunk speculates from
+                                    // the byte before it (x[-1]); SHARD_NEXT, its last chunk from the
+                                    // byte after it (x[len])
     uint32_t tmode;                 // TM_GLOBAL / TM_SMEM / TM_PAIR (see Tabs)
     uint32_t enc_in_smem;           // encoder table (DICT pair table, DENSE bitsets) in shared memory
     uint32_t merge_reg;             // one-byte tables: build & merge stages the classic-DFA rows and the
@@ -470,6 +475,7 @@ __host__ __device__ inline DevTables dfa_tables(const DevTables &t) {
 bool launch_reach(const Params &p, const CUtensorMap &text_map, const StateMaps &smaps, cudaStream_t s, uint32_t ms,
                   int sm_count);
 bool launch_join(const Params &p, cudaStream_t s, int sm_count);
+bool launch_shard_map(const Params &p, uint8_t *d_maps, cudaStream_t s, int sm_count);
 void launch_fixup(const Params &p, cudaStream_t s, int sm_count);
 void launch_merge(const Params &p, const CUtensorMap &out_map, cudaStream_t s, int sm_count);
 void launch_empty(const Params &p, cudaStream_t s);

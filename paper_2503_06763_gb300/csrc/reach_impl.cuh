@@ -382,8 +382,8 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
     uint32_t xs[WIDE ? kWide : 1], xk[WIDE ? kWide : 1], mx = 0;
     bool big = false;
     if (!FW) {
-    } else if (i == 0) {
-        mf = 1; sf[0] = enc_f<TM>(T, t.fI); kf[0] = 1; tstart = 0;      // J_0 = I
+    } else if (i == 0 && !(p.shard & SHARD_PREV)) {
+        mf = 1; sf[0] = enc_f<TM>(T, t.fI); kf[0] = 1; tstart = 0;      // J_0 = I (a slice: its entry state)
     } else {
         const uint32_t pr = class_of<TM>(T, t, __ldg(p.x + base - 1)) * t.ncls + class_of<TM>(T, t, __ldg(p.x + base));
         mf = __ldg(t.fSlotCount + pr);
@@ -399,8 +399,8 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
         tstart = 1;                                        // slot states follow byte 0
     }
     if (bwd) {
-        if (i == p.c - 1) {
-            mb = 1; sb[0] = enc_b<TM>(T, t.bF); kb[0] = 1; tlast = (int)len - 1;   // Ĵ_{c+1} = F
+        if (i == p.c - 1 && !(p.shard & SHARD_NEXT)) {
+            mb = 1; sb[0] = enc_b<TM>(T, t.bF); kb[0] = 1; tlast = (int)len - 1;   // Ĵ_{c+1} = F (or the slice's)
         } else {
             const uint32_t pr = class_of<TM>(T, t, __ldg(p.x + base + len - 1)) * t.ncls +
                                 class_of<TM>(T, t, __ldg(p.x + base + len));

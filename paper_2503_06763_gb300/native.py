@@ -35,6 +35,7 @@ EXPORTS = ["re_compile", "re_free", "re_get_info", "re_segment_name", "re_dict_c
            "re_slpf_layout", "re_workspace_size", "re_parse", "re_batch_plan", "re_batch_workspace_size",
            "re_batch_chunk_len", "re_parse_batch", "re_batch_run", "re_batch_free", "re_match_workspace_size",
            "re_matches", "re_autotune", "re_tuned", "re_parse_host",
+           "re_shard_map_size", "re_shard_map", "re_shard_entry", "re_parse_slice", "re_state_bits",
            "re_parse_static",
            "re_last_error"]
 RE_STATIC_SCRATCH_BYTES = 64 << 20
@@ -119,6 +120,16 @@ def load():
     lib.re_autotune.argtypes = [vp, vp, u64, ctypes.POINTER(Slpf), vp, u64, vp, ctypes.POINTER(ParseOpts),
                                 ctypes.POINTER(u32)]
     lib.re_autotune.restype = i32
+    lib.re_shard_map_size.argtypes = [vp, ctypes.POINTER(u32), ctypes.POINTER(u32)]
+    lib.re_shard_map_size.restype = i32
+    lib.re_shard_map.argtypes = [vp, vp, u64, u32, vp, vp, u64, vp, vp]
+    lib.re_shard_map.restype = i32
+    lib.re_shard_entry.argtypes = [vp, vp, u32, vp, vp, ctypes.POINTER(ctypes.c_int32)]
+    lib.re_shard_entry.restype = i32
+    lib.re_parse_slice.argtypes = [vp, vp, u64, u32, u32, vp, ctypes.POINTER(Slpf), vp, u64, ctypes.POINTER(ParseOpts)]
+    lib.re_parse_slice.restype = i32
+    lib.re_state_bits.argtypes = [vp, ctypes.c_int32, u32, vp, u32]
+    lib.re_state_bits.restype = i32
     lib.re_tuned.argtypes = [vp, u64, u32, ctypes.POINTER(u32), ctypes.POINTER(u32)]
     lib.re_tuned.restype = i32
     lib.re_parse_host.argtypes = [vp, vp, u64, vp, vp, vp, ctypes.POINTER(Slpf), vp, u64, vp, ctypes.POINTER(ParseOpts)]
@@ -347,6 +358,72 @@ class Regex:
                                    d_text.data_ptr() if n else None, ctypes.byref(slpf), workspace.data_ptr(),
                                    workspace.numel(), ctypes.c_void_p(s.cuda_stream), ctypes.byref(opts)))
         return kname
+
+    # ------------------------------------------------------------------ sharded parse
+    def shard_map_size(self):
+        """(forward entries, backward entries) of a slice's maps."""
+        f, b = ctypes.c_uint32(), ctypes.c_uint32()
+        check(load().re_shard_map_size(self._h, ctypes.byref(f), ctypes.byref(b)))
+        return f.value, b.value
+
+    def shard_map(self, text, prev: bool, nxt: bool, stream=None):
+        """re_shard_map on a CUDA uint8 slice (a view whose neighbouring bytes
+        are readable where prev / nxt is set): a host uint8 array of the
+        forward then backward map."""
+        import numpy as np
+        import torch
+        n = text.numel()
+        nf, nb = self.shard_map_size()
+        s = stream if stream is not None else torch.cuda.current_stream(text.device)
+        with torch.cuda.stream(s):
+            maps = torch.empty(nf + nb, dtype=torch.uint8, device=text.device)
+            st = torch.empty(1, dtype=torch.int32, device=text.device)
+            ws = torch.empty(max(self.workspace_size(n), 256), dtype=torch.uint8, device=text.device)
+        flags = (1 if prev else 0) | (2 if nxt else 0)
+        check(load().re_shard_map(self._h, text.data_ptr(), n, flags, ctypes.c_void_p(s.cuda_stream),
+                                  ws.data_ptr(), ws.numel(), maps.data_ptr(), st.data_ptr()))
+        s.synchronize()
+        status = int(st.item())
+        if status != RE_OK:
+            raise ReError(status, "slice map")
+        return maps.cpu().numpy().astype(np.uint8)
+
+    def shard_entry(self, maps):
+        """Host composition of the slices' maps (a [N, nf + nb] uint8 array):
+        (forward entry states, backward entry states, accepted)."""
+        import numpy as np
+        m = np.ascontiguousarray(maps, dtype=np.uint8)
+        cnt = m.shape[0]
+        e = np.zeros(cnt, dtype=np.uint32)
+        eb = np.zeros(cnt, dtype=np.uint32)
+        acc = ctypes.c_int32()
+        check(load().re_shard_entry(self._h, m.ctypes.data, cnt, e.ctypes.data, eb.ctypes.data, ctypes.byref(acc)))
+        return e, eb, bool(acc.value)
+
+    def parse_slice(self, text, entry: int, entry_bwd: int, kind: str = "auto", stream=None):
+        """re_parse_slice: the slice's len + 1 columns of the whole text's SLPF."""
+        import torch
+        n = text.numel()
+        kname, cb, _ = self.layout(n, kind)
+        dt = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}[cb]
+        s = stream if stream is not None else torch.cuda.current_stream(text.device)
+        with torch.cuda.stream(s):
+            out = torch.empty(n + 1, dtype=dt, device=text.device)
+            status = torch.empty(1, dtype=torch.int32, device=text.device)
+            ws = torch.empty(max(self.workspace_size(n), 256), dtype=torch.uint8, device=text.device)
+        slpf = Slpf(KINDS[kname], cb, 0, out.data_ptr(), out.numel() * out.element_size(), status.data_ptr())
+        opts = ParseOpts(KINDS[kname], 0, 0, 0, None)
+        check(load().re_parse_slice(self._h, text.data_ptr(), n, int(entry), int(entry_bwd),
+                                    ctypes.c_void_p(s.cuda_stream), ctypes.byref(slpf), ws.data_ptr(), ws.numel(),
+                                    ctypes.byref(opts)))
+        return out, status, kname
+
+    def state_bits(self, forward: bool, state: int):
+        """Segment set of a state as a [W] uint64 array (host)."""
+        import numpy as np
+        v = np.zeros(self.words, dtype=np.uint64)
+        check(load().re_state_bits(self._h, 1 if forward else 0, state, v.ctypes.data, self.words))
+        return v
 
     # ------------------------------------------------------------------ decoding
     def decode(self, cols, kind: str):
