@@ -44,7 +44,8 @@ typedef enum {
     RE_REJECTED = 1,               /* status word only: text not in L(e); all columns empty */
     RE_E_INVALID_ARG = -1,
     RE_E_SYNTAX = -2,              /* malformed RE */
-    RE_E_INFINITE_AMBIGUITY = -3,  /* an iterated sub-RE derives the empty text (Sect. 2.1, App. A) */
+    RE_E_INFINITE_AMBIGUITY = -3,  /* an iterated sub-RE derives the empty text (Sect. 2.1, App. A)
+                                      and re_compile_opts.sample_limit is 0 */
     RE_E_TOO_MANY_STATES = -4,     /* automaton exceeds re_compile_opts.max_states */
     RE_E_NOMEM = -5,               /* host or device allocation failed (re_compile only) */
     RE_E_CUDA = -6,                /* CUDA runtime error; see re_last_error() */
@@ -66,10 +67,27 @@ typedef enum {
  *           dictionary, else DENSE when ell <= 64.                            */
 typedef enum { RE_SLPF_AUTO = 0, RE_SLPF_DENSE = 1, RE_SLPF_DICT = 2 } re_slpf_kind;
 
+/* Infinitely ambiguous REs (App. A, "Infinite ambiguity"): an RE whose
+ * iterated sub-RE derives the empty text gives some texts infinitely many
+ * LSTs.  sample_limit = 0 rejects such an RE with RE_E_INFINITE_AMBIGUITY.
+ * sample_limit = L in [1, RE_SAMPLE_LIMIT_MAX] accepts it and keeps a finite
+ * sample: the segment computation counts the numbered symbols of each
+ * segment and keeps the segments in which every symbol (an operator
+ * parenthesis or an ε) occurs at most L times.  The SLPF of a text then
+ * holds exactly those LSTs of the text whose every segment obeys the limit;
+ * with L = 2 the sample of Fig. (infamb) holds its first three trees, with
+ * L = 3 all four shown.  On a finitely ambiguous RE no segment repeats a
+ * symbol, so every L gives the exact parser.  The segment count grows about
+ * linearly with L on the REs of App. A; re_compile returns
+ * RE_E_TOO_MANY_STATES when the enumeration or the automata outgrow their
+ * caps.                                                                    */
+#define RE_SAMPLE_LIMIT_MAX 16u
+
 typedef struct {
     uint32_t max_states;      /* cap on forward + reverse automaton states; 0 = 1<<20 */
     uint32_t max_dict;        /* cap on dictionary pairs considered; 0 = 1<<24 */
     uint32_t flags;           /* 0, RE_COMPILE_HOST_ONLY and/or RE_COMPILE_DFA_STARTS */
+    uint32_t sample_limit;    /* 0 = reject infinitely ambiguous REs; L >= 1 = sample them (above) */
 } re_compile_opts;
 
 /* Build the host tables only (no device upload, no CUDA call): the handle
@@ -159,6 +177,8 @@ typedef struct {
     uint32_t fwd_slots_max;   /* most forward speculative runs for one chunk */
     uint32_t bwd_slots_max;   /* most backward speculative runs for one chunk */
     uint64_t dict_size;       /* distinct non-empty columns C = B ∩ B̂ (0 = no dictionary) */
+    uint32_t inf_ambiguous;   /* 1 when the RE is infinitely ambiguous (its SLPFs are samples) */
+    uint32_t sample_limit;    /* the compile option's sample_limit */
 } re_info;
 
 /* Compile a pattern (Sect. 2.1 syntax plus App. A character features:

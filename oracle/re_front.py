@@ -34,7 +34,16 @@ Readings where the paper is silent or ambiguous:
     first symbol of every LST", which is ``1(`` whenever the root is an
     operator and the root leaf itself otherwise.
   * A star / cross whose body derives the empty text is infinitely ambiguous
-    and rejected (Sect. 2.1, App. A "Infinite ambiguity").
+    (Sect. 2.1, App. A "Infinite ambiguity").  With no sample limit such an RE
+    is rejected.  With a limit L >= 1 it is sampled as App. A describes: the
+    segment computation counts the numbered symbols of the meta-prefix being
+    extended and keeps only meta-prefixes where each symbol (parenthesis or ε)
+    occurs at most L times.  The count covers the whole segment, its first
+    symbol included; end-letters cannot repeat inside one segment anyway.  The
+    SLPF then holds exactly the LSTs whose every segment obeys the limit
+    (``trees.lsts_sampled`` enumerates them from the trees alone).  On a
+    finitely ambiguous RE no meta-prefix repeats a symbol (Sect. 2.3.3,
+    termination of the segment algorithm), so any L gives the full segment set.
 """
 from __future__ import annotations
 
@@ -383,6 +392,8 @@ class Compiled:
     initial: frozenset       # indices of I
     final: frozenset         # indices of F
     folseg: list             # index -> frozenset of follower indices (Eq. folsegdef)
+    sample_limit: int = 0    # 0: exact; L >= 1: each symbol at most L times per segment
+    infinitely_ambiguous: bool = False
 
     @property
     def ell(self) -> int:
@@ -412,25 +423,36 @@ def segment_key(seg):
     return tuple(symbol_key(s) for s in seg)
 
 
-def compile_re(pattern) -> Compiled:
-    """RE text -> segments, I, F and FolSeg (Sects. 2.2-2.3)."""
-    c = compile_tree(parse(pattern))
+def compile_re(pattern, sample_limit: int = 0) -> Compiled:
+    """RE text -> segments, I, F and FolSeg (Sects. 2.2-2.3).
+
+    sample_limit = 0 rejects an infinitely ambiguous RE (InfiniteAmbiguity);
+    L >= 1 accepts it and samples its LSTs (App. A, "Infinite ambiguity")."""
+    c = compile_tree(parse(pattern), sample_limit)
     c.pattern = pattern if isinstance(pattern, bytes) else pattern.encode("latin-1")
     return c
 
 
-def compile_tree(root: Node) -> Compiled:
+def compile_tree(root: Node, sample_limit: int = 0) -> Compiled:
     """Compile an already built structure tree (used for Ex. 5's e(k) family)."""
     import copy
     root = expand_repetitions(copy.deepcopy(root))
-    check_finite_ambiguity(root)
+    try:
+        check_finite_ambiguity(root)
+        infinite = False
+    except InfiniteAmbiguity:
+        if sample_limit < 1:
+            raise
+        infinite = True
     number(root)
     fol: dict = {}
     _, first, _ = _glushkov(("seq", [_lst_expr(root), ("sym", END)]), fol)
-    return _finish(root, fol, next(iter(first)))
+    c = _finish(root, fol, next(iter(first)), sample_limit)
+    c.infinitely_ambiguous = infinite
+    return c
 
 
-def _finish(root, fol, first_symbol) -> Compiled:
+def _finish(root, fol, first_symbol, sample_limit: int = 0) -> Compiled:
     """Symbols, Fig. segmentalgo (MetaPrefix), I, F and Eq. folsegdef."""
     symbols, classes = [], {}
 
@@ -459,8 +481,11 @@ def _finish(root, fol, first_symbol) -> Compiled:
             if is_end_letter(r):
                 Q.add(sigma)
             else:
-                if r in sigma:
+                seen = sigma.count(r)
+                if seen and sample_limit < 1:
                     raise InfiniteAmbiguity("repeated symbol in a meta-prefix")
+                if seen >= max(sample_limit, 1):
+                    continue                 # App. A: the counter of r is at its limit
                 meta_prefix(r, (r,) + sigma)
 
     for a in symbols:
@@ -474,4 +499,4 @@ def _finish(root, fol, first_symbol) -> Compiled:
               for rho in segments]
     return Compiled(pattern=b"", root=root, symbols=symbols, fol=fol, first_symbol=first_symbol,
                     classes=classes, segments=segments, index=index, initial=initial,
-                    final=final, folseg=folseg)
+                    final=final, folseg=folseg, sample_limit=sample_limit)

@@ -81,6 +81,75 @@ def lsts(c: Compiled, text: bytes, limit: int = 1_000_000):
     return [toks for j, toks in gen(id(c.root), 0) if j == n]
 
 
+def lsts_sampled(c: Compiled, text: bytes, sample_limit: int, cap: int = 200_000):
+    """The LSTs of ``text`` (tuples without ⊣) in which every segment holds
+    each numbered symbol at most ``sample_limit`` times (App. A, "Infinite
+    ambiguity").
+
+    Unlike ``lsts`` an iteration may derive the empty text, so an infinitely
+    ambiguous RE has infinitely many trees; the limit keeps finitely many.
+    The trees are built from the structure tree alone (Sect. 2.1, Example 1),
+    their LST written left to right; a branch ends as soon as the current
+    segment (the symbols since the last terminal) holds a symbol more than
+    ``sample_limit`` times, a terminal misses its byte, or the text runs out.
+    Every body instance of an iterator adds at least one symbol, so the search
+    is finite.  Raises OverflowError past ``cap`` trees.
+    """
+    n = len(text)
+    out = []
+    # work items: ("sym", s) emits s; ("node", nd) expands nd;
+    # ("iter", nd, k) decides on a further instance after k of them
+    stack0 = (("node", c.root),)
+
+    def run(work, pos, counts, lst):
+        while work:
+            item, work = work[0], work[1:]
+            if item[0] == "sym":
+                s = item[1]
+                if s[0] == "t":
+                    if pos >= n or text[pos] not in c.classes[s[1]]:
+                        return
+                    pos, counts = pos + 1, {}
+                else:
+                    k = counts.get(s, 0) + 1
+                    if k > sample_limit:
+                        return
+                    counts = dict(counts); counts[s] = k
+                lst = lst + (s,)
+                continue
+            nd = item[1]
+            if item[0] == "node":
+                num = nd.num
+                if nd.kind == "term":
+                    work = (("sym", ("t", num)),) + work
+                elif nd.kind == "eps":
+                    work = (("sym", ("e", num)),) + work
+                elif nd.kind in ("cat", "rep"):
+                    work = ((("sym", ("(", num)),) + tuple(("node", ch) for ch in nd.children)
+                            + (("sym", (")", num)),) + work)
+                elif nd.kind == "alt":
+                    for ch in nd.children:
+                        run((("sym", ("(", num)), ("node", ch), ("sym", (")", num))) + work, pos, counts, lst)
+                    return
+                elif nd.kind in ("star", "plus"):
+                    work = (("sym", ("(", num)), ("iter", nd, 0), ("sym", (")", num))) + work
+                else:
+                    raise AssertionError(nd.kind)
+                continue
+            k = item[2]                                     # "iter"
+            if k >= 1 or nd.kind == "star":                 # stop here
+                run(work, pos, counts, lst)
+            run((("node", nd.children[0]), ("iter", nd, k + 1)) + work, pos, counts, lst)
+            return
+        if pos == n and counts.get(END, 0) < 1:            # the last segment ends with ⊣
+            out.append(lst)
+            if len(out) > cap:
+                raise OverflowError("too many trees")
+
+    run(stack0, 0, {}, ())
+    return out
+
+
 def factor(lst) -> list:
     """Factor LST ⊣ into segments mu a (Sect. 2.3.2)."""
     segs, cur = [], []
@@ -93,9 +162,10 @@ def factor(lst) -> list:
     return segs
 
 
-def slpf_by_trees(c: Compiled, text: bytes):
-    """(columns as sets of segment indices, number of trees) by enumeration."""
-    trees = lsts(c, text)
+def slpf_by_trees(c: Compiled, text: bytes, sample_limit: int = 0):
+    """(columns as sets of segment indices, number of trees) by enumeration;
+    with sample_limit >= 1 over ``lsts_sampled``."""
+    trees = lsts_sampled(c, text, sample_limit) if sample_limit else lsts(c, text)
     cols = [set() for _ in range(len(text) + 1)]
     for t in trees:
         segs = factor(t)

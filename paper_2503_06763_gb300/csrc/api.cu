@@ -369,6 +369,8 @@ re_status re_get_info(const re_handle *h, re_info *info) {
     info->bwd_states = C.nb - 1; info->bwd_dfa_states = C.nbd;
     info->fwd_slots_max = C.msf; info->bwd_slots_max = C.msb;
     info->dict_size = C.has_dict ? C.dict_size : 0;
+    info->inf_ambiguous = C.inf_amb ? 1u : 0u;
+    info->sample_limit = C.sample_limit;
     return RE_OK;
 }
 

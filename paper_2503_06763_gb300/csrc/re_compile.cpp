@@ -380,8 +380,15 @@ re_status compile_pattern(const char *pattern, size_t len, const re_compile_opts
         err = "syntax: " + e.msg;
         return RE_E_SYNTAX;
     }
+    const uint32_t sample_limit = opts ? opts->sample_limit : 0;
+    if (sample_limit > RE_SAMPLE_LIMIT_MAX) {
+        err = "re_compile_opts.sample_limit above RE_SAMPLE_LIMIT_MAX";
+        return RE_E_INVALID_ARG;
+    }
     expand(nodes, root);
-    if (!finitely_ambiguous(nodes, root)) {
+    C.inf_amb = !finitely_ambiguous(nodes, root);
+    C.sample_limit = sample_limit;
+    if (C.inf_amb && sample_limit == 0) {
         err = "an iterated sub-expression derives the empty text (infinitely ambiguous)";
         return RE_E_INFINITE_AMBIGUITY;
     }
@@ -442,25 +449,33 @@ re_status compile_pattern(const char *pattern, size_t len, const re_compile_opts
     const int lst_first = first_sym[root];
     auto is_end_letter = [&](int s) { return syms[s].kind == LEAF_T || syms[s].kind == ENDMARK; };
 
-    // ---- segments: forward enumeration from every segment start
+    // ---- segments: forward enumeration from every segment start.  Each
+    // symbol may occur once on a path (finite ambiguity), or up to
+    // sample_limit times when an infinitely ambiguous RE is sampled (App. A,
+    // "Infinite ambiguity": counters for the numbered symbols).
     std::set<std::vector<int>> segset;
     std::vector<int> path;
-    std::vector<char> onpath(nsym, 0);
-    bool amb = false;
+    std::vector<uint32_t> onpath(nsym, 0);
+    const uint32_t per_symbol = sample_limit ? sample_limit : 1;
+    bool amb = false, over = false;
     size_t budget = 0;
     std::function<void(int)> extend = [&](int s) {
-        if (amb || ++budget > 50000000) { amb = true; return; }
+        if (amb || over) return;
+        if (++budget > 50000000) { over = true; return; }
         path.push_back(s);
-        onpath[s] = 1;
+        ++onpath[s];
         if (is_end_letter(s)) {
             segset.insert(path);
         } else {
             for (int nx : fol[s]) {
-                if (onpath[nx]) { amb = true; break; }
+                if (onpath[nx] >= per_symbol) {
+                    if (!sample_limit) { amb = true; break; }
+                    continue;
+                }
                 extend(nx);
             }
         }
-        onpath[s] = 0;
+        --onpath[s];
         path.pop_back();
     };
     std::vector<char> is_start(nsym, 0);
@@ -469,6 +484,7 @@ re_status compile_pattern(const char *pattern, size_t len, const re_compile_opts
         if (syms[s].kind == LEAF_T) for (int nx : fol[s]) is_start[nx] = 1;
     for (uint32_t s = 0; s < nsym; ++s) if (is_start[s]) extend((int)s);
     if (amb) { err = "segment enumeration did not terminate (infinite ambiguity)"; return RE_E_INFINITE_AMBIGUITY; }
+    if (over) { err = "segment enumeration exceeds its step budget"; return RE_E_TOO_MANY_STATES; }
 
     // canonical order: lexicographic over symbol keys (number, kind), ⊣ last
     auto key = [&](int s) -> std::pair<uint64_t, int> {

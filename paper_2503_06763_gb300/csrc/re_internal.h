@@ -86,6 +86,8 @@ struct Compiled {
     std::vector<uint64_t> folseg;             // [ell][W] FolSeg(q) (Eq. folsegdef)
     std::vector<std::vector<int32_t>> parens; // per segment, in order: +k for k(, -k for )k
     uint32_t max_group = 0;                   // largest operator number
+    bool inf_amb = false;                     // an iterated sub-RE derives the empty text
+    uint32_t sample_limit = 0;                // per-segment symbol limit when sampling (App. A)
 };
 
 // Compile; returns RE_OK or an error with a message in err.

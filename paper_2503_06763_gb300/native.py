@@ -48,7 +48,8 @@ class ReError(RuntimeError):
 
 
 class CompileOpts(ctypes.Structure):
-    _fields_ = [("max_states", ctypes.c_uint32), ("max_dict", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+    _fields_ = [("max_states", ctypes.c_uint32), ("max_dict", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("sample_limit", ctypes.c_uint32)]
 
 
 class ParseOpts(ctypes.Structure):
@@ -69,7 +70,8 @@ class Slpf(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in (
         "n_segments", "n_positions", "n_classes", "words_per_col", "fwd_states", "fwd_dfa_states",
-        "bwd_states", "bwd_dfa_states", "fwd_slots_max", "bwd_slots_max")] + [("dict_size", ctypes.c_uint64)]
+        "bwd_states", "bwd_dfa_states", "fwd_slots_max", "bwd_slots_max")] + [("dict_size", ctypes.c_uint64)] + [
+        ("inf_ambiguous", ctypes.c_uint32), ("sample_limit", ctypes.c_uint32)]
 
 
 _lib = None
@@ -151,14 +153,16 @@ class Regex:
     """A compiled RE (owns the library handle and its device tables)."""
 
     def __init__(self, pattern, max_states: int = 0, max_dict: int = 0, host_only: bool = False,
-                 dfa_starts: bool = False):
+                 dfa_starts: bool = False, sample_limit: int = 0):
         """dfa_starts: forward speculation from every DFA state instead of the
-        ME-DFA starts (RE_COMPILE_DFA_STARTS, an ablation)."""
+        ME-DFA starts (RE_COMPILE_DFA_STARTS, an ablation).  sample_limit: 0
+        rejects an infinitely ambiguous RE; L >= 1 samples its LSTs, each
+        numbered symbol at most L times per segment (App. A)."""
         lib = load()
         pat = pattern.encode("latin-1") if isinstance(pattern, str) else bytes(pattern)
         self.pattern = pat
         flags = (RE_COMPILE_HOST_ONLY if host_only else 0) | (RE_COMPILE_DFA_STARTS if dfa_starts else 0)
-        opts = CompileOpts(max_states, max_dict, flags)
+        opts = CompileOpts(max_states, max_dict, flags, sample_limit)
         h = ctypes.c_void_p()
         check(lib.re_compile(pat, len(pat), ctypes.byref(opts), ctypes.byref(h)))
         self._h = h

@@ -360,3 +360,43 @@ def test_every_reach_shape(lib, shape, case):
         got = rx.decode(cols.cpu().numpy(), kind)
         bad = np.nonzero(np.any(got != want, axis=1))[0]
         assert bad.size == 0, (name, shape, chunk_len, bad[:5].tolist())
+
+
+# ---------------------------------------------------------------- sampled infinite ambiguity (App. A)
+SAMPLED_RES = {
+    "(a*|ab)+": (lambda r: str(r.choice(["a", "ab", "aa"])), ""),
+    "(a?b?)*": (lambda r: str(r.choice(["a", "b", "ab"])), ""),
+    "((a*)*b)*": (lambda r: "a" * int(r.integers(0, 4)) + "b", ""),
+    "((ab)?|c*)+a": (lambda r: str(r.choice(["ab", "c", "cc"])), "a"),
+    "(a|()|b)*c?": (lambda r: str(r.choice(["a", "b"])), "c"),
+}
+
+
+@pytest.mark.parametrize("pattern", list(SAMPLED_RES))
+@pytest.mark.parametrize("limit", [1, 2, 3])
+def test_sampled_infinite_ambiguity(lib, pattern, limit):
+    """An infinitely ambiguous RE compiled with a sample limit (each numbered
+    symbol at most L times per segment) parses on the GPU to the oracle's
+    sampled SLPF, on valid texts across chunks and on corrupted ones."""
+    rx = lib(pattern, sample_limit=limit)
+    c = compile_re(pattern, sample_limit=limit)
+    assert rx.segment_names() == c.names() and rx.info["inf_ambiguous"] == 1
+    piece, suffix = SAMPLED_RES[pattern]
+    rng = np.random.Generator(np.random.PCG64(limit))
+    for n in (1, 70, 1000, 20_003):
+        parts, size = [], 0
+        while size < n:
+            parts.append(piece(rng)); size += len(parts[-1])
+        text = ("".join(parts) + suffix).encode()
+        variants = [text]
+        if len(text) > 8:
+            bad = bytearray(text); bad[len(text) // 3] = ord("x")
+            variants.append(bytes(bad))
+        for t in variants:
+            host = np.frombuffer(t, dtype=np.uint8)
+            want = serial.parse(c, t)
+            for chunk_len in (64, 0):
+                got, st = gpu_cols(rx, host, chunk_len=chunk_len)
+                assert st == (0 if serial.accepted(want) else 1), (pattern, limit, n)
+                bad_cols = np.nonzero(np.any(got != want, axis=1))[0]
+                assert bad_cols.size == 0, (pattern, limit, n, chunk_len, bad_cols[:5].tolist())
