@@ -86,7 +86,7 @@ typedef enum { RE_SLPF_AUTO = 0, RE_SLPF_DENSE = 1, RE_SLPF_DICT = 2 } re_slpf_k
 typedef struct {
     uint32_t max_states;      /* cap on forward + reverse automaton states; 0 = 1<<20 */
     uint32_t max_dict;        /* cap on dictionary pairs considered; 0 = 1<<24 */
-    uint32_t flags;           /* 0, RE_COMPILE_HOST_ONLY and/or RE_COMPILE_DFA_STARTS */
+    uint32_t flags;           /* 0 or RE_COMPILE_HOST_ONLY | RE_COMPILE_DFA_STARTS | RE_COMPILE_DFA_STARTS_BWD */
     uint32_t sample_limit;    /* 0 = reject infinitely ambiguous REs; L >= 1 = sample them (above) */
 } re_compile_opts;
 
@@ -105,6 +105,15 @@ typedef struct {
  * speculation cost differs.  re_compile returns RE_E_TOO_MANY_STATES when a
  * class pair would need more than 32 runs.                                  */
 #define RE_COMPILE_DFA_STARTS 2u
+
+/* The same ablation for the backward runs: a chunk's backward speculative
+ * runs start from every state of the classic reverse DFA (those reachable
+ * from F), one run per distinct state after the chunk's last byte, and the
+ * backward join looks up the run of the actual state at the chunk's right
+ * edge.  Combine with RE_COMPILE_DFA_STARTS for both directions.  Results
+ * are identical; re_compile returns RE_E_TOO_MANY_STATES when a byte class
+ * would need more than 32 runs.                                             */
+#define RE_COMPILE_DFA_STARTS_BWD 4u
 
 typedef struct {
     re_slpf_kind kind;        /* requested encoding */

@@ -24,7 +24,12 @@ What is here, and the passage of the paper each part follows
 * ``parallel_equations`` -- the parallel algorithm's Eqs. reacher, joiner,
   builder and merger (Sect. 3.2) with DFA / ME-DFA transition functions
   computed on segment sets (Sect. 3.1), used for the Example 6 pins and
-  chunk-invariance checks.
+  chunk-invariance checks; ``parse_parallel_dfa_starts`` starts either
+  direction from every DFA state instead (Sect. 5's comparison).
+* ``speculation`` -- counts a chunk's speculative runs and transitions under
+  ME-DFA starts, all-DFA-state starts, forward-restricted backward starts and
+  shifted chunk edges (Sects. 3.1, 4.3), for the measured comparison of the
+  speculation reductions.
 
 Every function here is pinned by a ``-m "not gpu"`` test against values the
 paper prints, closed forms, or brute force; none is "parity unpinned".

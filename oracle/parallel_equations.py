@@ -96,21 +96,37 @@ def parse_parallel(c: Compiled, text: bytes, k: int):
     return cols, dict(R=R, Rh=Rh, J=J, Jh=Jh, B=B, Bh=Bh)
 
 
-def parse_parallel_dfa_starts(c: Compiled, text: bytes, k: int):
-    """The same equations with the forward reach started from every DFA
-    state instead of every ME-DFA singleton: the alternative the ME-DFA of
-    Sect. 3.1 improves on (Sect. 5 measures both).  R_{i,T} = delta*(T, y_i)
+def parse_parallel_dfa_starts(c: Compiled, text: bytes, k: int, forward: bool = True,
+                              backward: bool = False):
+    """The same equations with the reach started from every DFA state instead
+    of every ME-DFA singleton: the alternative the ME-DFA of Sect. 3.1
+    improves on (Sect. 5 measures both).  Forward: R_{i,T} = delta*(T, y_i)
     for every DFA state T; the join takes the run of the input state itself,
     J_i = R_{i,J_{i-1}} (J_{i-1} is a DFA state, or the empty set when the
-    text cannot continue).  The backward side keeps the ME-DFA starts."""
+    text cannot continue).  Backward likewise from every reverse DFA state,
+    Ĵ_i = R̂_{i,Ĵ_{i+1}}.  A direction not selected keeps the ME-DFA starts."""
     y = split(text, k)
     cnum = len(y)
-    starts = dfa_states(c)
-    R = [None] + [{T: run(c, T, y[i - 1]) for T in starts} for i in range(1, cnum + 1)]
-    J = [frozenset(c.initial)]
-    for i in range(1, cnum + 1):
-        J.append(R[i].get(J[i - 1], frozenset()))
-    Rh, Jh = backward_join(c, y)
+    if forward:
+        starts = dfa_states(c)
+        R = [None] + [{T: run(c, T, y[i - 1]) for T in starts} for i in range(1, cnum + 1)]
+        J = [frozenset(c.initial)]
+        for i in range(1, cnum + 1):
+            J.append(R[i].get(J[i - 1], frozenset()))
+    else:
+        R = [None] + [[run(c, frozenset([j]), y[i - 1]) for j in range(c.ell)] for i in range(1, cnum + 1)]
+        J = [frozenset(c.initial)]
+        for i in range(1, cnum + 1):
+            J.append(frozenset().union(*[R[i][j] for j in J[i - 1]]))
+    if backward:
+        starts = dfa_states(c, reverse=True)
+        Rh = [None] + [{T: run(c, T, y[i - 1], reverse=True) for T in starts} for i in range(1, cnum + 1)]
+        Jh = [None] * (cnum + 2)
+        Jh[cnum + 1] = frozenset(c.final)
+        for i in range(cnum, 0, -1):
+            Jh[i] = Rh[i].get(Jh[i + 1], frozenset())
+    else:
+        Rh, Jh = backward_join(c, y)
     cols, B, Bh = build_merge_compose(c, y, J, Jh)
     return cols, dict(R=R, Rh=Rh, J=J, Jh=Jh, B=B, Bh=Bh)
 

@@ -316,6 +316,7 @@ re_status re_compile(const char *pattern, size_t len, const re_compile_opts *opt
     const size_t i_f2 = add(C.f2.data(), C.f2.size() * 4), i_b2 = add(C.b2.data(), C.b2.size() * 4);
     const size_t i_fs = add(C.folseg.data(), C.folseg.size() * 8), i_dc = add(C.dict.data(), C.dict.size() * 8);
     const size_t i_fso = add(C.fSlotOf.data(), C.fSlotOf.size());
+    const size_t i_bso = add(C.bSlotOf.data(), C.bSlotOf.size());
     const size_t i_fby = add(C.fbyte.data(), C.fbyte.size()), i_bby = add(C.bbyte.data(), C.bbyte.size());
     DevTables &t = h->dev;
     t.fHashMask = C.fHashMask; t.bHashMask = C.bHashMask;
@@ -344,6 +345,7 @@ re_status re_compile(const char *pattern, size_t len, const re_compile_opts *opt
     t.bSlotCount = (const uint32_t *)(b + pc[i_bSC].off);
     t.pt = (const uint32_t *)(b + pc[i_pt].off);
     t.fSlotOf = C.fSlotOf.empty() ? nullptr : (const uint8_t *)(b + pc[i_fso].off);
+    t.bSlotOf = C.bSlotOf.empty() ? nullptr : (const uint8_t *)(b + pc[i_bso].off);
     t.f2 = C.f2.empty() ? nullptr : (const uint32_t *)(b + pc[i_f2].off);
     t.b2 = C.b2.empty() ? nullptr : (const uint32_t *)(b + pc[i_b2].off);
     t.folseg = (const uint64_t *)(b + pc[i_fs].off);

@@ -57,8 +57,10 @@ __device__ uint32_t eval_chunk(const Params &p, bool fwd, uint32_t i, uint32_t S
         pr = pair_bwd(p, i); m = __ldg(t.bSlotCount + pr); ms = t.msb; R = p.w.Rb + (size_t)i * ms;
         mask = t.bSlotMask + (size_t)pr * ms * W; bits = t.bBits;
     }
-    if (fwd && t.fSlotOf) {                      // starts from every DFA state: exact lookup
-        const uint32_t j = S < t.nf ? __ldg(t.fSlotOf + (size_t)pr * t.nf + S) : 0xFFu;
+    const uint8_t *of = fwd ? t.fSlotOf : t.bSlotOf;
+    if (of) {                                    // starts from every DFA state: exact lookup
+        const uint32_t n = fwd ? t.nf : t.nb;
+        const uint32_t j = S < n ? __ldg(of + (size_t)pr * n + S) : 0xFFu;
         return j == 0xFFu ? 0u : R[j];
     }
     const uint64_t *sb = bits + (size_t)S * W;

@@ -141,8 +141,10 @@ __device__ __forceinline__ bool any_and(const uint64_t *a, const uint64_t *b, ui
 
 // Slots of the class pair pr that input state S enters (bit j: slot j).
 __device__ __forceinline__ uint32_t slot_hits(const DevTables &t, bool fwd, uint32_t pr, uint32_t S) {
-    if (fwd && t.fSlotOf) {                      // starts from every DFA state: S enters its own slot only
-        const uint32_t j = S < t.nf ? __ldg(t.fSlotOf + (size_t)pr * t.nf + S) : 0xFFu;
+    const uint8_t *of = fwd ? t.fSlotOf : t.bSlotOf;
+    if (of) {                                    // starts from every DFA state: S enters its own slot only
+        const uint32_t n = fwd ? t.nf : t.nb;
+        const uint32_t j = S < n ? __ldg(of + (size_t)pr * n + S) : 0xFFu;
         return j == 0xFFu ? 0u : 1u << j;
     }
     const uint32_t W = t.W;

@@ -365,7 +365,7 @@ re_status compile_pattern(const char *pattern, size_t len, const re_compile_opts
                           Compiled &C, std::string &err) {
     uint32_t max_states = (opts && opts->max_states) ? opts->max_states : (1u << 20);
     uint64_t max_dict = (opts && opts->max_dict) ? opts->max_dict : (1ull << 24);
-    if (opts && (opts->flags & ~(RE_COMPILE_HOST_ONLY | RE_COMPILE_DFA_STARTS))) {
+    if (opts && (opts->flags & ~(RE_COMPILE_HOST_ONLY | RE_COMPILE_DFA_STARTS | RE_COMPILE_DFA_STARTS_BWD))) {
         err = "unknown re_compile_opts.flags";
         return RE_E_INVALID_ARG;
     }
@@ -740,6 +740,33 @@ re_status compile_pattern(const char *pattern, size_t len, const re_compile_opts
                     if (it->second < 0xFF) C.fSlotOf[(size_t)pr * nf + st] = (uint8_t)it->second;
                 }
                 msf = std::max<uint32_t>(msf, (uint32_t)L.size());
+            }
+    }
+    if (opts && (opts->flags & RE_COMPILE_DFA_STARTS_BWD)) {
+        // The same ablation backwards: runs from every reverse DFA state
+        // (ids 1..nbd, reachable from F), one slot per distinct state after
+        // the chunk's last byte (class cl); the class after the chunk plays
+        // no part, so every pair (cl, cn) has the same slots.
+        const uint32_t nb = btab.size();
+        C.bSlotOf.assign((size_t)ncls * ncls * nb, 0xFF);
+        msb = 1;
+        for (uint32_t cl = 0; cl < ncls; ++cl)
+            for (uint32_t cn = 0; cn < ncls; ++cn) {
+                const uint32_t pr = cl * ncls + cn;
+                auto &L = bsl[pr];
+                L.clear();
+                std::map<uint32_t, size_t> by_start;
+                for (uint32_t st = 1; st <= nbd; ++st) {
+                    const uint32_t nx = C.bT[(size_t)st * ncls + cl];
+                    if (nx == 0) continue;                 // no text continues leftwards from st
+                    auto it = by_start.find(nx);
+                    if (it == by_start.end()) {
+                        it = by_start.emplace(nx, L.size()).first;
+                        L.push_back({nx, std::vector<uint64_t>(W, 0)});   // keys unused: exact lookup
+                    }
+                    if (it->second < 0xFF) C.bSlotOf[(size_t)pr * nb + st] = (uint8_t)it->second;
+                }
+                msb = std::max<uint32_t>(msb, (uint32_t)L.size());
             }
     }
     C.msf = msf; C.msb = msb;

@@ -50,6 +50,7 @@ struct DevTables {
     const uint32_t *bSlotCount;  // [ncls][ncls]
     const uint8_t *fSlotOf;      // RE_COMPILE_DFA_STARTS only: [ncls][ncls][nf] forward slot of an
                                  // input state (0xFF: none); null for ME-DFA starts
+    const uint8_t *bSlotOf;      // RE_COMPILE_DFA_STARTS_BWD only: [ncls][ncls][nb], the same backwards
     const uint32_t *pt;          // [nf][nb] dictionary index of B ∩ B̂ (DICT); pairs the
                                  // parse never produces hold 0xFFFFFFFF
     const uint32_t *f2, *b2;     // [n][ncls^2] two-byte tables (mid | end << 16), or null
@@ -79,6 +80,7 @@ struct Compiled {
     std::vector<uint32_t> fSlotStart, fSlotCount, bSlotStart, bSlotCount;
     std::vector<uint64_t> fSlotMask, bSlotMask;
     std::vector<uint8_t> fSlotOf;             // RE_COMPILE_DFA_STARTS: [ncls][ncls][nf] slot of a state
+    std::vector<uint8_t> bSlotOf;             // RE_COMPILE_DFA_STARTS_BWD: [ncls][ncls][nb] the same backwards
     std::vector<uint32_t> pt;                 // [nf][nb]
     std::vector<uint64_t> dict;               // [dict_size][W]
     uint32_t dict_size = 0;

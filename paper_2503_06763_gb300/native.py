@@ -21,6 +21,7 @@ KINDS = {"auto": 0, "dense": 1, "dict": 2}
 KIND_NAMES = {0: "auto", 1: "dense", 2: "dict"}
 RE_COMPILE_HOST_ONLY = 1
 RE_COMPILE_DFA_STARTS = 2
+RE_COMPILE_DFA_STARTS_BWD = 4
 RE_PARSE_RECOGNIZE_ONLY = 1
 RE_PARSE_TEST_STALL_JOIN = 0x80000000     # tests of the join's bounded waits only
 REACH_SHAPES = {1: "byte tables, one direction per block, 2 stages", 2: "warp pairs, class tables, 3 stages",
@@ -153,15 +154,20 @@ class Regex:
     """A compiled RE (owns the library handle and its device tables)."""
 
     def __init__(self, pattern, max_states: int = 0, max_dict: int = 0, host_only: bool = False,
-                 dfa_starts: bool = False, sample_limit: int = 0):
-        """dfa_starts: forward speculation from every DFA state instead of the
-        ME-DFA starts (RE_COMPILE_DFA_STARTS, an ablation).  sample_limit: 0
+                 dfa_starts=False, sample_limit: int = 0):
+        """dfa_starts: speculation from every DFA state instead of the ME-DFA
+        starts, an ablation: True or "fwd" forward (RE_COMPILE_DFA_STARTS),
+        "bwd" backward (RE_COMPILE_DFA_STARTS_BWD), "both".  sample_limit: 0
         rejects an infinitely ambiguous RE; L >= 1 samples its LSTs, each
         numbered symbol at most L times per segment (App. A)."""
         lib = load()
         pat = pattern.encode("latin-1") if isinstance(pattern, str) else bytes(pattern)
         self.pattern = pat
-        flags = (RE_COMPILE_HOST_ONLY if host_only else 0) | (RE_COMPILE_DFA_STARTS if dfa_starts else 0)
+        if dfa_starts not in (False, True, "fwd", "bwd", "both"):
+            raise ValueError(f"dfa_starts: {dfa_starts!r}")
+        flags = (RE_COMPILE_HOST_ONLY if host_only else 0)
+        flags |= RE_COMPILE_DFA_STARTS if dfa_starts in (True, "fwd", "both") else 0
+        flags |= RE_COMPILE_DFA_STARTS_BWD if dfa_starts in ("bwd", "both") else 0
         opts = CompileOpts(max_states, max_dict, flags, sample_limit)
         h = ctypes.c_void_p()
         check(lib.re_compile(pat, len(pat), ctypes.byref(opts), ctypes.byref(h)))

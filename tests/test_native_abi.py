@@ -86,23 +86,26 @@ def test_layout_and_errors(native):
     assert e.value.status == -4
 
 
-def oracle_dfa_start_count(pattern):
-    """Most forward runs for one first byte when every classic DFA state is a
-    start: distinct non-empty successors of the states reachable from I,
-    computed with the oracle's NFA image (Sect. 3.1), one byte at a time."""
-    from oracle.serial import nfa_image
+def oracle_dfa_start_count(pattern, reverse=False):
+    """Most runs for one first byte when every classic DFA state is a start:
+    distinct non-empty successors of the states reachable from I, computed
+    with the oracle's NFA image (Sect. 3.1), one byte at a time; reverse: the
+    same over the reverse DFA from F (Eq. reverseNFAdef), under the chunk's
+    last byte."""
+    from oracle.serial import nfa_image, nfa_preimage
+    step = nfa_preimage if reverse else nfa_image
     c = compile_re(pattern)
     alphabet = sorted(set().union(*c.classes.values()))
-    start = frozenset(c.initial)
+    start = frozenset(c.final if reverse else c.initial)
     seen, todo = {start}, [start]
     while todo:
         s = todo.pop()
         for b in alphabet:
-            t = nfa_image(c, s, b)
+            t = step(c, s, b)
             if t and t not in seen:
                 seen.add(t)
                 todo.append(t)
-    return max(len({nfa_image(c, s, b) for s in seen} - {frozenset()}) for b in alphabet)
+    return max(len({step(c, s, b) for s in seen} - {frozenset()}) for b in alphabet)
 
 
 @pytest.mark.parametrize("pattern", ["([ACGT]|ATG([ACGT][ACGT][ACGT])*(TAA|TAG|TGA))*", "(a|b|ab)*",
@@ -113,6 +116,17 @@ def test_dfa_starts_slot_counts(native, pattern):
     r = native.Regex(pattern, host_only=True, dfa_starts=True)
     assert r.info["fwd_slots_max"] == oracle_dfa_start_count(pattern)
     assert r.info["bwd_slots_max"] == native.Regex(pattern, host_only=True).info["bwd_slots_max"]
+    if pattern.startswith("([ACGT]"):               # 36 backward runs: past the 32 a lane holds
+        with pytest.raises(native.ReError) as e:
+            native.Regex(pattern, host_only=True, dfa_starts="bwd")
+        assert e.value.status == -4
+        return
+    rb = native.Regex(pattern, host_only=True, dfa_starts="bwd")
+    assert rb.info["bwd_slots_max"] == oracle_dfa_start_count(pattern, reverse=True)
+    assert rb.info["fwd_slots_max"] == native.Regex(pattern, host_only=True).info["fwd_slots_max"]
+    both = native.Regex(pattern, host_only=True, dfa_starts="both")
+    assert (both.info["fwd_slots_max"], both.info["bwd_slots_max"]) == (r.info["fwd_slots_max"],
+                                                                      rb.info["bwd_slots_max"])
 
 
 def test_dfa_starts_refused_past_32_runs(native):

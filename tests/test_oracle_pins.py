@@ -261,18 +261,21 @@ def test_chunk_invariance_of_parallel_equations(pattern):
 
 @pytest.mark.parametrize("pattern", ["(a|b|ab)*", "(ab|a)*", "a(b|c)*d", "((ab)*c|a(bc)*)*", "(a{0,2}b|a|c)*"])
 def test_dfa_start_equations_give_the_serial_slpf(pattern):
-    """Forward reach from every DFA state with an exact-state join (the
-    ablation of the ME-DFA, Sect. 3.1 / Sect. 5): for every chunk length the
-    columns equal the serial parser's, and every J_i equals the ME-DFA join's."""
+    """Reach from every DFA state with an exact-state join (the ablation of
+    the ME-DFA, Sect. 3.1 / Sect. 5), forward, backward or both: for every
+    chunk length the columns equal the serial parser's, and every J_i and
+    Ĵ_i equals the ME-DFA join's."""
     c = compile_re(pattern)
     rng = random.Random(11)
     for trial in range(12):
         text = bytes(rng.choice(b"abcd") for _ in range(rng.randint(0, 18)))
         want = [serial.from_bits(row) for row in serial.parse(c, text)]
         for k in range(1, max(len(text), 1) + 2):
-            cols, tr = pe.parse_parallel_dfa_starts(c, text, k)
-            assert cols == want, (pattern, text, k)
-            assert tr["J"] == pe.parse_parallel(c, text, k)[1]["J"]
+            _, me = pe.parse_parallel(c, text, k)
+            for fwd, bwd in ((True, False), (False, True), (True, True)):
+                cols, tr = pe.parse_parallel_dfa_starts(c, text, k, forward=fwd, backward=bwd)
+                assert cols == want, (pattern, text, k, fwd, bwd)
+                assert tr["J"] == me["J"] and tr["Jh"] == me["Jh"]
 
 
 def test_invariants_on_random_texts():
