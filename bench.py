@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--bytes", type=int, default=0, help="text size (default: the workload's)")
     ap.add_argument("--no-extra", action="store_true", help="single mode: skip the DNA line after the log one")
     ap.add_argument("--chunk-len", type=int, default=0)
+    ap.add_argument("--reach-shape", type=int, default=0,
+                    help="with --chunk-len: reach shape 1-4 (RE_PARSE_REACH); 0 = the library's default")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="single",
                     choices=["single", "batch", "serve", "matches", "latency", "ablation", "join", "shard"],
@@ -164,16 +166,18 @@ def cpu_baseline(text_host, pattern, sample_bytes):
                       f"{dt:.1f} s, host {os.uname().machine} nproc={os.cpu_count()}"}
 
 
-def lsu_roofline(phase_ms: dict, n: int, device: int, ncls: int):
-    """Reach against the shared-memory pipe, its real bound.  With at most 16
-    byte classes it does 3 shared-memory lookups per text byte (per direction
-    and byte pair: two class lookups and one two-byte table lookup); with more
-    classes 4 (per direction and byte: one class and one transition lookup).
-    Peak: one 32-lane wavefront per SM and cycle at the maximum SM clock."""
+def lsu_roofline(phase_ms: dict, n: int, device: int, ncls: int, shape: int):
+    """Reach against the shared-memory pipe, its real bound.  Shared-memory
+    lookups per text byte: 2 with byte-indexed tables (reach shape 1: one
+    transition per byte and direction); with class tables 3 for at most 16
+    byte classes (per direction and byte pair: two class lookups and one
+    two-byte table lookup), else 4 (per direction and byte: one class and one
+    transition lookup).  Peak: one 32-lane wavefront per SM and cycle at the
+    maximum SM clock (bank conflicts make a lookup cost more)."""
     import torch
     props = torch.cuda.get_device_properties(device)
     peak = props.multi_processor_count * 32 * 2.07e9 / 1e12
-    per_byte = 3 if ncls <= 16 else 4
+    per_byte = 2 if shape == 1 else 3 if ncls <= 16 else 4
     achieved = per_byte * n / (phase_ms["reach"] / 1e3) / 1e12
     return {"kernel": "reach", "bound": "lsu", "lookups_per_byte": per_byte, "achieved": round(achieved, 3),
             "peak": round(peak, 3),
@@ -255,7 +259,7 @@ def measure_single(args, name, n, rank, world, local, dist, full=True):
 
     def step(i=None):
         rx.parse(text, kind=kind, chunk_len=args.chunk_len, out=out, status=status, workspace=ws,
-                 events=ev[i] if i is not None else None)
+                 events=ev[i] if i is not None else None, reach_shape=args.reach_shape)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -290,6 +294,9 @@ def measure_single(args, name, n, rank, world, local, dist, full=True):
     phase_ms = {p: statistics.mean(ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(args.steps))
                 for j, p in enumerate(PHASES)}
     dominant = max(phase_ms, key=phase_ms.get)
+    shape = args.reach_shape if args.chunk_len else rx.tuned(n)[1]
+    if not shape:                       # the library's default: byte tables when they fit, else warp pairs
+        shape = 1 if rx.info["n_classes"] > 16 and rx.info["fwd_states"] < 256 and rx.info["bwd_states"] < 256 else 2
     # algorithmic bytes per launch: text read once, plus the SLPF written by build & merge
     alg = {"reach": n, "join": 0, "fixup": 0, "build_merge": n + (n + 1) * cb}
     hbm, src = peaks()
@@ -301,11 +308,13 @@ def measure_single(args, name, n, rank, world, local, dist, full=True):
                 "phase_timing": "second loop of the same K steps, CUDA events between phases",
                 "algorithmic_bytes": {k: v for k, v in alg.items() if v},
                 "whole_step_frac": round((n + (n + 1) * cb) / (ms / 1e3) / 1e9 / hbm, 4),
-                "lsu": lsu_roofline(phase_ms, n, local, rx.info["n_classes"])}
+                "lsu": lsu_roofline(phase_ms, n, local, rx.info["n_classes"], shape)}
     res = {"value": round(value, 3), "ms_per_step": round(ms, 4), "roofline": roofline, "clocks": clocks,
            "config": {"workload": desc, "text_bytes_per_gpu": n, "encoding": f"{kind}-{8 * cb}bit",
                       "chunk_len": args.chunk_len or tuned,
-                      "chunk_len_from": "fixed" if args.chunk_len else "re_autotune", "segments": rx.ell,
+                      "chunk_len_from": "fixed" if args.chunk_len else "re_autotune",
+                      "reach_shape": shape,
+                      "segments": rx.ell,
                       "byte_classes": rx.info["n_classes"],
                       "l2": f"text {n >> 20} MiB > 129 MB L2 (no flush needed)",
                       "parallelism": f"independent texts per GPU x{world}"}}
@@ -731,16 +740,19 @@ def latency_mode(args, rank, world, local):
 
 def ablation_mode(args, rank, world, local):
     """Speculation ablation (the ME-DFA of Sect. 3.1 against the DFA, as in
-    Sect. 5): the DNA workload and (a|b|ab)* over uniform a/b, each as large
-    as --bytes, parsed with the ME-DFA starts and with forward starts from
-    every DFA state (RE_COMPILE_DFA_STARTS).  Per variant: forward runs per
-    class pair, the autotuned chunk length, the full parse (GB/s, reach time)
-    and the recognizer (forward reach + join).  value = DNA full-parse time
-    with DFA starts / with ME-DFA starts."""
+    Sect. 5): the DNA workload, (a|b|ab)* over uniform a/b and
+    (a|b)*a(a|b){3} over uniform a/b (accepted: the fourth byte from the end
+    is a), each as large as --bytes, parsed with the ME-DFA starts and with
+    starts from every DFA state forward (RE_COMPILE_DFA_STARTS), backward
+    (RE_COMPILE_DFA_STARTS_BWD) and both.  Per variant: runs per class pair
+    each way, the autotuned chunk length, the full parse (GB/s, reach time)
+    and the recognizer (forward reach + join); a variant whose runs exceed
+    the 32 a lane holds is refused at compile and listed as such.  value =
+    DNA full-parse time with forward DFA starts / with ME-DFA starts."""
     import numpy as np
     import torch
     import workloads as W
-    from paper_2503_06763_gb300 import Regex
+    from paper_2503_06763_gb300 import Regex, ReError
     from paper_2503_06763_gb300.native import PHASES
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -748,10 +760,17 @@ def ablation_mode(args, rank, world, local):
     stream = torch.cuda.current_stream(dev)
     steps = max(args.steps, 5)
     rows = []
-    for name, pattern, host in (("dna", W.DNA_RE, W.dna_text(n, seed=1)), ("ab", W.AB_RE, W.ab_text(n, seed=0))):
+    suffix = np.random.Generator(np.random.PCG64(4)).choice(np.frombuffer(b"ab", dtype=np.uint8), size=n)
+    suffix[max(n - 4, 0)] = ord("a")
+    for name, pattern, host in (("dna", W.DNA_RE, W.dna_text(n, seed=1)), ("ab", W.AB_RE, W.ab_text(n, seed=0)),
+                                ("suffix", "(a|b)*a(a|b){3}", suffix)):
         text = torch.from_numpy(host).to(dev)
-        for starts in ("me-dfa", "dfa"):
-            rx = Regex(pattern, dfa_starts=starts == "dfa")
+        for starts, which in (("me-dfa", False), ("dfa-fwd", "fwd"), ("dfa-bwd", "bwd"), ("dfa-both", "both")):
+            try:
+                rx = Regex(pattern, dfa_starts=which)
+            except ReError as e:
+                rows.append({"workload": name, "starts": starts, "refused": str(e)})
+                continue
             k = rx.autotune(text)
             kind, cb, _ = rx.layout(n, "auto")
             dt = {1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}[cb]
@@ -763,7 +782,8 @@ def ablation_mode(args, rank, world, local):
                 rx.parse(text, kind=kind, out=out, status=status, workspace=ws, recognize_only=recognize,
                          events=events)
 
-            res = {"workload": name, "starts": starts, "fwd_runs_max": rx.info["fwd_slots_max"], "chunk_len": k}
+            res = {"workload": name, "starts": starts, "fwd_runs_max": rx.info["fwd_slots_max"],
+                   "bwd_runs_max": rx.info["bwd_slots_max"], "chunk_len": k}
             for recognize in (False, True):
                 for _ in range(max(args.warmup, 3)):
                     run(recognize)
@@ -790,12 +810,13 @@ def ablation_mode(args, rank, world, local):
             del rx, out, ws
             torch.cuda.empty_cache()
     by = {(r["workload"], r["starts"]): r for r in rows}
-    ratio = by[("dna", "dfa")]["parse_ms"] / by[("dna", "me-dfa")]["parse_ms"]
-    line = {"metric": "speculation ablation: DNA full-parse time, all-DFA-state starts / ME-DFA starts",
+    ratio = by[("dna", "dfa-fwd")]["parse_ms"] / by[("dna", "me-dfa")]["parse_ms"]
+    line = {"metric": "speculation ablation: DNA full-parse time, forward all-DFA-state starts / ME-DFA starts",
             "value": round(ratio, 3), "unit": "x", "n_gpus": world, "steps": steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": f"dna-motif and (a|b|ab)*, {n} bytes each, text resident",
-                       "variants": "ME-DFA starts with the last-class filter / forward starts from every DFA state"},
+            "config": {"workload": f"dna-motif, (a|b|ab)* and (a|b)*a(a|b){{3}}, {n} bytes each, text resident",
+                       "variants": "ME-DFA starts with the last-class filter / starts from every DFA state "
+                                   "forward, backward, both"},
             "rows": rows}
     if rank == 0:
         print(json.dumps(line))

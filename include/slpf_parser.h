@@ -63,9 +63,17 @@ typedef enum {
  *           (re_dict_copy); index 0 is the empty column.  col_bytes = 1 when
  *           the dictionary has fewer than 255 entries, 2 when it has fewer
  *           than 65535, else 4.
+ *   PAIRS : column r is the pair (f, b) of the forward DFA state B_r and the
+ *           reverse DFA state B̂_r at r (Eq. merger: C_r = B_r ∩ B̂_r): f in
+ *           the low half, b in the high half of col_bytes = 4 (both automata
+ *           of at most 65536 states) or 8 bytes.  re_state_bits gives the
+ *           segment sets; a rejected text has every column 0 (state 0 is the
+ *           empty set).  Exact for any ell and any automaton size, with no
+ *           dictionary; the ids are the handle's, so equal columns may come
+ *           from different pairs.
  *   AUTO  : DENSE when ell <= 16, else DICT when the handle has a
- *           dictionary, else DENSE when ell <= 64.                            */
-typedef enum { RE_SLPF_AUTO = 0, RE_SLPF_DENSE = 1, RE_SLPF_DICT = 2 } re_slpf_kind;
+ *           dictionary, else DENSE when ell <= 64, else PAIRS.                 */
+typedef enum { RE_SLPF_AUTO = 0, RE_SLPF_DENSE = 1, RE_SLPF_DICT = 2, RE_SLPF_PAIRS = 3 } re_slpf_kind;
 
 /* Infinitely ambiguous REs (App. A, "Infinite ambiguity"): an RE whose
  * iterated sub-RE derives the empty text gives some texts infinitely many
@@ -407,6 +415,47 @@ re_status re_parse_slice(re_handle *h, const uint8_t *d_text, uint64_t len, uint
 /* Segment set of a state (host): bit q of words [0, W) is segment q.
  * forward: 1 for the forward automaton, 0 for the reverse one.             */
 re_status re_state_bits(const re_handle *h, int32_t forward, uint32_t id, uint64_t *bits, uint32_t cap_words);
+
+/* ---------------------------------------------------------------------------
+ * SLPF compression (App. C, "SLPF compression").  App. C stores an SLPF as its
+ * initial column and a table delta(C_{r-1}, x_r) = C_r, and rebuilds it by
+ * running the table over the text.  A clean column can also depend on bytes
+ * after r, so the archive adds an exception (r, C_r) wherever the table's
+ * column differs, and a checkpoint column every `interval` positions so that
+ * the rebuild runs in independent pieces (App. C's evenly spaced columns).
+ * Columns are ids: DICT indices (re_dict_copy gives their segment sets), or
+ * DENSE values; ids must be below 65536.
+ *
+ * Archive layout (little-endian, every section 16-byte aligned): the header;
+ * table u32[n_ids][256] (row v, byte a: the column after the first (v, a),
+ * 0xFFFFFFFF if the pair never occurs); checkpoints u32[n_checkpoints]
+ * (C_0, C_K, C_2K, ...); exception positions u64[n_exceptions], ascending;
+ * exception ids u32[n_exceptions].                                          */
+typedef struct {
+    uint32_t magic;           /* 0x46504C53 */
+    uint32_t version;         /* 1 */
+    uint64_t n;               /* text length: columns 0 .. n */
+    uint32_t n_ids;           /* table rows: ids 0 .. n_ids - 1 */
+    uint32_t interval;        /* K: a checkpoint every K columns */
+    uint64_t n_exceptions;
+    uint64_t n_checkpoints;   /* n / K + 1 */
+} re_slpf_dfa_header;
+
+/* Host: build the archive of columns cols[0 .. len] (host memory, col_bytes
+ * 1, 2 or 4 per id) of the host text[0 .. len).  *size receives the archive's
+ * byte count; with cap below it nothing is written and RE_E_CAPACITY is
+ * returned (cap = 0 queries the size).  The archive starts with the header. */
+re_status re_slpf_dfa_encode(const void *cols, uint32_t col_bytes, const uint8_t *text, uint64_t len,
+                             uint32_t interval, void *archive, uint64_t cap, uint64_t *size);
+
+/* Device: rebuild columns 0 .. hdr->n into d_cols (col_bytes per id) from an
+ * archive copied to device memory (16-byte aligned, archive_bytes long; hdr is
+ * a host copy of its header) and the device text.  Asynchronous on stream;
+ * *d_status becomes RE_OK, or RE_E_INTERNAL when the table has no entry for a
+ * (column, byte) pair the text meets (an archive of another text).         */
+re_status re_slpf_dfa_decode(const re_slpf_dfa_header *hdr, const void *d_archive, uint64_t archive_bytes,
+                             const uint8_t *d_text, void *d_cols, uint64_t cols_cap_bytes, uint32_t col_bytes,
+                             int32_t *d_status, re_stream stream);
 
 /* Thread-local description of the last error returned on this thread.     */
 const char *re_last_error(void);

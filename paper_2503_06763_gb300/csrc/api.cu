@@ -201,7 +201,7 @@ re_status resolve_kind(const re_handle *h, re_slpf_kind kind, re_slpf_kind &out,
         if (C.ell <= 16) kind = RE_SLPF_DENSE;
         else if (C.has_dict) kind = RE_SLPF_DICT;
         else if (C.ell <= 64) kind = RE_SLPF_DENSE;
-        else { set_error("no encoding available: more than 64 segments and no dictionary"); return RE_E_CAPACITY; }
+        else kind = RE_SLPF_PAIRS;                      // more than 64 segments and no dictionary
     }
     if (kind == RE_SLPF_DENSE) {
         if (C.ell > 64) { set_error("DENSE needs at most 64 segments"); return RE_E_CAPACITY; }
@@ -209,6 +209,8 @@ re_status resolve_kind(const re_handle *h, re_slpf_kind kind, re_slpf_kind &out,
     } else if (kind == RE_SLPF_DICT) {
         if (!C.has_dict) { set_error("this RE has no column dictionary (too many state pairs)"); return RE_E_CAPACITY; }
         cb = C.dict_size < 255 ? 1 : C.dict_size < 65535 ? 2 : 4;
+    } else if (kind == RE_SLPF_PAIRS) {
+        cb = (C.nf <= 65536 && C.nb <= 65536) ? 4 : 8;
     } else {
         set_error("unknown SLPF kind");
         return RE_E_INVALID_ARG;
@@ -227,6 +229,7 @@ bool in_device_memory(const void *ptr) {
 
 // Shared memory the merge's encoder table takes when staged.
 size_t encoder_bytes(const DevTables &t, re_slpf_kind kind, uint32_t cb) {
+    if (kind == RE_SLPF_PAIRS) return 0;
     return kind == RE_SLPF_DICT ? (size_t)t.nf * t.nb * cb : (size_t)(t.nf + t.nb) * 8;
 }
 
@@ -620,6 +623,23 @@ extern "C" re_status re_autotune(re_handle *h, const uint8_t *d_text, uint64_t l
     std::vector<uint32_t> shapes;                              // every reach shape this automaton can run
     for (uint32_t v = 1; v <= 4; ++v)
         if (shapes_of(h) >> v & 1) shapes.push_back(v);
+    if (!h->host_only && (shapes_of(h) >> 1 & 1)) {
+        // Whole rounds of tiles: with m tiles for every warp of the byte-table
+        // reach, no warp idles while others walk a last tile.
+        Params q{};
+        q.t = h->dev;
+        q.recognize = (opts && (opts->flags & RE_PARSE_RECOGNIZE_ONLY)) ? 1u : 0u;
+        q.mat = mat_for(h, opts) ? 1u : 0u;
+        const uint32_t ms = std::max(h->dev.msf, q.recognize ? 1u : h->dev.msb);
+        const uint64_t warps = reach_byte8_warps(q, ms, sm_count_of(h->device));
+        for (uint64_t m = 1; m <= 4 && warps; ++m) {
+            uint64_t k = (len + 32 * warps * m - 1) / (32 * warps * m);
+            k = (k + kSub - 1) / kSub * kSub;
+            if (k < 256 || k > (1u << 20) || std::find(cand.begin(), cand.end(), (uint32_t)k) != cand.end()) continue;
+            if (layout_for(h, len, (uint32_t)k, mat_for(h, opts)).total > workspace_bytes) continue;
+            cand.push_back((uint32_t)k);
+        }
+    }
     if (cand.empty()) { set_error("workspace too small for any candidate chunk length"); return RE_E_CAPACITY; }
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
@@ -751,6 +771,8 @@ extern "C" re_status re_matches(re_handle *h, const re_slpf *slpf, uint64_t len,
     a.n = len;
     a.folseg = h->dev.folseg;
     a.dict = h->dev.dict;
+    a.fbits = h->dev.fBits;
+    a.bbits = h->dev.bBits;
     a.status = slpf->d_status;
     a.pairs = d_pairs;
     a.cap = cap_pairs;

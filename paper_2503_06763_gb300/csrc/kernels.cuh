@@ -180,7 +180,10 @@ __device__ inline void empty_text(const Params &p) {
     for (uint32_t w = 0; w < t.W; ++w) meet |= (t.fBits[(size_t)t.fI * t.W + w] & t.bBits[(size_t)t.bF * t.W + w]) != 0;
     *p.status = meet ? RE_OK : RE_REJECTED;
     if (!p.out) return;
-    if (p.kind == RE_SLPF_DICT) {
+    if (p.kind == RE_SLPF_PAIRS) {                              // (I, F), or (0, 0) when they do not meet
+        if (p.col_bytes == 4) reinterpret_cast<uint32_t *>(p.out)[0] = meet ? (t.fI | (t.bF << 16)) : 0u;
+        else reinterpret_cast<uint64_t *>(p.out)[0] = meet ? ((uint64_t)t.fI | ((uint64_t)t.bF << 32)) : 0ull;
+    } else if (p.kind == RE_SLPF_DICT) {
         const uint32_t d = meet ? t.pt[(size_t)t.fI * t.nb + t.bF] : 0u;
         if (p.col_bytes == 1) reinterpret_cast<uint8_t *>(p.out)[0] = (uint8_t)d;
         else if (p.col_bytes == 2) reinterpret_cast<uint16_t *>(p.out)[0] = (uint16_t)d;
@@ -476,6 +479,8 @@ __host__ __device__ inline DevTables dfa_tables(const DevTables &t) {
 }
 bool launch_reach(const Params &p, const CUtensorMap &text_map, const StateMaps &smaps, cudaStream_t s, uint32_t ms,
                   int sm_count);
+// Warps per direction of the byte-table reach (shape 1) on this device.
+uint64_t reach_byte8_warps(const Params &p, uint32_t ms, int sm_count);
 bool launch_join(const Params &p, cudaStream_t s, int sm_count);
 bool launch_shard_map(const Params &p, uint8_t *d_maps, cudaStream_t s, int sm_count);
 void launch_fixup(const Params &p, cudaStream_t s, int sm_count);
@@ -491,6 +496,7 @@ struct MatchArgs {
     uint64_t n;                               // text length (columns n + 1)
     const uint64_t *folseg;                   // [ell][W]
     const uint64_t *dict;                     // [dict_size][W] (DICT)
+    const uint64_t *fbits, *bbits;            // [states][W] segment sets of the states (PAIRS)
     uint64_t open[kMatchW], close_first[kMatchW], whole[kMatchW], none[kMatchW];
     const int32_t *status;                    // parse status: anything but RE_OK gives no matches
     uint64_t *cnt;                            // [G] pairs per warp range, then their exclusive offsets

@@ -26,7 +26,19 @@ namespace {
 
 template <int W>
 __device__ __forceinline__ void load_column(const MatchArgs &a, uint64_t r, uint64_t (&v)[W]) {
-    if (a.kind == RE_SLPF_DICT) {
+    if (a.kind == RE_SLPF_PAIRS) {                          // C_r = B_r ∩ B̂_r from the two state ids
+        uint64_t f, b;
+        if (a.col_bytes == 4) {
+            const uint32_t x = __ldg(reinterpret_cast<const uint32_t *>(a.cols) + r);
+            f = x & 0xFFFFu; b = x >> 16;
+        } else {
+            const uint64_t x = __ldg(reinterpret_cast<const unsigned long long *>(a.cols) + r);
+            f = x & 0xFFFFFFFFull; b = x >> 32;
+        }
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+            v[w] = w < (int)a.W ? __ldg(a.fbits + f * a.W + w) & __ldg(a.bbits + b * a.W + w) : 0ull;
+    } else if (a.kind == RE_SLPF_DICT) {
         const uint32_t id = a.col_bytes == 1   ? __ldg(reinterpret_cast<const uint8_t *>(a.cols) + r)
                             : a.col_bytes == 2 ? __ldg(reinterpret_cast<const uint16_t *>(a.cols) + r)
                                                : __ldg(reinterpret_cast<const uint32_t *>(a.cols) + r);

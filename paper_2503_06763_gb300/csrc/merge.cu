@@ -348,8 +348,12 @@ __global__ void __launch_bounds__(kFixupThreads, 4) fixup_batch_kernel(const __g
 }
 
 // ------------------------------------------------------------------ encodings
-enum { ENC_D1 = 1, ENC_D2 = 2, ENC_D4 = 4, ENC_D8 = 8, ENC_X1 = 0x11, ENC_X2 = 0x12, ENC_X4 = 0x14 };
+// DENSE bitsets (D), DICT indices (X), PAIRS of state ids (P: forward id in
+// the low half, backward id in the high half).
+enum { ENC_D1 = 1, ENC_D2 = 2, ENC_D4 = 4, ENC_D8 = 8, ENC_X1 = 0x11, ENC_X2 = 0x12, ENC_X4 = 0x14,
+       ENC_P4 = 0x24, ENC_P8 = 0x28 };
 constexpr bool is_dict(int E) { return E == ENC_X1 || E == ENC_X2 || E == ENC_X4; }
+constexpr bool is_pair(int E) { return E == ENC_P4 || E == ENC_P8; }
 
 struct Enc {
     const uint64_t *fbits, *bbits;   // DENSE: segment set of each state (W == 1)
@@ -366,6 +370,7 @@ __device__ __forceinline__ uint32_t enc_lo(const Enc &e, uint32_t f, uint32_t b,
         if (E == ENC_X1 && e.pt8) return e.pt8[at];
         return e.pt16 ? (uint32_t)e.pt16[at] : e.pt32[at];
     }
+    if (E == ENC_P4) return f | (b << 16);
     return (uint32_t)(e.fbits[f] & e.bbits[b]);
 }
 __device__ __forceinline__ uint64_t enc_d8(const Enc &e, uint32_t f, uint32_t b) { return e.fbits[f] & e.bbits[b]; }
@@ -374,11 +379,13 @@ template <int E>
 __device__ __forceinline__ void store_col(void *out, uint64_t r, uint64_t v) {
     if (E == ENC_D1 || E == ENC_X1) reinterpret_cast<uint8_t *>(out)[r] = (uint8_t)v;
     else if (E == ENC_D2 || E == ENC_X2) reinterpret_cast<uint16_t *>(out)[r] = (uint16_t)v;
-    else if (E == ENC_D4 || E == ENC_X4) reinterpret_cast<uint32_t *>(out)[r] = (uint32_t)v;
+    else if (E == ENC_D4 || E == ENC_X4 || E == ENC_P4) reinterpret_cast<uint32_t *>(out)[r] = (uint32_t)v;
     else reinterpret_cast<uint64_t *>(out)[r] = v;
 }
 
-constexpr int bytes_of(int E) { return (E == ENC_X1) ? 1 : (E == ENC_X2) ? 2 : (E == ENC_X4) ? 4 : E; }
+constexpr int bytes_of(int E) {
+    return (E == ENC_X1) ? 1 : (E == ENC_X2) ? 2 : (E == ENC_X4 || E == ENC_P4) ? 4 : (E == ENC_P8) ? 8 : E;
+}
 
 // Put one column value into a 16-byte vector being assembled (slot k).
 template <int CB>
@@ -396,6 +403,7 @@ __device__ __forceinline__ void put_col(uint32_t (&w4)[4], int k, uint64_t v) {
 
 template <int TM, int E>
 __device__ __forceinline__ uint64_t enc_col(const Enc &e, uint32_t f, uint32_t b, bool &bad) {
+    if (E == ENC_P8) return (uint64_t)f | ((uint64_t)b << 32);
     if (bytes_of(E) == 8) return enc_d8(e, f, b);
     return enc_lo<E>(e, f, b, bad);
 }
@@ -615,7 +623,7 @@ __device__ void group_tail(const Params &p, const Tabs &T, const Enc &e, uint64_
     B[ncol - 1] = b;
     for (int u = (int)ncol - 2; u >= 0; --u) B[u] = bnext<TM>(T, B[u + 1], clsof<TM>(T, __ldg(p.x + pos + u)));
     for (uint32_t u = 0; u < ncol; ++u) {
-        const uint64_t v = bytes_of(E) == 8 ? enc_d8(e, F[u], B[u]) : (uint64_t)enc_lo<E>(e, F[u], B[u], bad);
+        const uint64_t v = enc_col<TM, E>(e, F[u], B[u], bad);
         store_col<E>(p.out, pos + u, v);
     }
 }
@@ -633,7 +641,8 @@ __device__ void merge_setup(const DevTables &t0, uint32_t enc_in_smem, uint8_t *
     if (TM != TM_PAIR && !REG) rest += (2 * 32 * kBlockThreads * sizeof(St) + 15) & ~(size_t)15;
     e = Enc{};
     e.nb = t.nb;
-    if (is_dict(E)) {
+    if (is_pair(E)) {                                         // the state ids themselves: no encoder
+    } else if (is_dict(E)) {
         if (enc_in_smem) {
             const size_t cnt = (size_t)t.nf * t.nb;
             const uint32_t nbs = t0.nb;                       // row stride of the device pair table
@@ -818,12 +827,15 @@ __global__ void __launch_bounds__(kFixupThreads) fixup_mat_kernel(const __grid_c
             const uint32_t end = max(1u, min(64u * fv, len));  // columns [0, end)
             uint32_t st = p.w.FJ[i];
             if (st >= nfs) st = 0;                              // never for an accepted text
+            uint4 nx = load16(p.x, p.n, base);                  // text bytes 16 at a time, one group ahead
             for (uint32_t g = 0; g < end; g += 16) {
+                const uint4 x = nx;
+                if (g + 16 < end) nx = load16(p.x, p.n, base + g + 16);
                 uint32_t w[4] = {0, 0, 0, 0};
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {                  // column g + u: the state before byte g + u
                     w[u >> 2] |= (st & 0xFFu) << (8 * (u & 3));
-                    if (g + u + 1 < end) st = fnext<TM>(T, st, clsof<TM>(T, __ldg(p.x + base + g + u)));
+                    if (g + u + 1 < end) st = fnext<TM>(T, st, clsof<TM>(T, byte_of(x, u)));
                 }
                 if (g + 16 <= end) {
                     *reinterpret_cast<uint4 *>(p.w.FS + base + g) = make_uint4(w[0], w[1], w[2], w[3]);
@@ -839,12 +851,15 @@ __global__ void __launch_bounds__(kFixupThreads) fixup_mat_kernel(const __grid_c
             uint32_t st = p.w.BJ[i + 1];                        // column len
             if (st >= nbs) st = 0;
             const uint32_t top = (len + 15) & ~15u;             // 16-column groups, from the top
+            uint4 nx = load16(p.x, p.n, base + top - 16);
             for (uint32_t g = top; g > lo; g -= 16) {
                 const uint32_t g0 = g - 16;                     // columns g0 .. g0 + 15
+                const uint4 x = nx;
+                if (g0 > lo) nx = load16(p.x, p.n, base + g0 - 16);
                 uint32_t w[4] = {0, 0, 0, 0};
 #pragma unroll
                 for (int u = 15; u >= 0; --u) {                 // column g0 + u: after consuming byte g0 + u
-                    if (g0 + u < len) st = bnext<TM>(T, st, clsof<TM>(T, __ldg(p.x + base + g0 + u)));
+                    if (g0 + u < len) st = bnext<TM>(T, st, clsof<TM>(T, byte_of(x, u)));
                     w[u >> 2] |= (st & 0xFFu) << (8 * (u & 3));
                 }
                 if (g0 + 16 <= len && g0 >= lo) {
@@ -882,7 +897,7 @@ __global__ void __launch_bounds__(kBlockThreads) merge_gather_kernel(const __gri
         if (E == ENC_X1) e.pt8 = sm;
         else if (E == ENC_X2) e.pt16 = reinterpret_cast<uint16_t *>(sm);
         else e.pt32 = reinterpret_cast<uint32_t *>(sm);
-    } else {
+    } else if constexpr (!is_pair(E)) {
         uint64_t *fb = reinterpret_cast<uint64_t *>(sm), *bb = fb + nfs;
         for (uint32_t q = threadIdx.x; q < nfs; q += blockDim.x) fb[q] = __ldg(p.t.fBits + q);
         for (uint32_t q = threadIdx.x; q < nbs; q += blockDim.x) bb[q] = __ldg(p.t.bBits + q);
@@ -1001,7 +1016,10 @@ void merge_tma(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_c
 
 template <int TM>
 void merge_enc(const Params &p, const CUtensorMap &map, cudaStream_t s, int sm_count) {
-    if (p.kind == RE_SLPF_DICT) {
+    if (p.kind == RE_SLPF_PAIRS) {
+        if (p.col_bytes == 4) merge_tma<TM, ENC_P4>(p, map, s, sm_count);
+        else merge_tma<TM, ENC_P8>(p, map, s, sm_count);
+    } else if (p.kind == RE_SLPF_DICT) {
         if (p.col_bytes == 1) merge_tma<TM, ENC_X1>(p, map, s, sm_count);
         else if (p.col_bytes == 2) merge_tma<TM, ENC_X2>(p, map, s, sm_count);
         else merge_tma<TM, ENC_X4>(p, map, s, sm_count);
@@ -1028,7 +1046,10 @@ void merge_batch_one(const BatchGroup &b, const Params &like, cudaStream_t s, in
 
 template <int TM>
 void merge_batch_enc(const BatchGroup &b, const Params &like, cudaStream_t s, int sm_count) {
-    if (like.kind == RE_SLPF_DICT) {
+    if (like.kind == RE_SLPF_PAIRS) {
+        if (like.col_bytes == 4) merge_batch_one<TM, ENC_P4>(b, like, s, sm_count);
+        else merge_batch_one<TM, ENC_P8>(b, like, s, sm_count);
+    } else if (like.kind == RE_SLPF_DICT) {
         if (like.col_bytes == 1) merge_batch_one<TM, ENC_X1>(b, like, s, sm_count);
         else if (like.col_bytes == 2) merge_batch_one<TM, ENC_X2>(b, like, s, sm_count);
         else merge_batch_one<TM, ENC_X4>(b, like, s, sm_count);
@@ -1067,6 +1088,7 @@ void fixup_one(const Params &p, cudaStream_t s, int sm_count) {
 // classic-DFA states).
 size_t gather_smem(const Params &p) {
     const size_t nfs = p.t.nfd + 1, nbs = p.t.nbd + 1;
+    if (p.kind == RE_SLPF_PAIRS) return 0;
     return p.kind == RE_SLPF_DICT ? nfs * nbs * p.col_bytes : (nfs + nbs) * 8;
 }
 
@@ -1089,7 +1111,10 @@ void gather_one(const Params &p, cudaStream_t s, int sm_count) {
 }
 
 void launch_gather(const Params &p, cudaStream_t s, int sm_count) {
-    if (p.kind == RE_SLPF_DICT) {
+    if (p.kind == RE_SLPF_PAIRS) {
+        if (p.col_bytes == 4) gather_one<ENC_P4>(p, s, sm_count);
+        else gather_one<ENC_P8>(p, s, sm_count);
+    } else if (p.kind == RE_SLPF_DICT) {
         if (p.col_bytes == 1) gather_one<ENC_X1>(p, s, sm_count);
         else if (p.col_bytes == 2) gather_one<ENC_X2>(p, s, sm_count);
         else gather_one<ENC_X4>(p, s, sm_count);
@@ -1113,7 +1138,7 @@ size_t merge_extra_smem(const Params &p) {
     if (p.out_tma) a += 1024 + (size_t)(kBlockThreads / 32) * 32 * 64 * p.col_bytes;   // warp tiles + alignment
     if (p.tmode != TM_PAIR && !p.merge_reg)
         a += (2 * 32 * kBlockThreads * (p.tmode == TM_GLOBAL ? 4 : 2) + 15) & ~(size_t)15;
-    if (!p.enc_in_smem) return a;
+    if (!p.enc_in_smem || p.kind == RE_SLPF_PAIRS) return a;
     if (p.kind == RE_SLPF_DICT) return a + (size_t)t.nf * t.nb * p.col_bytes;
     return a + (size_t)(t.nf + t.nb) * 8;
 }

@@ -193,6 +193,10 @@ struct Ring {
     uint32_t bars;        // shared address of nst mbarriers
     uint32_t phase;       // bit s: parity of the next completion of stage s
     uint32_t nst = kStages;   // stages (kStages; 2 in the one-direction-per-block kernel)
+    uint32_t nout = 2;        // MAT: state tiles per warp (2; 1 in the one-direction-per-block kernel)
+    uint32_t obuf = 0;        // MAT: the state tile the next block fills; it alternates across the
+                              // warp's chunk tiles too, so the wait before a fill (at most one store
+                              // group still reading) always concerns the other tile
 };
 
 // Directions a warp walks: both (one lane per chunk), or one of them (the
@@ -420,13 +424,17 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
     bool fconv = mf <= 1 && !(FW && big), bconv = mb <= 1 && !(!FW && big);
     const bool single0 = FW ? fconv : bconv;                  // one run from the chunk's edge on
     uint32_t fconv_sub = fconv ? 1 : nsub, bconv_sub = bconv ? nsub - 1 : 0;
-    uint32_t obuf = 0;                                        // MAT: state tile being filled (0 / 1)
     uint32_t *fcnt = p.w.recFc + (size_t)i * kRecBounds, *bcnt = p.w.recBc + (size_t)i * kRecBounds;
     uint2 *fent = p.w.recFe + (size_t)i * kRecEntries, *bent = p.w.recBe + (size_t)i * kRecEntries;
     uint32_t fused = 0, bused = 0, fnrec = 0, bnrec = 0;
     bool fopen = true, bopen = true;
 
     const uint32_t lane = threadIdx.x & 31, i0 = i - lane;
+    if (MAT) {   // a new tile: earlier tiles' state stores have read their tiles (the plain path never waits)
+        const unsigned present = p.c - i0 >= 32 ? 0xFFFFFFFFu : ((1u << (p.c - i0)) - 1u);   // lanes with a chunk
+        if (lane == 0) bulk_wait_read_all();
+        __syncwarp(present);
+    }
     if (tma && lane == 0)                                     // prologue: first stages in flight
         for (uint32_t b = 0; b < ring.nst && b < nsub; ++b)
             ring_issue<DIR>(p, map, ring, b, i0, b, nsub - 1 - b, FW, bwd);
@@ -468,9 +476,12 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
         const uint8_t *frow = tile_f<DIR>(ring, stage) + lane * 64;
         const uint8_t *brow = tile_b<DIR>(ring, stage) + lane * 64;
         const uint32_t wm = max(wmf, wmb);
-        uint8_t *orow = MAT ? otile + obuf * kTileBytes + lane * 64 : nullptr;
-        if (MAT && tma) {                                     // the store two blocks back has read this tile
-            if (lane == 0) bulk_wait_read_1();
+        uint8_t *orow = MAT ? otile + ring.obuf * kTileBytes + lane * 64 : nullptr;
+        if (MAT && tma) {                                     // the store that last used this tile has read it
+            if (lane == 0) {
+                if (ring.nout == 1) bulk_wait_read_all();
+                else bulk_wait_read_1();
+            }
             __syncwarp();
         }
         if (edge) {
@@ -495,7 +506,7 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
                 fence_async_smem();
                 __syncwarp();
                 if (lane == 0) {
-                    tma_store_2d(smap, smem_u32(otile + obuf * kTileBytes), 64 * ob, (int32_t)i0);
+                    tma_store_2d(smap, smem_u32(otile + ring.obuf * kTileBytes), 64 * ob, (int32_t)i0);
                     bulk_commit();
                 }
             } else {                                          // plain stores, clipped to the chunk
@@ -513,7 +524,7 @@ __device__ bool reach_chunk(const Params &p, const Tabs &T, uint32_t i, const CU
                     }
                 }
             }
-            obuf ^= 1u;
+            if (ring.nout == 2) ring.obuf ^= 1u;
         }
         if (WIDE && big) {                                    // this lane's runs past the register arrays
             if (FW) walk_local<TM, true>(T, frow, xs, xk, mx, f_lo, f_hi);
@@ -658,10 +669,18 @@ __global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
 // One parse with byte-indexed tables (TM_BYTE8): every warp of a block walks
 // the same direction, so a block stages one direction's table (about 65 KB
 // for 251 states) instead of both.  Even blocks walk 32-chunk tiles forward,
-// odd blocks backward (every block forward in recognizer mode); 16 warps per
-// block, 2-stage TMA rings, and (MAT) two state tiles per warp.
-constexpr uint32_t kDirThreads = 512;
+// odd blocks backward (every block forward in recognizer mode); 24 warps per
+// block, 2-stage TMA rings, and (MAT) one state tile per warp, whose store
+// has read it before the next block's states go in: a warp's lookups wait on
+// shared-memory latency, so the smaller footprint buys warps to hide it.
+// Tiles are dealt round-robin over the blocks of a direction (tile t to
+// block t mod B), so a text of few tiles still spreads over every SM.
+constexpr uint32_t kDirThreads = 768;
 constexpr uint32_t kDirStages = 2;
+constexpr uint32_t kDirOut = 1;             // MAT state tiles per warp
+// Shared memory after the table: [1024-byte pad][text tiles, kDirStages per
+// warp][state tiles, kDirOut per warp][mbarriers, kDirStages per warp]; the
+// tiles are 1024-byte multiples, so one pad aligns them all.
 
 template <int MS, bool WIDE, bool MAT>
 __global__ void __launch_bounds__(kDirThreads, 1)
@@ -676,17 +695,15 @@ __global__ void __launch_bounds__(kDirThreads, 1)
     uint8_t *otile = nullptr;
     Ring ring{};
     ring.nst = kDirStages;
+    ring.nout = kDirOut;
     {
         const uint32_t a = smem_u32(rest);
         uint8_t *aligned = rest + ((1024 - (a & 1023)) & 1023);
+        const uint32_t outs = MAT ? kDirOut : 0;
         ring.tiles = aligned + warp * (kDirStages * kTileBytes);
-        ring.bars = smem_u32(aligned + wpb * (kDirStages * kTileBytes)) + warp * kDirStages * 8;
+        ring.bars = smem_u32(aligned + wpb * (kDirStages + outs) * kTileBytes) + warp * kDirStages * 8;
         ring.phase = 0;
-        if (MAT) {
-            uint8_t *after = aligned + wpb * (kDirStages * kTileBytes + kDirStages * 8);
-            after += (1024 - (smem_u32(after) & 1023)) & 1023;
-            otile = after + warp * 2 * kTileBytes;
-        }
+        if (MAT) otile = aligned + wpb * kDirStages * kTileBytes + warp * kDirOut * kTileBytes;
         if (p.text_tma && lane == 0) {
             for (uint32_t st = 0; st < kDirStages; ++st) mbar_init(ring.bars + 8 * st, 1);
             mbar_init_fence();
@@ -696,7 +713,7 @@ __global__ void __launch_bounds__(kDirThreads, 1)
     pdl_wait();
     pdl_trigger();
     const uint64_t gblk = pairs ? blockIdx.x >> 1 : blockIdx.x, nblk = pairs ? gridDim.x >> 1 : gridDim.x;
-    for (uint64_t t = gblk * wpb + warp; t * 32 < p.c; t += nblk * wpb) {
+    for (uint64_t t = (uint64_t)warp * nblk + gblk; t * 32 < p.c; t += nblk * wpb) {
         const uint32_t i = (uint32_t)(t * 32) + lane;
         const bool tma = p.text_tma && t * 32 + 32 <= p.c_full;
         if (i >= p.c) continue;                               // lanes past the text (plain path only)
@@ -721,23 +738,46 @@ __global__ void __launch_bounds__(kDirThreads, 1)
 inline size_t reach_dir_smem(const DevTables &t, bool mat) {
     const size_t tab = std::max(byte8_smem_bytes(t, true, false), byte8_smem_bytes(t, false, true));
     const size_t wpb = kDirThreads / 32;
-    return tab + 1024 + wpb * (kDirStages * kTileBytes + kDirStages * 8) + (mat ? 1024 + wpb * 2 * kTileBytes : 0);
+    return tab + 1024 + wpb * ((kDirStages + (mat ? kDirOut : 0)) * kTileBytes + kDirStages * 8);
 }
 
+// Blocks per direction: every resident block slot, split between the
+// directions, but no more blocks per direction than tiles (tiles go
+// round-robin over blocks).
 template <int MS, bool WIDE, bool MAT>
-void launch_dir(const Params &p, const CUtensorMap &map, const StateMaps &smaps, cudaStream_t s, int sm_count) {
+uint64_t dir_blocks(const Params &p, int sm_count) {
     const size_t smem = reach_dir_smem(p.t, MAT);
     static uint64_t attr_done = 0;
     allow_smem(reach_dir_kernel<MS, WIDE, MAT>, &attr_done, 227 * 1024);
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_dir_kernel<MS, WIDE, MAT>, kDirThreads, smem);
-    const uint64_t tiles = ((uint64_t)p.c + 31) / 32, wpb = kDirThreads / 32;
-    const uint64_t per_dir = (tiles + wpb - 1) / wpb;          // blocks one direction would want
+    const uint64_t tiles = ((uint64_t)p.c + 31) / 32;
     const uint64_t dirs = p.recognize ? 1 : 2;
-    uint64_t blocks = std::min<uint64_t>(per_dir * dirs, (uint64_t)std::max(per_sm, 1) * sm_count);
-    if (dirs == 2) blocks = std::max<uint64_t>(2, blocks & ~1ull);   // pairs of blocks: one per direction
+    const uint64_t slots = (uint64_t)std::max(per_sm, 1) * sm_count;
+    return std::max<uint64_t>(1, std::min<uint64_t>(tiles, slots / dirs));
+}
+
+template <int MS, bool WIDE, bool MAT>
+void launch_dir(const Params &p, const CUtensorMap &map, const StateMaps &smaps, cudaStream_t s, int sm_count) {
+    const size_t smem = reach_dir_smem(p.t, MAT);
+    const uint64_t dirs = p.recognize ? 1 : 2;
+    const uint64_t per_dir = dir_blocks<MS, WIDE, MAT>(p, sm_count);
+    const uint64_t blocks = per_dir * dirs;                    // even: one block of each pair per direction
     launch_dependent(reach_dir_kernel<MS, WIDE, MAT>, (uint32_t)std::max<uint64_t>(blocks, 1), kDirThreads, smem, s,
                      p, map, smaps);
+}
+
+// Warps per direction the one-direction-per-block reach runs at most (every
+// resident block of a direction, kDirThreads / 32 warps each).
+template <bool MAT>
+uint64_t dir_warps(const Params &p, uint32_t ms, int sm_count) {
+    Params q = p;
+    q.c = 0xFFFFFFFFu;                                         // as many tiles as block slots
+    const uint64_t b = ms <= 2 ? dir_blocks<2, false, MAT>(q, sm_count)
+                     : ms <= 4 ? dir_blocks<4, false, MAT>(q, sm_count)
+                     : ms <= 8 ? dir_blocks<8, false, MAT>(q, sm_count)
+                               : dir_blocks<4, true, MAT>(q, sm_count);
+    return b * (kDirThreads / 32);
 }
 
 template <bool MAT>

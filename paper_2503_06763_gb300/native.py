@@ -17,8 +17,8 @@ RE_OK, RE_REJECTED = 0, 1
 STATUS_NAMES = {0: "RE_OK", 1: "RE_REJECTED", -1: "RE_E_INVALID_ARG", -2: "RE_E_SYNTAX",
                 -3: "RE_E_INFINITE_AMBIGUITY", -4: "RE_E_TOO_MANY_STATES", -5: "RE_E_NOMEM",
                 -6: "RE_E_CUDA", -7: "RE_E_TIMEOUT", -8: "RE_E_CAPACITY", -9: "RE_E_INTERNAL"}
-KINDS = {"auto": 0, "dense": 1, "dict": 2}
-KIND_NAMES = {0: "auto", 1: "dense", 2: "dict"}
+KINDS = {"auto": 0, "dense": 1, "dict": 2, "pairs": 3}
+KIND_NAMES = {0: "auto", 1: "dense", 2: "dict", 3: "pairs"}
 RE_COMPILE_HOST_ONLY = 1
 RE_COMPILE_DFA_STARTS = 2
 RE_COMPILE_DFA_STARTS_BWD = 4
@@ -37,7 +37,7 @@ EXPORTS = ["re_compile", "re_free", "re_get_info", "re_segment_name", "re_dict_c
            "re_batch_chunk_len", "re_parse_batch", "re_batch_run", "re_batch_free", "re_match_workspace_size",
            "re_matches", "re_autotune", "re_tuned", "re_parse_host",
            "re_shard_map_size", "re_shard_map", "re_shard_entry", "re_parse_slice", "re_state_bits",
-           "re_parse_static",
+           "re_parse_static", "re_slpf_dfa_encode", "re_slpf_dfa_decode",
            "re_last_error"]
 RE_STATIC_SCRATCH_BYTES = 64 << 20
 
@@ -66,6 +66,12 @@ class Slpf(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("col_bytes", ctypes.c_uint32), ("n_cols", ctypes.c_uint64),
                 ("d_cols", ctypes.c_void_p), ("cols_cap_bytes", ctypes.c_uint64),
                 ("d_status", ctypes.c_void_p)]
+
+
+class DfaHeader(ctypes.Structure):
+    _fields_ = [("magic", ctypes.c_uint32), ("version", ctypes.c_uint32), ("n", ctypes.c_uint64),
+                ("n_ids", ctypes.c_uint32), ("interval", ctypes.c_uint32), ("n_exceptions", ctypes.c_uint64),
+                ("n_checkpoints", ctypes.c_uint64)]
 
 
 class Info(ctypes.Structure):
@@ -132,6 +138,10 @@ def load():
     lib.re_parse_slice.argtypes = [vp, vp, u64, u32, u32, vp, ctypes.POINTER(Slpf), vp, u64, ctypes.POINTER(ParseOpts)]
     lib.re_parse_slice.restype = i32
     lib.re_state_bits.argtypes = [vp, ctypes.c_int32, u32, vp, u32]
+    lib.re_slpf_dfa_encode.argtypes = [vp, u32, vp, u64, u32, vp, u64, ctypes.POINTER(u64)]
+    lib.re_slpf_dfa_encode.restype = i32
+    lib.re_slpf_dfa_decode.argtypes = [ctypes.POINTER(DfaHeader), vp, u64, vp, vp, u64, u32, vp, vp]
+    lib.re_slpf_dfa_decode.restype = i32
     lib.re_state_bits.restype = i32
     lib.re_tuned.argtypes = [vp, u64, u32, ctypes.POINTER(u32), ctypes.POINTER(u32)]
     lib.re_tuned.restype = i32
@@ -443,6 +453,18 @@ class Regex:
         if kind == "dense":
             v = cols.view({1: np.uint8, 2: np.uint16, 4: np.uint32, 8: np.uint64}[cols.dtype.itemsize])
             return v.astype(np.uint64).reshape(-1, 1)
+        if kind == "pairs":                         # (forward state, backward state): C_r = B_r ∩ B̂_r
+            if cols.dtype.itemsize == 4:
+                v = cols.view(np.uint32).astype(np.uint64)
+                f, b = v & 0xFFFF, v >> 16
+            else:
+                v = cols.view(np.uint64)
+                f, b = v & 0xFFFFFFFF, v >> 32
+            uf, fi = np.unique(f, return_inverse=True)
+            ub, bi = np.unique(b, return_inverse=True)
+            fb = np.stack([self.state_bits(True, int(s)) for s in uf]) if uf.size else np.zeros((0, self.words), np.uint64)
+            bb = np.stack([self.state_bits(False, int(s)) for s in ub]) if ub.size else np.zeros((0, self.words), np.uint64)
+            return fb[fi.reshape(-1)] & bb[bi.reshape(-1)]
         idx = cols.view({1: np.uint8, 2: np.uint16, 4: np.uint32}[cols.dtype.itemsize]).astype(np.int64)
         d = self.dictionary()
         table = np.concatenate([np.zeros((1, self.words), dtype=np.uint64), d], axis=0)
@@ -550,3 +572,55 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------- SLPF archives (App. C)
+def slpf_dfa_encode(cols, text, interval: int = 4096):
+    """re_slpf_dfa_encode on host arrays: ``cols`` the n + 1 column ids (a numpy
+    array of 1, 2 or 4 bytes per id: DICT indices or DENSE values), ``text``
+    the n bytes.  Returns the archive as a numpy uint8 array."""
+    import numpy as np
+    cols = np.ascontiguousarray(cols)
+    x = np.ascontiguousarray(np.frombuffer(bytes(text), dtype=np.uint8) if isinstance(text, (bytes, bytearray))
+                             else np.asarray(text, dtype=np.uint8))
+    if cols.size != x.size + 1:
+        raise ValueError("one column per position 0..n")
+    lib = load()
+    size = ctypes.c_uint64()
+    st = lib.re_slpf_dfa_encode(cols.ctypes.data, cols.dtype.itemsize, x.ctypes.data if x.size else None, x.size,
+                                interval, None, 0, ctypes.byref(size))
+    if st not in (RE_OK, -8):
+        check(st)
+    out = np.zeros(size.value, dtype=np.uint8)
+    check(lib.re_slpf_dfa_encode(cols.ctypes.data, cols.dtype.itemsize, x.ctypes.data if x.size else None, x.size,
+                                 interval, out.ctypes.data, out.size, ctypes.byref(size)))
+    return out
+
+
+def slpf_dfa_header(archive) -> dict:
+    """The header of an archive (host numpy array) as a dict."""
+    import numpy as np
+    h = DfaHeader.from_buffer_copy(np.asarray(archive, dtype=np.uint8)[:ctypes.sizeof(DfaHeader)].tobytes())
+    return {n: getattr(h, n) for n, _ in DfaHeader._fields_}
+
+
+def slpf_dfa_decode(archive, text, col_bytes: int, stream=None):
+    """re_slpf_dfa_decode: ``archive`` a host numpy array (copied to the
+    device) and ``text`` a CUDA uint8 tensor.  Returns (columns, status) as
+    CUDA tensors; enqueued on ``stream``."""
+    import numpy as np
+    import torch
+    arch = np.ascontiguousarray(archive, dtype=np.uint8)
+    hdr = DfaHeader.from_buffer_copy(arch[:ctypes.sizeof(DfaHeader)].tobytes())
+    dev = text.device
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    dt = {1: torch.uint8, 2: torch.int16, 4: torch.int32}[col_bytes]
+    with torch.cuda.stream(s):
+        d_arch = torch.from_numpy(arch).to(dev, non_blocking=False)
+        cols = torch.empty(hdr.n + 1, dtype=dt, device=dev)
+        status = torch.empty(1, dtype=torch.int32, device=dev)
+    check(load().re_slpf_dfa_decode(ctypes.byref(hdr), d_arch.data_ptr(), d_arch.numel(),
+                                    text.data_ptr() if hdr.n else None, cols.data_ptr(), cols.numel() * col_bytes,
+                                    col_bytes, status.data_ptr(), ctypes.c_void_p(s.cuda_stream)))
+    cols._archive = d_arch                       # keep the device archive alive until the columns are used
+    return cols, status

@@ -32,9 +32,9 @@ def groups(c):
     return sorted({s[1] for seg in c.segments for s in seg if s[0] == "("})
 
 
-def device_matches(rx, host, group, chunk_len=0):
+def device_matches(rx, host, group, chunk_len=0, kind="auto"):
     t = torch.from_numpy(np.ascontiguousarray(host)).cuda()
-    cols, st, kind = rx.parse(t, chunk_len=chunk_len)
+    cols, st, kind = rx.parse(t, chunk_len=chunk_len, kind=kind)
     pairs, total = rx.matches(cols, st, len(host), group, kind)
     torch.cuda.synchronize()
     return [tuple(p) for p in pairs.cpu().numpy().tolist()], total, int(st.item())
@@ -129,4 +129,18 @@ def test_wide_columns_log_re(lib):
     for k in pick:
         want = M.matches_by_slpf(c, host.tobytes(), k, cols)
         got, total, st = device_matches(rx, host, k)
+        assert st == 0 and total == len(want) and got == want, k
+
+
+def test_pair_columns_log_re(lib):
+    """Columns written as (forward state, backward state) pairs (RE_SLPF_PAIRS)
+    give the same spans: the device intersects the two states' segment sets."""
+    rx = lib(W.LOG_RE)
+    c = compile_re(W.LOG_RE)
+    host = W.log_text(20_000, seed=6)
+    cols = [serial.from_bits(row) for row in serial.parse(c, host.tobytes())]
+    ks = groups(c)
+    for k in (ks[0], ks[len(ks) // 2], ks[-1]):
+        want = M.matches_by_slpf(c, host.tobytes(), k, cols)
+        got, total, st = device_matches(rx, host, k, kind="pairs")
         assert st == 0 and total == len(want) and got == want, k

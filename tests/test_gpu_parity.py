@@ -404,3 +404,39 @@ def test_sampled_infinite_ambiguity(lib, pattern, limit):
                 assert st == (0 if serial.accepted(want) else 1), (pattern, limit, n)
                 bad_cols = np.nonzero(np.any(got != want, axis=1))[0]
                 assert bad_cols.size == 0, (pattern, limit, n, chunk_len, bad_cols[:5].tolist())
+
+
+# ---------------------------------------------------------------- PAIRS columns (no dictionary needed)
+@pytest.mark.parametrize("case", ["log", "dna", "log-nodict"])
+def test_pair_columns(lib, case):
+    """RE_SLPF_PAIRS: every column is the pair of the forward and backward DFA
+    states there, and their segment sets meet in the oracle's column (Eq.
+    merger).  Log and DNA force the encoding (per-position-state and
+    checkpoint merges); the log RE (162 segments) compiled with no room for a
+    dictionary gets it from AUTO."""
+    if case == "log":
+        pattern, rx, kind = W.LOG_RE, lib(W.LOG_RE), "pairs"
+        texts = [W.log_text(n, seed=9) for n in (1, 900, 70_000)]
+    elif case == "dna":
+        pattern, rx, kind = W.DNA_RE, lib(W.DNA_RE), "pairs"
+        texts = [W.dna_text(n, seed=9) for n in (1, 900, 70_001)]
+    else:
+        pattern = W.LOG_RE
+        rx, kind = lib(pattern, max_dict=1), "auto"
+        assert rx.info["dict_size"] == 0 and rx.ell > 64 and rx.layout(100, "auto")[0] == "pairs"
+        texts = [W.log_text(n, seed=10) for n in (1, 900, 70_000)]
+        bad = W.log_text(5000, seed=11).copy()
+        bad[-1] = ord("x")                                   # no final newline: rejected
+        texts.append(bad)
+    for host in texts:
+        host = np.ascontiguousarray(host)
+        want = oracle_cols(pattern, host.tobytes())
+        for chunk_len in (64, 0):
+            t = torch.from_numpy(host.copy()).cuda()
+            cols, st, kname = rx.parse(t, chunk_len=chunk_len, kind=kind)
+            torch.cuda.synchronize()
+            assert kname == "pairs"
+            assert int(st.item()) == (0 if serial.accepted(want) else 1)
+            got = rx.decode(cols.cpu().numpy(), kname)
+            bad = np.nonzero(np.any(got != want, axis=1))[0]
+            assert bad.size == 0, (case, len(host), chunk_len, bad[:5].tolist())

@@ -66,6 +66,23 @@ def test_host_compile_matches_oracle_segments_and_dfa(native, pattern):
         assert set(sets) == inter
 
 
+def test_pair_layout_without_a_dictionary(native):
+    """No dictionary and more than 64 segments: AUTO picks PAIRS (4 bytes per
+    column while both automata have at most 65536 states); DICT is refused,
+    DENSE too."""
+    import workloads as W
+    r = native.Regex(W.LOG_RE, host_only=True, max_dict=1)     # 162 segments, no room for a dictionary
+    assert r.info["dict_size"] == 0 and r.ell > 64
+    assert r.layout(100, "auto") == ("pairs", 4, 404)
+    assert r.layout(100, "pairs") == ("pairs", 4, 404)
+    for kind in ("dict", "dense"):
+        with pytest.raises(native.ReError) as e:
+            r.layout(100, kind)
+        assert e.value.status == -8
+    small = native.Regex("(a|b|ab)*", host_only=True)
+    assert small.layout(10, "pairs") == ("pairs", 4, 44)
+
+
 def test_layout_and_errors(native):
     r = native.Regex("(a|b|ab)*", host_only=True)
     assert r.layout(100, "auto") == ("dense", 2, 202)
