@@ -799,6 +799,7 @@ struct re_batch {
     struct Group {
         re_handle *h = nullptr;
         uint32_t tmode = 0, ms = 0, enc_in_smem = 0, cb = 1;
+        bool mat = false;               // per-position states (byte-table reach, fix-up of heads, gather)
         re_slpf_kind kind = RE_SLPF_DENSE;
         std::vector<uint32_t> members;  // caller indices, longest chunks first
         size_t params_off = 0, cbase_off = 0, rbase_off = 0, mbase_off = 0;
@@ -838,6 +839,7 @@ Params group_like(const re_batch::Group &g, bool recognize) {
     q.col_bytes = g.cb;
     q.recognize = recognize ? 1u : 0u;
     q.enc_in_smem = g.enc_in_smem;
+    q.mat = g.mat ? 1u : 0u;
     return q;
 }
 
@@ -857,6 +859,16 @@ re_status batch_run(re_batch *b, cudaStream_t s) {
         bg.chunks = g.chunks; bg.n_reach = g.n_reach; bg.n_merge = g.n_merge;
         bg.nt = (uint32_t)g.members.size();
         bg.recognize = b->recognize ? 1u : 0u;
+        if (g.mat) {
+            if (g.n_reach && !launch_reach_batch_byte8(bg, g.ms, s, b->sms)) {
+                set_error("too many speculative starts");
+                return RE_E_INTERNAL;
+            }
+            launch_join_batch(bg, s);
+            launch_fixup_mat_batch(bg, s, b->sms);
+            launch_gather_batch(bg, group_like(g, b->recognize), s, b->sms);
+            continue;
+        }
         if (g.n_reach && !launch_reach_batch(bg, g.tmode, g.ms, s, b->sms)) {
             set_error("too many speculative starts");
             return RE_E_INTERNAL;
@@ -906,6 +918,9 @@ re_status re_batch_plan(re_handle *const *hs, const uint64_t *lens, uint32_t cou
             g.h = h;
             g.tmode = table_mode(h->dev);
             g.ms = std::max(h->host.msf, b->recognize ? 1u : h->host.msb);
+            // per-position states where the single-text parse would use them (byte
+            // tables for both automata) and the slots fit the byte-table reach
+            g.mat = !b->recognize && mat_capable(h) && g.ms <= 32;
             if (!b->recognize) {
                 const re_status st = resolve_kind(h, opts ? opts->kind : RE_SLPF_AUTO, g.kind, g.cb);
                 if (st != RE_OK) return st;
@@ -923,7 +938,7 @@ re_status re_batch_plan(re_handle *const *hs, const uint64_t *lens, uint32_t cou
         re_batch::Text &t = b->texts[j];
         t.k = batch_chunk(t.len, gbytes[t.group], b->sms, opts);
         if (t.len / t.k >= 0xFFFFFFF0ull) { set_error("text too long for this chunk length"); return RE_E_INVALID_ARG; }
-        if (t.len) t.L = layout_for(b->groups[t.group].h, t.len, t.k, false);
+        if (t.len) t.L = layout_for(b->groups[t.group].h, t.len, t.k, b->groups[t.group].mat);
     }
     uint32_t slot = 0;                                       // every text's Params, group after group
     for (auto &g : b->groups) {

@@ -272,6 +272,70 @@ __device__ void verify_at(const Params &p, uint32_t i) {
     }
 }
 
+// verify_at with a warp per chunk: lane j tests slot j (whether the input
+// enters it, whether its run is live) and a ballot gathers the masks; lane 0
+// does the rest.  Slot counts are at most 32.
+__device__ uint32_t hits_warp(const Params &p, bool fwd, uint32_t i, uint32_t pr, uint32_t S, uint32_t &live) {
+    const DevTables &t = p.t;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t m = __ldg((fwd ? t.fSlotCount : t.bSlotCount) + pr);
+    const uint32_t ms = fwd ? t.msf : t.msb;
+    const uint32_t *R = (fwd ? p.w.Rf : p.w.Rb) + (size_t)i * ms;
+    live = __ballot_sync(0xFFFFFFFFu, lane < m && R[lane] != 0);
+    const uint8_t *of = fwd ? t.fSlotOf : t.bSlotOf;
+    if (of) {                                    // starts from every DFA state: S enters its own slot only
+        const uint32_t n = fwd ? t.nf : t.nb;
+        const uint32_t j = S < n ? __ldg(of + (size_t)pr * n + S) : 0xFFu;
+        return j == 0xFFu ? 0u : 1u << j;
+    }
+    const uint32_t W = t.W;
+    const uint64_t *mask = (fwd ? t.fSlotMask : t.bSlotMask) + (size_t)pr * ms * W;
+    const uint64_t *sb = (fwd ? t.fBits : t.bBits) + (size_t)S * W;
+    return __ballot_sync(0xFFFFFFFFu, lane < m && any_and(sb, mask + (size_t)lane * W, W));
+}
+
+__device__ void verify_warp(const Params &p, uint32_t i) {
+    const uint32_t lane = threadIdx.x & 31;
+    {   // forward: input FJ[i] -> output FJ[i+1]
+        const uint32_t in = p.w.FJ[i], out = p.w.FJ[i + 1];
+        bool fail = in == 0 || out == 0;
+        uint32_t H = 0;
+        if (i > 0 && in != 0) {
+            const uint32_t pr = pair_fwd(p, i);
+            uint32_t L;
+            H = hits_warp(p, true, i, pr, in, L);
+            if (!fail && p.w.fkind[i] == 0) fail = (H & L) == 0;
+        }
+        if (lane == 0) {
+            p.w.fhit[i] = H;
+            if (fail) atomicMin(&p.w.flags[FLAG_FFAIL], (int32_t)i);
+            p.w.FC[(uint64_t)i * p.S] = in;                              // position i*k
+            if (i == p.c - 1 && (p.n & 63) == 0) p.w.FC[p.n >> 6] = p.w.FJ[p.c];   // position n
+        }
+    }
+    if (p.recognize) return;
+    {   // backward: input BJ[i+1] -> output BJ[i]
+        const uint32_t in = p.w.BJ[i + 1], out = p.w.BJ[i];
+        bool fail = in == 0 || out == 0;
+        uint32_t H = 0;
+        if (i < p.c - 1 && in != 0) {
+            const uint32_t pr = pair_bwd(p, i);
+            uint32_t L;
+            H = hits_warp(p, false, i, pr, in, L);
+            if (!fail && p.w.bkind[i] == 0) fail = (H & L) == 0;
+        }
+        if (lane == 0) {
+            p.w.bhit[i] = H;
+            if (fail) atomicMin(&p.w.flags[FLAG_BFAIL], (int32_t)i);
+            if (i + 1 < p.c) {
+                p.w.BC[(uint64_t)(i + 1) * p.S - 1] = in;                // position (i+1)*k
+            } else {                                                     // groups whose end is clipped to n
+                for (uint64_t g = (p.n + 63) / 64 - 1; g < p.Gc; ++g) p.w.BC[g] = in;
+            }
+        }
+    }
+}
+
 // Accept iff both joins ran through and C_0 = I ∩ Ĵ_1 is not empty
 // (recognizer: iff the forward join ran through and J_c ∩ F is not empty).
 __device__ void status_of(const Params &p) {
@@ -299,8 +363,8 @@ __device__ void status_of(const Params &p) {
 __global__ void join_verify_kernel(const __grid_constant__ Params p) {
     pdl_wait();
     pdl_trigger();
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < p.c) verify_at(p, i);
+    const uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // a warp per chunk
+    if (i < p.c) verify_warp(p, (uint32_t)i);
     __shared__ int last;
     __threadfence();
     __syncthreads();
@@ -500,7 +564,8 @@ bool launch_join(const Params &p, cudaStream_t s, int sm_count) {
     } else {
         launch_dependent(join_chain_kernel, blocks, kBlockThreads, 0, s, p);
     }
-    launch_dependent(join_verify_kernel, blocks, kBlockThreads, 0, s, p);
+    const uint32_t vblocks = (uint32_t)(((uint64_t)p.c * 32 + kBlockThreads - 1) / kBlockThreads);
+    launch_dependent(join_verify_kernel, vblocks, kBlockThreads, 0, s, p);
     return true;
 }
 

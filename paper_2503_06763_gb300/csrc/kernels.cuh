@@ -479,6 +479,11 @@ __host__ __device__ inline DevTables dfa_tables(const DevTables &t) {
 }
 bool launch_reach(const Params &p, const CUtensorMap &text_map, const StateMaps &smaps, cudaStream_t s, uint32_t ms,
                   int sm_count);
+// Batch group with per-position states: the byte-table reach over its tiles,
+// the fix-up of the chunk heads and the gather of the columns.
+bool launch_reach_batch_byte8(const BatchGroup &b, uint32_t ms, cudaStream_t s, int sm_count);
+void launch_fixup_mat_batch(const BatchGroup &b, cudaStream_t s, int sm_count);
+void launch_gather_batch(const BatchGroup &b, const Params &like, cudaStream_t s, int sm_count);
 // Warps per direction of the byte-table reach (shape 1) on this device.
 uint64_t reach_byte8_warps(const Params &p, uint32_t ms, int sm_count);
 bool launch_join(const Params &p, cudaStream_t s, int sm_count);

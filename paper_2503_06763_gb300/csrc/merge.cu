@@ -802,22 +802,10 @@ __global__ void __launch_bounds__(kBlockThreads, 3) merge_batch_kernel(const __g
 // the exact Ĵ_{i+1} (bv: the blocks below it were walked with one run).
 // Eq. (builder) from the join's exact boundary states, one thread per chunk
 // and direction, with the classic-DFA rows of the one-byte tables.
+// One item: chunk i of text p in one direction.
 template <int TM>
-__global__ void __launch_bounds__(kFixupThreads) fixup_mat_kernel(const __grid_constant__ Params p) {
-    extern __shared__ __align__(16) uint8_t sm[];
-    __shared__ int ok;
-    Tabs T;
-    stage_tables<TM>(dfa_tables(p.t), sm, T);
-    pdl_wait();
-    pdl_trigger();
-    if (threadIdx.x == 0) ok = *p.status == RE_OK;
-    __syncthreads();
-    if (!ok) return;                                            // rejected: build & merge writes zeros
-    const uint64_t items = 2 * (uint64_t)p.c;
-    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < items;
-         j += (uint64_t)gridDim.x * blockDim.x) {
-        const bool fwd = j < p.c;
-        const uint32_t i = (uint32_t)(fwd ? j : j - p.c);
+__device__ void fixup_mat_item(const Params &p, const Tabs &T, uint32_t i, bool fwd) {
+    {
         const uint64_t base = (uint64_t)i * p.k;
         const uint32_t len = chunk_len(p, i);
         const uint32_t nfs = p.t.nfd + 1, nbs = p.t.nbd + 1;  // the staged rows
@@ -875,21 +863,58 @@ __global__ void __launch_bounds__(kFixupThreads) fixup_mat_kernel(const __grid_c
     }
 }
 
+template <int TM>
+__global__ void __launch_bounds__(kFixupThreads) fixup_mat_kernel(const __grid_constant__ Params p) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    __shared__ int ok;
+    Tabs T;
+    stage_tables<TM>(dfa_tables(p.t), sm, T);
+    pdl_wait();
+    pdl_trigger();
+    if (threadIdx.x == 0) ok = *p.status == RE_OK;
+    __syncthreads();
+    if (!ok) return;                                            // rejected: build & merge writes zeros
+    const uint64_t items = 2 * (uint64_t)p.c;
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < items;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        const bool fwd = j < p.c;
+        fixup_mat_item<TM>(p, T, (uint32_t)(fwd ? j : j - p.c), fwd);
+    }
+}
+
+// Batch: items are (chunk, direction) over every text of the group.
+template <int TM>
+__global__ void __launch_bounds__(kFixupThreads) fixup_mat_batch_kernel(const __grid_constant__ BatchGroup b) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    Tabs T;
+    stage_tables<TM>(dfa_tables(b.t), sm, T);
+    const uint64_t items = 2 * b.chunks;
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < items;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        const bool fwd = j < b.chunks;
+        const uint64_t f = fwd ? j : j - b.chunks;
+        const uint32_t ti = text_of(b.chunk_base, b.nt, f);
+        const Params &p = b.texts[ti];
+        if (*p.status != RE_OK) continue;                       // rejected: the gather writes zeros
+        fixup_mat_item<TM>(p, T, (uint32_t)(f - __ldg(b.chunk_base + ti)), fwd);
+    }
+}
+
 // Build & merge from the stored states: C_r = B_r ∩ B̂_r (Eq. merger) for
 // every column, encoded (DENSE bitset, or DICT index through the pair table
 // over classic-DFA state pairs).  A thread takes 16 consecutive columns: two
 // 16-byte state loads, 16 encoder lookups in shared memory, one vector store.
+// The gather's encoder over classic-DFA state pairs, staged in shared memory
+// (the caller synchronises): the DICT pair table, or the states' segment sets.
 template <int E>
-__global__ void __launch_bounds__(kBlockThreads) merge_gather_kernel(const __grid_constant__ Params p) {
-    extern __shared__ __align__(16) uint8_t sm[];
-    constexpr int CB = bytes_of(E);
-    const uint32_t nfs = p.t.nfd + 1, nbs = p.t.nbd + 1;
+__device__ Enc stage_gather_enc(const DevTables &t, uint8_t *sm) {
+    const uint32_t nfs = t.nfd + 1, nbs = t.nbd + 1;
     Enc e{};
     e.nb = nbs;
     if constexpr (is_dict(E)) {
         const size_t cnt = (size_t)nfs * nbs;
         for (size_t q = threadIdx.x; q < cnt; q += blockDim.x) {
-            const uint32_t v = __ldg(p.t.pt + (q / nbs) * p.t.nb + q % nbs);
+            const uint32_t v = __ldg(t.pt + (q / nbs) * t.nb + q % nbs);
             if (E == ENC_X1) sm[q] = (uint8_t)v;
             else if (E == ENC_X2) reinterpret_cast<uint16_t *>(sm)[q] = (uint16_t)v;
             else reinterpret_cast<uint32_t *>(sm)[q] = v;
@@ -899,11 +924,70 @@ __global__ void __launch_bounds__(kBlockThreads) merge_gather_kernel(const __gri
         else e.pt32 = reinterpret_cast<uint32_t *>(sm);
     } else if constexpr (!is_pair(E)) {
         uint64_t *fb = reinterpret_cast<uint64_t *>(sm), *bb = fb + nfs;
-        for (uint32_t q = threadIdx.x; q < nfs; q += blockDim.x) fb[q] = __ldg(p.t.fBits + q);
-        for (uint32_t q = threadIdx.x; q < nbs; q += blockDim.x) bb[q] = __ldg(p.t.bBits + q);
+        for (uint32_t q = threadIdx.x; q < nfs; q += blockDim.x) fb[q] = __ldg(t.fBits + q);
+        for (uint32_t q = threadIdx.x; q < nbs; q += blockDim.x) bb[q] = __ldg(t.bBits + q);
         e.fbits = fb;
         e.bbits = bb;
     }
+    return e;
+}
+
+// 16 columns from r0 on: their forward states a and backward states b (one
+// byte each) -> encoded columns, one 16-byte store per CB.
+template <int E>
+__device__ __forceinline__ void gather_unit(const Params &p, const Enc &e, uint32_t nfs, uint32_t nbs, bool ok,
+                                            bool &bad, uint64_t r0, const uint4 &a, const uint4 &b) {
+    constexpr int CB = bytes_of(E);
+    const uint32_t fw[4] = {a.x, a.y, a.z, a.w}, bw[4] = {b.x, b.y, b.z, b.w};
+    uint32_t ow[CB * 4];                                        // 16 columns of CB bytes
+#pragma unroll
+    for (int k = 0; k < CB * 4; ++k) ow[k] = 0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const uint32_t f = (fw[k >> 2] >> (8 * (k & 3))) & 0xFFu, g = (bw[k >> 2] >> (8 * (k & 3))) & 0xFFu;
+        uint64_t v = 0;
+        if (ok) {
+            if (f >= nfs || g >= nbs) bad = true;
+            else v = enc_col<TM_SMEM, E>(e, f, g, bad);
+        }
+        if constexpr (CB == 8) {
+            ow[2 * k] = (uint32_t)v;
+            ow[2 * k + 1] = (uint32_t)(v >> 32);
+        } else if constexpr (CB == 4) {
+            ow[k] = (uint32_t)v;
+        } else {
+            constexpr uint32_t m = (1u << (8 * CB)) - 1;
+            ow[(k * CB) >> 2] |= ((uint32_t)v & m) << (8 * ((k * CB) & 3));
+        }
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(p.out) + r0 * CB);
+#pragma unroll
+    for (int q = 0; q < CB; ++q) __stcs(dst + q, make_uint4(ow[4 * q], ow[4 * q + 1], ow[4 * q + 2], ow[4 * q + 3]));
+}
+
+// Column r alone (the tail of a text, fewer than 16 columns).
+template <int E>
+__device__ __forceinline__ void gather_one_column(const Params &p, const Enc &e, uint32_t nfs, uint32_t nbs, bool ok,
+                                                  bool &bad, uint64_t r) {
+    uint64_t v = 0;
+    if (ok) {
+        const uint32_t f = p.w.FS[r], b = p.w.BS[r];
+        if (f >= nfs || b >= nbs) bad = true;
+        else v = enc_col<TM_SMEM, E>(e, f, b, bad);
+    }
+    store_col<E>(p.out, r, v);
+}
+
+// Build & merge from the stored states: C_r = B_r ∩ B̂_r (Eq. merger) for
+// every column, encoded (DENSE bitset, DICT index through the pair table over
+// classic-DFA state pairs, or the PAIRS of ids).  A thread takes 16
+// consecutive columns: two 16-byte state loads, 16 encoder lookups in shared
+// memory, one vector store.
+template <int E>
+__global__ void __launch_bounds__(kBlockThreads) merge_gather_kernel(const __grid_constant__ Params p) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    const uint32_t nfs = p.t.nfd + 1, nbs = p.t.nbd + 1;
+    const Enc e = stage_gather_enc<E>(p.t, sm);
     __syncthreads();
     pdl_wait();
     const bool ok = *p.status == RE_OK;
@@ -911,33 +995,6 @@ __global__ void __launch_bounds__(kBlockThreads) merge_gather_kernel(const __gri
     const uint64_t ncol = p.n + 1, full = ncol / 16;
     // two units of 16 columns per thread and step (their four 16-byte loads
     // in flight together); every index static, so the values stay in registers
-    auto unit = [&](uint64_t r0, const uint4 &a, const uint4 &b) {
-        const uint32_t fw[4] = {a.x, a.y, a.z, a.w}, bw[4] = {b.x, b.y, b.z, b.w};
-        uint32_t ow[CB * 4];                                    // 16 columns of CB bytes
-#pragma unroll
-        for (int k = 0; k < CB * 4; ++k) ow[k] = 0;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const uint32_t f = (fw[k >> 2] >> (8 * (k & 3))) & 0xFFu, g = (bw[k >> 2] >> (8 * (k & 3))) & 0xFFu;
-            uint64_t v = 0;
-            if (ok) {
-                if (f >= nfs || g >= nbs) bad = true;
-                else v = enc_col<TM_SMEM, E>(e, f, g, bad);
-            }
-            if constexpr (CB == 8) {
-                ow[2 * k] = (uint32_t)v;
-                ow[2 * k + 1] = (uint32_t)(v >> 32);
-            } else if constexpr (CB == 4) {
-                ow[k] = (uint32_t)v;
-            } else {
-                constexpr uint32_t m = (1u << (8 * CB)) - 1;
-                ow[(k * CB) >> 2] |= ((uint32_t)v & m) << (8 * ((k * CB) & 3));
-            }
-        }
-        uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(p.out) + r0 * CB);
-#pragma unroll
-        for (int q = 0; q < CB; ++q) __stcs(dst + q, make_uint4(ow[4 * q], ow[4 * q + 1], ow[4 * q + 2], ow[4 * q + 3]));
-    };
     const uint64_t pairs = full / 2;
     const uint4 zero = make_uint4(0, 0, 0, 0);
     for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < pairs;
@@ -950,8 +1007,8 @@ __global__ void __launch_bounds__(kBlockThreads) merge_gather_kernel(const __gri
             b0 = __ldcs(reinterpret_cast<const uint4 *>(p.w.BS + r0));
             b1 = __ldcs(reinterpret_cast<const uint4 *>(p.w.BS + r0 + 16));
         }
-        unit(r0, a0, b0);
-        unit(r0 + 16, a1, b1);
+        gather_unit<E>(p, e, nfs, nbs, ok, bad, r0, a0, b0);
+        gather_unit<E>(p, e, nfs, nbs, ok, bad, r0 + 16, a1, b1);
     }
     if (full & 1) {                                             // an odd last full unit
         const uint64_t r0 = 16 * (full - 1);
@@ -961,21 +1018,43 @@ __global__ void __launch_bounds__(kBlockThreads) merge_gather_kernel(const __gri
                 a = __ldcs(reinterpret_cast<const uint4 *>(p.w.FS + r0));
                 b = __ldcs(reinterpret_cast<const uint4 *>(p.w.BS + r0));
             }
-            unit(r0, a, b);
+            gather_unit<E>(p, e, nfs, nbs, ok, bad, r0, a, b);
         }
     }
     // the last columns (fewer than 16), one at a time
-    if (blockIdx.x == 0 && threadIdx.x < ncol - 16 * full) {
-        const uint64_t r = 16 * full + threadIdx.x;
-        uint64_t v = 0;
-        if (ok) {
-            const uint32_t f = p.w.FS[r], b = p.w.BS[r];
-            if (f >= nfs || b >= nbs) bad = true;
-            else v = enc_col<TM_SMEM, E>(e, f, b, bad);
-        }
-        store_col<E>(p.out, r, v);
-    }
+    if (blockIdx.x == 0 && threadIdx.x < ncol - 16 * full) gather_one_column<E>(p, e, nfs, nbs, ok, bad, 16 * full + threadIdx.x);
     if (bad) atomicExch(p.status, RE_E_INTERNAL);
+}
+
+// Batch: a warp per merge tile (2048 columns of one text of the group).
+template <int E>
+__global__ void __launch_bounds__(kBlockThreads) gather_batch_kernel(const __grid_constant__ BatchGroup b) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    const uint32_t nfs = b.t.nfd + 1, nbs = b.t.nbd + 1;
+    const Enc e = stage_gather_enc<E>(b.t, sm);
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    for (uint64_t tile = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; tile < b.n_merge; tile += warps) {
+        const uint32_t ti = text_of(b.mtile_base, b.nt, tile);
+        const Params &p = b.texts[ti];
+        const bool ok = *p.status == RE_OK;
+        bool bad = false;
+        const uint64_t c0 = (tile - __ldg(b.mtile_base + ti)) * 2048;
+        const uint64_t c1 = min(c0 + 2048, p.n + 1);
+        const uint4 zero = make_uint4(0, 0, 0, 0);
+        for (uint64_t r0 = c0 + 16 * lane; r0 + 16 <= c1; r0 += 512) {
+            uint4 a = zero, bb = zero;
+            if (ok) {
+                a = __ldcs(reinterpret_cast<const uint4 *>(p.w.FS + r0));
+                bb = __ldcs(reinterpret_cast<const uint4 *>(p.w.BS + r0));
+            }
+            gather_unit<E>(p, e, nfs, nbs, ok, bad, r0, a, bb);
+        }
+        const uint64_t tail = c0 + ((c1 - c0) & ~(uint64_t)15);   // fewer than 16 columns left
+        if (tail + lane < c1) gather_one_column<E>(p, e, nfs, nbs, ok, bad, tail + lane);
+        if (bad) atomicExch(p.status, RE_E_INTERNAL);
+    }
 }
 
 __global__ void empty_text_kernel(const __grid_constant__ Params p) { empty_text(p); }
@@ -1167,6 +1246,43 @@ void launch_merge(const Params &p, const CUtensorMap &map, cudaStream_t s, int s
 }
 
 void launch_empty(const Params &p, cudaStream_t s) { empty_text_kernel<<<1, 1, 0, s>>>(p); }
+
+void launch_fixup_mat_batch(const BatchGroup &b, cudaStream_t s, int sm_count) {
+    if (b.recognize || !b.chunks) return;
+    const size_t smem = tables_smem_bytes(dfa_tables(b.t), TM_SMEM8);
+    static uint64_t attr_done = 0;
+    allow_smem(fixup_mat_batch_kernel<TM_SMEM8>, &attr_done);
+    const int blocks = grid_for(fixup_mat_batch_kernel<TM_SMEM8>, smem, 2 * b.chunks, sm_count, kFixupThreads);
+    fixup_mat_batch_kernel<TM_SMEM8><<<blocks, kFixupThreads, smem, s>>>(b);
+}
+
+template <int E>
+void gather_batch_one(const BatchGroup &b, const Params &like, cudaStream_t s, int sm_count) {
+    const size_t smem = gather_smem(like);
+    static uint64_t attr_done = 0;
+    allow_smem(gather_batch_kernel<E>, &attr_done);
+    const int blocks = grid_for(gather_batch_kernel<E>, smem, b.n_merge * 32, sm_count, kBlockThreads);
+    gather_batch_kernel<E><<<blocks, kBlockThreads, smem, s>>>(b);
+}
+
+void launch_gather_batch(const BatchGroup &b, const Params &like, cudaStream_t s, int sm_count) {
+    if (b.recognize || !b.n_merge) return;
+    if (like.kind == RE_SLPF_PAIRS) {
+        if (like.col_bytes == 4) gather_batch_one<ENC_P4>(b, like, s, sm_count);
+        else gather_batch_one<ENC_P8>(b, like, s, sm_count);
+    } else if (like.kind == RE_SLPF_DICT) {
+        if (like.col_bytes == 1) gather_batch_one<ENC_X1>(b, like, s, sm_count);
+        else if (like.col_bytes == 2) gather_batch_one<ENC_X2>(b, like, s, sm_count);
+        else gather_batch_one<ENC_X4>(b, like, s, sm_count);
+    } else {
+        switch (like.col_bytes) {
+            case 1: gather_batch_one<ENC_D1>(b, like, s, sm_count); break;
+            case 2: gather_batch_one<ENC_D2>(b, like, s, sm_count); break;
+            case 4: gather_batch_one<ENC_D4>(b, like, s, sm_count); break;
+            default: gather_batch_one<ENC_D8>(b, like, s, sm_count); break;
+        }
+    }
+}
 
 void launch_fixup_batch(const BatchGroup &b, uint32_t tmode, cudaStream_t s, int sm_count) {
     if (b.recognize || !b.chunks) return;

@@ -767,6 +767,58 @@ void launch_dir(const Params &p, const CUtensorMap &map, const StateMaps &smaps,
                      p, map, smaps);
 }
 
+// A batch group (one RE) with byte-indexed tables and per-position states:
+// the single-text kernel's shape (blocks alternate directions, one table per
+// block) over the 32-chunk tiles of every text of the group, dealt
+// round-robin over the blocks; text and state rows move by plain loads and
+// stores (the texts have no tensor maps).
+template <int MS, bool WIDE>
+__global__ void __launch_bounds__(kDirThreads, 1) reach_dir_batch_kernel(const __grid_constant__ BatchGroup b) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    const bool backward_block = blockIdx.x & 1;
+    Tabs T;
+    uint8_t *rest = stage_byte8(b.t, sm, T, !backward_block, backward_block);
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x / 32;
+    Ring ring{};
+    ring.nst = kDirStages;
+    ring.nout = kDirOut;
+    const uint32_t a = smem_u32(rest);
+    uint8_t *aligned = rest + ((1024 - (a & 1023)) & 1023);
+    ring.tiles = aligned + warp * (kDirStages * kTileBytes);
+    ring.bars = smem_u32(aligned + wpb * (kDirStages + kDirOut) * kTileBytes) + warp * kDirStages * 8;   // unused
+    uint8_t *otile = aligned + wpb * kDirStages * kTileBytes + warp * kDirOut * kTileBytes;
+    const uint64_t gblk = blockIdx.x >> 1, nblk = gridDim.x >> 1;
+    for (uint64_t t = (uint64_t)warp * nblk + gblk; t < b.n_reach; t += nblk * wpb) {
+        const uint32_t ti = text_of(b.rtile_base, b.nt, t);
+        const Params &p = b.texts[ti];
+        const uint32_t i = (uint32_t)((t - __ldg(b.rtile_base + ti)) * 32) + lane;
+        if (i >= p.c) continue;                               // lanes past the text's last chunk
+        if (backward_block) reach_chunk<TM_BYTE8, MS, DIR_B, WIDE, true>(p, T, i, nullptr, ring, false, nullptr, otile);
+        else reach_chunk<TM_BYTE8, MS, DIR_F, WIDE, true>(p, T, i, nullptr, ring, false, nullptr, otile);
+    }
+}
+
+template <int MS, bool WIDE>
+void launch_dir_batch_one(const BatchGroup &b, cudaStream_t s, int sm_count) {
+    const size_t smem = reach_dir_smem(b.t, true);
+    static uint64_t attr_done = 0;
+    allow_smem(reach_dir_batch_kernel<MS, WIDE>, &attr_done, 227 * 1024);
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_dir_batch_kernel<MS, WIDE>, kDirThreads, smem);
+    const uint64_t slots = (uint64_t)std::max(per_sm, 1) * sm_count;
+    const uint64_t per_dir = std::max<uint64_t>(1, std::min<uint64_t>(b.n_reach, slots / 2));
+    reach_dir_batch_kernel<MS, WIDE><<<(uint32_t)(per_dir * 2), kDirThreads, smem, s>>>(b);
+}
+
+inline bool launch_dir_batch(const BatchGroup &b, uint32_t ms, cudaStream_t s, int sm_count) {
+    if (ms <= 2) launch_dir_batch_one<2, false>(b, s, sm_count);
+    else if (ms <= 4) launch_dir_batch_one<4, false>(b, s, sm_count);
+    else if (ms <= 8) launch_dir_batch_one<8, false>(b, s, sm_count);
+    else if (ms <= 32) launch_dir_batch_one<4, true>(b, s, sm_count);
+    else return false;
+    return true;
+}
+
 // Warps per direction the one-direction-per-block reach runs at most (every
 // resident block of a direction, kDirThreads / 32 warps each).
 template <bool MAT>
