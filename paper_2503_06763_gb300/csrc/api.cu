@@ -783,6 +783,55 @@ extern "C" re_status re_matches(re_handle *h, const re_slpf *slpf, uint64_t len,
 }
 
 // ------------------------------------------------------------------ batch
+namespace slpf {
+// Pinned descriptor buffers of batch plans, kept for reuse: pinning host pages
+// costs far more than a small batch's whole parse, and a serving loop plans a
+// batch per launch.  Buffers are powers of two of at least 4 KiB; at most 64
+// are kept.
+struct PinnedPool {
+    std::mutex m;
+    std::multimap<size_t, void *> free;
+    ~PinnedPool() {
+        for (auto &kv : free) cudaFreeHost(kv.second);
+    }
+};
+PinnedPool &pinned_pool() {
+    static PinnedPool *pool = new PinnedPool();                 // never destroyed: outlives every plan
+    return *pool;
+}
+size_t pinned_size(size_t bytes) {
+    size_t s = 4096;
+    while (s < bytes) s <<= 1;
+    return s;
+}
+cudaError_t pinned_take(size_t bytes, uint8_t **out) {
+    const size_t sz = pinned_size(bytes);
+    PinnedPool &pool = pinned_pool();
+    {
+        std::lock_guard<std::mutex> g(pool.m);
+        auto it = pool.free.find(sz);
+        if (it != pool.free.end()) {
+            *out = static_cast<uint8_t *>(it->second);
+            pool.free.erase(it);
+            return cudaSuccess;
+        }
+    }
+    return cudaHostAlloc((void **)out, sz, cudaHostAllocDefault);
+}
+void pinned_give(uint8_t *buf, size_t bytes) {
+    if (!buf) return;
+    PinnedPool &pool = pinned_pool();
+    {
+        std::lock_guard<std::mutex> g(pool.m);
+        if (pool.free.size() < 64) {
+            pool.free.emplace(pinned_size(bytes), buf);
+            return;
+        }
+    }
+    cudaFreeHost(buf);
+}
+}  // namespace slpf
+
 // A planned batch: per text its group (compiled RE), chunk length and
 // workspace layout; per group the table mode, encoding and unit counts.  The
 // descriptor area at the start of the workspace holds every text's Params,
@@ -814,6 +863,20 @@ struct re_batch {
     cudaEvent_t uploaded = nullptr;
     bool pending = false;
     uint8_t *d_ws = nullptr;
+    // Groups are independent: they run on a few streams of their own, forked
+    // from and joined back into the caller's stream by events (also inside a
+    // CUDA-graph capture), so one group's small join and fix-up launches
+    // overlap another's reach and merge.
+    std::vector<cudaStream_t> aux;
+    std::vector<cudaEvent_t> done;
+    cudaEvent_t fork = nullptr;
+    ~re_batch() {
+        for (cudaStream_t st : aux) cudaStreamDestroy(st);
+        for (cudaEvent_t ev : done) cudaEventDestroy(ev);
+        if (fork) cudaEventDestroy(fork);
+        if (uploaded) cudaEventDestroy(uploaded);
+        slpf::pinned_give(pinned, desc_bytes);
+    }
 };
 
 namespace slpf {
@@ -843,12 +906,18 @@ Params group_like(const re_batch::Group &g, bool recognize) {
     return q;
 }
 
-re_status batch_run(re_batch *b, cudaStream_t s) {
+re_status batch_run(re_batch *b, cudaStream_t s0) {
     uint8_t *w = b->d_ws;
     launch_batch_init(reinterpret_cast<const Params *>(w), (uint32_t)b->texts.size(),
-                      reinterpret_cast<uint32_t *>(w + b->queue_off), (uint32_t)b->groups.size() * kQueues, s);
+                      reinterpret_cast<uint32_t *>(w + b->queue_off), (uint32_t)b->groups.size() * kQueues, s0);
+    const size_t na = b->aux.size();
+    if (na) {
+        CUDA_TRY(cudaEventRecord(b->fork, s0), "batch fork");
+        for (cudaStream_t a : b->aux) CUDA_TRY(cudaStreamWaitEvent(a, b->fork, 0), "batch fork");
+    }
     for (size_t gi = 0; gi < b->groups.size(); ++gi) {
         const re_batch::Group &g = b->groups[gi];
+        const cudaStream_t s = na ? b->aux[gi % na] : s0;
         BatchGroup bg{};
         bg.t = g.h->dev;
         bg.texts = reinterpret_cast<const Params *>(w + g.params_off);
@@ -876,6 +945,10 @@ re_status batch_run(re_batch *b, cudaStream_t s) {
         launch_join_batch(bg, s);
         launch_fixup_batch(bg, g.tmode, s, b->sms);
         launch_merge_batch(bg, group_like(g, b->recognize), s, b->sms);
+    }
+    for (size_t a = 0; a < na; ++a) {                         // join: the caller's stream waits for every group
+        CUDA_TRY(cudaEventRecord(b->done[a], b->aux[a]), "batch join");
+        CUDA_TRY(cudaStreamWaitEvent(s0, b->done[a], 0), "batch join");
     }
     CUDA_TRY(cudaGetLastError(), "batch launch");
     return RE_OK;
@@ -969,7 +1042,7 @@ re_status re_batch_plan(re_handle *const *hs, const uint64_t *lens, uint32_t cou
         off += align256(t.L.total);
     }
     b->total = std::max<size_t>(off, 256);
-    CUDA_TRY(cudaHostAlloc((void **)&b->pinned, b->desc_bytes, cudaHostAllocDefault), "batch descriptor buffer");
+    CUDA_TRY(pinned_take(b->desc_bytes, &b->pinned), "batch descriptor buffer");
     std::memset(b->pinned, 0, b->desc_bytes);
     for (auto &g : b->groups) {                              // prefix sums of the units of each kind
         uint64_t *cb = reinterpret_cast<uint64_t *>(b->pinned + g.cbase_off);
@@ -993,6 +1066,20 @@ re_status re_batch_plan(re_handle *const *hs, const uint64_t *lens, uint32_t cou
         }
     }
     CUDA_TRY(cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming), "batch event");
+    uint64_t all_bytes = 0;
+    for (uint64_t g : gbytes) all_bytes += g;
+    if (b->groups.size() > 1 && all_bytes >= (64ull << 20)) {   // small batches: no stream set-up cost
+        const size_t na = std::min<size_t>(4, b->groups.size());
+        CUDA_TRY(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "batch event");
+        for (size_t a = 0; a < na; ++a) {
+            cudaStream_t st;
+            cudaEvent_t ev;
+            CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "batch stream");
+            b->aux.push_back(st);
+            CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "batch event");
+            b->done.push_back(ev);
+        }
+    }
     *out = b.release();
     return RE_OK;
 }
@@ -1071,9 +1158,7 @@ re_status re_batch_run(re_batch *b, re_stream stream) {
 void re_batch_free(re_batch *b) {
     if (!b) return;
     if (b->pending) cudaEventSynchronize(b->uploaded);
-    if (b->uploaded) cudaEventDestroy(b->uploaded);
-    if (b->pinned) cudaFreeHost(b->pinned);
-    delete b;
+    delete b;                                                   // the destructor releases streams, events, buffers
 }
 
 }  // extern "C"
