@@ -858,7 +858,7 @@ struct re_batch {
     bool recognize = false;
     std::vector<Text> texts;
     std::vector<Group> groups;
-    size_t queue_off = 0, desc_bytes = 0, total = 0;
+    size_t queue_off = 0, maps_off = 0, desc_bytes = 0, total = 0;
     uint8_t *pinned = nullptr;
     cudaEvent_t uploaded = nullptr;
     bool pending = false;
@@ -1022,6 +1022,8 @@ re_status re_batch_plan(re_handle *const *hs, const uint64_t *lens, uint32_t cou
         for (uint32_t j : g.members) b->texts[j].slot = slot++;
     }
     size_t off = align256((size_t)count * sizeof(Params));
+    b->maps_off = off;                                       // per text: text, FS and BS tensor maps
+    off = align256(off + (size_t)count * 3 * sizeof(CUtensorMap));
     for (auto &g : b->groups) {
         const size_t arr = (g.members.size() + 1) * sizeof(uint64_t);
         g.cbase_off = off; off = align256(off + arr);
@@ -1135,6 +1137,15 @@ re_status re_parse_batch(re_batch *b, const uint8_t *const *d_texts, re_slpf *ou
         p.Gfast = t.len / kSub;
         p.c_full = (uint32_t)(t.len / t.k);
         if (t.len) carve(p, t.L, w + t.ws_off);
+        if (g.mat && t.len) {                                // TMA for full tiles: maps in the descriptor area
+            CUtensorMap *hm = reinterpret_cast<CUtensorMap *>(b->pinned + b->maps_off) + 3 * (size_t)t.slot;
+            uint8_t *ws = w + t.ws_off;
+            p.text_tma = text_tensor_map(hm[0], d_texts[j], t.k, p.c_full) &&
+                         text_tensor_map(hm[1], ws + t.L.off[24], t.k, p.c_full) &&
+                         text_tensor_map(hm[2], ws + t.L.off[25], t.k, p.c_full) ? 1u : 0u;
+            p.state_tma = p.text_tma;
+            p.tmaps = reinterpret_cast<const CUtensorMap *>(w + b->maps_off) + 3 * (size_t)t.slot;
+        }
         std::memcpy(b->pinned + (size_t)t.slot * sizeof(Params), &p, sizeof(Params));
         outs[j].n_cols = t.len + 1;
     }

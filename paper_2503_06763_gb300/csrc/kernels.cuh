@@ -86,6 +86,7 @@ struct Params {
                                     // half of each builder's states in registers
     uint32_t out_tma;               // full column groups leave through TMA tensor stores
     uint32_t text_tma;              // reach reads full chunks through TMA tiles
+    const CUtensorMap *tmaps;       // batch texts: device copies of the text, FS and BS tensor maps
     uint32_t c_full;                // chunks of exactly k bytes (rows of the text tensor map)
     uint64_t Gfast;                 // groups g with 64g + 64 <= n (computed on the fast path)
 };
@@ -388,6 +389,12 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, uint32_t sr
                  :: "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(src) : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// A tensor map read from global memory (a batch text's): acquire it for the
+// tensor-map proxy before the first copy that uses it.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap *map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" :: "l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
+}
 // 2D tiled load global -> shared, completion counted on an mbarrier (bytes).
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int32_t x, int32_t y, uint32_t bar) {
     asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"

@@ -785,17 +785,43 @@ __global__ void __launch_bounds__(kDirThreads, 1) reach_dir_batch_kernel(const _
     const uint32_t a = smem_u32(rest);
     uint8_t *aligned = rest + ((1024 - (a & 1023)) & 1023);
     ring.tiles = aligned + warp * (kDirStages * kTileBytes);
-    ring.bars = smem_u32(aligned + wpb * (kDirStages + kDirOut) * kTileBytes) + warp * kDirStages * 8;   // unused
+    ring.bars = smem_u32(aligned + wpb * (kDirStages + kDirOut) * kTileBytes) + warp * kDirStages * 8;
+    ring.phase = 0;
     uint8_t *otile = aligned + wpb * kDirStages * kTileBytes + warp * kDirOut * kTileBytes;
+    if (lane == 0) {
+        for (uint32_t st = 0; st < kDirStages; ++st) mbar_init(ring.bars + 8 * st, 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
     const uint64_t gblk = blockIdx.x >> 1, nblk = gridDim.x >> 1;
     for (uint64_t t = (uint64_t)warp * nblk + gblk; t < b.n_reach; t += nblk * wpb) {
         const uint32_t ti = text_of(b.rtile_base, b.nt, t);
         const Params &p = b.texts[ti];
-        const uint32_t i = (uint32_t)((t - __ldg(b.rtile_base + ti)) * 32) + lane;
-        if (i >= p.c) continue;                               // lanes past the text's last chunk
-        if (backward_block) reach_chunk<TM_BYTE8, MS, DIR_B, WIDE, true>(p, T, i, nullptr, ring, false, nullptr, otile);
-        else reach_chunk<TM_BYTE8, MS, DIR_F, WIDE, true>(p, T, i, nullptr, ring, false, nullptr, otile);
+        const uint64_t tile = t - __ldg(b.rtile_base + ti);
+        const uint32_t i = (uint32_t)(tile * 32) + lane;
+        // full tiles of a text with tensor maps go through TMA (text in, state rows out)
+        const bool tma = p.text_tma && p.state_tma && tile * 32 + 32 <= p.c_full;
+        if (tma && lane == 0) {
+            tensormap_acquire(p.tmaps);
+            tensormap_acquire(p.tmaps + (backward_block ? 2 : 1));
+        }
+        if (tma) __syncwarp();
+        if (i >= p.c) continue;                               // lanes past the text's last chunk (plain tiles only)
+        const bool ok = backward_block
+                            ? reach_chunk<TM_BYTE8, MS, DIR_B, WIDE, true>(p, T, i, p.tmaps, ring, tma, p.tmaps + 2, otile)
+                            : reach_chunk<TM_BYTE8, MS, DIR_F, WIDE, true>(p, T, i, p.tmaps, ring, tma, p.tmaps + 1, otile);
+        if (!ok) {
+            atomicExch(p.status, RE_E_INTERNAL);
+            for (uint32_t st = 0; st < kDirStages; ++st) {   // drain: bounded wait on every stage
+                bool done = false;
+                for (uint32_t it = 0; it < kWaitLimit && !done; ++it)
+                    done = mbar_try_wait(ring.bars + 8 * st, (ring.phase >> st) & 1u);
+            }
+            if (lane == 0) bulk_wait_all();
+            return;
+        }
     }
+    if (lane == 0) bulk_wait_all();
 }
 
 template <int MS, bool WIDE>
