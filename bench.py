@@ -586,8 +586,9 @@ def batch_mode(args, rank, world, local):
 def serve_mode(args, rank, world, local):
     """Poisson request streams against 16 resident random REs (20-300
     positions); lengths lognormal (median 64 KiB, sigma 1.5, at most 64 MiB).
-    Each rate is served twice: continuous batching (slots of re_parse_batch)
-    and one launch per request (the same loop with batches of one)."""
+    Each rate is served three times: continuous batching in the Python loop
+    (slots of re_parse_batch), one launch per request (the same loop with
+    batches of one), and the library's request loop (re_server)."""
     import numpy as np
     import torch
     import workloads as W
@@ -626,6 +627,45 @@ def serve_mode(args, rank, world, local):
                             "batches": srv.stats["batches"], "not_ok": bad, "wall_s": round(wall, 3)})
             srv.stats.update(batches=0, requests=0, max_batch=0, max_inflight=0)
         srv.close()
+    # the library's own request loop (re_server): submissions from this thread at
+    # the arrival times, completion times taken on the server's clock
+    from paper_2503_06763_gb300.native import NativeServer
+    nsrv = NativeServer([r[2] for r in res], slots=4, arena_bytes=2 << 30)
+    for j in range(64):
+        nsrv.wait(nsrv.submit(bank[j][0], bank[j][1]))
+    nsrv.poll(cap=1 << 16)
+    for j in range(64):
+        nsrv.result(j + 1)
+    for rate in rates:
+        n = int(min(max(rate * args.duration, 200), 20_000))
+        arr = np.cumsum(rng.exponential(1.0 / rate, size=n))
+        st0 = dict(nsrv.stats())
+        start = time.perf_counter()
+        sub = {}
+        for j in range(n):
+            while time.perf_counter() - start < arr[j]:
+                pass
+            sub[nsrv.submit(bank[j % len(bank)][0], bank[j % len(bank)][1])] = (nsrv.clock_ns(), j)
+        lat, done_ns = [], []
+        got = 0
+        while got < n:
+            for t, ns in nsrv.poll(cap=1 << 16):
+                if t in sub:
+                    lat.append((ns - sub[t][0]) / 1e6)
+                    done_ns.append(ns)
+                    got += 1
+                    _, st = nsrv.result(t)
+        nbytes = sum(len(bank[j % len(bank)][1]) for j in range(n))
+        first = min(v[0] for v in sub.values())
+        span = (max(done_ns) - first) / 1e9
+        lat = np.array(lat)
+        st1 = nsrv.stats()
+        results.append({"mode": "native_loop", "rate_rps": rate, "requests": n, "text_bytes": nbytes,
+                        "offered_GBps": round(nbytes / arr[-1] / 1e9, 3), "served_GBps": round(nbytes / span / 1e9, 3),
+                        "achieved_rps": round(n / span, 1), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                        "p99_ms": round(float(np.percentile(lat, 99)), 3), "mean_ms": round(float(lat.mean()), 3),
+                        "max_ms": round(float(lat.max()), 3), "batches": st1["batches"] - st0["batches"]})
+    nsrv.close()
     best = max((r for r in results if r["mode"] == "continuous_batching"), key=lambda r: r["served_GBps"])
     line = {
         "metric": "served SLPF parse: p50/p99 latency (ms) and GB/s under Poisson load",

@@ -457,6 +457,56 @@ re_status re_slpf_dfa_decode(const re_slpf_dfa_header *hdr, const void *d_archiv
                              const uint8_t *d_text, void *d_cols, uint64_t cols_cap_bytes, uint32_t col_bytes,
                              int32_t *d_status, re_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * Request loop (no counterpart in the paper: a deployment layer over
+ * re_parse and re_parse_batch).  A server keeps compiled REs resident and
+ * runs a worker thread over `slots`, each with its own stream, device arena
+ * and pinned staging buffers, allocated once.  Submitted requests wait in a
+ * queue; while no more wait than slots are free each runs alone at once,
+ * beyond that a free slot takes as many as fit (batches grow with the load);
+ * the worker launches each
+ * slot's requests as one re_parse or re_parse_batch with one copy in and one
+ * copy out, and completes a request when its slot's event fires.  Results are
+ * those of re_parse on each text alone.                                     */
+typedef struct re_server re_server;
+
+typedef struct {
+    uint32_t slots;           /* concurrent launches (0 = 4) */
+    uint64_t arena_bytes;     /* device bytes per slot: texts, columns, workspace (0 = 1 GiB) */
+    uint64_t staging_bytes;   /* pinned host bytes per slot, for texts and again for columns (0 = arena / 2) */
+    uint32_t max_batch;       /* requests per launch (0 = 4096) */
+} re_server_opts;
+
+/* Start a server over count compiled REs (all on the current device; the
+ * handles must outlive it).  Columns use each RE's AUTO encoding.           */
+re_status re_server_create(re_handle *const *hs, uint32_t count, const re_server_opts *opts, re_server **out);
+
+/* Queue the parse of host text[0 .. len) under RE re_index.  Its columns (the
+ * AUTO layout of re_slpf_layout, cols_cap bytes at least) and status word are
+ * written to the host buffers cols and *status when it completes; text, cols
+ * and status must stay valid until then.  *ticket identifies the request.
+ * RE_E_CAPACITY: the request does not fit one slot's arena or staging.
+ * Thread-safe.                                                               */
+re_status re_server_submit(re_server *s, uint32_t re_index, const uint8_t *text, uint64_t len, void *cols,
+                           uint64_t cols_cap, int32_t *status, uint64_t *ticket);
+
+/* Block until request `ticket` is complete (timeout_ms < 0: no limit).
+ * RE_E_TIMEOUT when the limit passes first.                                 */
+re_status re_server_wait(re_server *s, uint64_t ticket, int32_t timeout_ms);
+
+/* Tickets completed since the last call (at most cap of them; *n set), and
+ * when done_ns is not NULL their completion times on the server clock.      */
+re_status re_server_poll(re_server *s, uint64_t *tickets, uint64_t *done_ns, uint32_t cap, uint32_t *n);
+
+/* The server clock: nanoseconds since re_server_create (steady).           */
+uint64_t re_server_clock_ns(const re_server *s);
+
+/* stats[0..3]: launches, requests, largest batch, most slots in flight.     */
+re_status re_server_stats(re_server *s, uint64_t *stats);
+
+/* Finish every queued request, stop the worker and free the server.        */
+void re_server_destroy(re_server *s);
+
 /* Thread-local description of the last error returned on this thread.     */
 const char *re_last_error(void);
 

@@ -38,6 +38,8 @@ EXPORTS = ["re_compile", "re_free", "re_get_info", "re_segment_name", "re_dict_c
            "re_matches", "re_autotune", "re_tuned", "re_parse_host",
            "re_shard_map_size", "re_shard_map", "re_shard_entry", "re_parse_slice", "re_state_bits",
            "re_parse_static", "re_slpf_dfa_encode", "re_slpf_dfa_decode",
+           "re_server_create", "re_server_submit", "re_server_wait", "re_server_poll", "re_server_stats",
+           "re_server_clock_ns", "re_server_destroy",
            "re_last_error"]
 RE_STATIC_SCRATCH_BYTES = 64 << 20
 
@@ -66,6 +68,11 @@ class Slpf(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("col_bytes", ctypes.c_uint32), ("n_cols", ctypes.c_uint64),
                 ("d_cols", ctypes.c_void_p), ("cols_cap_bytes", ctypes.c_uint64),
                 ("d_status", ctypes.c_void_p)]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_uint32), ("arena_bytes", ctypes.c_uint64), ("staging_bytes", ctypes.c_uint64),
+                ("max_batch", ctypes.c_uint32)]
 
 
 class DfaHeader(ctypes.Structure):
@@ -138,6 +145,20 @@ def load():
     lib.re_parse_slice.argtypes = [vp, vp, u64, u32, u32, vp, ctypes.POINTER(Slpf), vp, u64, ctypes.POINTER(ParseOpts)]
     lib.re_parse_slice.restype = i32
     lib.re_state_bits.argtypes = [vp, ctypes.c_int32, u32, vp, u32]
+    lib.re_server_create.argtypes = [vp, u32, ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]
+    lib.re_server_create.restype = i32
+    lib.re_server_submit.argtypes = [vp, u32, vp, u64, vp, u64, vp, ctypes.POINTER(u64)]
+    lib.re_server_submit.restype = i32
+    lib.re_server_wait.argtypes = [vp, u64, ctypes.c_int32]
+    lib.re_server_wait.restype = i32
+    lib.re_server_poll.argtypes = [vp, vp, vp, u32, ctypes.POINTER(u32)]
+    lib.re_server_poll.restype = i32
+    lib.re_server_stats.argtypes = [vp, vp]
+    lib.re_server_stats.restype = i32
+    lib.re_server_clock_ns.argtypes = [vp]
+    lib.re_server_clock_ns.restype = u64
+    lib.re_server_destroy.argtypes = [vp]
+    lib.re_server_destroy.restype = None
     lib.re_slpf_dfa_encode.argtypes = [vp, u32, vp, u64, u32, vp, u64, ctypes.POINTER(u64)]
     lib.re_slpf_dfa_encode.restype = i32
     lib.re_slpf_dfa_decode.argtypes = [ctypes.POINTER(DfaHeader), vp, u64, vp, vp, u64, u32, vp, vp]
@@ -624,3 +645,72 @@ def slpf_dfa_decode(archive, text, col_bytes: int, stream=None):
                                     col_bytes, status.data_ptr(), ctypes.c_void_p(s.cuda_stream)))
     cols._archive = d_arch                       # keep the device archive alive until the columns are used
     return cols, status
+
+
+# ---------------------------------------------------------------------- request loop in the library
+class NativeServer:
+    """re_server: the library's request loop over resident compiled REs.
+    ``submit`` queues a host text and returns a ticket; the columns and status
+    land in host numpy arrays the server allocates and keeps until the ticket
+    is collected with ``result``."""
+
+    def __init__(self, regexes, slots: int = 4, arena_bytes: int = 1 << 30, staging_bytes: int = 0,
+                 max_batch: int = 0):
+        import numpy as np
+        self._np = np
+        self.regexes = list(regexes)
+        hs = (ctypes.c_void_p * len(self.regexes))(*[r._h for r in self.regexes])
+        opts = ServerOpts(slots, arena_bytes, staging_bytes, max_batch)
+        h = ctypes.c_void_p()
+        check(load().re_server_create(hs, len(self.regexes), ctypes.byref(opts), ctypes.byref(h)))
+        self._h = h
+        self._live = {}                      # ticket -> (text, cols, status) kept alive until collected
+
+    def clock_ns(self) -> int:
+        return load().re_server_clock_ns(self._h)
+
+    def submit(self, re_index: int, text) -> int:
+        np = self._np
+        x = np.ascontiguousarray(text, dtype=np.uint8)
+        _, cb, nbytes = self.regexes[re_index].layout(x.size, "auto")
+        cols = np.empty(nbytes // cb, dtype={1: np.uint8, 2: np.uint16, 4: np.uint32, 8: np.uint64}[cb])
+        status = np.full(1, -100, dtype=np.int32)
+        t = ctypes.c_uint64()
+        check(load().re_server_submit(self._h, re_index, x.ctypes.data if x.size else None, x.size,
+                                      cols.ctypes.data, cols.nbytes, status.ctypes.data, ctypes.byref(t)))
+        self._live[t.value] = (x, cols, status)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        check(load().re_server_wait(self._h, ticket, timeout_ms))
+
+    def result(self, ticket: int):
+        """(columns, status) of a completed request (call after wait/poll)."""
+        x, cols, status = self._live.pop(ticket)
+        return cols, int(status[0])
+
+    def poll(self, cap: int = 4096):
+        """[(ticket, completion time in ns on the server clock)] since the last poll."""
+        np = self._np
+        t = np.zeros(cap, dtype=np.uint64)
+        ns = np.zeros(cap, dtype=np.uint64)
+        n = ctypes.c_uint32()
+        check(load().re_server_poll(self._h, t.ctypes.data, ns.ctypes.data, cap, ctypes.byref(n)))
+        return list(zip(t[:n.value].tolist(), ns[:n.value].tolist()))
+
+    def stats(self) -> dict:
+        np = self._np
+        v = np.zeros(4, dtype=np.uint64)
+        check(load().re_server_stats(self._h, v.ctypes.data))
+        return dict(zip(("batches", "requests", "max_batch", "max_inflight"), v.tolist()))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().re_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -230,13 +230,18 @@ class Server:
                     pending -= len(s.reqs)
                     self._retire(s, time.perf_counter() - t0, keep_cols)
                     progressed = True
+            free = sum(1 for s in self.slots if s.event is None)
             for s in self.slots:                                   # admit into free slots
                 if not waiting:
                     break
                 if s.event is not None:
                     continue
+                # light load (no more waiting requests than free slots): every request
+                # gets a slot of its own at once; otherwise one slot takes all it can
+                share = 1 if len(waiting) <= free else self.max_batch
+                free -= 1
                 take, dev_used, in_used, out_used = [], 1 << 20, 0, 4096
-                while waiting and len(take) < self.max_batch:
+                while waiting and len(take) < min(self.max_batch, share):
                     d, i, o = fp[id(waiting[0])]
                     if take and (dev_used + d > self.arena_bytes or in_used + i > s.pin_in.numel()
                                  or out_used + o > s.pin_out.numel()):

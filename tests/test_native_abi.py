@@ -177,3 +177,11 @@ def test_serving_workspace_bound_covers_the_library(native):
         for n in (0, 1, 63, 64, 255, 256, 257, 4095, 65536, 1_000_003, 64 << 20):
             for k in (256, 320, 4608):
                 assert rx.workspace_size(n, chunk_len=k) <= srv.ws_bound(ri, n), (pats[ri][:20], n, k)
+
+
+def test_server_refuses_host_only_handles(native):
+    """re_server_create checks its handles before touching the device."""
+    r = native.Regex("(a|b|ab)*", host_only=True)
+    with pytest.raises(native.ReError) as e:
+        native.NativeServer([r])
+    assert e.value.status == -1
