@@ -344,12 +344,14 @@ def measure_single(args, name, n, rank, world, local, dist, full=True):
     del rec_ws
 
     # end to end through re_parse_host: pinned host text in, columns and status
-    # back to pinned host memory, every step.  Two streams with their own device
-    # buffers take alternate steps, so one step's copies overlap the other's
-    # kernels (the link carries about 200 GB/s each way).
+    # back to pinned host memory, every step.  Three streams with their own
+    # device buffers take steps in turn, so one step's copy in, another's
+    # kernels and a third's copy out run at once (the link carries about 200
+    # GB/s each way, 171 GB/s each way when both directions are busy).
+    E2E_STREAMS = 3
     pin_in = torch.from_numpy(host).pin_memory()
     sets = []
-    for _ in range(2):
+    for _ in range(E2E_STREAMS):
         sets.append({"s": torch.cuda.Stream(dev), "out": torch.empty(n + 1, dtype=dt).pin_memory(),
                      "st": torch.empty(1, dtype=torch.int32).pin_memory(),
                      "d_text": torch.empty(n, dtype=torch.uint8, device=dev),
@@ -358,14 +360,14 @@ def measure_single(args, name, n, rank, world, local, dist, full=True):
                      "ws": torch.empty(ws.numel(), dtype=torch.uint8, device=dev)})
 
     def e2e_step(k):
-        b = sets[k % 2]
+        b = sets[k % E2E_STREAMS]
         rx.parse_host(pin_in, b["out"], b["st"], b["d_text"], b["d_out"], b["d_st"], b["ws"], stream=b["s"],
                       kind=kind, chunk_len=args.chunk_len)
 
-    for k in range(4):                          # warm-up: first use of the pinned buffers and copy paths
+    for k in range(2 * E2E_STREAMS):            # warm-up: first use of the pinned buffers and copy paths
         e2e_step(k)
     torch.cuda.synchronize()
-    e_steps = max(4, min(args.steps, 8))
+    e_steps = max(2 * E2E_STREAMS, min(args.steps, 9))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for b in sets:
@@ -383,7 +385,7 @@ def measure_single(args, name, n, rank, world, local, dist, full=True):
         raise SystemExit("end-to-end columns differ from the device-resident parse")
     res["e2e"] = {"value": round(n * world / (e_ms / 1e3) / 1e9, 3), "unit": "GB/s",
                   "h2d_bytes_per_step": n, "d2h_bytes_per_step": (n + 1) * cb + 4,
-                  "api": "re_parse_host, 2 streams alternating"}
+                  "api": f"re_parse_host, {E2E_STREAMS} streams taking steps in turn"}
     del sets, pin_in, text, out, ws
     torch.cuda.empty_cache()
     res["cpu_baseline"] = None
