@@ -167,3 +167,26 @@ def test_fixed_chunk_length_and_only_empty_texts(lib):
     for j, t in enumerate(texts):
         want, wst = _alone(rx, t)
         assert int(status[j].item()) == wst and np.array_equal(outs[j].cpu().numpy(), want)
+
+
+def test_pair_columns_in_a_batch(lib):
+    """RE_SLPF_PAIRS through a batch (per-position-state groups and the
+    checkpoint path alike): each text's pairs equal its single parse's, and
+    decode to the oracle's columns."""
+    Batch, Regex = lib
+    pats = _patterns()
+    rxs = [Regex(p) for p, _ in pats]
+    items = [(pi, pats[pi][1](n, 300 + pi * 7 + n % 5)) for pi in range(len(pats)) for n in (0, 700, 9000, 200_001)]
+    texts = [torch.from_numpy(np.ascontiguousarray(h)).cuda() for _, h in items]
+    b = Batch([rxs[pi] for pi, _ in items], [len(h) for _, h in items], kind="pairs")
+    outs, status, kinds = b.parse(texts)
+    torch.cuda.synchronize()
+    st = status.cpu().numpy()
+    for j, ((pi, h), t) in enumerate(zip(items, texts)):
+        cols, wst, _ = rxs[pi].parse(t, kind="pairs")
+        torch.cuda.synchronize()
+        assert kinds[j] == "pairs" and st[j] == int(wst.item())
+        assert np.array_equal(outs[j].cpu().numpy(), cols.cpu().numpy()), (pi, len(h))
+        if len(h) <= 9000:
+            want = serial.parse(compile_re(pats[pi][0]), h.tobytes())
+            assert np.array_equal(rxs[pi].decode(outs[j].cpu().numpy(), "pairs"), want), (pi, len(h))
