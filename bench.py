@@ -65,7 +65,8 @@ def parse_args():
                     help="with --chunk-len: reach shape 1-4 (RE_PARSE_REACH); 0 = the library's default")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="single",
-                    choices=["single", "batch", "serve", "matches", "latency", "ablation", "join", "shard"],
+                    choices=["single", "batch", "serve", "matches", "latency", "ablation", "join", "shard",
+                             "archive"],
                     help="single: one 256 MiB text (default); batch: 4096 texts under 8 random REs; "
                          "serve: Poisson request stream")
     ap.add_argument("--texts", type=int, default=4096, help="batch mode: number of texts")
@@ -416,6 +417,8 @@ def main():
         return join_mode(args, rank, world, local)
     if args.mode == "shard":
         return shard_mode(args, rank, world, local)
+    if args.mode == "archive":
+        return archive_mode(args, rank, world, local)
 
     import torch
     torch.cuda.set_device(local)
@@ -860,6 +863,72 @@ def ablation_mode(args, rank, world, local):
                        "variants": "ME-DFA starts with the last-class filter / starts from every DFA state "
                                    "forward, backward, both"},
             "rows": rows}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def archive_mode(args, rank, world, local):
+    """SLPF archives (App. C): the log, DNA and ab texts (256 MiB, or --bytes)
+    parsed, their columns archived by the host encoder (checkpoint every 4096
+    columns) and rebuilt by the device decoder.  Per workload: archive bytes
+    against the columns' bytes, the exception rate, host encode time, and the
+    device rebuild in GB/s of columns written (value: the log's rebuild)."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2503_06763_gb300 import Regex
+    from paper_2503_06763_gb300 import native
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n0 = args.bytes or (256 << 20)
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    for name, pattern, host in (("log", W.LOG_RE, W.log_text(n0, seed=2)), ("dna", W.DNA_RE, W.dna_text(n0, seed=1)),
+                                ("ab", W.AB_RE, W.ab_text(n0, seed=0))):
+        n = host.size
+        rx = Regex(pattern)
+        text = torch.from_numpy(host).to(dev)
+        cols, st, kind = rx.parse(text)
+        torch.cuda.synchronize()
+        cb = cols.element_size()
+        hcols = cols.cpu().numpy().view({1: np.uint8, 2: np.uint16, 4: np.uint32}[cb])
+        t0 = time.perf_counter()
+        arch = native.slpf_dfa_encode(hcols, host, 4096)
+        enc_s = time.perf_counter() - t0
+        hdr = native.slpf_dfa_header(arch)
+        for _ in range(3):
+            got, gst = native.slpf_dfa_decode(arch, text, cb)
+        torch.cuda.synchronize()
+        if int(gst.item()) != 0 or not torch.equal(got.view(torch.uint8), cols.view(torch.uint8)):
+            raise SystemExit(f"{name}: rebuilt columns differ")
+        steps = max(args.steps, 5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        d_arch = torch.from_numpy(arch).to(dev)
+        hdr_c = native.DfaHeader(**hdr)
+        out = torch.empty_like(cols)
+        status = torch.empty(1, dtype=torch.int32, device=dev)
+        lib = native.load()
+        e0.record(stream)
+        for _ in range(steps):
+            native.check(lib.re_slpf_dfa_decode(native.ctypes.byref(hdr_c), d_arch.data_ptr(), d_arch.numel(),
+                                                text.data_ptr(), out.data_ptr(), out.numel() * cb, cb,
+                                                status.data_ptr(), native.ctypes.c_void_p(stream.cuda_stream)))
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        rows.append({"workload": name, "text_bytes": n, "encoding": f"{kind}-{8 * cb}bit",
+                     "column_bytes": (n + 1) * cb, "archive_bytes": int(arch.size),
+                     "ratio": round((n + 1) * cb / arch.size, 3),
+                     "exceptions_per_column": round(hdr["n_exceptions"] / (n + 1), 4),
+                     "table_rows": hdr["n_ids"], "encode_s": round(enc_s, 3),
+                     "rebuild_ms": round(ms, 4), "rebuild_GBps": round((n + 1) * cb / ms / 1e6, 1)})
+        del text, cols, got, out, d_arch
+        torch.cuda.empty_cache()
+    line = {"metric": "SLPF archive rebuild GB/s of columns (App. C, re_slpf_dfa_decode), log text",
+            "value": rows[0]["rebuild_GBps"], "unit": "GB/s", "n_gpus": world, "steps": max(args.steps, 5),
+            "warmup": 3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "config": {"workload": f"log, DNA and (a|b|ab)* texts of {n0} bytes, "
+                                                        "checkpoint every 4096 columns"}, "rows": rows}
     if rank == 0:
         print(json.dumps(line))
 

@@ -424,16 +424,17 @@ re_status re_state_bits(const re_handle *h, int32_t forward, uint32_t id, uint64
  * column differs, and a checkpoint column every `interval` positions so that
  * the rebuild runs in independent pieces (App. C's evenly spaced columns).
  * Columns are ids: DICT indices (re_dict_copy gives their segment sets), or
- * DENSE values; ids must be below 65536.
+ * DENSE values; ids must be below 65535, the interval at most 65536.
  *
  * Archive layout (little-endian, every section 16-byte aligned): the header;
- * table u32[n_ids][256] (row v, byte a: the column after the first (v, a),
- * 0xFFFFFFFF if the pair never occurs); checkpoints u32[n_checkpoints]
- * (C_0, C_K, C_2K, ...); exception positions u64[n_exceptions], ascending;
- * exception ids u32[n_exceptions].                                          */
+ * table u16[n_ids][256] (row v, byte a: the column after the first (v, a),
+ * 0xFFFF if the pair never occurs); checkpoints u16[n_checkpoints] (C_0, C_K,
+ * C_2K, ...); per piece the index of its first exception, u64[n_checkpoints
+ * + 1]; exceptions u32[n_exceptions], ascending, each (offset of the column
+ * in its piece) << 16 | id, none at a checkpoint column.                    */
 typedef struct {
     uint32_t magic;           /* 0x46504C53 */
-    uint32_t version;         /* 1 */
+    uint32_t version;         /* 2 */
     uint64_t n;               /* text length: columns 0 .. n */
     uint32_t n_ids;           /* table rows: ids 0 .. n_ids - 1 */
     uint32_t interval;        /* K: a checkpoint every K columns */

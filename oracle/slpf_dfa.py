@@ -12,11 +12,11 @@ archive exact with an exception list:
 
 * the table maps each key (column id of C_{r-1}, byte x_r) to the column
   that follows the key's first occurrence (r smallest);
-* every position r whose column differs from the table's value is an
-  exception (r, id of C_r);
 * every K-th column (r = 0, K, 2K, ...) is stored as a checkpoint, so the
   columns can be rebuilt in independent pieces ("a selection of evenly spaced
-  columns stored together with the SLPF-DFA", the improvement App. C names).
+  columns stored together with the SLPF-DFA", the improvement App. C names);
+* every other position r whose column differs from the table's value is an
+  exception (r, id of C_r).
 
 Columns are given as ids (any integer labelling of the distinct columns, e.g.
 the DICT encoding or ``serial.parse_ids``).
@@ -38,7 +38,7 @@ def encode(ids, text: bytes, K: int):
         key = (ids[r - 1], text[r - 1])
         if key not in table:
             table[key] = ids[r]
-        elif table[key] != ids[r]:
+        elif table[key] != ids[r] and r % K:
             exceptions.append((r, ids[r]))
     checkpoints = [ids[r] for r in range(0, n + 1, K)]
     return table, exceptions, checkpoints

@@ -75,17 +75,23 @@ def _native():
 
 
 def _parse_archive(native, arch, cb):
+    """Sections of an archive as the header of slpf_parser.h lays them out;
+    exceptions come back as absolute positions and ids."""
     h = native.slpf_dfa_header(arch)
     hdr = ctypes.sizeof(native.DfaHeader)
     al = lambda v: (v + 15) & ~15
     off_t = al(hdr)
-    off_c = off_t + al(h["n_ids"] * 256 * 4)
-    off_p = off_c + al(h["n_checkpoints"] * 4)
-    off_i = off_p + al(h["n_exceptions"] * 8)
-    table = arch[off_t:off_t + h["n_ids"] * 1024].view(np.uint32).reshape(h["n_ids"], 256)
-    cps = arch[off_c:off_c + h["n_checkpoints"] * 4].view(np.uint32)
-    pos = arch[off_p:off_p + h["n_exceptions"] * 8].view(np.uint64)
-    ids = arch[off_i:off_i + h["n_exceptions"] * 4].view(np.uint32)
+    off_c = off_t + al(h["n_ids"] * 256 * 2)
+    off_s = off_c + al(h["n_checkpoints"] * 2)
+    off_e = off_s + al((h["n_checkpoints"] + 1) * 8)
+    table = arch[off_t:off_t + h["n_ids"] * 512].view(np.uint16).reshape(h["n_ids"], 256)
+    cps = arch[off_c:off_c + h["n_checkpoints"] * 2].view(np.uint16)
+    starts = arch[off_s:off_s + (h["n_checkpoints"] + 1) * 8].view(np.uint64)
+    exc = arch[off_e:off_e + h["n_exceptions"] * 4].view(np.uint32)
+    assert starts[0] == 0 and starts[-1] == h["n_exceptions"] and np.all(np.diff(starts.astype(np.int64)) >= 0)
+    piece = np.repeat(np.arange(h["n_checkpoints"], dtype=np.uint64), np.diff(starts.astype(np.int64)))
+    pos = piece * np.uint64(h["interval"]) + (exc >> 16).astype(np.uint64)
+    ids = exc & 0xFFFF
     return h, table, cps, pos, ids
 
 
@@ -102,7 +108,7 @@ def test_native_encoder_equals_the_oracle(k, K):
     otable, oexc, ocps = SD.encode(ids, text, K)
     assert h["magic"] == 0x46504C53 and h["n"] == len(text) and h["interval"] == K
     assert h["n_ids"] == int(ids.max()) + 1
-    want = np.full((h["n_ids"], 256), 0xFFFFFFFF, dtype=np.uint32)
+    want = np.full((h["n_ids"], 256), 0xFFFF, dtype=np.uint16)
     for (v, a), w in otable.items():
         want[v, a] = w
     assert np.array_equal(table, want)
@@ -117,4 +123,6 @@ def test_native_encoder_errors():
     with pytest.raises(ValueError):
         native.slpf_dfa_encode(np.zeros(2, dtype=np.uint8), b"ab", 4)       # one column short
     with pytest.raises(native.ReError):
-        native.slpf_dfa_encode(np.full(3, 70000, dtype=np.uint32), b"ab", 4)  # ids past 65535
+        native.slpf_dfa_encode(np.full(3, 70000, dtype=np.uint32), b"ab", 4)  # ids past 65534
+    with pytest.raises(native.ReError):
+        native.slpf_dfa_encode(np.zeros(3, dtype=np.uint8), b"ab", 70000)    # interval past 65536
