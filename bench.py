@@ -186,14 +186,18 @@ def lsu_roofline(phase_ms: dict, n: int, device: int, ncls: int, shape: int):
             "peak_source": "SM count x 32 lanes x 2070 MHz (one conflict-free wavefront per SM and cycle)"}
 
 
+# The sources of the kernels whose DRAM traffic profiles/traffic.json records
+# (reach, fix-up, build & merge) and of the structures they share.
+KERNEL_SOURCES = ("kernels.cuh", "re_internal.h", "reach_impl.cuh", "reach_byte8.cu", "merge.cu")
+
+
 def csrc_hash() -> str:
-    """SHA-256 over every CUDA source of the library, in name order."""
+    """SHA-256 over the sources of the profiled kernels, in name order."""
     d = os.path.join(ROOT, "paper_2503_06763_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(f.encode())
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in sorted(KERNEL_SOURCES):
+        h.update(f.encode())
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()
 
 
