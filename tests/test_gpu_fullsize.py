@@ -11,6 +11,10 @@ benchmark uses (automatic chunk length, AUTO encoding).
   of 48 sampled texts up to 256 KiB and of 6 texts of 1-4 MiB against the
   oracle.
 """
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -29,6 +33,19 @@ def lib():
     __graft_entry__.build()
     from paper_2503_06763_gb300 import Batch, Regex, ReError
     return Batch, Regex, ReError
+
+
+def golden_sha(name):
+    """The oracle's SHA-256 of a benchmark text's canonical SLPF bytes
+    (tests/golden/make_slpf_sha256.py)."""
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "slpf_sha256.json")) as f:
+        return json.load(f)[name]
+
+
+def assert_sha(cols, kind, name):
+    g = golden_sha(name)
+    assert kind == g["encoding"] and cols.dtype.itemsize == g["col_bytes"]
+    assert hashlib.sha256(np.ascontiguousarray(cols).tobytes()).hexdigest() == g["sha256"], name
 
 
 def gpu_parse(rx, host):
@@ -57,6 +74,7 @@ def test_ab_1mib(lib):
     want = serial.parse(compile_re(W.AB_RE), host)
     assert st == 0 and kind == "dense"
     assert_columns_equal(rx, cols, kind, want)
+    assert_sha(cols, kind, "ab_1MiB_seed0")
 
 
 def test_dna_256mib_every_column(lib):
@@ -67,6 +85,7 @@ def test_dna_256mib_every_column(lib):
     want = serial.parse(compile_re(W.DNA_RE), host)
     assert st == (0 if serial.accepted(want) else 1) == 0
     assert_columns_equal(rx, cols, kind, want)
+    assert_sha(cols, kind, "dna_256MiB_seed1")
 
 
 def assert_interned_equal(rx, cols, kind, ids, table):
@@ -101,6 +120,7 @@ def test_log_1gib_every_column(lib):
     accepted = bool(table[ids[0]].any())
     assert st == (0 if accepted else 1) == 0
     assert_interned_equal(rx, cols, kind, ids, table)
+    assert_sha(cols, kind, "log_1GiB_seed2")
 
 
 def test_batch_4096_texts_sampled(lib):
