@@ -90,3 +90,37 @@ def test_wait_errors_and_timeout(native):
         assert srv.result(t)[1] == 0
     finally:
         srv.close()
+
+
+def test_concurrent_submitters(native):
+    """Four host threads submit at once (re_server_submit is thread-safe);
+    every request still equals its parse alone."""
+    import threading
+    rxs = [native.Regex(W.LOG_RE), native.Regex(W.AB_RE)]
+    srv = native.NativeServer(rxs, slots=4, arena_bytes=128 << 20)
+    texts = [(j % 2, (W.log_text if j % 2 == 0 else W.ab_text)(1000 + 997 * j, seed=100 + j)) for j in range(64)]
+    tickets = [None] * len(texts)
+    errors = []
+
+    def submit(lo):
+        try:
+            for j in range(lo, len(texts), 4):
+                tickets[j] = srv.submit(texts[j][0], texts[j][1])
+        except Exception as e:                           # surfaced below
+            errors.append(e)
+
+    threads = [threading.Thread(target=submit, args=(lo,)) for lo in range(4)]
+    try:
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        assert not errors
+        assert len(set(tickets)) == len(texts)
+        for (ri, host), t in zip(texts, tickets):
+            srv.wait(t, 60_000)
+            cols, st = srv.result(t)
+            want, wst = _alone(rxs[ri], host)
+            assert st == wst and np.array_equal(cols.view(np.uint8), want.view(np.uint8)), (ri, len(host))
+    finally:
+        srv.close()
