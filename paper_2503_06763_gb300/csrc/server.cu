@@ -325,7 +325,10 @@ void worker_loop(re_server *S) {
             S->stats[2] = std::max<uint64_t>(S->stats[2], s.reqs.size());
             S->stats[3] = std::max<uint64_t>(S->stats[3], busy);
             lk.unlock();
-            if (!launch(S, s)) retire(S, s, false, tickets);
+            if (!launch(S, s)) {                                // refused: let what it enqueued finish first
+                cudaStreamSynchronize(s.stream);
+                retire(S, s, false, tickets);
+            }
             lk.lock();
             idle = false;
         }
