@@ -248,9 +248,12 @@ re_status re_parse(re_handle *h, const uint8_t *d_text, uint64_t len, re_stream 
  *
  * Use: re_batch_plan (host only; sizes, chunk lengths, a pinned descriptor
  * buffer) -> re_batch_workspace_size -> re_parse_batch (binds text, output
- * and workspace pointers, uploads the descriptors, enqueues the kernels) ->
- * re_batch_run to parse the same bound buffers again (kernels only, nothing
- * copied) -> re_batch_free.                                                 */
+ * and workspace pointers, encodes each text's tensor maps, uploads the
+ * descriptors, enqueues the kernels) -> re_batch_run to parse the same bound
+ * buffers again (kernels only, nothing copied) -> re_batch_free.
+ * A batch of 64 MiB or more under several REs runs its groups on up to four
+ * streams of its own, forked from and joined back into the caller's stream
+ * by events (a CUDA graph capture of the call captures them too).           */
 typedef struct re_batch re_batch;       /* opaque: a planned batch */
 
 /* Plan count texts: text j has lens[j] bytes and is parsed under hs[j] (all
