@@ -188,7 +188,7 @@ def lsu_roofline(phase_ms: dict, n: int, device: int, ncls: int, shape: int):
 
 # The sources of the kernels whose DRAM traffic profiles/traffic.json records
 # (reach, fix-up, build & merge) and of the structures they share.
-KERNEL_SOURCES = ("kernels.cuh", "re_internal.h", "reach_impl.cuh", "reach_byte8.cu", "merge.cu")
+KERNEL_SOURCES = ("kernels.cuh", "re_internal.h", "reach_impl.cuh", "reach_byte8.cu", "reach_ascii.cu", "merge.cu")
 
 
 def csrc_hash() -> str:

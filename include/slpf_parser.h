@@ -196,6 +196,9 @@ typedef struct {
     uint64_t dict_size;       /* distinct non-empty columns C = B ∩ B̂ (0 = no dictionary) */
     uint32_t inf_ambiguous;   /* 1 when the RE is infinitely ambiguous (its SLPFs are samples) */
     uint32_t sample_limit;    /* the compile option's sample_limit */
+    uint32_t ascii_rows;      /* 1 when every byte class holding a byte >= 128 also holds one
+                                 below 128: the byte-table reach then stages table rows of the
+                                 128 bytes below 128 only and folds the others onto them */
 } re_info;
 
 /* Compile a pattern (Sect. 2.1 syntax plus App. A character features:

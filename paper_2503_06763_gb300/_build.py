@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libslpf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 HOST_SOURCES = ["re_compile.cpp"]
-CUDA_SOURCES = ["api.cu", "reach_pair.cu", "reach_smem.cu", "reach_smem8.cu", "reach_byte8.cu", "reach_global.cu", "join.cu", "merge.cu", "matches.cu", "noalloc.cu", "slpf_dfa.cu", "server.cu"]
+CUDA_SOURCES = ["api.cu", "reach_pair.cu", "reach_smem.cu", "reach_smem8.cu", "reach_byte8.cu", "reach_ascii.cu", "reach_global.cu", "join.cu", "merge.cu", "matches.cu", "noalloc.cu", "slpf_dfa.cu", "server.cu"]
 
 
 def _cuda_home() -> str:

@@ -321,6 +321,7 @@ re_status re_compile(const char *pattern, size_t len, const re_compile_opts *opt
     const size_t i_fso = add(C.fSlotOf.data(), C.fSlotOf.size());
     const size_t i_bso = add(C.bSlotOf.data(), C.bSlotOf.size());
     const size_t i_fby = add(C.fbyte.data(), C.fbyte.size()), i_bby = add(C.bbyte.data(), C.bbyte.size());
+    const size_t i_hr = add(C.hirep.data(), C.hirep.size());
     DevTables &t = h->dev;
     t.fHashMask = C.fHashMask; t.bHashMask = C.bHashMask;
     t.ncls = C.ncls; t.W = C.W; t.ell = C.ell;
@@ -354,6 +355,7 @@ re_status re_compile(const char *pattern, size_t len, const re_compile_opts *opt
     t.folseg = (const uint64_t *)(b + pc[i_fs].off);
     t.fbyte = C.fbyte.empty() ? nullptr : b + pc[i_fby].off;
     t.bbyte = C.bbyte.empty() ? nullptr : b + pc[i_bby].off;
+    t.hirep = C.hirep.empty() ? nullptr : b + pc[i_hr].off;
     t.dict = C.dict.empty() ? nullptr : (const uint64_t *)(b + pc[i_dc].off);
     *out = h;
     return RE_OK;
@@ -376,6 +378,7 @@ re_status re_get_info(const re_handle *h, re_info *info) {
     info->dict_size = C.has_dict ? C.dict_size : 0;
     info->inf_ambiguous = C.inf_amb ? 1u : 0u;
     info->sample_limit = C.sample_limit;
+    info->ascii_rows = C.hirep.empty() ? 0u : 1u;
     return RE_OK;
 }
 

@@ -213,11 +213,17 @@ __device__ inline void empty_text(const Params &p) {
 //              rows of kByteRow bytes (256 entries and 4 of padding, which
 //              puts equal bytes of different states in different banks); a
 //              reach block stages one direction's table (about 65 KB).
+//   TM_BYTE7:  the same with rows of the bytes below 128 only (kAsciiRow
+//              bytes: 128 entries and 4 of padding, so entry (s, b) sits in
+//              bank (s + b / 4) mod 32 as in TM_BYTE8); the walk first
+//              replaces every byte >= 128 by a byte below 128 of its class
+//              (DevTables::hirep), which every class holding one has.
 // Row s, column = byte class (or class pair c1*ncls + c2 for the left and
 // right byte of the pair).  A forward pair consumes c1 then c2, a backward
 // pair c2 then c1.
-enum { TM_GLOBAL = 0, TM_SMEM = 1, TM_PAIR = 2, TM_SMEM8 = 3, TM_BYTE8 = 4 };
+enum { TM_GLOBAL = 0, TM_SMEM = 1, TM_PAIR = 2, TM_SMEM8 = 3, TM_BYTE8 = 4, TM_BYTE7 = 5 };
 constexpr uint32_t kByteRow = 260;
+constexpr uint32_t kAsciiRow = 132;
 
 struct Tabs {
     const uint8_t *cls;
@@ -227,6 +233,7 @@ struct Tabs {
     const uint32_t *f2, *b2;
     uint32_t ncls, nc2;
     uint32_t rowb, nf, magic;       // reach in pair mode: run-state encoding (see reach_impl.cuh)
+    const uint8_t *rep;             // TM_BYTE7: [128] representative of byte b + 128 (shared memory)
 };
 
 template <int TM>
@@ -234,6 +241,7 @@ __device__ __forceinline__ uint32_t fnext(const Tabs &T, uint32_t s, uint32_t c)
     if (TM == TM_SMEM) return T.f16[s * T.ncls + c];
     if (TM == TM_SMEM8) return T.f8[s * T.ncls + c];
     if (TM == TM_BYTE8) return T.f8[s * kByteRow + c];          // c is the byte itself
+    if (TM == TM_BYTE7) return T.f8[s * kAsciiRow + c];         // c is the byte, folded below 128
     if (TM == TM_PAIR) return T.f2[s * T.nc2 + c * T.ncls] & 0xFFFFu;
     return __ldg(T.f32 + (size_t)s * T.ncls + c);
 }
@@ -242,6 +250,7 @@ __device__ __forceinline__ uint32_t bnext(const Tabs &T, uint32_t s, uint32_t c)
     if (TM == TM_SMEM) return T.b16[s * T.ncls + c];
     if (TM == TM_SMEM8) return T.b8[s * T.ncls + c];
     if (TM == TM_BYTE8) return T.b8[s * kByteRow + c];
+    if (TM == TM_BYTE7) return T.b8[s * kAsciiRow + c];
     if (TM == TM_PAIR) return T.b2[s * T.nc2 + c] & 0xFFFFu;
     return __ldg(T.b32 + (size_t)s * T.ncls + c);
 }
@@ -250,20 +259,35 @@ __device__ __forceinline__ uint32_t bpair(const Tabs &T, uint32_t s, uint32_t cp
 
 template <int TM>
 __device__ __forceinline__ uint32_t clsof(const Tabs &T, uint32_t b) {
-    if (TM == TM_BYTE8) return b;                               // the tables are indexed by the byte
+    if (TM == TM_BYTE8 || TM == TM_BYTE7) return b;             // the tables are indexed by the byte
     if (TM != TM_GLOBAL) return T.cls[b];
     return __ldg(T.cls + b);
 }
 // The byte class itself (slot selection), in every table mode.
 template <int TM>
 __device__ __forceinline__ uint32_t class_of(const Tabs &T, const DevTables &t, uint32_t b) {
-    if (TM == TM_BYTE8) return __ldg(t.cls + b);
+    if (TM == TM_BYTE8 || TM == TM_BYTE7) return __ldg(t.cls + b);
     return clsof<TM>(T, b);
+}
+
+// TM_BYTE7: bytes >= 128 of a word replaced by their representatives below
+// 128 (one shared-memory lookup per such byte; none for ASCII text).
+__device__ __forceinline__ uint32_t fold_word(const uint8_t *rep, uint32_t w) {
+    for (uint32_t hi = w & 0x80808080u; hi; hi &= hi - 1) {
+        const uint32_t sh = (uint32_t)__ffs(hi) - 8;             // the byte's lowest bit
+        w = (w & ~(0xFFu << sh)) | ((uint32_t)rep[(w >> sh) & 0x7Fu] << sh);
+    }
+    return w;
+}
+__device__ __forceinline__ uint4 fold_high_bytes(const uint8_t *rep, uint4 x) {
+    if (((x.x | x.y | x.z | x.w) & 0x80808080u) == 0) return x;
+    return make_uint4(fold_word(rep, x.x), fold_word(rep, x.y), fold_word(rep, x.z), fold_word(rep, x.w));
 }
 
 // Stage the byte-indexed tables of the directions asked for (block-wide;
 // ends with __syncthreads).  Returns the end of the used area.
-__device__ inline uint8_t *stage_byte8(const DevTables &t, uint8_t *sm, Tabs &T, bool fwd, bool bwd) {
+__device__ inline uint8_t *stage_byte8(const DevTables &t, uint8_t *sm, Tabs &T, bool fwd, bool bwd,
+                                       bool ascii = false) {
     T.ncls = t.ncls;
     T.nc2 = t.ncls * t.ncls;
     T.cls = t.cls;
@@ -278,18 +302,31 @@ __device__ inline uint8_t *stage_byte8(const DevTables &t, uint8_t *sm, Tabs &T,
         const uint8_t *src = d == 0 ? t.fbyte : t.bbyte;
         const uint32_t n = d == 0 ? t.nf : t.nb;
         uint32_t *dst = reinterpret_cast<uint32_t *>(at);
-        // row s: 64 words of entries, then one word of padding
-        for (uint32_t q = threadIdx.x; q < n * 64; q += blockDim.x)
-            dst[(q >> 6) * (kByteRow / 4) + (q & 63)] = __ldg(reinterpret_cast<const uint32_t *>(src) + q);
+        const uint32_t *src32 = reinterpret_cast<const uint32_t *>(src);
+        if (ascii) {   // row s: the 32 words of bytes 0..127, then one word of padding
+            for (uint32_t q = threadIdx.x; q < n * 32; q += blockDim.x)
+                dst[(q >> 5) * (kAsciiRow / 4) + (q & 31)] = __ldg(src32 + (q >> 5) * 64 + (q & 31));
+        } else {       // row s: 64 words of entries, then one word of padding
+            for (uint32_t q = threadIdx.x; q < n * 64; q += blockDim.x)
+                dst[(q >> 6) * (kByteRow / 4) + (q & 63)] = __ldg(src32 + q);
+        }
         (d == 0 ? T.f8 : T.b8) = at;
-        at += (((size_t)n * kByteRow) + 15) & ~(size_t)15;
+        at += (((size_t)n * (ascii ? kAsciiRow : kByteRow)) + 15) & ~(size_t)15;
+    }
+    T.rep = nullptr;
+    if (ascii) {
+        for (uint32_t q = threadIdx.x; q < 32; q += blockDim.x)
+            reinterpret_cast<uint32_t *>(at)[q] = __ldg(reinterpret_cast<const uint32_t *>(t.hirep) + q);
+        T.rep = at;
+        at += 128;
     }
     __syncthreads();
     return at;
 }
-__host__ __device__ inline size_t byte8_smem_bytes(const DevTables &t, bool fwd, bool bwd) {
-    return (fwd ? (((size_t)t.nf * kByteRow) + 15) & ~(size_t)15 : 0) +
-           (bwd ? (((size_t)t.nb * kByteRow) + 15) & ~(size_t)15 : 0);
+__host__ __device__ inline size_t byte8_smem_bytes(const DevTables &t, bool fwd, bool bwd, bool ascii = false) {
+    const size_t row = ascii ? kAsciiRow : kByteRow;
+    return (fwd ? (((size_t)t.nf * row) + 15) & ~(size_t)15 : 0) +
+           (bwd ? (((size_t)t.nb * row) + 15) & ~(size_t)15 : 0) + (ascii ? 128 : 0);
 }
 
 // Bytes of shared memory used by stage_tables.

@@ -875,6 +875,22 @@ re_status compile_pattern(const char *pattern, size_t len, const re_compile_opts
         for (uint32_t st = 0; st < C.nb; ++st)
             for (uint32_t b = 0; b < 256; ++b) C.bbyte[(size_t)st * 256 + b] = (uint8_t)C.bT[(size_t)st * ncls + C.cls[b]];
     }
+    // ---- bytes 128..255 folded onto bytes below 128 of the same class: when
+    // every class holding a byte >= 128 also holds one below, the byte-indexed
+    // rows need only their first 128 entries (half the shared memory, so a
+    // reach block holds more warps), and a byte >= 128 is replaced by the
+    // smallest byte of its class before the lookup.
+    C.hirep.clear();
+    if (!C.fbyte.empty()) {
+        int rep[256];
+        for (int &r : rep) r = -1;
+        for (int b = 127; b >= 0; --b) rep[C.cls[b]] = b;
+        C.hirep.resize(128);
+        for (int b = 128; b < 256; ++b) {
+            if (rep[C.cls[b]] < 0) { C.hirep.clear(); break; }
+            C.hirep[b - 128] = (uint8_t)rep[C.cls[b]];
+        }
+    }
     C.fHash = build_device_hash(C.fBits, C.nf, W, C.fHashMask);
     C.bHash = build_device_hash(C.bBits, C.nb, W, C.bHashMask);
     return RE_OK;

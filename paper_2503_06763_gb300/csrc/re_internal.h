@@ -55,6 +55,8 @@ struct DevTables {
                                  // parse never produces hold 0xFFFFFFFF
     const uint32_t *f2, *b2;     // [n][ncls^2] two-byte tables (mid | end << 16), or null
     const uint8_t *fbyte, *bbyte;  // [n][256] next state by byte (not class), u8; null unless n <= 256
+    const uint8_t *hirep;        // [128] byte b + 128 -> a byte below 128 of its class; null unless
+                                 // every class holding a byte >= 128 holds one below (and fbyte is set)
     uint32_t fHashMask, bHashMask;
     uint32_t ncls, W, ell;
     uint32_t nf, nb, nfd, nbd;   // states incl. empty row 0; nfd/nbd = classic DFA states
@@ -74,6 +76,7 @@ struct Compiled {
     std::vector<uint32_t> fT, bT;             // [n][ncls]
     std::vector<uint32_t> f2, b2;             // [n][ncls^2] two-byte tables (empty when too large)
     std::vector<uint8_t> fbyte, bbyte;        // [n][256] next state by byte (empty unless n <= 256)
+    std::vector<uint8_t> hirep;               // [128] representative below 128 of byte b + 128 (or empty)
     std::vector<uint64_t> fBits, bBits;       // [n][W]
     std::vector<uint32_t> fHash, bHash;
     uint32_t fHashMask = 0, bHashMask = 0;

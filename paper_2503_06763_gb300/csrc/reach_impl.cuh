@@ -139,10 +139,14 @@ __device__ __forceinline__ void walk_block(const Params &p, const Tabs &T, const
     const uint32_t swz = ((threadIdx.x & 31) >> 1) & 3;
 #pragma unroll 1
     for (int q = 0; q < 4; ++q) {
-        const uint4 fx = FW ? *reinterpret_cast<const uint4 *>(frow + (((uint32_t)q ^ swz) << 4))
-                            : make_uint4(0, 0, 0, 0);
-        const uint4 bx = bwd ? *reinterpret_cast<const uint4 *>(brow + (((uint32_t)(3 - q) ^ swz) << 4))
-                             : make_uint4(0, 0, 0, 0);
+        uint4 fx = FW ? *reinterpret_cast<const uint4 *>(frow + (((uint32_t)q ^ swz) << 4))
+                      : make_uint4(0, 0, 0, 0);
+        uint4 bx = bwd ? *reinterpret_cast<const uint4 *>(brow + (((uint32_t)(3 - q) ^ swz) << 4))
+                       : make_uint4(0, 0, 0, 0);
+        if (TM == TM_BYTE7) {                         // rows hold bytes below 128 only
+            if (FW) fx = fold_high_bytes(T.rep, fx);
+            if (bwd) bx = fold_high_bytes(T.rep, bx);
+        }
         if (TM == TM_PAIR && !EDGE) {                 // two bytes per table lookup (run states are row offsets)
             extern __shared__ __align__(16) uint8_t sm[];
             const uint32_t fw[4] = {fx.x, fx.y, fx.z, fx.w}, bw[4] = {bx.x, bx.y, bx.z, bx.w};
@@ -305,7 +309,8 @@ __device__ __forceinline__ void walk_local(const Tabs &T, const uint8_t *row, ui
     const uint32_t swz = ((threadIdx.x & 31) >> 1) & 3;
     for (int u = 0; u < hi - lo; ++u) {
         const int t = FWD ? lo + u : hi - 1 - u;
-        const uint32_t b = row[((((uint32_t)t >> 4) ^ swz) << 4) | ((uint32_t)t & 15)];
+        uint32_t b = row[((((uint32_t)t >> 4) ^ swz) << 4) | ((uint32_t)t & 15)];
+        if (TM == TM_BYTE7 && b >= 128) b = T.rep[b - 128];
         const uint32_t c = clsof<T1>(T, b);
         for (uint32_t j = 0; j < m; ++j) s[j] = FWD ? fnext<T1>(T, s[j], c) : bnext<T1>(T, s[j], c);
         compact_local(s, mk, m);
@@ -666,31 +671,51 @@ __global__ void __launch_bounds__(kSplitThreads, (SPLIT && MS <= 8) ? 3 : 1)
     if (MAT && lane == 0) bulk_wait_all();                    // state rows written before the grid ends
 }
 
-// One parse with byte-indexed tables (TM_BYTE8): every warp of a block walks
+// One parse with byte-indexed tables (TM_BYTE8, or TM_BYTE7 when the bytes
+// >= 128 fold onto ASCII bytes of their class): every warp of a block walks
 // the same direction, so a block stages one direction's table (about 65 KB
-// for 251 states) instead of both.  Even blocks walk 32-chunk tiles forward,
-// odd blocks backward (every block forward in recognizer mode); 24 warps per
-// block, 2-stage TMA rings, and (MAT) one state tile per warp, whose store
-// has read it before the next block's states go in: a warp's lookups wait on
-// shared-memory latency, so the smaller footprint buys warps to hide it.
-// Tiles are dealt round-robin over the blocks of a direction (tile t to
-// block t mod B), so a text of few tiles still spreads over every SM.
+// for 251 states; half that with ASCII rows) instead of both.  Even blocks
+// walk 32-chunk tiles forward, odd blocks backward (every block forward in
+// recognizer mode); 2-stage TMA rings, and (MAT) one state tile per warp,
+// whose store has read it before the next block's states go in.  A warp's
+// lookups wait on shared-memory latency, so the block takes as many warps as
+// the shared memory left by its table holds (24 with full rows; up to 32
+// with ASCII rows, whose kernel is compiled for 1024 threads).  Tiles are
+// dealt round-robin over the blocks of a direction (tile t to block t mod
+// B), so a text of few tiles still spreads over every SM.
 constexpr uint32_t kDirThreads = 768;
+constexpr uint32_t kDirThreadsAscii = 1024;
 constexpr uint32_t kDirStages = 2;
 constexpr uint32_t kDirOut = 1;             // MAT state tiles per warp
 // Shared memory after the table: [1024-byte pad][text tiles, kDirStages per
 // warp][state tiles, kDirOut per warp][mbarriers, kDirStages per warp]; the
 // tiles are 1024-byte multiples, so one pad aligns them all.
+template <bool ASC> constexpr uint32_t dir_threads_max() { return ASC ? kDirThreadsAscii : kDirThreads; }
 
-template <int MS, bool WIDE, bool MAT>
-__global__ void __launch_bounds__(kDirThreads, 1)
+inline size_t dir_table_smem(const DevTables &t, bool asc) {
+    return std::max(byte8_smem_bytes(t, true, false, asc), byte8_smem_bytes(t, false, true, asc));
+}
+inline size_t dir_warp_smem(bool mat) { return (kDirStages + (mat ? kDirOut : 0)) * kTileBytes + kDirStages * 8; }
+// Warps per block: as many as the shared memory holds, at most the kernel's bound.
+inline uint32_t dir_wpb(const DevTables &t, bool mat, bool asc) {
+    const size_t cap = asc ? kDirThreadsAscii / 32 : kDirThreads / 32;
+    const size_t avail = 227 * 1024 - dir_table_smem(t, asc) - 1024;
+    return (uint32_t)std::max<size_t>(1, std::min(cap, avail / dir_warp_smem(mat)));
+}
+inline size_t reach_dir_smem(const DevTables &t, bool mat, bool asc) {
+    return dir_table_smem(t, asc) + 1024 + dir_wpb(t, mat, asc) * dir_warp_smem(mat);
+}
+
+template <int MS, bool WIDE, bool MAT, bool ASC>
+__global__ void __launch_bounds__(dir_threads_max<ASC>(), 1)
     reach_dir_kernel(const __grid_constant__ Params p, const __grid_constant__ CUtensorMap map,
                      const __grid_constant__ StateMaps smaps) {
+    constexpr int TM = ASC ? TM_BYTE7 : TM_BYTE8;
     extern __shared__ __align__(16) uint8_t sm[];
     const bool pairs = !p.recognize;
     const bool backward_block = pairs && (blockIdx.x & 1);
     Tabs T;
-    uint8_t *rest = stage_byte8(p.t, sm, T, !backward_block, backward_block);
+    uint8_t *rest = stage_byte8(p.t, sm, T, !backward_block, backward_block, ASC);
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x / 32;
     uint8_t *otile = nullptr;
     Ring ring{};
@@ -718,8 +743,8 @@ __global__ void __launch_bounds__(kDirThreads, 1)
         const bool tma = p.text_tma && t * 32 + 32 <= p.c_full;
         if (i >= p.c) continue;                               // lanes past the text (plain path only)
         const bool ok = backward_block
-                            ? reach_chunk<TM_BYTE8, MS, DIR_B, WIDE, MAT>(p, T, i, &map, ring, tma, &smaps.b, otile)
-                            : reach_chunk<TM_BYTE8, MS, DIR_F, WIDE, MAT>(p, T, i, &map, ring, tma, &smaps.f, otile);
+                            ? reach_chunk<TM, MS, DIR_B, WIDE, MAT>(p, T, i, &map, ring, tma, &smaps.b, otile)
+                            : reach_chunk<TM, MS, DIR_F, WIDE, MAT>(p, T, i, &map, ring, tma, &smaps.f, otile);
         if (!ok) {
             atomicExch(p.status, RE_E_INTERNAL);
             atomicExch(&p.w.flags[FLAG_INTERNAL], 1);
@@ -735,49 +760,45 @@ __global__ void __launch_bounds__(kDirThreads, 1)
     if (MAT && lane == 0) bulk_wait_all();
 }
 
-inline size_t reach_dir_smem(const DevTables &t, bool mat) {
-    const size_t tab = std::max(byte8_smem_bytes(t, true, false), byte8_smem_bytes(t, false, true));
-    const size_t wpb = kDirThreads / 32;
-    return tab + 1024 + wpb * ((kDirStages + (mat ? kDirOut : 0)) * kTileBytes + kDirStages * 8);
-}
-
 // Blocks per direction: every resident block slot, split between the
 // directions, but no more blocks per direction than tiles (tiles go
 // round-robin over blocks).
-template <int MS, bool WIDE, bool MAT>
+template <int MS, bool WIDE, bool MAT, bool ASC>
 uint64_t dir_blocks(const Params &p, int sm_count) {
-    const size_t smem = reach_dir_smem(p.t, MAT);
+    const size_t smem = reach_dir_smem(p.t, MAT, ASC);
     static uint64_t attr_done = 0;
-    allow_smem(reach_dir_kernel<MS, WIDE, MAT>, &attr_done, 227 * 1024);
+    allow_smem(reach_dir_kernel<MS, WIDE, MAT, ASC>, &attr_done, 227 * 1024);
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_dir_kernel<MS, WIDE, MAT>, kDirThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_dir_kernel<MS, WIDE, MAT, ASC>,
+                                                  dir_wpb(p.t, MAT, ASC) * 32, smem);
     const uint64_t tiles = ((uint64_t)p.c + 31) / 32;
     const uint64_t dirs = p.recognize ? 1 : 2;
     const uint64_t slots = (uint64_t)std::max(per_sm, 1) * sm_count;
     return std::max<uint64_t>(1, std::min<uint64_t>(tiles, slots / dirs));
 }
 
-template <int MS, bool WIDE, bool MAT>
+template <int MS, bool WIDE, bool MAT, bool ASC>
 void launch_dir(const Params &p, const CUtensorMap &map, const StateMaps &smaps, cudaStream_t s, int sm_count) {
-    const size_t smem = reach_dir_smem(p.t, MAT);
+    const size_t smem = reach_dir_smem(p.t, MAT, ASC);
     const uint64_t dirs = p.recognize ? 1 : 2;
-    const uint64_t per_dir = dir_blocks<MS, WIDE, MAT>(p, sm_count);
+    const uint64_t per_dir = dir_blocks<MS, WIDE, MAT, ASC>(p, sm_count);
     const uint64_t blocks = per_dir * dirs;                    // even: one block of each pair per direction
-    launch_dependent(reach_dir_kernel<MS, WIDE, MAT>, (uint32_t)std::max<uint64_t>(blocks, 1), kDirThreads, smem, s,
-                     p, map, smaps);
+    launch_dependent(reach_dir_kernel<MS, WIDE, MAT, ASC>, (uint32_t)std::max<uint64_t>(blocks, 1),
+                     dir_wpb(p.t, MAT, ASC) * 32, smem, s, p, map, smaps);
 }
 
 // A batch group (one RE) with byte-indexed tables and per-position states:
 // the single-text kernel's shape (blocks alternate directions, one table per
 // block) over the 32-chunk tiles of every text of the group, dealt
-// round-robin over the blocks; text and state rows move by plain loads and
-// stores (the texts have no tensor maps).
-template <int MS, bool WIDE>
-__global__ void __launch_bounds__(kDirThreads, 1) reach_dir_batch_kernel(const __grid_constant__ BatchGroup b) {
+// round-robin over the blocks; full tiles of texts with tensor maps move by
+// TMA, the rest by plain loads and stores.
+template <int MS, bool WIDE, bool ASC>
+__global__ void __launch_bounds__(dir_threads_max<ASC>(), 1) reach_dir_batch_kernel(const __grid_constant__ BatchGroup b) {
+    constexpr int TM = ASC ? TM_BYTE7 : TM_BYTE8;
     extern __shared__ __align__(16) uint8_t sm[];
     const bool backward_block = blockIdx.x & 1;
     Tabs T;
-    uint8_t *rest = stage_byte8(b.t, sm, T, !backward_block, backward_block);
+    uint8_t *rest = stage_byte8(b.t, sm, T, !backward_block, backward_block, ASC);
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x / 32;
     Ring ring{};
     ring.nst = kDirStages;
@@ -808,8 +829,8 @@ __global__ void __launch_bounds__(kDirThreads, 1) reach_dir_batch_kernel(const _
         if (tma) __syncwarp();
         if (i >= p.c) continue;                               // lanes past the text's last chunk (plain tiles only)
         const bool ok = backward_block
-                            ? reach_chunk<TM_BYTE8, MS, DIR_B, WIDE, true>(p, T, i, p.tmaps, ring, tma, p.tmaps + 2, otile)
-                            : reach_chunk<TM_BYTE8, MS, DIR_F, WIDE, true>(p, T, i, p.tmaps, ring, tma, p.tmaps + 1, otile);
+                            ? reach_chunk<TM, MS, DIR_B, WIDE, true>(p, T, i, p.tmaps, ring, tma, p.tmaps + 2, otile)
+                            : reach_chunk<TM, MS, DIR_F, WIDE, true>(p, T, i, p.tmaps, ring, tma, p.tmaps + 1, otile);
         if (!ok) {
             atomicExch(p.status, RE_E_INTERNAL);
             for (uint32_t st = 0; st < kDirStages; ++st) {   // drain: bounded wait on every stage
@@ -824,47 +845,49 @@ __global__ void __launch_bounds__(kDirThreads, 1) reach_dir_batch_kernel(const _
     if (lane == 0) bulk_wait_all();
 }
 
-template <int MS, bool WIDE>
+template <int MS, bool WIDE, bool ASC>
 void launch_dir_batch_one(const BatchGroup &b, cudaStream_t s, int sm_count) {
-    const size_t smem = reach_dir_smem(b.t, true);
+    const size_t smem = reach_dir_smem(b.t, true, ASC);
+    const uint32_t threads = dir_wpb(b.t, true, ASC) * 32;
     static uint64_t attr_done = 0;
-    allow_smem(reach_dir_batch_kernel<MS, WIDE>, &attr_done, 227 * 1024);
+    allow_smem(reach_dir_batch_kernel<MS, WIDE, ASC>, &attr_done, 227 * 1024);
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_dir_batch_kernel<MS, WIDE>, kDirThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reach_dir_batch_kernel<MS, WIDE, ASC>, threads, smem);
     const uint64_t slots = (uint64_t)std::max(per_sm, 1) * sm_count;
     const uint64_t per_dir = std::max<uint64_t>(1, std::min<uint64_t>(b.n_reach, slots / 2));
-    reach_dir_batch_kernel<MS, WIDE><<<(uint32_t)(per_dir * 2), kDirThreads, smem, s>>>(b);
+    reach_dir_batch_kernel<MS, WIDE, ASC><<<(uint32_t)(per_dir * 2), threads, smem, s>>>(b);
 }
 
-inline bool launch_dir_batch(const BatchGroup &b, uint32_t ms, cudaStream_t s, int sm_count) {
-    if (ms <= 2) launch_dir_batch_one<2, false>(b, s, sm_count);
-    else if (ms <= 4) launch_dir_batch_one<4, false>(b, s, sm_count);
-    else if (ms <= 8) launch_dir_batch_one<8, false>(b, s, sm_count);
-    else if (ms <= 32) launch_dir_batch_one<4, true>(b, s, sm_count);
+template <bool ASC>
+bool launch_dir_batch(const BatchGroup &b, uint32_t ms, cudaStream_t s, int sm_count) {
+    if (ms <= 2) launch_dir_batch_one<2, false, ASC>(b, s, sm_count);
+    else if (ms <= 4) launch_dir_batch_one<4, false, ASC>(b, s, sm_count);
+    else if (ms <= 8) launch_dir_batch_one<8, false, ASC>(b, s, sm_count);
+    else if (ms <= 32) launch_dir_batch_one<4, true, ASC>(b, s, sm_count);
     else return false;
     return true;
 }
 
 // Warps per direction the one-direction-per-block reach runs at most (every
-// resident block of a direction, kDirThreads / 32 warps each).
-template <bool MAT>
+// resident block of a direction, dir_wpb warps each).
+template <bool MAT, bool ASC>
 uint64_t dir_warps(const Params &p, uint32_t ms, int sm_count) {
     Params q = p;
     q.c = 0xFFFFFFFFu;                                         // as many tiles as block slots
-    const uint64_t b = ms <= 2 ? dir_blocks<2, false, MAT>(q, sm_count)
-                     : ms <= 4 ? dir_blocks<4, false, MAT>(q, sm_count)
-                     : ms <= 8 ? dir_blocks<8, false, MAT>(q, sm_count)
-                               : dir_blocks<4, true, MAT>(q, sm_count);
-    return b * (kDirThreads / 32);
+    const uint64_t b = ms <= 2 ? dir_blocks<2, false, MAT, ASC>(q, sm_count)
+                     : ms <= 4 ? dir_blocks<4, false, MAT, ASC>(q, sm_count)
+                     : ms <= 8 ? dir_blocks<8, false, MAT, ASC>(q, sm_count)
+                               : dir_blocks<4, true, MAT, ASC>(q, sm_count);
+    return b * dir_wpb(p.t, MAT, ASC);
 }
 
-template <bool MAT>
+template <bool MAT, bool ASC>
 bool launch_dir_ms(const Params &p, const CUtensorMap &map, const StateMaps &smaps, cudaStream_t s, uint32_t ms,
                    int sm_count) {
-    if (ms <= 2) launch_dir<2, false, MAT>(p, map, smaps, s, sm_count);
-    else if (ms <= 4) launch_dir<4, false, MAT>(p, map, smaps, s, sm_count);
-    else if (ms <= 8) launch_dir<8, false, MAT>(p, map, smaps, s, sm_count);
-    else if (ms <= 32) launch_dir<4, true, MAT>(p, map, smaps, s, sm_count);
+    if (ms <= 2) launch_dir<2, false, MAT, ASC>(p, map, smaps, s, sm_count);
+    else if (ms <= 4) launch_dir<4, false, MAT, ASC>(p, map, smaps, s, sm_count);
+    else if (ms <= 8) launch_dir<8, false, MAT, ASC>(p, map, smaps, s, sm_count);
+    else if (ms <= 32) launch_dir<4, true, MAT, ASC>(p, map, smaps, s, sm_count);
     else return false;
     return true;
 }

@@ -337,10 +337,33 @@ def test_dfa_starts_give_the_same_slpf(lib, pattern, which):
 
 
 # ---------------------------------------------------------------- reach shapes
+def _log_high_bytes(n, seed):
+    """Log records with 2 % of the bytes other than newlines replaced by bytes
+    >= 128 (the lines hit become malformed; [^\\n]* still takes them)."""
+    rng = np.random.default_rng(seed)
+    host = W.log_text(n, seed=seed).copy()
+    hit = (rng.random(host.size) < 0.02) & (host != ord("\n"))
+    host[hit] = rng.integers(128, 256, size=int(hit.sum()))
+    return host
+
+
+def _tokens(n, seed, toks):
+    rng = np.random.default_rng(seed)
+    parts = [toks[j] for j in rng.integers(0, len(toks), size=n)]
+    return np.frombuffer(b"".join(parts), dtype=np.uint8).copy()
+
+
 SHAPE_CASES = [("dna", W.DNA_RE, lambda: W.dna_text(200_003, seed=5, mean_gap=700)),
                ("ab", W.AB_RE, lambda: W.ab_text(100_001, seed=6)),
                ("log", W.LOG_RE, lambda: W.log_text(150_000, seed=7)),
-               ("aa", "(aa)*", lambda: np.full(70_000, ord("a"), dtype=np.uint8))]
+               ("aa", "(aa)*", lambda: np.full(70_000, ord("a"), dtype=np.uint8)),
+               # bytes >= 128 folded onto their class's ASCII byte before the byte-table lookups
+               ("log-high-bytes", W.LOG_RE, lambda: _log_high_bytes(150_000, seed=8)),
+               ("fold-many", r"([\x7f-\xff]a|b)*",
+                lambda: _tokens(40_000, 9, [bytes([v, 97]) for v in range(127, 256)] + [b"b"] * 40)),
+               # a class of high bytes alone: full 256-byte rows
+               ("high-class", r"([ab]|[\x80-\xff]c)*",
+                lambda: _tokens(40_000, 10, [b"a", b"b"] + [bytes([v, 99]) for v in range(128, 256, 7)]))]
 
 
 @pytest.mark.parametrize("shape", [1, 2, 3, 4])

@@ -66,6 +66,18 @@ def test_host_compile_matches_oracle_segments_and_dfa(native, pattern):
         assert set(sets) == inter
 
 
+def test_ascii_rows_when_high_bytes_share_a_class_with_ascii(native):
+    """The byte-table reach stages rows of the bytes below 128 only when
+    every class holding a byte >= 128 holds one below it too: true for the
+    benchmark REs (high bytes fall in the classes of [^\\n] or of no symbol),
+    false once a class is made of high bytes alone."""
+    import workloads as W
+    for pattern in (W.LOG_RE, W.DNA_RE, W.AB_RE, "[^a]*", r"([\x7f-\xff]a|b)*"):
+        assert native.Regex(pattern, host_only=True).info["ascii_rows"] == 1, pattern
+    for pattern in (r"([ab]|[\x80-\xff]c)*", r"[\x80-\xff]*", r"(\xffa|b)*"):
+        assert native.Regex(pattern, host_only=True).info["ascii_rows"] == 0, pattern
+
+
 def test_pair_layout_without_a_dictionary(native):
     """No dictionary and more than 64 segments: AUTO picks PAIRS (4 bytes per
     column while both automata have at most 65536 states); DICT is refused,
