@@ -149,8 +149,10 @@ typedef struct {
  * end states and the same SLPF).  re_autotune chooses one per handle and
  * length bucket together with the chunk length; RE_PARSE_REACH(v) in
  * re_parse_opts.flags forces one (tests, measurements):
- *   1: tables indexed by the byte itself, one direction per 16-warp block,
- *      2-stage TMA ring (automata of at most 256 states per direction);
+ *   1: tables indexed by the byte itself, one direction per block of 24
+ *      warps (32 when every class with a byte >= 128 has one below, so the
+ *      rows hold bytes 0..127 only), 2-stage TMA ring (automata of at most
+ *      256 states per direction);
  *   2: a warp per direction of each 32-chunk tile (two lanes per chunk),
  *      tables by byte class, 3-stage TMA ring;
  *   3: as 2 with a 2-stage ring;
@@ -199,6 +201,7 @@ typedef struct {
     uint32_t ascii_rows;      /* 1 when every byte class holding a byte >= 128 also holds one
                                  below 128: the byte-table reach then stages table rows of the
                                  128 bytes below 128 only and folds the others onto them */
+    uint32_t reach_shapes;    /* bit v set: reach shape v (RE_PARSE_REACH) runs for this automaton */
 } re_info;
 
 /* Compile a pattern (Sect. 2.1 syntax plus App. A character features:

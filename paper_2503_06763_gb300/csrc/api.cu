@@ -85,7 +85,7 @@ uint32_t tuned_shape(re_handle *h, uint64_t n, const re_parse_opts *opts) {
 // Reach shapes this handle can run (bit v: shape v of RE_PARSE_REACH).
 uint32_t shapes_of(const re_handle *h) {
     uint32_t m = (1u << 2) | (1u << 3) | (1u << 4);
-    if (h->dev.fbyte && h->dev.bbyte) m |= 1u << 1;
+    if (!h->host.fbyte.empty() && !h->host.bbyte.empty()) m |= 1u << 1;
     return m;
 }
 
@@ -379,6 +379,7 @@ re_status re_get_info(const re_handle *h, re_info *info) {
     info->inf_ambiguous = C.inf_amb ? 1u : 0u;
     info->sample_limit = C.sample_limit;
     info->ascii_rows = C.hirep.empty() ? 0u : 1u;
+    info->reach_shapes = shapes_of(h);
     return RE_OK;
 }
 

@@ -85,7 +85,8 @@ class Info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in (
         "n_segments", "n_positions", "n_classes", "words_per_col", "fwd_states", "fwd_dfa_states",
         "bwd_states", "bwd_dfa_states", "fwd_slots_max", "bwd_slots_max")] + [("dict_size", ctypes.c_uint64)] + [
-        ("inf_ambiguous", ctypes.c_uint32), ("sample_limit", ctypes.c_uint32), ("ascii_rows", ctypes.c_uint32)]
+        ("inf_ambiguous", ctypes.c_uint32), ("sample_limit", ctypes.c_uint32), ("ascii_rows", ctypes.c_uint32),
+        ("reach_shapes", ctypes.c_uint32)]
 
 
 _lib = None

@@ -78,6 +78,16 @@ def test_ascii_rows_when_high_bytes_share_a_class_with_ascii(native):
         assert native.Regex(pattern, host_only=True).info["ascii_rows"] == 0, pattern
 
 
+def test_reach_shapes_available(native):
+    """Shapes 2-4 run for every automaton; shape 1 needs byte tables, that is
+    at most 256 states per direction."""
+    import workloads as W
+    shapes = lambda p: native.Regex(p, host_only=True).info["reach_shapes"]
+    for pattern in (W.DNA_RE, W.AB_RE, W.LOG_RE):
+        assert shapes(pattern) == 0b11110, pattern
+    assert shapes("(a|b)*a(a|b){10}") == 0b11100                 # 2^11 DFA states
+
+
 def test_pair_layout_without_a_dictionary(native):
     """No dictionary and more than 64 segments: AUTO picks PAIRS (4 bytes per
     column while both automata have at most 65536 states); DICT is refused,
