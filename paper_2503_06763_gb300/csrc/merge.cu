@@ -994,21 +994,31 @@ __global__ void __launch_bounds__(kBlockThreads) merge_gather_kernel(const __gri
     bool bad = false;
     const uint64_t ncol = p.n + 1, full = ncol / 16;
     // two units of 16 columns per thread and step (their four 16-byte loads
-    // in flight together); every index static, so the values stay in registers
+    // in flight together), and the next step's four loads issued before this
+    // step's lookups; every index static, so the values stay in registers
     const uint64_t pairs = full / 2;
     const uint4 zero = make_uint4(0, 0, 0, 0);
-    for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < pairs;
-         u += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t r0 = 32 * u;
-        uint4 a0 = zero, a1 = zero, b0 = zero, b1 = zero;
-        if (ok) {
-            a0 = __ldcs(reinterpret_cast<const uint4 *>(p.w.FS + r0));
-            a1 = __ldcs(reinterpret_cast<const uint4 *>(p.w.FS + r0 + 16));
-            b0 = __ldcs(reinterpret_cast<const uint4 *>(p.w.BS + r0));
-            b1 = __ldcs(reinterpret_cast<const uint4 *>(p.w.BS + r0 + 16));
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint4 a0 = zero, a1 = zero, b0 = zero, b1 = zero;
+    if (ok && u < pairs) {
+        a0 = __ldcs(reinterpret_cast<const uint4 *>(p.w.FS + 32 * u));
+        a1 = __ldcs(reinterpret_cast<const uint4 *>(p.w.FS + 32 * u + 16));
+        b0 = __ldcs(reinterpret_cast<const uint4 *>(p.w.BS + 32 * u));
+        b1 = __ldcs(reinterpret_cast<const uint4 *>(p.w.BS + 32 * u + 16));
+    }
+    for (; u < pairs; u += stride) {
+        const uint64_t r0 = 32 * u, rn = r0 + 32 * stride;
+        uint4 na0 = zero, na1 = zero, nb0 = zero, nb1 = zero;
+        if (ok && u + stride < pairs) {
+            na0 = __ldcs(reinterpret_cast<const uint4 *>(p.w.FS + rn));
+            na1 = __ldcs(reinterpret_cast<const uint4 *>(p.w.FS + rn + 16));
+            nb0 = __ldcs(reinterpret_cast<const uint4 *>(p.w.BS + rn));
+            nb1 = __ldcs(reinterpret_cast<const uint4 *>(p.w.BS + rn + 16));
         }
         gather_unit<E>(p, e, nfs, nbs, ok, bad, r0, a0, b0);
         gather_unit<E>(p, e, nfs, nbs, ok, bad, r0 + 16, a1, b1);
+        a0 = na0; a1 = na1; b0 = nb0; b1 = nb1;
     }
     if (full & 1) {                                             // an odd last full unit
         const uint64_t r0 = 16 * (full - 1);
