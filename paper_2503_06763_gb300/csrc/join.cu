@@ -275,7 +275,8 @@ __device__ void verify_at(const Params &p, uint32_t i) {
 // verify_at with a warp per chunk: lane j tests slot j (whether the input
 // enters it, whether its run is live) and a ballot gathers the masks; lane 0
 // does the rest.  Slot counts are at most 32.
-__device__ uint32_t hits_warp(const Params &p, bool fwd, uint32_t i, uint32_t pr, uint32_t S, uint32_t &live) {
+__device__ __forceinline__ uint32_t hits_warp(const Params &p, bool fwd, uint32_t i, uint32_t pr, uint32_t S,
+                                              uint32_t &live) {
     const DevTables &t = p.t;
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t m = __ldg((fwd ? t.fSlotCount : t.bSlotCount) + pr);
@@ -294,45 +295,41 @@ __device__ uint32_t hits_warp(const Params &p, bool fwd, uint32_t i, uint32_t pr
     return __ballot_sync(0xFFFFFFFFu, lane < m && any_and(sb, mask + (size_t)lane * W, W));
 }
 
+// Both directions' loads come before any store (a store could alias a later
+// load, so the compiler would keep them in order), so the two dependent load
+// chains of a chunk overlap.
 __device__ void verify_warp(const Params &p, uint32_t i) {
     const uint32_t lane = threadIdx.x & 31;
-    {   // forward: input FJ[i] -> output FJ[i+1]
-        const uint32_t in = p.w.FJ[i], out = p.w.FJ[i + 1];
-        bool fail = in == 0 || out == 0;
-        uint32_t H = 0;
-        if (i > 0 && in != 0) {
-            const uint32_t pr = pair_fwd(p, i);
-            uint32_t L;
-            H = hits_warp(p, true, i, pr, in, L);
-            if (!fail && p.w.fkind[i] == 0) fail = (H & L) == 0;
-        }
-        if (lane == 0) {
-            p.w.fhit[i] = H;
-            if (fail) atomicMin(&p.w.flags[FLAG_FFAIL], (int32_t)i);
-            p.w.FC[(uint64_t)i * p.S] = in;                              // position i*k
-            if (i == p.c - 1 && (p.n & 63) == 0) p.w.FC[p.n >> 6] = p.w.FJ[p.c];   // position n
-        }
+    const bool both = !p.recognize;
+    // forward: input FJ[i] -> output FJ[i+1]; backward: input BJ[i+1] -> output BJ[i]
+    const uint32_t fin = p.w.FJ[i], fout = p.w.FJ[i + 1];
+    const uint32_t bin = both ? p.w.BJ[i + 1] : 0u, bout = both ? p.w.BJ[i] : 0u;
+    const uint32_t fkind = p.w.fkind[i], bkind = both ? p.w.bkind[i] : 1u;
+    const uint32_t fend = (i == p.c - 1 && (p.n & 63) == 0) ? p.w.FJ[p.c] : 0u;
+    bool ffail = fin == 0 || fout == 0, bfail = both && (bin == 0 || bout == 0);
+    uint32_t fH = 0, bH = 0;
+    if (i > 0 && fin != 0) {
+        uint32_t L;
+        fH = hits_warp(p, true, i, pair_fwd(p, i), fin, L);
+        if (!ffail && fkind == 0) ffail = (fH & L) == 0;
     }
-    if (p.recognize) return;
-    {   // backward: input BJ[i+1] -> output BJ[i]
-        const uint32_t in = p.w.BJ[i + 1], out = p.w.BJ[i];
-        bool fail = in == 0 || out == 0;
-        uint32_t H = 0;
-        if (i < p.c - 1 && in != 0) {
-            const uint32_t pr = pair_bwd(p, i);
-            uint32_t L;
-            H = hits_warp(p, false, i, pr, in, L);
-            if (!fail && p.w.bkind[i] == 0) fail = (H & L) == 0;
-        }
-        if (lane == 0) {
-            p.w.bhit[i] = H;
-            if (fail) atomicMin(&p.w.flags[FLAG_BFAIL], (int32_t)i);
-            if (i + 1 < p.c) {
-                p.w.BC[(uint64_t)(i + 1) * p.S - 1] = in;                // position (i+1)*k
-            } else {                                                     // groups whose end is clipped to n
-                for (uint64_t g = (p.n + 63) / 64 - 1; g < p.Gc; ++g) p.w.BC[g] = in;
-            }
-        }
+    if (both && i < p.c - 1 && bin != 0) {
+        uint32_t L;
+        bH = hits_warp(p, false, i, pair_bwd(p, i), bin, L);
+        if (!bfail && bkind == 0) bfail = (bH & L) == 0;
+    }
+    if (lane != 0) return;
+    p.w.fhit[i] = fH;
+    if (ffail) atomicMin(&p.w.flags[FLAG_FFAIL], (int32_t)i);
+    p.w.FC[(uint64_t)i * p.S] = fin;                                     // position i*k
+    if (i == p.c - 1 && (p.n & 63) == 0) p.w.FC[p.n >> 6] = fend;       // position n
+    if (!both) return;
+    p.w.bhit[i] = bH;
+    if (bfail) atomicMin(&p.w.flags[FLAG_BFAIL], (int32_t)i);
+    if (i + 1 < p.c) {
+        p.w.BC[(uint64_t)(i + 1) * p.S - 1] = bin;                       // position (i+1)*k
+    } else {                                                             // groups whose end is clipped to n
+        for (uint64_t g = (p.n + 63) / 64 - 1; g < p.Gc; ++g) p.w.BC[g] = bin;
     }
 }
 
