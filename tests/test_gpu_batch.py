@@ -190,3 +190,37 @@ def test_pair_columns_in_a_batch(lib):
         if len(h) <= 9000:
             want = serial.parse(compile_re(pats[pi][0]), h.tobytes())
             assert np.array_equal(rxs[pi].decode(outs[j].cpu().numpy(), "pairs"), want), (pi, len(h))
+
+
+def test_high_bytes_in_a_batch(lib):
+    """Bytes >= 128 through the batch's byte-table reach, whose rows hold
+    bytes below 128 only (each high byte replaced by an ASCII byte of its
+    class first): log records with 2 % of their bytes set >= 128, and an RE
+    whose class [\\x7f-\\xff] is mostly high bytes, against the oracle."""
+    Batch, Regex = lib
+    rng = np.random.default_rng(17)
+
+    def log_high(n, s):
+        h = W.log_text(n, seed=s).copy()
+        hit = (rng.random(h.size) < 0.02) & (h != ord("\n"))
+        h[hit] = rng.integers(128, 256, size=int(hit.sum()))
+        return h
+
+    def fold_tokens(n, s):
+        r = np.random.default_rng(s)
+        toks = [bytes([v, 97]) for v in range(127, 256)] + [b"b"] * 40
+        return np.frombuffer(b"".join(toks[j] for j in r.integers(0, len(toks), size=n // 2)), dtype=np.uint8).copy()
+
+    pats = [(W.LOG_RE, log_high), (r"([\x7f-\xff]a|b)*", fold_tokens)]
+    rxs = [Regex(p) for p, _ in pats]
+    assert all(rx.info["ascii_rows"] == 1 for rx in rxs)
+    items = [(pi, pats[pi][1](n, 500 + 3 * pi + n % 7)) for pi in range(2) for n in (0, 900, 9000, 70_001, 300_000)]
+    texts = [torch.from_numpy(np.ascontiguousarray(h)).cuda() for _, h in items]
+    b = Batch([rxs[pi] for pi, _ in items], [len(h) for _, h in items])
+    outs, status, kinds = b.parse(texts)
+    torch.cuda.synchronize()
+    st = status.cpu().numpy()
+    for j, (pi, h) in enumerate(items):
+        want = serial.parse(compile_re(pats[pi][0]), h.tobytes())
+        assert st[j] == (0 if serial.accepted(want) else 1), (pi, len(h))
+        assert np.array_equal(rxs[pi].decode(outs[j].cpu().numpy(), kinds[j]), want), (pi, len(h))
