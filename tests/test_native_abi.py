@@ -78,6 +78,23 @@ def test_ascii_rows_when_high_bytes_share_a_class_with_ascii(native):
         assert native.Regex(pattern, host_only=True).info["ascii_rows"] == 0, pattern
 
 
+def test_ascii_rows_follow_the_byte_classes(native):
+    """The library's choice of ASCII rows, checked against the byte classes
+    as the oracle's segments define them (two bytes are alike when every
+    segment reads both or neither): true exactly when each byte >= 128 has an
+    alike byte below 128."""
+    import workloads as W
+    pats = [W.LOG_RE, W.DNA_RE, W.AB_RE, "[^a]*", r"(\xffa|b)*", r"([ab]|[\x80-\xff]c)*",
+            r"([\x7f-\xff]a|b)*", r"([^\x00-\x7f]|x)*y", r"(a|[\x80-\x9f]|[\xa0-\xff])*"]
+    pats += [W.random_re(seed, 8, 30)[0] for seed in (3, 4, 5)]
+    for pattern in pats:
+        c = compile_re(pattern)
+        sig = [tuple(c.matches(q, b) for q in range(c.ell)) for b in range(256)]
+        low = set(sig[:128])
+        want = all(sig[h] in low for h in range(128, 256))
+        assert native.Regex(pattern, host_only=True).info["ascii_rows"] == int(want), pattern
+
+
 def test_reach_shapes_available(native):
     """Shapes 2-4 run for every automaton; shape 1 needs byte tables, that is
     at most 256 states per direction."""
